@@ -1,0 +1,236 @@
+"""FP64 CPU oracle of the compact fourth-order staggered Maxwell scheme (arXiv 2306.17263).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never uses it; the two share no code.
+
+The arithmetic lives in ``maxwell_oracle.c`` (plain C, FP64, single thread),
+compiled on demand with gcc into ``oracle/_build/liboracle.so``.  This module
+only marshals numpy arrays to it.  Each wrapper names the passage of the paper
+its C routine follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "maxwell_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+F_EZ, F_HX, F_HY = 0, 1, 2
+CLOSURE_PAPER, CLOSURE_REFLECT = 0, 1
+HALF_TO_NODE, NODE_TO_HALF = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no fast-math) if it is missing or stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            D = ctypes.POINTER(ctypes.c_double)
+            V = ctypes.c_void_p
+            L.or2d_setup.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+            L.or2d_set_cg.argtypes = [V, ctypes.c_double, ctypes.c_int]
+            L.or2d_field_size.argtypes = [V, ctypes.c_int]
+            L.or2d_field_size.restype = ctypes.c_int
+            L.or_pade_line.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, D, D]
+            L.or_pade_matvec24.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
+            for name in ("or2d_laplacian", "or2d_filter", "or2d_p1_apply", "or2d_p2_apply"):
+                getattr(L, name).argtypes = [V, ctypes.c_int, D, D]
+            L.or2d_p1_solve_cg.argtypes = [V, ctypes.c_int, D, D]
+            L.or2d_p1_solve_cg.restype = ctypes.c_int
+            L.or2d_curl_h_to_e.argtypes = [V, D, D, D]
+            L.or2d_curl_e_to_h.argtypes = [V, D, D, D]
+            L.or2d_h_increment.argtypes = [V, D, D, D]
+            L.or2d_step.argtypes = [V, D, D, D]
+            L.or2d_yee_step.argtypes = [V, D, D, D]
+            L.or2d_exact.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D, D]
+            L.or2d_error.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D, D, D]
+            L.or2d_energy.argtypes = [V, D, D, D]
+            L.or2d_energy.restype = ctypes.c_double
+            L.or2d_divergence.argtypes = [V, D, D, D]
+            L.or2d_divergence.restype = ctypes.c_double
+            L.or2d_run.argtypes = [V, D, D, D, ctypes.c_int, D, ctypes.c_int]
+            L.or2d_run.restype = ctypes.c_double
+            L.or2d_cg_iters_total.argtypes = [V]
+            L.or2d_cg_iters_total.restype = ctypes.c_long
+            L.or2d_cg_solves.argtypes = [V]
+            L.or2d_cg_solves.restype = ctypes.c_long
+            L.or2d_sizeof.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def pade_line(f: np.ndarray, h: float, closure: int = CLOSURE_PAPER, kind: int = HALF_TO_NODE) -> np.ndarray:
+    """Pade first derivative of one line (App. A.1, Eq. "eq:lhs"): A f' = D1 f / h, len(f') = len(f) - 1."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    M = f.size - 1
+    out = np.zeros(M)
+    lib().or_pade_line(M, closure, kind, h, _p(f), _p(out))
+    return out
+
+
+def pade_matvec24(y: np.ndarray, closure: int = CLOSURE_PAPER, kind: int = HALF_TO_NODE) -> np.ndarray:
+    """Apply 24 A (the left-hand matrix of Eq. "eq:lhs") to y."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    out = np.zeros_like(y)
+    lib().or_pade_matvec24(y.size, closure, kind, _p(y), _p(out))
+    return out
+
+
+class Oracle2D:
+    """2D TM_z grid of the scheme (Sec. 5: E_z, H_x, H_y on the unit square, PEC walls)."""
+
+    def __init__(self, N: int, r: float, Z: float = 1.0, closure: int = CLOSURE_PAPER):
+        L = lib()
+        self._buf = ctypes.create_string_buffer(L.or2d_sizeof())
+        self.g = ctypes.cast(self._buf, ctypes.c_void_p)
+        L.or2d_setup(self.g, int(N), float(r), float(Z), int(closure))
+        self.N, self.r, self.Z, self.closure = int(N), float(r), float(Z), int(closure)
+        self.h = 1.0 / N
+        self.ht = r * self.h
+        self.kappa2 = 24.0 / self.ht ** 2
+        self.beta = 1.0 + self.kappa2 * self.h ** 2 / 12.0
+        self.c1 = self.kappa2 * self.beta
+
+    # shapes (rows = y, cols = x), Eq. "eq:meshes" restricted to TM_z
+    def shape(self, f: int):
+        N = self.N
+        return {F_EZ: (N + 1, N + 1), F_HX: (N, N + 1), F_HY: (N + 1, N)}[f]
+
+    def zeros(self, f: int) -> np.ndarray:
+        return np.zeros(self.shape(f))
+
+    def set_cg(self, tol: float, maxit: int = 200):
+        lib().or2d_set_cg(self.g, tol, maxit)
+
+    def _unary(self, name, f, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = self.zeros(f)
+        getattr(lib(), name)(self.g, f, _p(u), _p(out))
+        return out
+
+    def laplacian(self, f, u):
+        """Delta_h = D_xx + D_yy with the field's Dirichlet / even-ghost Neumann boundaries."""
+        return self._unary("or2d_laplacian", f, u)
+
+    def filter(self, f, u):
+        """G = (1 + kappa^2 h^2 / 12) u + (h^2/12) Delta_h u (right side of Eq. "eq:ell")."""
+        return self._unary("or2d_filter", f, u)
+
+    def p1(self, f, x):
+        """P1 x (Definition "def:operatorsP")."""
+        return self._unary("or2d_p1_apply", f, x)
+
+    def p2(self, f, x):
+        """P2 x (Definition "def:operatorsP")."""
+        return self._unary("or2d_p2_apply", f, x)
+
+    def p1_solve(self, f, b):
+        """CG solve of P1 x = b (Sec. 3.2); returns (x, iterations)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = self.zeros(f)
+        it = lib().or2d_p1_solve_cg(self.g, f, _p(b), _p(x))
+        return x, it
+
+    def curl_h_to_e(self, Gx, Gy):
+        """R_E = kappa^2 Z (delta_x G_y - delta_y G_x) (Step 1, Sec. 3.4)."""
+        Gx = np.ascontiguousarray(Gx, dtype=np.float64)
+        Gy = np.ascontiguousarray(Gy, dtype=np.float64)
+        R = self.zeros(F_EZ)
+        lib().or2d_curl_h_to_e(self.g, _p(Gx), _p(Gy), _p(R))
+        return R
+
+    def curl_e_to_h(self, GE):
+        """(R_x, R_y) = (kappa^2/Z) (-delta_y G_E, delta_x G_E) (Step 2, Sec. 3.4)."""
+        GE = np.ascontiguousarray(GE, dtype=np.float64)
+        Rx, Ry = self.zeros(F_HX), self.zeros(F_HY)
+        lib().or2d_curl_e_to_h(self.g, _p(GE), _p(Rx), _p(Ry))
+        return Rx, Ry
+
+    def h_increment(self, ez):
+        ez = np.ascontiguousarray(ez, dtype=np.float64)
+        hxs, hys = self.zeros(F_HX), self.zeros(F_HY)
+        lib().or2d_h_increment(self.g, _p(ez), _p(hxs), _p(hys))
+        return hxs, hys
+
+    def step(self, ez, hx, hy):
+        """One full step in place (Sec. 3.4 Step 1 then Step 2)."""
+        lib().or2d_step(self.g, _p(ez), _p(hx), _p(hy))
+
+    def yee_step(self, ez, hx, hy):
+        """One plain second-order Yee step in place (Sec. 5.2, stencil S with c = 1)."""
+        lib().or2d_yee_step(self.g, _p(ez), _p(hx), _p(hy))
+
+    @staticmethod
+    def _modes(modes):
+        m = np.ascontiguousarray(np.asarray(modes, dtype=np.float64).reshape(-1, 3))
+        return m, m.shape[0]
+
+    def exact(self, modes, tE, tH):
+        """Exact cavity-mode superposition (Eq. "eq:data"); modes rows are (k_x, k_y, amplitude)."""
+        m, nm = self._modes(modes)
+        ez, hx, hy = self.zeros(F_EZ), self.zeros(F_HX), self.zeros(F_HY)
+        lib().or2d_exact(self.g, _p(m), nm, tE, tH, _p(ez), _p(hx), _p(hy))
+        return ez, hx, hy
+
+    def init_modes(self, modes):
+        """E^0 and H^{1/2} from the closed form (Sec. 5.1)."""
+        return self.exact(modes, 0.0, 0.5 * self.ht)
+
+    def error(self, modes, n, ez, hx, hy):
+        """(L2 abs, L2 rel, max abs, sum |err|) of (E^n, H^{n+1/2}) against the exact modes."""
+        m, nm = self._modes(modes)
+        out = np.zeros(4)
+        lib().or2d_error(self.g, _p(m), nm, n * self.ht, (n + 0.5) * self.ht, _p(ez), _p(hx), _p(hy), _p(out))
+        return out
+
+    def energy(self, ez, hx, hy):
+        """W^n = Z^-1 ||E^n||^2 + Z <H^{n-1/2}, H^{n+1/2}> (h^2-weighted)."""
+        return lib().or2d_energy(self.g, _p(ez), _p(hx), _p(hy))
+
+    def divergence(self, hx, hy):
+        """(||div_h H||_h, div field) with the node->half-node Pade derivatives."""
+        div = np.zeros((self.N, self.N))
+        n = lib().or2d_divergence(self.g, _p(hx), _p(hy), _p(div))
+        return n, div
+
+    def run(self, ez, hx, hy, nsteps, modes=None):
+        """Run nsteps in place; with modes, return the mean absolute error of Sec. 5.1."""
+        if modes is None:
+            lib().or2d_run(self.g, _p(ez), _p(hx), _p(hy), int(nsteps), None, 0)
+            return None
+        m, nm = self._modes(modes)
+        acc = lib().or2d_run(self.g, _p(ez), _p(hx), _p(hy), int(nsteps), _p(m), nm)
+        return acc / (3.0 * nsteps * self.N ** 2)
+
+    def cg_stats(self):
+        L = lib()
+        return L.or2d_cg_iters_total(self.g), L.or2d_cg_solves(self.g)

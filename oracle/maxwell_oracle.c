@@ -1,0 +1,567 @@
+/*
+ * Plain FP64 CPU oracle of the compact fourth-order staggered scheme for the
+ * first-order Maxwell equations (Versano, Turkel & Tsynkov, arXiv 2306.17263).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * statement of what the scheme computes.  Only the test-suite, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it.  The CUDA library in
+ * paper_2306_17263_gb300/ never calls, links or includes anything from here,
+ * and nothing here is shared with it.
+ *
+ * Every routine is written straight from the paper's definitions, with no
+ * blocking, fusion or reordering beyond them:
+ *   - meshes and PEC boundary values: Sec. 2, Eq. (2.1) "eq:meshes", "eq:bc_E=0";
+ *   - Dirichlet / Neumann type of each time derivative: Table "tab:bc";
+ *   - compact modified-Helmholtz scheme: Sec. 3.2, Eq. "eq:ell";
+ *   - operators P1, P2: Definition "def:operatorsP" and App. A.2;
+ *   - even ghost reflection for homogeneous Neumann: Corollary "cor:ghost_cor";
+ *   - Pade first derivative A f' = D1 f / h: App. A.1, Eq. "eq:lhs";
+ *   - D2 and the Kronecker lifts D_xx, D_yy: App. A.1;
+ *   - the time step (Step 1 then Step 2): Sec. 3.4;
+ *   - conjugate-gradient solves of the SPD systems: Sec. 3.2 and Sec. 6;
+ *   - exact PEC cavity modes and the mean absolute error: Sec. 5.1, Eq. "eq:data";
+ *   - Yee updating rules with the second-order stencil (c=1): Sec. 5.2.
+ *
+ * Readings of points the paper leaves open (all listed in the design notes):
+ *   - the third rows of Step 1 / Step 2 are E_z and H_z (the printed E_y, H_y
+ *     rows are typos);
+ *   - the Laplacian inside the right-hand-side filter is Delta_h for both
+ *     half-steps (the form analysed in Sec. 4);
+ *   - the filter is applied on the source grid and then the Pade curl;
+ *   - closure PAPER uses the one-sided rows [26,-5,4,-1]/24 of Eq. "eq:lhs" at
+ *     both ends of every Pade system; closure REFLECT replaces them by the rows
+ *     that follow from the field's parity about the wall (see pade_row);
+ *   - G_E = 0 on the PEC boundary nodes (E_z = 0 and Delta E_z = d_tt E_z = 0);
+ *   - boundary values of the Dirichlet components are held at zero.
+ *
+ * Array layout (2D TM_z, N cells per side, h = 1/N): row-major [y][x].
+ *   E_z : (N+1) x (N+1) at (x_i, y_j)           Dirichlet in x and y
+ *   H_x : N rows x (N+1) cols at (x_i, y_{j+1/2}) Dirichlet in x, Neumann in y
+ *   H_y : (N+1) rows x N cols at (x_{i+1/2}, y_j) Neumann in x, Dirichlet in y
+ * 3D: array [z][y][x]; the six components follow Eq. "eq:meshes".
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { BC_DIR = 0, BC_NEU = 1 };
+enum { CLOSURE_PAPER = 0, CLOSURE_REFLECT = 1 };
+/* Pade direction: HALF_TO_NODE maps N half-node values to the N-1 interior
+ * nodes; NODE_TO_HALF maps the N+1 node values to the N half-nodes. */
+enum { HALF_TO_NODE = 0, NODE_TO_HALF = 1 };
+enum { F_EZ = 0, F_HX = 1, F_HY = 2 };
+
+typedef struct {
+  int N;
+  double r, Z, h, ht, kappa2, beta, c1;
+  int closure;
+  double cg_tol;
+  int cg_maxit;
+  long cg_iters_total; /* CG iterations summed over all solves since setup */
+  long cg_solves;
+} or_grid2d;
+
+/* ------------------------------------------------------------------ */
+/* Grid constants: h = 1/N, h_tau = r h, kappa^2 = 24 / h_tau^2 (Sec. 3.2),
+ * beta = 1 + kappa^2 h^2 / 12 = 1 + 2/r^2, c1 = kappa^2 beta (Def. "def:operatorsP"). */
+void or2d_setup(or_grid2d* g, int N, double r, double Z, int closure) {
+  g->N = N;
+  g->r = r;
+  g->Z = Z;
+  g->h = 1.0 / N;
+  g->ht = r * g->h;
+  g->kappa2 = 24.0 / (g->ht * g->ht);
+  g->beta = 1.0 + g->kappa2 * g->h * g->h / 12.0;
+  g->c1 = g->kappa2 * g->beta;
+  g->closure = closure;
+  g->cg_tol = 1e-14;
+  g->cg_maxit = 200;
+  g->cg_iters_total = 0;
+  g->cg_solves = 0;
+}
+
+void or2d_set_cg(or_grid2d* g, double tol, int maxit) {
+  g->cg_tol = tol;
+  g->cg_maxit = maxit;
+}
+
+/* Field shapes and boundary types (Eq. "eq:meshes", Table "tab:bc"). */
+static void field_dims(const or_grid2d* g, int f, int* nx, int* ny, int* bcx, int* bcy) {
+  int N = g->N;
+  if (f == F_EZ) { *nx = N + 1; *ny = N + 1; *bcx = BC_DIR; *bcy = BC_DIR; }
+  else if (f == F_HX) { *nx = N + 1; *ny = N; *bcx = BC_DIR; *bcy = BC_NEU; }
+  else { *nx = N; *ny = N + 1; *bcx = BC_NEU; *bcy = BC_DIR; }
+}
+
+int or2d_field_size(const or_grid2d* g, int f) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  return nx * ny;
+}
+
+/* interior test on one axis: Dirichlet axes (N+1 nodes) exclude 0 and N */
+static int axis_interior(int bc, int i, int n) {
+  return bc == BC_NEU ? 1 : (i > 0 && i < n - 1);
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D Pade row coefficients, App. A.1 Eq. "eq:lhs" (scaled by 24).
+ * Row i of the M x M matrix 24*A.  Writes up to 4 (col, value) pairs.
+ *  interior rows: [1, 22, 1];
+ *  PAPER closure: first row [26,-5,4,-1], last row [-1,4,-5,26];
+ *  REFLECT closure: NODE_TO_HALF first/last rows [23,1] / [1,23] (the derivative of a
+ *  field that vanishes at the wall is even about it); HALF_TO_NODE first/last rows
+ *  [22,1] / [1,22] (the derivative of a field that is even about the wall is zero there). */
+static int pade_row(int M, int closure, int kind, int i, int* col, double* val) {
+  int n = 0;
+  if (i == 0 || i == M - 1) {
+    int first = (i == 0);
+    if (closure == CLOSURE_PAPER) {
+      static const double rowc[4] = {26.0, -5.0, 4.0, -1.0};
+      for (int k = 0; k < 4; ++k) {
+        col[n] = first ? k : M - 1 - k;
+        val[n] = rowc[k];
+        ++n;
+      }
+      return n;
+    } else {
+      double d = (kind == NODE_TO_HALF) ? 23.0 : 22.0;
+      col[n] = i; val[n] = d; ++n;
+      col[n] = first ? i + 1 : i - 1; val[n] = 1.0; ++n;
+      return n;
+    }
+  }
+  col[n] = i - 1; val[n] = 1.0; ++n;
+  col[n] = i; val[n] = 22.0; ++n;
+  col[n] = i + 1; val[n] = 1.0; ++n;
+  return n;
+}
+
+/* Solve (24 A) y = rhs for one line by banded Gaussian elimination without
+ * pivoting (A is strictly diagonally dominant by rows).  Band half-width 3. */
+#define PB 3
+static void pade_solve24(int M, int closure, int kind, double* rhs, double* y) {
+  /* band[i][k] holds entry (i, i - PB + k), k in [0, 2 PB] */
+  double* band = (double*)calloc((size_t)M * (2 * PB + 1), sizeof(double));
+  for (int i = 0; i < M; ++i) {
+    int col[4];
+    double val[4];
+    int n = pade_row(M, closure, kind, i, col, val);
+    for (int k = 0; k < n; ++k) band[(size_t)i * (2 * PB + 1) + (col[k] - i + PB)] += val[k];
+  }
+  for (int k = 0; k < M; ++k) {
+    double piv = band[(size_t)k * (2 * PB + 1) + PB];
+    for (int i = k + 1; i <= k + PB && i < M; ++i) {
+      double* ri = band + (size_t)i * (2 * PB + 1);
+      double* rk = band + (size_t)k * (2 * PB + 1);
+      double a = ri[k - i + PB];
+      if (a == 0.0) continue;
+      double l = a / piv;
+      for (int j = k; j <= k + PB && j < M; ++j) ri[j - i + PB] -= l * rk[j - k + PB];
+      rhs[i] -= l * rhs[k];
+    }
+  }
+  for (int i = M - 1; i >= 0; --i) {
+    double* ri = band + (size_t)i * (2 * PB + 1);
+    double s = rhs[i];
+    for (int j = i + 1; j <= i + PB && j < M; ++j) s -= ri[j - i + PB] * y[j];
+    y[i] = s / ri[PB];
+  }
+  free(band);
+}
+
+/* Pade derivative of one line: f has M+1 samples, fp receives M derivative values,
+ * A fp = D1 f / h (Eq. "eq:lhs"; D1 is the (M) x (M+1) two-point difference). */
+void or_pade_line(int M, int closure, int kind, double h, const double* f, double* fp) {
+  double* rhs = (double*)malloc(sizeof(double) * M);
+  for (int i = 0; i < M; ++i) rhs[i] = 24.0 * (f[i + 1] - f[i]) / h;
+  pade_solve24(M, closure, kind, rhs, fp);
+  free(rhs);
+}
+
+/* Apply 24*A (the matrix of Eq. "eq:lhs" times 24) to a vector: used by tests. */
+void or_pade_matvec24(int M, int closure, int kind, const double* y, double* out) {
+  for (int i = 0; i < M; ++i) {
+    int col[4];
+    double val[4];
+    int n = pade_row(M, closure, kind, i, col, val);
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += val[k] * y[col[k]];
+    out[i] = s;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* D_2 along one axis (App. A.1) of a field with its boundary type:
+ * Dirichlet axes use the stored zeros at nodes 0 and N; Neumann axes use the
+ * even ghosts u(-1) = u(0), u(n) = u(n-1) (Corollary "cor:ghost_cor").
+ * Result is written at interior points and set to 0 at Dirichlet boundary points. */
+static void d2_axis(const or_grid2d* g, int f, int axis, const double* u, double* out) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  double ih2 = 1.0 / (g->h * g->h);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) { out[p] = 0.0; continue; }
+      double um, up;
+      if (axis == 0) {
+        um = (i - 1 >= 0) ? u[p - 1] : u[p];            /* i-1 < 0 only on Neumann axes */
+        up = (i + 1 < nx) ? u[p + 1] : u[p];
+      } else {
+        um = (j - 1 >= 0) ? u[p - nx] : u[p];
+        up = (j + 1 < ny) ? u[p + nx] : u[p];
+      }
+      out[p] = (um - 2.0 * u[p] + up) * ih2;
+    }
+}
+
+/* Delta_h = D_xx + D_yy (Sec. 3.2). */
+void or2d_laplacian(const or_grid2d* g, int f, const double* u, double* out) {
+  int n = or2d_field_size(g, f);
+  double* t = (double*)malloc(sizeof(double) * n);
+  d2_axis(g, f, 0, u, out);
+  d2_axis(g, f, 1, u, t);
+  for (int p = 0; p < n; ++p) out[p] += t[p];
+  free(t);
+}
+
+/* Right-hand-side filter of Eq. "eq:ell": G = (1 + kappa^2 h^2/12) u + (h^2/12) Delta_h u,
+ * written on interior points, 0 on Dirichlet boundary points. */
+void or2d_filter(const or_grid2d* g, int f, const double* u, double* G) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  int n = nx * ny;
+  or2d_laplacian(g, f, u, G);
+  double h2_12 = g->h * g->h / 12.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) G[p] = 0.0;
+      else G[p] = g->beta * u[p] + h2_12 * G[p];
+    }
+  (void)n;
+}
+
+/* P1 = -(D_xx + D_yy + (h^2/6) D_xx D_yy) + c1 (Def. "def:operatorsP", 2D: Upsilon_h = D_xx D_yy).
+ * Applied as the Kronecker composition of App. A.1. */
+void or2d_p1_apply(const or_grid2d* g, int f, const double* x, double* y) {
+  int n = or2d_field_size(g, f);
+  double* dxx = (double*)malloc(sizeof(double) * n);
+  double* dyy = (double*)malloc(sizeof(double) * n);
+  double* dxxdyy = (double*)malloc(sizeof(double) * n);
+  d2_axis(g, f, 0, x, dxx);
+  d2_axis(g, f, 1, x, dyy);
+  d2_axis(g, f, 0, dyy, dxxdyy);
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  double h2_6 = g->h * g->h / 6.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) { y[p] = 0.0; continue; }
+      y[p] = g->c1 * x[p] - (dxx[p] + dyy[p] + h2_6 * dxxdyy[p]);
+    }
+  free(dxx);
+  free(dyy);
+  free(dxxdyy);
+}
+
+/* P2 = (24/h_tau^2)(-1 - 2/r^2 - (h^2/12) Delta_h) (Def. "def:operatorsP"). */
+void or2d_p2_apply(const or_grid2d* g, int f, const double* x, double* y) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  or2d_laplacian(g, f, x, y);
+  double k = 24.0 / (g->ht * g->ht), b = 1.0 + 2.0 / (g->r * g->r), h2_12 = g->h * g->h / 12.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) y[p] = 0.0;
+      else y[p] = k * (-b * x[p] - h2_12 * y[p]);
+    }
+}
+
+static double dot_interior(const or_grid2d* g, int f, const double* a, const double* b) {
+  int n = or2d_field_size(g, f);
+  double s = 0.0;
+  for (int p = 0; p < n; ++p) s += a[p] * b[p]; /* boundary entries are zero */
+  return s;
+}
+
+/* Conjugate gradients for P1 x = b (the paper's solver, Sec. 3.2 and Sec. 6),
+ * started from x = 0, stopped when ||r||_2 <= tol ||b||_2.  Returns iterations. */
+int or2d_p1_solve_cg(or_grid2d* g, int f, const double* b, double* x) {
+  int n = or2d_field_size(g, f);
+  double* r = (double*)malloc(sizeof(double) * n);
+  double* p = (double*)malloc(sizeof(double) * n);
+  double* Ap = (double*)malloc(sizeof(double) * n);
+  for (int i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; p[i] = b[i]; }
+  double bb = dot_interior(g, f, b, b), rr = bb;
+  int it = 0;
+  if (bb > 0.0) {
+    while (it < g->cg_maxit && rr > g->cg_tol * g->cg_tol * bb) {
+      or2d_p1_apply(g, f, p, Ap);
+      double alpha = rr / dot_interior(g, f, p, Ap);
+      for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * Ap[i]; }
+      double rr2 = dot_interior(g, f, r, r);
+      double beta = rr2 / rr;
+      for (int i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+      rr = rr2;
+      ++it;
+    }
+  }
+  g->cg_iters_total += it;
+  g->cg_solves += 1;
+  free(r);
+  free(p);
+  free(Ap);
+  return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* Pade derivative of a whole field along an axis (App. A.1, delta_s = a_s^{-1} D_s).
+ * src is a field of type fs, dst a field of type fd.  HALF_TO_NODE: the axis of src is
+ * Neumann type (N half-nodes) and dst's is Dirichlet type (values at nodes 1..N-1, 0 at
+ * the boundary nodes).  NODE_TO_HALF: the reverse (N+1 nodes -> N half-nodes).
+ * Lines of the other axis are copied index for index (same extent in both fields). */
+static void pade_field(const or_grid2d* g, int fs, int fd, int axis, int kind, const double* src, double* dst) {
+  int snx, sny, sbx, sby, dnx, dny, dbx, dby;
+  field_dims(g, fs, &snx, &sny, &sbx, &sby);
+  field_dims(g, fd, &dnx, &dny, &dbx, &dby);
+  int N = g->N;
+  int M = (kind == HALF_TO_NODE) ? N - 1 : N;
+  int nl = (axis == 0) ? sny : snx;  /* number of lines */
+  double* f = (double*)malloc(sizeof(double) * (M + 1));
+  double* fp = (double*)malloc(sizeof(double) * M);
+  memset(dst, 0, sizeof(double) * (size_t)dnx * dny);
+  for (int l = 0; l < nl; ++l) {
+    for (int k = 0; k <= M; ++k) f[k] = (axis == 0) ? src[(size_t)l * snx + k] : src[(size_t)k * snx + l];
+    or_pade_line(M, g->closure, kind, g->h, f, fp);
+    for (int k = 0; k < M; ++k) {
+      int o = (kind == HALF_TO_NODE) ? k + 1 : k; /* derivative at node k+1, or half-node k */
+      if (axis == 0) dst[(size_t)l * dnx + o] = fp[k];
+      else dst[(size_t)o * dnx + l] = fp[k];
+    }
+  }
+  free(f);
+  free(fp);
+}
+
+/* Zero the Dirichlet boundary points of a field. */
+static void zero_boundary(const or_grid2d* g, int f, double* u) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) u[(size_t)j * nx + i] = 0.0;
+}
+
+/* Step 1 right-hand side (Sec. 3.4): R_E = kappa^2 Z (delta_x G_y - delta_y G_x),
+ * with G_x, G_y the filtered H fields (third row of curl_h, App. A.1). */
+void or2d_curl_h_to_e(const or_grid2d* g, const double* Gx, const double* Gy, double* R) {
+  int n = or2d_field_size(g, F_EZ);
+  double* a = (double*)malloc(sizeof(double) * n);
+  double* b = (double*)malloc(sizeof(double) * n);
+  pade_field(g, F_HY, F_EZ, 0, HALF_TO_NODE, Gy, a); /* delta_x G_y */
+  pade_field(g, F_HX, F_EZ, 1, HALF_TO_NODE, Gx, b); /* delta_y G_x */
+  for (int p = 0; p < n; ++p) R[p] = g->kappa2 * g->Z * (a[p] - b[p]);
+  zero_boundary(g, F_EZ, R);
+  free(a);
+  free(b);
+}
+
+/* Step 2 right-hand side (Sec. 3.4): -(kappa^2/Z) curl_h G_E restricted to TM_z:
+ * R_x = -(kappa^2/Z) delta_y G_E, R_y = +(kappa^2/Z) delta_x G_E. */
+void or2d_curl_e_to_h(const or_grid2d* g, const double* GE, double* Rx, double* Ry) {
+  int nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  pade_field(g, F_EZ, F_HX, 1, NODE_TO_HALF, GE, Rx); /* delta_y G_E */
+  pade_field(g, F_EZ, F_HY, 0, NODE_TO_HALF, GE, Ry); /* delta_x G_E */
+  double s = g->kappa2 / g->Z;
+  for (int p = 0; p < nx_; ++p) Rx[p] *= -s;
+  for (int p = 0; p < ny_; ++p) Ry[p] *= s;
+  zero_boundary(g, F_HX, Rx);
+  zero_boundary(g, F_HY, Ry);
+}
+
+/* The H increment of Step 2 for a given E: P1^{H} H* = R_H(E).  hxs, hys receive H*. */
+void or2d_h_increment(or_grid2d* g, const double* ez, double* hxs, double* hys) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* GE = (double*)malloc(sizeof(double) * ne);
+  double* Rx = (double*)malloc(sizeof(double) * nx_);
+  double* Ry = (double*)malloc(sizeof(double) * ny_);
+  or2d_filter(g, F_EZ, ez, GE);
+  or2d_curl_e_to_h(g, GE, Rx, Ry);
+  or2d_p1_solve_cg(g, F_HX, Rx, hxs);
+  or2d_p1_solve_cg(g, F_HY, Ry, hys);
+  free(GE);
+  free(Rx);
+  free(Ry);
+}
+
+/* One full time step (Sec. 3.4, Step 1 then Step 2), J = rho = 0:
+ *   P1^{E} E* = kappa^2 Z curl_h[(1 + kappa^2 h^2/12) H + (h^2/12) Delta_h H],  E += h_tau E*;
+ *   P1^{H} H* = -(kappa^2/Z) curl_h[(1 + kappa^2 h^2/12) E + (h^2/12) Delta_h E], H += h_tau H*. */
+void or2d_step(or_grid2d* g, double* ez, double* hx, double* hy) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* Gx = (double*)malloc(sizeof(double) * nx_);
+  double* Gy = (double*)malloc(sizeof(double) * ny_);
+  double* R = (double*)malloc(sizeof(double) * ne);
+  double* Es = (double*)malloc(sizeof(double) * ne);
+  double* Hxs = (double*)malloc(sizeof(double) * nx_);
+  double* Hys = (double*)malloc(sizeof(double) * ny_);
+  or2d_filter(g, F_HX, hx, Gx);
+  or2d_filter(g, F_HY, hy, Gy);
+  or2d_curl_h_to_e(g, Gx, Gy, R);
+  or2d_p1_solve_cg(g, F_EZ, R, Es);
+  for (int p = 0; p < ne; ++p) ez[p] += g->ht * Es[p];
+  or2d_h_increment(g, ez, Hxs, Hys);
+  for (int p = 0; p < nx_; ++p) hx[p] += g->ht * Hxs[p];
+  for (int p = 0; p < ny_; ++p) hy[p] += g->ht * Hys[p];
+  free(Gx);
+  free(Gy);
+  free(R);
+  free(Es);
+  free(Hxs);
+  free(Hys);
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact PEC cavity modes (Sec. 5.1, Eq. "eq:data"), superposed.  modes[3m..3m+2] =
+ * (k_x, k_y, amplitude).  omega = pi sqrt(k_x^2 + k_y^2); for general Z the H fields
+ * carry 1/Z (Faraday's law, Eq. "maxh").  E at time tE, H at time tH. */
+void or2d_exact(const or_grid2d* g, const double* modes, int nmodes, double tE, double tH, double* ez,
+                double* hx, double* hy) {
+  int N = g->N;
+  double h = g->h, pi = M_PI;
+  memset(ez, 0, sizeof(double) * (N + 1) * (N + 1));
+  memset(hx, 0, sizeof(double) * N * (N + 1));
+  memset(hy, 0, sizeof(double) * N * (N + 1));
+  for (int m = 0; m < nmodes; ++m) {
+    double kx = modes[3 * m], ky = modes[3 * m + 1], A = modes[3 * m + 2];
+    double w = pi * sqrt(kx * kx + ky * ky);
+    double ce = A * cos(w * tE), sh = A * sin(w * tH) / (w * g->Z);
+    for (int j = 1; j < N; ++j)
+      for (int i = 1; i < N; ++i)
+        ez[(size_t)j * (N + 1) + i] += ce * sin(pi * kx * i * h) * sin(pi * ky * j * h);
+    for (int j = 0; j < N; ++j)
+      for (int i = 1; i < N; ++i)
+        hx[(size_t)j * (N + 1) + i] += -sh * pi * ky * sin(pi * kx * i * h) * cos(pi * ky * (j + 0.5) * h);
+    for (int j = 1; j < N; ++j)
+      for (int i = 0; i < N; ++i)
+        hy[(size_t)j * N + i] += sh * pi * kx * cos(pi * kx * (i + 0.5) * h) * sin(pi * ky * j * h);
+  }
+}
+
+/* Error of the state against the exact modes at t_E = n h_tau, t_H = (n + 1/2) h_tau.
+ * out[0] = L2 abs = sqrt(h^2 sum (u - u_ex)^2) over the three fields, out[1] = L2 rel,
+ * out[2] = max abs, out[3] = sum |u - u_ex| (the summand of the mean absolute error, Sec. 5.1). */
+void or2d_error(const or_grid2d* g, const double* modes, int nmodes, double tE, double tH, const double* ez,
+                const double* hx, const double* hy, double* out) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* e = (double*)malloc(sizeof(double) * ne);
+  double* a = (double*)malloc(sizeof(double) * nx_);
+  double* b = (double*)malloc(sizeof(double) * ny_);
+  or2d_exact(g, modes, nmodes, tE, tH, e, a, b);
+  double s2 = 0.0, r2 = 0.0, mx = 0.0, s1 = 0.0;
+  const double* num[3] = {ez, hx, hy};
+  const double* ex[3] = {e, a, b};
+  int sz[3] = {ne, nx_, ny_};
+  for (int f = 0; f < 3; ++f)
+    for (int p = 0; p < sz[f]; ++p) {
+      double d = num[f][p] - ex[f][p];
+      s2 += d * d;
+      r2 += ex[f][p] * ex[f][p];
+      s1 += fabs(d);
+      if (fabs(d) > mx) mx = fabs(d);
+    }
+  double h2 = g->h * g->h;
+  out[0] = sqrt(h2 * s2);
+  out[1] = r2 > 0 ? sqrt(s2 / r2) : 0.0;
+  out[2] = mx;
+  out[3] = s1;
+  free(e);
+  free(a);
+  free(b);
+}
+
+/* Discrete energy W^n = Z^{-1} ||E^n||_h^2 + Z <H^{n-1/2}, H^{n+1/2}>_h, with h^2-weighted sums.
+ * (The paper is silent on a discrete energy; this is the leapfrog invariant of the scheme
+ * written as in Sec. 4, Eq. "eq:eh".)  H^{n-1/2} = H^{n+1/2} - h_tau H*(E^n). */
+double or2d_energy(or_grid2d* g, const double* ez, const double* hx, const double* hy) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* hxs = (double*)malloc(sizeof(double) * nx_);
+  double* hys = (double*)malloc(sizeof(double) * ny_);
+  or2d_h_increment(g, ez, hxs, hys);
+  double se = 0.0, sh = 0.0;
+  for (int p = 0; p < ne; ++p) se += ez[p] * ez[p];
+  for (int p = 0; p < nx_; ++p) sh += (hx[p] - g->ht * hxs[p]) * hx[p];
+  for (int p = 0; p < ny_; ++p) sh += (hy[p] - g->ht * hys[p]) * hy[p];
+  free(hxs);
+  free(hys);
+  double h2 = g->h * g->h;
+  return h2 * (se / g->Z + g->Z * sh);
+}
+
+/* Pade divergence of H on the N x N cell centres: div_h H = delta_x H_x + delta_y H_y
+ * (App. A.1 delta operators, node -> half-node direction).  Returns sqrt(h^2 sum div^2). */
+double or2d_divergence(const or_grid2d* g, const double* hx, const double* hy, double* div_out) {
+  int N = g->N, M = N;
+  double* f = (double*)malloc(sizeof(double) * (N + 1));
+  double* fp = (double*)malloc(sizeof(double) * N);
+  double* div = div_out ? div_out : (double*)malloc(sizeof(double) * N * N);
+  for (int j = 0; j < N; ++j) { /* rows of H_x: nodes i = 0..N at y_{j+1/2} */
+    for (int i = 0; i <= N; ++i) f[i] = hx[(size_t)j * (N + 1) + i];
+    or_pade_line(M, g->closure, NODE_TO_HALF, g->h, f, fp);
+    for (int i = 0; i < N; ++i) div[(size_t)j * N + i] = fp[i];
+  }
+  for (int i = 0; i < N; ++i) { /* columns of H_y: nodes j = 0..N at x_{i+1/2} */
+    for (int j = 0; j <= N; ++j) f[j] = hy[(size_t)j * N + i];
+    or_pade_line(M, g->closure, NODE_TO_HALF, g->h, f, fp);
+    for (int j = 0; j < N; ++j) div[(size_t)j * N + i] += fp[j];
+  }
+  double s = 0.0;
+  for (int p = 0; p < N * N; ++p) s += div[p] * div[p];
+  free(f);
+  free(fp);
+  if (!div_out) free(div);
+  return sqrt(g->h * g->h * s);
+}
+
+/* Run nsteps steps from (E^0, H^{1/2}); if modes != NULL, accumulate the mean-absolute-error
+ * summand of Sec. 5.1 over steps n = 1..nsteps (errors of E^n and H^{n+1/2}).  Returns the
+ * summand; mae = summand / (3 nsteps N^2). */
+double or2d_run(or_grid2d* g, double* ez, double* hx, double* hy, int nsteps, const double* modes, int nmodes) {
+  double acc = 0.0, e[4];
+  for (int n = 1; n <= nsteps; ++n) {
+    or2d_step(g, ez, hx, hy);
+    if (modes) {
+      or2d_error(g, modes, nmodes, n * g->ht, (n + 0.5) * g->ht, ez, hx, hy, e);
+      acc += e[3];
+    }
+  }
+  return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Plain second-order Yee step (Sec. 5.2 updating rules with stencil S, c = 1, a = b = d = 0):
+ *   E_z += h_tau Z (D_x H_y - D_y H_x);  H_x -= (h_tau/Z) D_y E_z;  H_y += (h_tau/Z) D_x E_z. */
+void or2d_yee_step(const or_grid2d* g, double* ez, double* hx, double* hy) {
+  int N = g->N;
+  double c = g->ht / g->h;
+  for (int j = 1; j < N; ++j)
+    for (int i = 1; i < N; ++i) {
+      double dxhy = hy[(size_t)j * N + i] - hy[(size_t)j * N + i - 1];
+      double dyhx = hx[(size_t)j * (N + 1) + i] - hx[(size_t)(j - 1) * (N + 1) + i];
+      ez[(size_t)j * (N + 1) + i] += c * g->Z * (dxhy - dyhx);
+    }
+  for (int j = 0; j < N; ++j)
+    for (int i = 1; i < N; ++i)
+      hx[(size_t)j * (N + 1) + i] -= c / g->Z * (ez[(size_t)(j + 1) * (N + 1) + i] - ez[(size_t)j * (N + 1) + i]);
+  for (int j = 1; j < N; ++j)
+    for (int i = 0; i < N; ++i)
+      hy[(size_t)j * N + i] += c / g->Z * (ez[(size_t)j * (N + 1) + i + 1] - ez[(size_t)j * (N + 1) + i]);
+}
+
+long or2d_cg_iters_total(const or_grid2d* g) { return g->cg_iters_total; }
+long or2d_cg_solves(const or_grid2d* g) { return g->cg_solves; }
+int or2d_sizeof(void) { return (int)sizeof(or_grid2d); }

@@ -1,0 +1,63 @@
+"""Closed forms that pin the oracle: operator symbols on the cavity-mode bases.
+
+These are derived independently of the oracle's code, from the symbols of the
+operators of the paper (App. A.1 Pade and D_2 matrices, Def. "def:operatorsP",
+Eq. "eq:ell") acting on the sine / cosine bases of the staggered grids.  Under
+the REFLECT closure every operator of the scheme is diagonal in these bases, so
+a single cavity mode evolves by a 3x3 matrix per step (the recurrence of Sec. 4,
+Eq. "eq:stab1").
+"""
+import math
+
+import numpy as np
+
+# Per-mode symbols of the operators (closed forms used to pin the oracle).
+# For a cavity mode with indices (k_x, k_y), theta = pi k h; the sine / cosine
+# bases of each staggered grid are eigenvectors of every operator under the
+# REFLECT closure, so one step acts on the mode coefficients as a 3x3 matrix.
+
+def pade_symbol(theta: float, h: float) -> float:
+    """Magnitude d of the Pade derivative symbol: i (2/h) sin(theta/2) 24 / (22 + 2 cos theta)."""
+    return (2.0 / h) * math.sin(theta / 2) * 24.0 / (22.0 + 2.0 * math.cos(theta))
+
+
+def d2_symbol(theta: float, h: float) -> float:
+    """Eigenvalue of D_2 on sin / cos(theta (j + 1/2)) bases: -(4/h^2) sin^2(theta/2)."""
+    return -(4.0 / h ** 2) * math.sin(theta / 2) ** 2
+
+
+def mode_step_matrix(N: int, r: float, kx: int, ky: int, Z: float = 1.0) -> np.ndarray:
+    """Matrix of one full step on the coefficients (e, a, b) of
+    E_z = e sin(tx i) sin(ty j), H_x = a sin(tx i) cos(ty (j+1/2)), H_y = b cos(tx (i+1/2)) sin(ty j),
+    written from the symbols of D_2, Delta_h, P1, the filter and the Pade derivative."""
+    h = 1.0 / N
+    ht = r * h
+    k2 = 24.0 / ht ** 2
+    beta = 1.0 + k2 * h * h / 12.0
+    tx, ty = math.pi * kx * h, math.pi * ky * h
+    mx, my = -d2_symbol(tx, h), -d2_symbol(ty, h)  # eigenvalues of -D_xx, -D_yy (>= 0)
+    filt = beta - (h * h / 12.0) * (mx + my)
+    p1 = k2 * beta + mx + my - (h * h / 6.0) * mx * my
+    g = k2 * filt / p1
+    dx, dy = pade_symbol(tx, h), pade_symbol(ty, h)
+    # Step 1: e' = e + ht Z g (dy a - dx b)
+    S1 = np.array([[1.0, ht * Z * g * dy, -ht * Z * g * dx], [0, 1, 0], [0, 0, 1]])
+    # Step 2: a' = a - (ht/Z) g dy e', b' = b + (ht/Z) g dx e'
+    S2 = np.array([[1.0, 0, 0], [-(ht / Z) * g * dy, 1, 0], [(ht / Z) * g * dx, 0, 1]])
+    return S2 @ S1
+
+
+def mode_basis(N: int, kx: int, ky: int):
+    """Basis fields (E_z, H_x, H_y) of the mode on the staggered grids."""
+    h = 1.0 / N
+    i_n = np.arange(N + 1)
+    i_h = np.arange(N) + 0.5
+    tx, ty = math.pi * kx * h, math.pi * ky * h
+    ez = np.outer(np.sin(ty * i_n), np.sin(tx * i_n))
+    hx = np.outer(np.cos(ty * i_h), np.sin(tx * i_n))
+    hy = np.outer(np.sin(ty * i_n), np.cos(tx * i_h))
+    ez[0, :] = ez[-1, :] = 0.0
+    ez[:, 0] = ez[:, -1] = 0.0
+    hx[:, 0] = hx[:, -1] = 0.0
+    hy[0, :] = hy[-1, :] = 0.0
+    return ez, hx, hy
