@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the compact fourth-order Maxwell scheme on GB300.
+
+One benchmark step = one full time step of the scheme (Step 1 + Step 2, every kernel of the
+hot path) on the 2048 x 2048 2D TM_z cavity with 8 seeded modes (the configuration the
+cell-updates/s metric is quoted on).  The default run is the whole 4000-step workload.
+
+Output: one JSON line (rank 0).  `value` = cell-updates/s over all ranks, where one
+cell-update is one Yee cell advanced one full step.  L2 is flushed (256 MB write) between
+timed steps; each step is timed with CUDA events on the grid's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32_refined|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "2D TM_z PEC cavity 2048x2048 cells, 8 seeded modes (m,n in [1,40], N(0,1) amplitudes, seed 0), r=0.5"
+FALLBACK_HBM_GBS = 6800.0
+# FP64 ALU peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz (measured 1.19 TF/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64"])
+    p.add_argument("--closure", default="paper", choices=["paper", "reflect"])
+    p.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
+    return p.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_17263_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind: str):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_sha") != kernel_sources_hash():
+        return None
+    v = d.get("per_launch_dram_bytes", {}).get(kind)
+    return float(v) if v is not None else None
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_rate(n: int, steps: int, modes, time_budget: float = None):
+    """Cell-updates/s of the FP64 CPU oracle (1 thread) on an n x n grid."""
+    import oracle
+    o = oracle.Oracle2D(n, 0.5)
+    ez, hx, hy = o.init_modes([m for m in modes if m[0] < n and m[1] < n] or [(1, 1, 1.0)])
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        o.step(ez, hx, hy)
+        done += 1
+        if time_budget is not None and time.perf_counter() - t0 > time_budget:
+            break
+    dt = time.perf_counter() - t0
+    return n * n * done / dt, done, dt
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    cfg = workloads.config2()
+    K = args.steps if args.steps is not None else 20
+    W = args.warmup
+    # each step is one oracle step on an n_s x n_s sample of the workload; n_s keeps the run
+    # within about two minutes (an oracle step costs ~0.45 us per cell on one core)
+    n_s = int(min(2048, max(64, math.sqrt(120.0 / (max(K, 1) * 0.45e-6)))))
+    n_s -= n_s % 32
+    oracle_rate(n_s, W, cfg["modes"])
+    value, done, dt = oracle_rate(n_s, K, cfg["modes"])
+    line = {
+        "impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / max(done, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_n": n_s, "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{done} oracle steps on a {n_s}x{n_s} grid of the same workload"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2306_17263_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    # one non-default stream for the grid and every torch op (the L2 flush), so they are ordered
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    cfg = workloads.config2()
+    N, r, modes = cfg["n"], cfg["r"], cfg["modes"]
+    K = args.steps if args.steps is not None else cfg["steps"]
+    W = max(3, args.warmup)
+    prec = pkg.FP32_REFINED if args.precision == "fp32_refined" else pkg.FP64
+    closure = pkg.CLOSURE_PAPER if args.closure == "paper" else pkg.CLOSURE_REFLECT
+    g = pkg.Grid(N, r, precision=prec, closure=closure, stream="torch")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    g.init_modes(modes)
+    for _ in range(W):
+        g.step_profiled()
+        flush.zero_()
+    g.init_modes(modes)  # the timed steps are the workload from t = 0
+    torch.cuda.synchronize()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms = 0.0
+    per_kind = {}
+    launches = 0
+    t_wall = time.perf_counter()
+    for _ in range(K):
+        prof = g.step_profiled()
+        launches += len(prof)
+        for kind, ms, nbytes in prof:
+            total_ms += ms
+            a = per_kind.setdefault(kind, [0, 0.0, 0.0])
+            a[0] += 1
+            a[1] += ms
+            a[2] += nbytes
+        flush.zero_()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    barrier()
+    ms_step = total_ms / K
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * N * N / (ms_step * 1e-3)
+
+    l2_abs, l2_rel, max_abs, _ = g.error_vs_exact(modes)
+
+    # dominant kernel and its roofline
+    dom = max(per_kind.items(), key=lambda kv: kv[1][1])
+    kind, (cnt, kms, kbytes) = dom
+    avg_ms = kms / cnt
+    bytes_per_launch = kbytes / cnt
+    hbm, hbm_src = measured_peaks()
+    if kind.endswith("64"):
+        # FP64 kernels are bound by the FP64 pipe: report achieved GB/s against HBM and note
+        # the ALU bound in the line's extras
+        pass
+    achieved_gbs = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm, "traffic": ncu_traffic(kind), "kernel": kind,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
+    kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / total_ms, "GBps": v[2] / (v[1] * 1e-3) / 1e9}
+               for k, v in sorted(per_kind.items(), key=lambda kv: -kv[1][1])}
+
+    line = {
+        "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": K,
+        "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == pkg.FP32_REFINED else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "r": r, "precision": args.precision, "closure": args.closure,
+                   "l2": "flushed between timed steps (256 MB write); each step timed with CUDA events",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+        "accuracy": {"t": K * r / N, "l2_abs": l2_abs, "l2_rel": l2_rel, "max_abs": max_abs},
+        "clocks": clk,
+        "wall_s_timed_loop": wall,
+    }
+
+    if not args.no_extras and rank == 0:
+        # end to end through the C ABI with pinned host buffers: upload E^0, H^{1/2}, run K steps,
+        # download the final fields
+        shapes = g.shapes()
+        host_in = [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes]
+        host_out = [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes]
+        g.init_modes(modes)
+        L = pkg.load()
+        ptr_in = pkg._ptrs([t.data_ptr() for t in host_in])
+        ptr_out = pkg._ptrs([t.data_ptr() for t in host_out])
+        pkg._check(L.ms_get_fields(g._h, ptr_in))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg._check(L.ms_set_fields(g._h, ptr_in, 0))
+        pkg._check(L.ms_run(g._h, K))
+        pkg._check(L.ms_get_fields(g._h, ptr_out))
+        e2e_s = time.perf_counter() - t0
+        nbytes = sum(t.numel() * 8 for t in host_in)
+        line["e2e"] = {"value": N * N * K / e2e_s, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / K,
+                       "d2h_bytes_per_step": nbytes / K, "seconds": e2e_s,
+                       "what": "ms_set_fields (host) + ms_run(K) (graph replay, no L2 flush) + ms_get_fields (host)"}
+        # FP64 GPU form on the same workload (a shorter run), for the mixed-vs-FP64 comparison
+        if prec == pkg.FP32_REFINED:
+            g64 = pkg.Grid(N, r, precision=pkg.FP64, closure=closure, stream="torch")
+            g64.init_modes(modes)
+            k64 = min(K, 100)
+            for _ in range(3):
+                g64.step_profiled()
+            t64 = 0.0
+            for _ in range(k64):
+                t64 += sum(ms for _, ms, _ in g64.step_profiled())
+                flush.zero_()
+            line["fp64_gpu"] = {"value": N * N / (t64 / k64 * 1e-3), "unit": "cell-updates/s", "steps": k64,
+                                "ms_per_step": t64 / k64}
+            g64.close()
+        # CPU oracle on a bounded sample of the workload (rank 0, one core)
+        v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} oracle steps ({dt:.1f} s) on the full 2048x2048 grid"}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * maxwell4.h -- C ABI of the GB300 (sm_103a) implementation of the compact
+ * fourth-order staggered scheme for the first-order Maxwell equations
+ * (Versano, Turkel & Tsynkov, arXiv 2306.17263).
+ *
+ * One time step is the paper's Step 1 / Step 2 (Sec. 3.4):
+ *   P1^E E* = kappa^2 Z curl_h[(1 + kappa^2 h^2/12) H^{n+1/2} + (h^2/12) Delta_h H^{n+1/2}]
+ *   E^{n+1} = E^n + h_tau E*
+ *   P1^H H* = -(kappa^2/Z) curl_h[(1 + kappa^2 h^2/12) E^{n+1} + (h^2/12) Delta_h E^{n+1}]
+ *   H^{n+3/2} = H^{n+1/2} + h_tau H*
+ * with kappa^2 = 24/h_tau^2 (Sec. 3.2), P1 = -(Delta_h + (h^2/6) Upsilon_h) + kappa^2(1 + 2/r^2)
+ * (Definition "def:operatorsP"), curl_h the Pade compact curl of App. A.1 (Eq. "eq:lhs"),
+ * Dirichlet / even-ghost Neumann boundaries of Table "tab:bc" and Corollary "cor:ghost_cor",
+ * and J = rho = 0.
+ *
+ * Conventions for every entry point:
+ *   - Status codes are returned, never thrown.  On failure a message is available from
+ *     ms_last_error() (thread-local, valid until the next call on the same thread).
+ *   - Pointers passed in are borrowed for the duration of the call only; nothing is retained.
+ *   - Host field arrays are FP64 in the full staggered layout (boundary points included),
+ *     row-major with x fastest.  2D TM_z (Sec. 5, Eq. "maxwell2d"), N cells per side:
+ *         comps[0] = E_z : (N+1) rows x (N+1) cols, point (x_i, y_j)
+ *         comps[1] = H_x : N rows     x (N+1) cols, point (x_i, y_{j+1/2})
+ *         comps[2] = H_y : (N+1) rows x N cols,     point (x_{i+1/2}, y_j)
+ *     E is at time n h_tau and H at (n + 1/2) h_tau (Sec. 2).  Boundary values of the
+ *     Dirichlet components are zero on input and output (PEC walls, Eq. "eq:bc_E=0").
+ *   - The grid owns all device memory it needs; it is allocated in ms_create_grid and
+ *     released in ms_destroy.  All work is issued on the grid's stream.
+ *   - A grid handle must not be used from two threads at once.
+ */
+#ifndef MAXWELL4_H
+#define MAXWELL4_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ms_grid ms_grid;
+
+typedef enum {
+  MS_OK = 0,
+  MS_EINVAL = -1,        /* invalid argument or descriptor */
+  MS_ECFL = -2,          /* CFL number at or above the stability limit */
+  MS_ENOMEM = -3,        /* device or host allocation failed */
+  MS_ECUDA = -4,         /* a CUDA runtime call failed */
+  MS_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+  MS_ENOTCONV = -6,      /* an iterative solve did not reach its tolerance */
+  MS_EUNSUPPORTED = -7   /* valid but not implemented combination */
+} ms_status;
+
+/* Arithmetic of the time step.
+ *   MS_FP64:          every kernel computes in FP64.
+ *   MS_FP32_REFINED:  FP32 arithmetic; every scalar coefficient that is not exact in FP32 is
+ *                     applied as an error-free hi+lo pair, the elliptic and Pade solves are
+ *                     iterated to convergence against residuals with those exact coefficients,
+ *                     and the state is kept as an unevaluated FP32 hi+lo sum updated with
+ *                     error-free transformations (about 48 significant bits). */
+typedef enum { MS_FP64 = 0, MS_FP32_REFINED = 1 } ms_precision;
+
+/* Rows of the Pade matrix A at the two ends of each line (App. A.1, Eq. "eq:lhs").
+ *   MS_CLOSURE_PAPER:   the printed one-sided rows [26,-5,4,-1]/24 at both ends.
+ *   MS_CLOSURE_REFLECT: rows from the parity of the field about the wall ([23,1]/24 on the
+ *                       node-to-half-node lines, [22,1]/24 on half-node-to-node lines); with it
+ *                       every operator of the step is diagonal on the cavity modes. */
+typedef enum { MS_CLOSURE_PAPER = 0, MS_CLOSURE_REFLECT = 1 } ms_closure;
+
+/* Time-stepping scheme.  MS_SCHEME_C4 is the paper's compact scheme (Sec. 3.4);
+ * MS_SCHEME_YEE2 is the plain second-order Yee update (Sec. 5.2, stencil S with c = 1),
+ * kept as a same-hardware comparator. */
+typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1 } ms_scheme;
+
+typedef struct {
+  int dim;          /* 2 (TM_z: E_z, H_x, H_y).  3 is reserved. */
+  int n;            /* cells per side of the unit square, h = 1/n; 4 <= n <= 32768 */
+  double z_imp;     /* Z = sqrt(mu/epsilon) of Eq. "eq:maxwellv"; > 0 (1.0 in the paper) */
+  double r;         /* CFL number h_tau / h, 0 < r < stability limit (Sec. 4) */
+  int precision;    /* ms_precision */
+  int closure;      /* ms_closure */
+  int scheme;       /* ms_scheme */
+  void* stream;     /* cudaStream_t to issue work on, or NULL for a stream the grid creates */
+} ms_grid_desc;
+
+/* A cavity mode of the 2D TM_z problem (Sec. 5.1, Eq. "eq:data"):
+ *   E_z = amp cos(w t) sin(pi m x) sin(pi n y),  w = pi sqrt(m^2 + n^2),
+ *   H_x = -amp (1/Z) (sin(w t)/w) pi n sin(pi m x) cos(pi n y),
+ *   H_y =  amp (1/Z) (sin(w t)/w) pi m cos(pi m x) sin(pi n y).
+ * m, n >= 1. */
+typedef struct {
+  int m, n;
+  double amp;
+} ms_mode;
+
+/* Create a grid.  Validates the descriptor (MS_EINVAL), rejects r at or above the exact
+ * Fourier stability limit of the scheme (MS_ECFL; about 0.6895 in 2D, Sec. 4 gives the
+ * sufficient bound 5/(6 sqrt 2)), allocates the state and all scratch on the device, and
+ * zeroes the fields.  *out receives the handle; it is NULL on failure. */
+ms_status ms_create_grid(const ms_grid_desc* desc, ms_grid** out);
+
+/* Release the grid's device memory and stream.  NULL is accepted. */
+ms_status ms_destroy(ms_grid* g);
+
+/* Set E^0 and H^{1/2} to the exact superposition of nmodes cavity modes (Eq. "eq:data") at
+ * t = 0 and t = h_tau/2, and reset the step counter to 0.  modes is a host array. */
+ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes);
+
+/* Copy host FP64 fields (layout above) to the device state and set the step counter to
+ * `step` (E at step h_tau, H at (step + 1/2) h_tau).  Dirichlet boundary entries are ignored
+ * and stored as zero. */
+ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step);
+
+/* Copy the device state to host FP64 arrays (layout above). */
+ms_status ms_get_fields(ms_grid* g, double* const* comps);
+
+/* Same as ms_set_fields / ms_get_fields with device FP64 arrays (no host copy). */
+ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step);
+ms_status ms_get_fields_device(ms_grid* g, double* const* comps);
+
+/* Advance one full time step (Step 1 then Step 2), asynchronously on the grid's stream. */
+ms_status ms_step(ms_grid* g);
+
+/* Advance nsteps steps (nsteps >= 0), replaying a CUDA graph of the step captured on first
+ * use; asynchronous on the grid's stream. */
+ms_status ms_run(ms_grid* g, long nsteps);
+
+/* Wait for all work issued on the grid's stream; returns MS_ECUDA if any of it failed. */
+ms_status ms_sync(ms_grid* g);
+
+/* Current step counter n (E at n h_tau). */
+ms_status ms_get_step(ms_grid* g, long* step);
+
+/* Discrete energy at the current state, FP64 reductions:
+ *   W^n = Z^{-1} h^2 sum E^n.E^n + Z h^2 sum H^{n-1/2}.H^{n+1/2},
+ * with H^{n-1/2} = H^{n+1/2} - h_tau H*(E^n) recomputed on the device.  This is the
+ * leapfrog invariant of the scheme in the form of Sec. 4, Eq. "eq:eh" (the paper states
+ * no discrete energy); exact under MS_CLOSURE_REFLECT, bounded under MS_CLOSURE_PAPER.
+ * Synchronous. */
+ms_status ms_energy(ms_grid* g, double* W);
+
+/* L2 norm sqrt(h^2 sum div^2) of the Pade divergence of H on the n x n cell centres,
+ * div_h H = delta_x H_x + delta_y H_y (node-to-half-node derivatives of App. A.1). Synchronous. */
+ms_status ms_divergence(ms_grid* g, double* norm);
+
+/* Error of the current state against a superposition of exact modes at t_E = n h_tau,
+ * t_H = (n + 1/2) h_tau, FP64 on the device:
+ *   l2_abs = sqrt(h^2 sum (u - u_exact)^2) over E_z, H_x, H_y;  l2_rel = l2_abs / sqrt(h^2 sum u_exact^2);
+ *   max_abs = max |u - u_exact|;  sum_abs = sum |u - u_exact| (the summand of the mean absolute
+ *   error of Sec. 5.1).  Any output pointer may be NULL.  Synchronous. */
+ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double* l2_abs, double* l2_rel,
+                            double* max_abs, double* sum_abs);
+
+/* Operator-level entry points on device FP64 arrays in the full staggered layout (used to
+ * check each kernel against the oracle).  Available on MS_FP64 grids (MS_EUNSUPPORTED otherwise).
+ *   MS_OP_FILTER_{EZ,HX,HY}: out[0] = (1 + kappa^2 h^2/12) in[0] + (h^2/12) Delta_h in[0]
+ *                            (right side of Eq. "eq:ell"; zero on Dirichlet boundary points).
+ *   MS_OP_CURL_HE:  out[0] = kappa^2 Z (delta_x in[1] - delta_y in[0]), in = (G_x, G_y) (Step 1).
+ *   MS_OP_CURL_EH:  out[0] = -(kappa^2/Z) delta_y in[0], out[1] = (kappa^2/Z) delta_x in[0] (Step 2).
+ *   MS_OP_P1_{EZ,HX,HY}:       out[0] = P1 in[0] (Definition "def:operatorsP").
+ *   MS_OP_P1SOLVE_{EZ,HX,HY}:  out[0] = P1^{-1} in[0], iterated to the FP64 tolerance.
+ * in / out point to 1 or 2 device pointers as listed; inputs and outputs must not overlap.
+ * Asynchronous on the grid's stream. */
+typedef enum {
+  MS_OP_FILTER_EZ = 0, MS_OP_FILTER_HX = 1, MS_OP_FILTER_HY = 2,
+  MS_OP_CURL_HE = 3, MS_OP_CURL_EH = 4,
+  MS_OP_P1_EZ = 5, MS_OP_P1_HX = 6, MS_OP_P1_HY = 7,
+  MS_OP_P1SOLVE_EZ = 8, MS_OP_P1SOLVE_HX = 9, MS_OP_P1SOLVE_HY = 10
+} ms_op;
+ms_status ms_apply_op(ms_grid* g, int op, const double* const* in, double* const* out);
+
+/* Largest CFL number r for which every Fourier mode of the scheme is neutrally stable
+ * (Sec. 4: a mode is stable iff |h_tau lambda| <= 2 in sigma^2 - (2 - lambda^2 h_tau^2) sigma + 1 = 0),
+ * computed from the symbols of the operators.  dim must be 2.  Needs no GPU. */
+ms_status ms_stability_limit(int dim, double* rmax);
+
+/* Advance one step like ms_step, recording a CUDA event on the grid's stream after every
+ * kernel launch, then wait for it.  On return count = number of launches (at most cap are
+ * written), launch_ms[k] = time between the end of launch k-1 (or the step's start) and the
+ * end of launch k, kinds[k] = kernel kind (see ms_kernel_kind_name), bytes[k] = the launch's
+ * algorithmic bytes (each input array element read once, each output element written once).
+ * Synchronous. */
+ms_status ms_step_profiled(ms_grid* g, int cap, float* launch_ms, int* kinds, double* bytes, int* count);
+
+/* Name of a kernel kind reported by ms_step_profiled ("" for an unknown kind). */
+const char* ms_kernel_kind_name(int kind);
+
+/* Number of kernel launches one ms_step issues (for launch accounting). */
+ms_status ms_launches_per_step(ms_grid* g, int* launches);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* ms_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAXWELL4_H */

@@ -1,0 +1,249 @@
+"""GB300 (sm_103a) implementation of the compact fourth-order staggered scheme for the
+first-order Maxwell equations (Versano, Turkel & Tsynkov, arXiv 2306.17263).
+
+This module is a thin ctypes binding of ``include/maxwell4.h``: it marshals arguments
+and raises on non-zero status codes.  Every step of the scheme runs in the CUDA kernels of
+``libmaxwell4.so``; there is no CPU path.  If the library cannot be built or loaded,
+importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Grid", "MaxwellError", "load", "lib_path", "FP64", "FP32_REFINED", "CLOSURE_PAPER", "CLOSURE_REFLECT",
+           "SCHEME_C4", "SCHEME_YEE2", "OPS", "stability_limit"]
+
+FP64, FP32_REFINED = 0, 1
+CLOSURE_PAPER, CLOSURE_REFLECT = 0, 1
+SCHEME_C4, SCHEME_YEE2 = 0, 1
+OPS = {
+    "filter_ez": 0, "filter_hx": 1, "filter_hy": 2, "curl_he": 3, "curl_eh": 4,
+    "p1_ez": 5, "p1_hx": 6, "p1_hy": 7, "p1solve_ez": 8, "p1solve_hx": 9, "p1solve_hy": 10,
+}
+STATUS = {0: "MS_OK", -1: "MS_EINVAL", -2: "MS_ECFL", -3: "MS_ENOMEM", -4: "MS_ECUDA", -5: "MS_ETIMEOUT",
+          -6: "MS_ENOTCONV", -7: "MS_EUNSUPPORTED"}
+
+
+class MaxwellError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("z_imp", ctypes.c_double), ("r", ctypes.c_double),
+                ("precision", ctypes.c_int), ("closure", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class _Mode(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("amp", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Build (in-tree, if stale) and load libmaxwell4.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        V, I, D, L_ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+        PD = ctypes.POINTER(ctypes.c_double)
+        PPD = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "ms_create_grid": [ctypes.POINTER(_Desc), ctypes.POINTER(V)],
+            "ms_destroy": [V],
+            "ms_init_modes": [V, ctypes.POINTER(_Mode), I],
+            "ms_set_fields": [V, PPD, L_],
+            "ms_get_fields": [V, PPD],
+            "ms_set_fields_device": [V, PPD, L_],
+            "ms_get_fields_device": [V, PPD],
+            "ms_step": [V],
+            "ms_run": [V, L_],
+            "ms_sync": [V],
+            "ms_get_step": [V, ctypes.POINTER(L_)],
+            "ms_energy": [V, PD],
+            "ms_divergence": [V, PD],
+            "ms_error_vs_exact": [V, ctypes.POINTER(_Mode), I, PD, PD, PD, PD],
+            "ms_apply_op": [V, I, PPD, PPD],
+            "ms_launches_per_step": [V, ctypes.POINTER(I)],
+            "ms_stability_limit": [I, PD],
+            "ms_step_profiled": [V, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), PD, ctypes.POINTER(I)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = I
+        L.ms_kernel_kind_name.argtypes = [I]
+        L.ms_kernel_kind_name.restype = ctypes.c_char_p
+        L.ms_last_error.argtypes = []
+        L.ms_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise MaxwellError(status, load().ms_last_error().decode())
+
+
+def _modes(modes):
+    modes = list(modes)
+    arr = (_Mode * max(1, len(modes)))()
+    for k, (m, n, a) in enumerate(modes):
+        arr[k].m, arr[k].n, arr[k].amp = int(m), int(n), float(a)
+    return arr, len(modes)
+
+
+def _ptrs(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+
+
+def stability_limit(dim: int = 2) -> float:
+    """Largest stable CFL number of the scheme (from its Fourier symbol); needs no GPU."""
+    v = ctypes.c_double()
+    _check(load().ms_stability_limit(int(dim), ctypes.byref(v)))
+    return v.value
+
+
+class Grid:
+    """A 2D TM_z cavity (unit square, PEC walls) advanced by the compact scheme on the GPU.
+
+    precision: FP64 or FP32_REFINED; closure: CLOSURE_PAPER or CLOSURE_REFLECT;
+    scheme: SCHEME_C4 (the paper's scheme) or SCHEME_YEE2 (plain Yee comparator).
+    stream: a cudaStream_t handle (int), "torch" for torch's current stream, or None.
+    """
+
+    def __init__(self, n: int, r: float, z: float = 1.0, precision: int = FP64, closure: int = CLOSURE_PAPER,
+                 scheme: int = SCHEME_C4, stream=None):
+        L = load()
+        if stream == "torch":
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        d = _Desc(2, int(n), float(z), float(r), int(precision), int(closure), int(scheme),
+                  ctypes.c_void_p(int(stream)) if stream else None)
+        h = ctypes.c_void_p()
+        _check(L.ms_create_grid(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n, self.r, self.z = int(n), float(r), float(z)
+        self.precision, self.closure, self.scheme = int(precision), int(closure), int(scheme)
+        self.h = 1.0 / n
+        self.ht = r * self.h
+
+    # ------------------------------------------------------------------
+    def shapes(self):
+        N = self.n
+        return (N + 1, N + 1), (N, N + 1), (N + 1, N)
+
+    def close(self):
+        if self._h:
+            load().ms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def init_modes(self, modes):
+        arr, nm = _modes(modes)
+        _check(load().ms_init_modes(self._h, arr, nm))
+
+    def set_fields(self, ez, hx, hy, step: int = 0):
+        """Host FP64 arrays (numpy) in the full staggered layout."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ez, hx, hy)]
+        for a, s in zip(arrs, self.shapes()):
+            if a.shape != s:
+                raise ValueError(f"expected shape {s}, got {a.shape}")
+        _check(load().ms_set_fields(self._h, _ptrs([a.ctypes.data for a in arrs]), int(step)))
+
+    def get_fields(self):
+        out = [np.zeros(s) for s in self.shapes()]
+        _check(load().ms_get_fields(self._h, _ptrs([a.ctypes.data for a in out])))
+        return tuple(out)
+
+    def set_fields_device(self, ez, hx, hy, step: int = 0):
+        """torch CUDA float64 tensors (contiguous) in the full staggered layout."""
+        for t, s in zip((ez, hx, hy), self.shapes()):
+            if tuple(t.shape) != s or not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
+                raise ValueError("expected contiguous CUDA float64 tensors of the staggered shapes")
+        _check(load().ms_set_fields_device(self._h, _ptrs([t.data_ptr() for t in (ez, hx, hy)]), int(step)))
+
+    def get_fields_device(self, ez, hx, hy):
+        _check(load().ms_get_fields_device(self._h, _ptrs([t.data_ptr() for t in (ez, hx, hy)])))
+
+    def step(self):
+        _check(load().ms_step(self._h))
+
+    def run(self, nsteps: int):
+        _check(load().ms_run(self._h, int(nsteps)))
+
+    def sync(self):
+        _check(load().ms_sync(self._h))
+
+    @property
+    def step_count(self) -> int:
+        v = ctypes.c_long()
+        _check(load().ms_get_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def launches_per_step(self) -> int:
+        v = ctypes.c_int()
+        _check(load().ms_launches_per_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    def energy(self) -> float:
+        v = ctypes.c_double()
+        _check(load().ms_energy(self._h, ctypes.byref(v)))
+        return v.value
+
+    def divergence(self) -> float:
+        v = ctypes.c_double()
+        _check(load().ms_divergence(self._h, ctypes.byref(v)))
+        return v.value
+
+    def error_vs_exact(self, modes):
+        """(l2_abs, l2_rel, max_abs, sum_abs) of the state against the exact modes."""
+        arr, nm = _modes(modes)
+        out = [ctypes.c_double() for _ in range(4)]
+        _check(load().ms_error_vs_exact(self._h, arr, nm, *[ctypes.byref(v) for v in out]))
+        return tuple(v.value for v in out)
+
+    def step_profiled(self, cap: int = 512):
+        """One step with an event after every launch: list of (kernel kind, ms, algorithmic bytes)."""
+        L = load()
+        ms = (ctypes.c_float * cap)()
+        kinds = (ctypes.c_int * cap)()
+        nbytes = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(L.ms_step_profiled(self._h, cap, ms, kinds, nbytes, ctypes.byref(n)))
+        return [(L.ms_kernel_kind_name(kinds[k]).decode(), ms[k], nbytes[k]) for k in range(min(n.value, cap))]
+
+    def apply_op(self, op: str, ins, outs):
+        """Operator entry point on CUDA float64 tensors (see maxwell4.h, ms_apply_op)."""
+        _check(load().ms_apply_op(self._h, OPS[op], _ptrs([t.data_ptr() for t in ins]),
+                                  _ptrs([t.data_ptr() for t in outs])))

@@ -1,0 +1,723 @@
+// C ABI of include/maxwell4.h: grid life cycle, the time step (Sec. 3.4 Step 1 / Step 2),
+// graph-captured time loop, diagnostics and operator-level entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "k_fp64.cuh"
+#include "k_mixed.cuh"
+
+using namespace ms;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ms_status fail(ms_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define MS_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(MS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define MS_TRY(expr)              \
+  do {                            \
+    ms_status s_ = (expr);        \
+    if (s_ != MS_OK) return s_;   \
+  } while (0)
+
+ms_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+template <typename T>
+ms_status dalloc(T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 256);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(MS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return MS_OK;
+}
+
+// Number of Richardson sweeps for P~ = h^2 P1 with spectrum in [c1h2, c1h2 + 16/3] (App. A.2)
+// to reduce the error below tol (x0 = 0, contraction (16/3) / (2 c1h2 + 16/3) per sweep).
+int richardson_sweeps(double c1h2, double tol) {
+  const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
+  int s = (int)std::ceil(std::log(tol) / std::log(rho));
+  if (s < 1) s = 1;
+  if (s > 64) s = 64;
+  return s;
+}
+
+double omega_of(double c1h2) { return 2.0 / (2.0 * c1h2 + 16.0 / 3.0); }
+
+// ---------------------------------------------------------------------------------------
+// FP64 operator building blocks on arbitrary device arrays.
+
+// R = kappa^2 Z (delta_x G_y - delta_y G_x) on E_z (Step 1, third row of curl_h).
+void curl_he64(ms_grid* g, const double* Gx, const double* Gy, double* R, int* nl) {
+  const int N = g->N;
+  const double s = g->kappa2 * g->Z / g->h;
+  // delta_x G_y: rows j = 1..N-1 of H_y (N half-node values) -> E_z columns 1..N-1
+  launch_pade64(0, Gy, R, N + 1, N, N + 1, N + 1, 1, 1, N, g->pade[HALF_TO_NODE], s, 0, g->stream);
+  prof_mark(g, KK_PADE64, 8.0 * ((double)(N - 1) * N + (double)(N + 1) * (N + 1)));
+  // delta_y G_x: columns i = 1..N-1 of H_x (N half-node values) -> E_z rows 1..N-1
+  launch_pade64(1, Gx, R, N + 1, N + 1, N + 1, N + 1, 1, 1, N, g->pade[HALF_TO_NODE], -s, 1, g->stream);
+  prof_mark(g, KK_PADE64, 8.0 * ((double)(N - 1) * N + 2.0 * (N + 1) * (N + 1)));
+  *nl += 2;
+}
+
+// (R_x, R_y) = (kappa^2/Z) (-delta_y G_E, delta_x G_E) (Step 2).
+void curl_eh64(ms_grid* g, const double* GE, double* Rx, double* Ry, int* nl) {
+  const int N = g->N;
+  const double s = g->kappa2 / (g->Z * g->h);
+  // delta_y G_E: columns i = 1..N-1 of E_z (N+1 node values) -> H_x rows 0..N-1
+  launch_pade64(1, GE, Rx, N + 1, N + 1, N, N + 1, 0, 1, N, g->pade[NODE_TO_HALF], -s, 0, g->stream);
+  prof_mark(g, KK_PADE64, 8.0 * ((double)(N - 1) * (N + 1) + (double)N * (N + 1)));
+  // delta_x G_E: rows j = 1..N-1 of E_z -> H_y columns 0..N-1
+  launch_pade64(0, GE, Ry, N + 1, N + 1, N, N, 0, 1, N, g->pade[NODE_TO_HALF], s, 0, g->stream);
+  prof_mark(g, KK_PADE64, 8.0 * ((double)(N - 1) * (N + 1) + (double)N * (N + 1)));
+  *nl += 2;
+}
+
+// x = P1^{-1} b by Richardson sweeps; the last sweep writes `out` and, if upd != nullptr,
+// adds upd_scale * x to upd (the state update E += h_tau E*).
+void p1_solve64(ms_grid* g, int f, const double* b, double* out, double* upd, double upd_scale, int* nl) {
+  const Shape& s = g->sh[f];
+  const double c1h2 = g->c1 * g->h * g->h, om = omega_of(c1h2), h2 = g->h * g->h;
+  const int S = g->p1_sweeps;
+  double* buf[2] = {g->s64[3], g->s64[4]};
+  const double* xin = nullptr;
+  for (int k = 0; k < S; ++k) {
+    const bool last = (k == S - 1);
+    double* xo = last ? out : buf[k & 1];
+    launch_p1_sweep64(b, xin, xo, s, c1h2, om, h2, k == 0, last ? upd : nullptr, upd_scale, g->stream);
+    prof_mark(g, KK_P1SWEEP64, 8.0 * (double)s.size() * ((k == 0 ? 2 : 3) + (last && upd ? 2 : 0)));
+    xin = xo;
+  }
+  *nl += S;
+}
+
+// H* = P1^{-1} R_H(E) for a given E (Step 2 without the update) into hxs, hys.
+void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, double* hx_upd, double* hy_upd, int* nl) {
+  double* GE = g->s64[0];
+  double* Rx = g->s64[1];
+  double* Ry = g->s64[2];
+  launch_filter64(ez, GE, g->sh[EZ], g->beta, g->stream);
+  prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[EZ].size());
+  *nl += 1;
+  curl_eh64(g, GE, Rx, Ry, nl);
+  p1_solve64(g, HX, Rx, hxs, hx_upd, g->ht, nl);
+  p1_solve64(g, HY, Ry, hys, hy_upd, g->ht, nl);
+}
+
+ms_status step64(ms_grid* g) {
+  int nl = 0;
+  double *ez = g->f64[EZ], *hx = g->f64[HX], *hy = g->f64[HY];
+  if (g->desc.scheme == MS_SCHEME_YEE2) {
+    const double ne = (double)g->sh[EZ].size(), nh = (double)g->sh[HX].size();
+    launch_yee_e64(ez, hx, hy, g->N, g->desc.r * g->Z, g->stream);
+    prof_mark(g, KK_YEE64, 8.0 * (2 * ne + 2 * nh));
+    launch_yee_h64(ez, hx, hy, g->N, g->desc.r / g->Z, g->stream);
+    prof_mark(g, KK_YEE64, 8.0 * (ne + 4 * nh));
+    g->launches_per_step = 2;
+    return check_launch("yee step");
+  }
+  // Step 1: G = (beta + (h^2/12) Delta_h) H, R = kappa^2 Z curl_h G, P1 E* = R, E += h_tau E*
+  double* Gx = g->s64[0];
+  double* Gy = g->s64[1];
+  double* R = g->s64[2];
+  launch_filter64(hx, Gx, g->sh[HX], g->beta, g->stream);
+  prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[HX].size());
+  launch_filter64(hy, Gy, g->sh[HY], g->beta, g->stream);
+  prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[HY].size());
+  nl += 2;
+  curl_he64(g, Gx, Gy, R, &nl);
+  // the solve's result lands in s64[5]; the last sweep also performs E += h_tau E*
+  p1_solve64(g, EZ, R, g->s64[5], ez, g->ht, &nl);
+  // Step 2 on E^{n+1}
+  h_increment64(g, ez, g->s64[5], g->s64[5], hx, hy, &nl);
+  g->launches_per_step = nl;
+  return check_launch("fp64 step");
+}
+
+ms_status step_any(ms_grid* g) {
+  if (g->desc.precision == MS_FP64) return step64(g);
+  int nl = 0;
+  ms_status s = step_mixed(g, &nl);
+  if (s != MS_OK) return fail(s, mixed_last_error());
+  g->launches_per_step = nl;
+  return check_launch("mixed step");
+}
+
+ms_status capture(ms_grid* g, Graph* gr, int steps) {
+  if (gr->exec) return MS_OK;
+  MS_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+  ms_status st = MS_OK;
+  for (int k = 0; k < steps && st == MS_OK; ++k) st = step_any(g);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+  if (st != MS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(MS_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&gr->exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(MS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  gr->graph = graph;
+  gr->steps = steps;
+  return MS_OK;
+}
+
+void free_graph(Graph* gr) {
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  *gr = Graph{};
+}
+
+ms_status ensure_partial(ms_grid* g, size_t n) {
+  int b = reduce_blocks(n);
+  if (b <= g->partial_cap) return MS_OK;
+  if (g->d_partial) cudaFree(g->d_partial);
+  MS_TRY(dalloc(&g->d_partial, (size_t)b * 4));
+  g->partial_cap = b;
+  return MS_OK;
+}
+
+// 1D tables of the separable cavity modes on the three grids (Eq. "eq:data").
+// Per field: [tab_x (nm x nx)] [tab_y (nm x ny)] [coef (nm)].
+ms_status exact_fields64(ms_grid* g, const ms_mode* modes, int nm, double tE, double tH, double* out[3]) {
+  const int N = g->N;
+  const double pi = M_PI;
+  std::vector<double> host;
+  size_t offs[3][3];
+  for (int f = 0; f < 3; ++f) {
+    const Shape& s = g->sh[f];
+    offs[f][0] = host.size();
+    host.resize(host.size() + (size_t)nm * s.nx);
+    offs[f][1] = host.size();
+    host.resize(host.size() + (size_t)nm * s.ny);
+    offs[f][2] = host.size();
+    host.resize(host.size() + nm);
+  }
+  // sin(pi k i / N) and cos(pi k (2i+1) / (2N)) with exact integer argument reduction
+  auto sin_node = [&](int k, int i) {
+    if (i == 0 || i == N) return 0.0;
+    long q = ((long)k * i) % (2L * N);
+    return std::sin(pi * (double)q / N);
+  };
+  auto cos_half = [&](int k, int i) {
+    long q = ((long)k * (2L * i + 1)) % (4L * N);
+    return std::cos(pi * (double)q / (2.0 * N));
+  };
+  for (int m = 0; m < nm; ++m) {
+    const int kx = modes[m].m, ky = modes[m].n;
+    const double A = modes[m].amp, w = pi * std::sqrt((double)kx * kx + (double)ky * ky);
+    // E_z
+    for (int i = 0; i <= N; ++i) host[offs[EZ][0] + (size_t)m * (N + 1) + i] = sin_node(kx, i);
+    for (int j = 0; j <= N; ++j) host[offs[EZ][1] + (size_t)m * (N + 1) + j] = sin_node(ky, j);
+    host[offs[EZ][2] + m] = A * std::cos(w * tE);
+    // H_x at (x_i, y_{j+1/2})
+    for (int i = 0; i <= N; ++i) host[offs[HX][0] + (size_t)m * (N + 1) + i] = sin_node(kx, i);
+    for (int j = 0; j < N; ++j) host[offs[HX][1] + (size_t)m * N + j] = cos_half(ky, j);
+    host[offs[HX][2] + m] = -A * std::sin(w * tH) / (w * g->Z) * pi * ky;
+    // H_y at (x_{i+1/2}, y_j)
+    for (int i = 0; i < N; ++i) host[offs[HY][0] + (size_t)m * N + i] = cos_half(kx, i);
+    for (int j = 0; j <= N; ++j) host[offs[HY][1] + (size_t)m * (N + 1) + j] = sin_node(ky, j);
+    host[offs[HY][2] + m] = A * std::sin(w * tH) / (w * g->Z) * pi * kx;
+  }
+  if (host.size() > g->modetab_cap) {
+    if (g->d_modetab) cudaFree(g->d_modetab);
+    g->d_modetab = nullptr;
+    g->modetab_cap = 0;
+    MS_TRY(dalloc(&g->d_modetab, host.size()));
+    g->modetab_cap = host.size();
+  }
+  MS_CUDA(cudaMemcpyAsync(g->d_modetab, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  for (int f = 0; f < 3; ++f)
+    launch_mode_field(out[f], g->sh[f], g->d_modetab + offs[f][0], g->d_modetab + offs[f][1],
+                      g->d_modetab + offs[f][2], nm, g->stream);
+  MS_TRY(check_launch("mode field"));
+  MS_CUDA(cudaStreamSynchronize(g->stream));  // the host table is released on return
+  return MS_OK;
+}
+
+// FP64 view of the state: the FP64 arrays themselves, or hi+lo joined into dst scratch.
+ms_status state64(ms_grid* g, double* dst[3], const double* view[3]) {
+  for (int f = 0; f < 3; ++f) {
+    if (g->desc.precision == MS_FP64) {
+      view[f] = g->f64[f];
+    } else {
+      launch_join(g->hi[f], g->lo[f], dst[f], g->sh[f].size(), g->stream);
+      view[f] = dst[f];
+    }
+  }
+  return check_launch("join");
+}
+
+ms_status store_state(ms_grid* g, const double* const* src) {
+  for (int f = 0; f < 3; ++f) {
+    const size_t n = g->sh[f].size();
+    if (g->desc.precision == MS_FP64) {
+      if (src[f] != g->f64[f])
+        MS_CUDA(cudaMemcpyAsync(g->f64[f], src[f], n * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+      launch_zero_dirichlet64(g->f64[f], g->sh[f], g->stream);
+    } else {
+      // zero the Dirichlet entries in a scratch copy, then split
+      double* tmp = g->s64[0];
+      MS_CUDA(cudaMemcpyAsync(tmp, src[f], n * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+      launch_zero_dirichlet64(tmp, g->sh[f], g->stream);
+      launch_split(tmp, g->hi[f], g->lo[f], n, g->stream);
+    }
+  }
+  return check_launch("store state");
+}
+
+bool valid_grid(ms_grid* g) { return g != nullptr && g->N > 0; }
+
+}  // namespace
+
+namespace ms {
+
+void prof_mark(ms_grid* g, int kind, double bytes) {
+  Prof& p = g->prof;
+  if (!p.on) return;
+  if (p.next >= p.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    p.pool.push_back(e);
+  }
+  cudaEventRecord(p.pool[p.next++], g->stream);
+  p.kinds.push_back(kind);
+  p.bytes.push_back(bytes);
+}
+
+const char* kernel_kind_name(int k) {
+  static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64",
+                                        "filter32", "pade32", "p1sweep32"};
+  return (k >= 0 && k < KK_COUNT) ? names[k] : "";
+}
+
+}  // namespace ms
+
+// =======================================================================================
+extern "C" {
+
+const char* ms_last_error(void) { return g_last_error.c_str(); }
+
+ms_status ms_stability_limit(int dim, double* rmax) {
+  if (!rmax) return fail(MS_EINVAL, "rmax is NULL");
+  if (dim != 2) return fail(dim == 3 ? MS_EUNSUPPORTED : MS_EINVAL, "dim must be 2");
+  *rmax = stability_limit_2d();
+  return MS_OK;
+}
+
+ms_status ms_create_grid(const ms_grid_desc* d, ms_grid** out) {
+  g_last_error.clear();
+  if (!out) return fail(MS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(MS_EINVAL, "desc is NULL");
+  if (d->dim != 2) return fail(d->dim == 3 ? MS_EUNSUPPORTED : MS_EINVAL, "dim must be 2 (3 is reserved)");
+  if (d->n < 4 || d->n > 32768) return fail(MS_EINVAL, "n must be in [4, 32768]");
+  if (!(d->z_imp > 0.0) || !std::isfinite(d->z_imp)) return fail(MS_EINVAL, "z_imp must be positive");
+  if (!(d->r > 0.0) || !std::isfinite(d->r)) return fail(MS_EINVAL, "r must be positive");
+  if (d->precision != MS_FP64 && d->precision != MS_FP32_REFINED) return fail(MS_EINVAL, "unknown precision");
+  if (d->closure != MS_CLOSURE_PAPER && d->closure != MS_CLOSURE_REFLECT) return fail(MS_EINVAL, "unknown closure");
+  if (d->scheme != MS_SCHEME_C4 && d->scheme != MS_SCHEME_YEE2) return fail(MS_EINVAL, "unknown scheme");
+  if (d->scheme == MS_SCHEME_YEE2 && d->precision != MS_FP64)
+    return fail(MS_EUNSUPPORTED, "the Yee comparator runs in FP64 only");
+  if (d->scheme == MS_SCHEME_C4) {
+    const double rmax = stability_limit_2d();
+    if (d->r >= rmax) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "r = %.6g is at or above the stability limit %.6g of the 2D scheme", d->r, rmax);
+      return fail(MS_ECFL, buf);
+    }
+  } else if (d->r * std::sqrt(2.0) >= 1.0) {
+    return fail(MS_ECFL, "Yee scheme requires r < 1/sqrt(2)");
+  }
+  ms_grid* g = new ms_grid();
+  g->desc = *d;
+  g->N = d->n;
+  g->Z = d->z_imp;
+  g->h = 1.0 / d->n;
+  g->ht = d->r * g->h;
+  g->kappa2 = 24.0 / (g->ht * g->ht);
+  g->beta = 1.0 + g->kappa2 * g->h * g->h / 12.0;
+  g->c1 = g->kappa2 * g->beta;
+  for (int f = 0; f < 3; ++f) g->sh[f] = field_shape(g->N, f);
+  auto cleanup = [&](ms_status s) {
+    ms_destroy(g);
+    return s;
+  };
+  if (d->stream) {
+    g->stream = (cudaStream_t)d->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(MS_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    g->own_stream = true;
+  }
+  // Pade tables (FP64 truncation 1e-18 of the row's absolute sum)
+  std::string err;
+  for (int kind = 0; kind < 2; ++kind) {
+    const int M = (kind == HALF_TO_NODE) ? g->N - 1 : g->N;
+    if (build_pade_table(M, d->closure, kind, 1e-18, &g->pade[kind], &err) != 0) return cleanup(fail(MS_EINVAL, err));
+    PadeTable& t = g->pade[kind];
+    std::vector<float> whi(t.w.size()), wlo(t.w.size());
+    for (size_t k = 0; k < t.w.size(); ++k) {
+      whi[k] = (float)t.w[k];
+      wlo[k] = (float)(t.w[k] - (double)whi[k]);
+    }
+    ms_status s = dalloc(&t.d_w, t.w.size());
+    if (s == MS_OK) s = dalloc(&t.d_whi, t.w.size());
+    if (s == MS_OK) s = dalloc(&t.d_wlo, t.w.size());
+    if (s != MS_OK) return cleanup(s);
+    if (cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.d_whi, whi.data(), whi.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.d_wlo, wlo.data(), wlo.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(fail(MS_ECUDA, "copy of Pade tables failed"));
+  }
+  g->p1_sweeps = richardson_sweeps(g->c1 * g->h * g->h, 1e-17);
+  const size_t nmax = (size_t)(g->N + 1) * (g->N + 1);
+  ms_status s = MS_OK;
+  // FP64 scratch is used by the FP64 step and by the diagnostics of both precisions
+  for (int k = 0; k < 6 && s == MS_OK; ++k) s = dalloc(&g->s64[k], nmax);
+  if (d->precision == MS_FP64) {
+    for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->f64[f], g->sh[f].size());
+  } else {
+    for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->hi[f], g->sh[f].size());
+    for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->lo[f], g->sh[f].size());
+    if (s == MS_OK) {
+      s = mixed_setup(g);
+      if (s != MS_OK) fail(s, mixed_last_error());
+    }
+  }
+  if (s == MS_OK) s = dalloc(&g->d_result, 8);
+  if (s == MS_OK) s = ensure_partial(g, nmax);
+  if (s != MS_OK) return cleanup(s);
+  for (int f = 0; f < 3; ++f) {
+    if (g->f64[f]) cudaMemsetAsync(g->f64[f], 0, g->sh[f].size() * sizeof(double), g->stream);
+    if (g->hi[f]) cudaMemsetAsync(g->hi[f], 0, g->sh[f].size() * sizeof(float), g->stream);
+    if (g->lo[f]) cudaMemsetAsync(g->lo[f], 0, g->sh[f].size() * sizeof(float), g->stream);
+  }
+  for (int k = 0; k < 6; ++k)
+    if (g->s64[k]) cudaMemsetAsync(g->s64[k], 0, nmax * sizeof(double), g->stream);
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cleanup(fail(MS_ECUDA, std::string("create: ") + cudaGetErrorString(e)));
+  *out = g;
+  return MS_OK;
+}
+
+ms_status ms_destroy(ms_grid* g) {
+  if (!g) return MS_OK;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  free_graph(&g->graph1);
+  free_graph(&g->graphk);
+  for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(g->pade[k].d_w);
+    cudaFree(g->pade[k].d_whi);
+    cudaFree(g->pade[k].d_wlo);
+  }
+  for (int f = 0; f < 3; ++f) {
+    cudaFree(g->f64[f]);
+    cudaFree(g->hi[f]);
+    cudaFree(g->lo[f]);
+  }
+  for (int k = 0; k < 6; ++k) cudaFree(g->s64[k]);
+  for (int k = 0; k < 8; ++k) cudaFree(g->s32[k]);
+  mixed_teardown(g);
+  cudaFree(g->d_partial);
+  cudaFree(g->d_result);
+  cudaFree(g->d_modetab);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return MS_OK;
+}
+
+ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (nmodes < 0 || (nmodes > 0 && !modes)) return fail(MS_EINVAL, "invalid modes");
+  for (int m = 0; m < nmodes; ++m)
+    if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
+  double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  MS_TRY(exact_fields64(g, modes, nmodes, 0.0, 0.5 * g->ht, dst));
+  MS_TRY(store_state(g, dst));
+  g->step = 0;
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step) {
+  if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  for (int f = 0; f < 3; ++f)
+    if (!comps[f]) return fail(MS_EINVAL, "NULL component");
+  MS_TRY(store_state(g, comps));
+  g->step = step;
+  return MS_OK;
+}
+
+ms_status ms_get_fields_device(ms_grid* g, double* const* comps) {
+  if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  for (int f = 0; f < 3; ++f) {
+    if (!comps[f]) return fail(MS_EINVAL, "NULL component");
+    const size_t n = g->sh[f].size();
+    if (g->desc.precision == MS_FP64)
+      MS_CUDA(cudaMemcpyAsync(comps[f], g->f64[f], n * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    else
+      launch_join(g->hi[f], g->lo[f], comps[f], n, g->stream);
+  }
+  return check_launch("get fields");
+}
+
+ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
+  if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  for (int f = 0; f < 3; ++f) {
+    if (!comps[f]) return fail(MS_EINVAL, "NULL component");
+    MS_CUDA(cudaMemcpyAsync(dst[f], comps[f], g->sh[f].size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  }
+  MS_TRY(store_state(g, dst));
+  g->step = step;
+  return MS_OK;
+}
+
+ms_status ms_get_fields(ms_grid* g, double* const* comps) {
+  if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  const double* view[3];
+  for (int f = 0; f < 3; ++f)
+    if (!comps[f]) return fail(MS_EINVAL, "NULL component");
+  MS_TRY(state64(g, tmp, view));
+  for (int f = 0; f < 3; ++f)
+    MS_CUDA(cudaMemcpyAsync(comps[f], view[f], g->sh[f].size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status ms_step(ms_grid* g) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  MS_TRY(step_any(g));
+  g->step += 1;
+  return MS_OK;
+}
+
+ms_status ms_run(ms_grid* g, long nsteps) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (nsteps < 0) return fail(MS_EINVAL, "nsteps must be >= 0");
+  const int chunk = 16;
+  if (nsteps >= chunk) MS_TRY(capture(g, &g->graphk, chunk));
+  if (nsteps % chunk) MS_TRY(capture(g, &g->graph1, 1));
+  long left = nsteps;
+  while (left >= chunk) {
+    MS_CUDA(cudaGraphLaunch(g->graphk.exec, g->stream));
+    left -= chunk;
+  }
+  while (left > 0) {
+    MS_CUDA(cudaGraphLaunch(g->graph1.exec, g->stream));
+    left -= 1;
+  }
+  g->step += nsteps;
+  return MS_OK;
+}
+
+ms_status ms_sync(ms_grid* g) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status ms_get_step(ms_grid* g, long* step) {
+  if (!valid_grid(g) || !step) return fail(MS_EINVAL, "invalid argument");
+  *step = g->step;
+  return MS_OK;
+}
+
+ms_status ms_step_profiled(ms_grid* g, int cap, float* launch_ms, int* kinds, double* bytes, int* count) {
+  if (!valid_grid(g) || !count || cap < 0 || (cap > 0 && (!launch_ms || !kinds || !bytes)))
+    return fail(MS_EINVAL, "invalid argument");
+  Prof& p = g->prof;
+  p.on = true;
+  p.next = 0;
+  p.kinds.clear();
+  p.bytes.clear();
+  prof_mark(g, -1);
+  ms_status s = step_any(g);
+  p.on = false;
+  if (s != MS_OK) return s;
+  g->step += 1;
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  const int n = (int)p.next - 1;
+  for (int k = 0; k < n && k < cap; ++k) {
+    float ms = 0.0f;
+    MS_CUDA(cudaEventElapsedTime(&ms, p.pool[k], p.pool[k + 1]));
+    launch_ms[k] = ms;
+    kinds[k] = p.kinds[k + 1];
+    bytes[k] = p.bytes[k + 1];
+  }
+  *count = n;
+  return MS_OK;
+}
+
+const char* ms_kernel_kind_name(int kind) { return kernel_kind_name(kind); }
+
+ms_status ms_launches_per_step(ms_grid* g, int* launches) {
+  if (!valid_grid(g) || !launches) return fail(MS_EINVAL, "invalid argument");
+  if (g->launches_per_step == 0) {
+    // count by issuing one captured step into a throw-away graph
+    Graph tmp;
+    MS_TRY(capture(g, &tmp, 1));
+    free_graph(&tmp);
+  }
+  *launches = g->launches_per_step;
+  return MS_OK;
+}
+
+ms_status ms_energy(ms_grid* g, double* W) {
+  if (!valid_grid(g) || !W) return fail(MS_EINVAL, "invalid argument");
+  if (g->desc.scheme != MS_SCHEME_C4) return fail(MS_EUNSUPPORTED, "energy is defined for the compact scheme");
+  // FP64 view of the state in scratch slots that the H increment does not touch
+  double* tmp[3] = {nullptr, nullptr, nullptr};
+  std::vector<double*> extra;
+  const double* view[3];
+  if (g->desc.precision != MS_FP64) {
+    for (int f = 0; f < 3; ++f) {
+      double* p = nullptr;
+      MS_TRY(dalloc(&p, g->sh[f].size()));
+      tmp[f] = p;
+      extra.push_back(p);
+    }
+  }
+  auto release = [&](ms_status s) {
+    cudaStreamSynchronize(g->stream);
+    for (double* p : extra) cudaFree(p);
+    return s;
+  };
+  ms_status s = state64(g, tmp, view);
+  if (s != MS_OK) return release(s);
+  double* hxs = nullptr;
+  double* hys = nullptr;
+  s = dalloc(&hxs, g->sh[HX].size());
+  if (s == MS_OK) extra.push_back(hxs);
+  if (s == MS_OK) s = dalloc(&hys, g->sh[HY].size());
+  if (s == MS_OK) extra.push_back(hys);
+  if (s != MS_OK) return release(s);
+  int nl = 0;
+  h_increment64(g, view[EZ], hxs, hys, nullptr, nullptr, &nl);
+  // W = h^2 [ Z^-1 E.E + Z (H.H - h_tau H*.H) ]
+  const int bE = reduce_blocks(g->sh[EZ].size());
+  launch_dot(view[EZ], view[EZ], g->sh[EZ].size(), g->d_partial, bE, g->d_result, 0, 0, g->stream);
+  launch_dot(view[HX], view[HX], g->sh[HX].size(), g->d_partial, reduce_blocks(g->sh[HX].size()), g->d_result, 1, 0,
+             g->stream);
+  launch_dot(view[HY], view[HY], g->sh[HY].size(), g->d_partial, reduce_blocks(g->sh[HY].size()), g->d_result, 1, 1,
+             g->stream);
+  launch_dot(hxs, view[HX], g->sh[HX].size(), g->d_partial, reduce_blocks(g->sh[HX].size()), g->d_result, 2, 0,
+             g->stream);
+  launch_dot(hys, view[HY], g->sh[HY].size(), g->d_partial, reduce_blocks(g->sh[HY].size()), g->d_result, 2, 1,
+             g->stream);
+  s = check_launch("energy");
+  if (s != MS_OK) return release(s);
+  double r[3];
+  if (cudaMemcpyAsync(r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+      cudaStreamSynchronize(g->stream) != cudaSuccess)
+    return release(fail(MS_ECUDA, "energy readback failed"));
+  const double h2 = g->h * g->h;
+  *W = h2 * (r[0] / g->Z + g->Z * (r[1] - g->ht * r[2]));
+  return release(MS_OK);
+}
+
+ms_status ms_divergence(ms_grid* g, double* norm) {
+  if (!valid_grid(g) || !norm) return fail(MS_EINVAL, "invalid argument");
+  double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  const double* view[3];
+  MS_TRY(state64(g, tmp, view));
+  const int N = g->N;
+  double* div = g->s64[0];
+  const PadeTable& t = g->pade[NODE_TO_HALF];
+  // delta_x H_x: rows j = 0..N-1 of H_x (N+1 nodes) -> N cell centres
+  launch_pade64(0, view[HX], div, N, N + 1, N, N, 0, 0, N, t, 1.0 / g->h, 0, g->stream);
+  // delta_y H_y: columns i = 0..N-1 of H_y (N+1 nodes) -> N cell centres
+  launch_pade64(1, view[HY], div, N, N, N, N, 0, 0, N, t, 1.0 / g->h, 1, g->stream);
+  const size_t n = (size_t)N * N;
+  launch_dot(div, div, n, g->d_partial, reduce_blocks(n), g->d_result, 0, 0, g->stream);
+  MS_TRY(check_launch("divergence"));
+  double r;
+  MS_CUDA(cudaMemcpyAsync(&r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  *norm = std::sqrt(g->h * g->h * r);
+  return MS_OK;
+}
+
+ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double* l2_abs, double* l2_rel,
+                            double* max_abs, double* sum_abs) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (nmodes < 0 || (nmodes > 0 && !modes)) return fail(MS_EINVAL, "invalid modes");
+  for (int m = 0; m < nmodes; ++m)
+    if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
+  double* ex[3] = {g->s64[0], g->s64[1], g->s64[2]};
+  MS_TRY(exact_fields64(g, modes, nmodes, g->step * g->ht, (g->step + 0.5) * g->ht, ex));
+  double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  const double* view[3];
+  MS_TRY(state64(g, tmp, view));
+  for (int f = 0; f < 3; ++f) {
+    const size_t n = g->sh[f].size();
+    launch_err_reduce(view[f], ex[f], n, g->d_partial, reduce_blocks(n), g->d_result, f > 0, g->stream);
+  }
+  MS_TRY(check_launch("error reduce"));
+  double r[4];
+  MS_CUDA(cudaMemcpyAsync(r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  if (l2_abs) *l2_abs = std::sqrt(g->h * g->h * r[0]);
+  if (l2_rel) *l2_rel = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
+  if (max_abs) *max_abs = r[2];
+  if (sum_abs) *sum_abs = r[3];
+  return MS_OK;
+}
+
+ms_status ms_apply_op(ms_grid* g, int op, const double* const* in, double* const* out) {
+  if (!valid_grid(g) || !in || !out) return fail(MS_EINVAL, "invalid argument");
+  if (g->desc.precision != MS_FP64 || g->desc.scheme != MS_SCHEME_C4)
+    return fail(MS_EUNSUPPORTED, "operator entry points need an FP64 compact-scheme grid");
+  int nl = 0;
+  const double c1h2 = g->c1 * g->h * g->h;
+  switch (op) {
+    case MS_OP_FILTER_EZ:
+    case MS_OP_FILTER_HX:
+    case MS_OP_FILTER_HY:
+      launch_filter64(in[0], out[0], g->sh[op - MS_OP_FILTER_EZ], g->beta, g->stream);
+      break;
+    case MS_OP_CURL_HE:
+      curl_he64(g, in[0], in[1], out[0], &nl);
+      break;
+    case MS_OP_CURL_EH:
+      curl_eh64(g, in[0], out[0], out[1], &nl);
+      break;
+    case MS_OP_P1_EZ:
+    case MS_OP_P1_HX:
+    case MS_OP_P1_HY:
+      launch_p1_apply64(in[0], out[0], g->sh[op - MS_OP_P1_EZ], c1h2, 1.0 / (g->h * g->h), g->stream);
+      break;
+    case MS_OP_P1SOLVE_EZ:
+    case MS_OP_P1SOLVE_HX:
+    case MS_OP_P1SOLVE_HY:
+      p1_solve64(g, op - MS_OP_P1SOLVE_EZ, in[0], out[0], nullptr, 0.0, &nl);
+      break;
+    default:
+      return fail(MS_EINVAL, "unknown operator");
+  }
+  return check_launch("apply op");
+}
+
+}  // extern "C"

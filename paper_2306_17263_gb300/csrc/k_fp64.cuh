@@ -1,0 +1,52 @@
+// Device helpers and launcher declarations shared by the kernels of the library.
+#pragma once
+
+#include "ms_internal.h"
+
+namespace ms {
+
+// Interior test on one axis: Dirichlet axes (nodes 0..n-1 with n-1 = N) exclude both ends.
+__host__ __device__ __forceinline__ bool interior(int bc, int i, int n) {
+  return bc == NEU ? true : (i > 0 && i < n - 1);
+}
+
+// Even ghost reflection (u(-1) = u(0), u(n) = u(n-1)); a no-op for in-range indices.
+__host__ __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// Row i of a Pade table (layout of PadeTable).
+template <typename T>
+__host__ __device__ __forceinline__ const T* pade_row_ptr(const T* tab, int i, int M, int K, int B, int all_explicit) {
+  const int rs = 2 * K + 2;
+  if (all_explicit) return tab + (size_t)i * rs;
+  if (i < B) return tab + (size_t)i * rs;
+  if (i >= M - B) return tab + (size_t)(B + i - (M - B)) * rs;
+  return tab + (size_t)(2 * B) * rs;
+}
+
+void launch_filter64(const double* u, double* G, const Shape& s, double beta, cudaStream_t st);
+void launch_pade64(int axis, const double* in, double* out, int n_lines, int in_ld, int out_len, int out_ld,
+                   int out_off, int line_lo, int line_hi, const PadeTable& t, double scale, int accumulate,
+                   cudaStream_t st);
+void launch_p1_sweep64(const double* b, const double* xin, double* xout, const Shape& s, double c1h2, double omega,
+                       double bscale, int first, double* upd, double upd_scale, cudaStream_t st);
+void launch_p1_apply64(const double* x, double* out, const Shape& s, double c1h2, double out_scale, cudaStream_t st);
+void launch_yee_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
+void launch_yee_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);
+
+// Diagnostics (k_diag.cu)
+void launch_mode_field(double* out, const Shape& s, const double* tab_x, const double* tab_y, const double* coef,
+                       int nmodes, cudaStream_t st);
+// Reductions over n points: results[0..3] = sum (a-b)^2, sum b^2, max |a-b|, sum |a-b| (accumulated
+// over calls when accumulate != 0).  partial must hold 4 * blocks doubles.
+void launch_err_reduce(const double* a, const double* b, size_t n, double* partial, int blocks, double* results,
+                       int accumulate, cudaStream_t st);
+// results[slot] (+)= sum a*b
+void launch_dot(const double* a, const double* b, size_t n, double* partial, int blocks, double* results, int slot,
+                int accumulate, cudaStream_t st);
+// FP32 hi/lo <-> FP64 conversion
+void launch_split(const double* v, float* hi, float* lo, size_t n, cudaStream_t st);
+void launch_join(const float* hi, const float* lo, double* v, size_t n, cudaStream_t st);
+void launch_zero_dirichlet64(double* u, const Shape& s, cudaStream_t st);
+int reduce_blocks(size_t n);
+
+}  // namespace ms

@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads, exports every
+entry point that include/maxwell4.h declares, and validates descriptors before touching CUDA."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2306_17263_gb300 as pkg
+from closed_forms import mode_step_matrix
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "maxwell4.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ms_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    L = pkg.load()
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def _desc(**kw):
+    d = dict(dim=2, n=64, z_imp=1.0, r=0.5, precision=0, closure=0, scheme=0, stream=None)
+    d.update(kw)
+    return pkg._Desc(d["dim"], d["n"], d["z_imp"], d["r"], d["precision"], d["closure"], d["scheme"], d["stream"])
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(dim=1), -1), (dict(dim=3), -7), (dict(n=3), -1), (dict(n=40000), -1), (dict(z_imp=0.0), -1),
+    (dict(r=-0.1), -1), (dict(r=float("nan")), -1), (dict(precision=5), -1), (dict(closure=9), -1),
+    (dict(scheme=4), -1), (dict(r=0.70), -2), (dict(r=1 / math.sqrt(2)), -2),
+    (dict(scheme=1, r=0.75), -2), (dict(scheme=1, precision=1), -7),
+])
+def test_descriptor_validation(kw, status):
+    L = pkg.load()
+    h = ctypes.c_void_p()
+    d = _desc(**kw)
+    assert L.ms_create_grid(ctypes.byref(d), ctypes.byref(h)) == status
+    assert not h.value
+    assert L.ms_last_error().decode() != ""
+
+
+def test_null_arguments_rejected():
+    L = pkg.load()
+    h = ctypes.c_void_p()
+    assert L.ms_create_grid(None, ctypes.byref(h)) == -1
+    assert L.ms_step(None) == -1
+    assert L.ms_run(None, 5) == -1
+    assert L.ms_destroy(None) == 0
+
+
+def test_stability_limit_matches_mode_recurrence():
+    """The exported limit agrees with the closed-form per-mode step matrix (Sec. 4 recurrence)."""
+    rmax = pkg.stability_limit(2)
+    assert 5 / (6 * math.sqrt(2)) < rmax < 1 / math.sqrt(2)
+    N = 512
+
+    def amp(r):
+        return max(np.max(np.abs(np.linalg.eigvals(mode_step_matrix(N, r, kx, ky))))
+                   for kx in (N - 1, N - 2) for ky in (N - 1, N - 2))
+    assert amp(rmax * 0.999) < 1 + 1e-9
+    assert amp(rmax * 1.003) > 1 + 1e-6
