@@ -184,6 +184,28 @@ ms_status ms_step_profiled(ms_grid* g, int cap, float* launch_ms, int* kinds, do
 /* Name of a kernel kind reported by ms_step_profiled ("" for an unknown kind). */
 const char* ms_kernel_kind_name(int kind);
 
+/* P1 solve that allocates no device memory.  The paper has no counterpart: this is a
+ * library-usage variant of MS_OP_P1SOLVE_{EZ,HX,HY} for callers that cannot call cudaMalloc,
+ * e.g. code in a latency-critical loop where an allocation may synchronise the device, or an
+ * application (or plugin host) that owns all device memory through its own pool or a fixed
+ * budget.  It needs no grid handle.
+ *   n:      cells per side, 4 <= n <= MS_STATIC_MAX_N (MS_EINVAL otherwise, with a message);
+ *   r:      CFL number (> 0), which with n fixes P1 (Definition "def:operatorsP");
+ *   field:  0 = E_z, 1 = H_x, 2 = H_y (boundary types of Table "tab:bc");
+ *   b, x:   distinct device FP64 arrays of that field in the full staggered layout, owned by
+ *           the caller; x receives P1^{-1} b (zero on Dirichlet boundary points);
+ *   stream: cudaStream_t to issue the work on (NULL: the legacy default stream).
+ * The iteration's two scratch planes live in one file-scope __device__ array of
+ * MS_STATIC_SCRATCH_BYTES, which every GPU that loads this library keeps until the process
+ * exits.  The first call on a device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
+ * uses the same array: calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.  Nothing in the array needs clearing, since
+ * every sweep writes all points before the next reads them.  Asynchronous on `stream`. */
+#define MS_STATIC_MAX_N 512
+#define MS_STATIC_SCRATCH_BYTES (2u * (MS_STATIC_MAX_N + 1u) * (MS_STATIC_MAX_N + 1u) * 8u)
+ms_status ms_p1_solve_static(int n, double r, int field, const double* b, double* x, void* stream);
+
 /* Number of kernel launches one ms_step issues (for launch accounting). */
 ms_status ms_launches_per_step(ms_grid* g, int* launches);
 

@@ -291,6 +291,8 @@ bool valid_grid(ms_grid* g) { return g != nullptr && g->N > 0; }
 
 namespace ms {
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 void prof_mark(ms_grid* g, int kind, double bytes) {
   Prof& p = g->prof;
   if (!p.on) return;

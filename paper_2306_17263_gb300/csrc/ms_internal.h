@@ -72,6 +72,8 @@ struct ms_grid;
 namespace ms {
 // Record an event after a launch of the given kind when the grid is being profiled.
 void prof_mark(ms_grid* g, int kind, double bytes = 0.0);
+// Set the message returned by ms_last_error on this thread.
+void set_last_error(const char* msg);
 }  // namespace ms
 
 struct ms_grid {
