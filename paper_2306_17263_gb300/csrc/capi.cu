@@ -308,7 +308,7 @@ void prof_mark(ms_grid* g, int kind, double bytes) {
 
 const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64",
-                                        "filter32", "pade32", "p1sweep32"};
+                                        "filter32", "pade32", "p1sweep32", "curl32", "solve32"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }
 

@@ -1,0 +1,512 @@
+// Tiled kernels of the FP32_REFINED step: two launches per half-step.
+//
+//   k_curl_tile  : right-hand side b of one half-step on a 64 x 64 output tile.  For every
+//                  Pade line through the tile it forms the first differences of the source
+//                  state in float-float, delta_m = (hi_{m+1} - hi_m) + (lo_{m+1} - lo_m), filters
+//                  them, d = 12 beta delta + L delta (the filter of Eq. "eq:ell" commutes with the
+//                  difference: D1 (12 beta + L) u = (12 beta + L') D1 u with the ghost rules below),
+//                  and applies the band of A^{-1} (App. A.1, Eq. "eq:lhs") from shared memory with
+//                  a register window.  Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y)
+//                  on E_z; Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x).
+//   k_solve_tile : S Richardson sweeps of 6 h^2 P1 (Def. "def:operatorsP") on the tile plus an
+//                  (S-1)-cell halo in shared memory, then the float-float state update of the
+//                  paper's E += h_tau E* / H += h_tau H* with the exact two-product residual and
+//                  the split last correction (see k_mixed.cu).
+//
+// Ghost rules of the difference field along a Pade line: a source that is Neumann along the
+// line (H_y along x, H_x along y; even ghost u(-1) = u(0), Cor. "cor:ghost_cor") has zero
+// differences beyond the ends; a source that is Dirichlet along the line (E_z, zero at the
+// wall, filter zero there) has even differences (delta_{-1} = delta_0, delta_M = delta_{M-1}).
+// Across the line every source is Dirichlet with stored zeros.
+//
+// Instruction budget: both kernels are bound by issue, not by DRAM, so loops have constant
+// strides and 32-bit offsets, tiles away from the walls take block-uniform paths without any
+// boundary test, and the interior band of A^{-1} (the same Toeplitz row for every grid,
+// 24 (-rho) rho^|d| / (1 - rho^2), rho = -11 + sqrt(120)) is read from constant memory.
+#include <cmath>
+
+#include "k_fp64.cuh"
+#include "k_tiled.cuh"
+
+namespace ms {
+namespace {
+
+constexpr int TB = 64;               // output tile edge
+constexpr int KB = kTiledKFast;      // band half-width of the interior fast path
+constexpr int KMAX = kTiledKMax;     // largest band half-width of the explicit end rows
+constexpr int NT = 512;              // threads per block
+constexpr int NW = NT / 32;          // warps per block
+constexpr int SEG = 8;               // outputs per thread along a line
+constexpr int DL = TB + 2 * KMAX + 2;  // filtered differences held per line
+constexpr int DLP = DL | 1;            // odd row pitch: conflict-free across lanes
+constexpr int XL = DL + 2;             // raw differences per line (one more on each side)
+constexpr int XLP = XL | 1;
+constexpr int XROWS = TB + 2;          // lines of raw differences (one more on each side)
+constexpr int YSP = TB + 1;
+constexpr int RS = 64;                     // solve region edge (output tile + 2 x halo)
+constexpr int RSP = RS + 1;
+
+// interior row of A^{-1} at offsets -KB .. KB+1 (hi), and the lo parts of offsets -1, 0, 1
+__constant__ float c_w[2 * KB + 2];
+__constant__ float c_wl[3];
+
+struct PhaseArgs {
+  const float* hi;
+  const float* lo;
+  int snx;           // row length of the source array
+  int axis;          // 0: lines along x, 1: lines along y
+  int M;             // differences (= outputs) per line
+  int ghost_even;    // 1: source Dirichlet along the line
+  int n_across;      // source lines
+  const float* whi;  // A^{-1} band table (hi, lo), layout of PadeTable
+  const float* wlo;
+  int Kt, Bt, all_explicit;
+  float cb_hi, cb_lo;  // 12 beta
+};
+
+// One Pade phase on the tile: y(a, r) for lines c = c0 + a (a < TB) and outputs r = r0 + o
+// (o < TB), handed to out(a, o, y).  Caller synchronises before reusing dlt / dd.
+template <typename Out>
+__device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, float* dlt, float* dd, Out out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mb = r0 - KMAX - 1;  // along index of raw-difference column 0
+  // the whole strip lies inside the lines and needs no ghost: no per-element tests
+  const bool inside = (mb >= 0) && (mb + XL <= p.M) && (c0 >= 1) && (c0 + TB + 1 <= p.n_across);
+  // 1) raw differences delta on lines c0-1 .. c0+TB, along m in [mb, mb + XL)
+  if (p.axis == 0) {
+    for (int a = warp; a < XROWS; a += NW) {
+      const int c = c0 - 1 + a;
+      const bool line_ok = c >= 0 && c < p.n_across;
+      const float* hr = p.hi + (size_t)(line_ok ? c : 0) * p.snx;
+      const float* lr = p.lo + (size_t)(line_ok ? c : 0) * p.snx;
+      for (int q = lane; q < XL; q += 32) {
+        const int m = mb + q;
+        float v = 0.0f;
+        if (inside) {
+          v = (hr[m + 1] - hr[m]) + (lr[m + 1] - lr[m]);
+        } else if (line_ok) {
+          int mm = m;
+          bool zero = false;
+          if (m < 0 || m >= p.M) {
+            if (!p.ghost_even || m < -1 || m > p.M) zero = true;
+            else mm = (m < 0) ? 0 : p.M - 1;
+          }
+          if (!zero) v = (hr[mm + 1] - hr[mm]) + (lr[mm + 1] - lr[mm]);
+        }
+        dlt[a * XLP + q] = v;
+      }
+    }
+  } else {
+    for (int q = warp; q < XL; q += NW) {
+      const int m = mb + q;
+      int mm = m;
+      bool zero = false;
+      if (!inside && (m < 0 || m >= p.M)) {
+        if (!p.ghost_even || m < -1 || m > p.M) zero = true;
+        else mm = (m < 0) ? 0 : p.M - 1;
+      }
+      const size_t row0 = (size_t)(zero ? 0 : mm) * p.snx;
+      const float* h0 = p.hi + row0;
+      const float* l0 = p.lo + row0;
+      const float* h1 = h0 + p.snx;
+      const float* l1 = l0 + p.snx;
+      for (int a = lane; a < XROWS; a += 32) {
+        const int c = c0 - 1 + a;
+        float v = 0.0f;
+        if (!zero && (inside || (c >= 0 && c < p.n_across))) v = (h1[c] - h0[c]) + (l1[c] - l0[c]);
+        dlt[a * XLP + q] = v;
+      }
+    }
+  }
+  __syncthreads();
+  // 2) filtered differences d = 12 beta delta + L delta on lines c0 .. c0+TB-1, m in [mb+1, mb+1+DL)
+  for (int a = warp; a < TB; a += NW) {
+    const int c = c0 + a;
+    const bool line_ok = inside || (c >= 1 && c <= p.n_across - 2);
+    const float* r1 = dlt + (a + 1) * XLP + 1;
+    for (int q = lane; q < DL; q += 32) {
+      const int m = mb + 1 + q;
+      float v = 0.0f;
+      if (line_ok && (inside || (m >= 0 && m < p.M))) {
+        const float x = r1[q];
+        const float lap = ((r1[q - 1] - x) + (r1[q + 1] - x)) + ((r1[q - XLP] - x) + (r1[q + XLP] - x));
+        v = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
+      }
+      dd[a * DLP + q] = v;
+    }
+  }
+  __syncthreads();
+  // 3) band of A^{-1}: lane -> line, warp -> (line half, segment of SEG outputs)
+  const int a = lane + 32 * (warp & 1);
+  const int s = warp >> 1;
+  const int rf = r0 + s * SEG;  // first output of this thread
+  const float* drow = dd + a * DLP + (rf - (mb + 1));  // drow[j] = d_{rf + j}
+  float yv[SEG];
+  const bool fast = !p.all_explicit && rf >= p.Bt && rf + SEG - 1 < p.M - p.Bt;
+  // Summation order matters: the taps fall off like |rho|^|d| ~ 0.046^|d|, so a tap added after
+  // the centre tap (|w| ~ 1.1) is lost once it drops below half an ulp of the partial sum (from
+  // |d| = 6 on).  Losing the taps of one side only is a coherent, odd-symmetric error of the
+  // derivative (~1e-8, a phase error that grows with time), so the taps are summed farthest
+  // first from both sides, then the lo parts, then the centre.
+  if (fast) {
+    float dv[SEG + 2 * KB + 1];
+#pragma unroll
+    for (int q = 0; q < SEG + 2 * KB + 1; ++q) dv[q] = drow[q - KB];
+#pragma unroll
+    for (int k = 0; k < SEG; ++k) {
+      float acc = c_w[2 * KB + 1] * dv[k + 2 * KB + 1];  // offset +(KB+1)
+#pragma unroll
+      for (int dist = KB; dist >= 1; --dist) {
+        acc = fmaf(c_w[KB + dist], dv[k + KB + dist], acc);
+        acc = fmaf(c_w[KB - dist], dv[k + KB - dist], acc);
+      }
+      acc = fmaf(c_wl[0], dv[k + KB - 1], acc);
+      acc = fmaf(c_wl[2], dv[k + KB + 1], acc);
+      acc = fmaf(c_wl[1], dv[k + KB], acc);
+      yv[k] = fmaf(c_w[KB], dv[k + KB], acc);
+    }
+  } else {
+    for (int k = 0; k < SEG; ++k) {
+      const int r = rf + k;
+      float acc = 0.0f, lo = 0.0f;
+      if (r >= 0 && r < p.M) {
+        const float* wh = pade_row_ptr(p.whi, r, p.M, p.Kt, p.Bt, p.all_explicit);
+        const float* wl = pade_row_ptr(p.wlo, r, p.M, p.Kt, p.Bt, p.all_explicit);
+        for (int dist = p.Kt + 1; dist >= 1; --dist) {
+          for (int side = 1; side >= -1; side -= 2) {
+            const int m = r + side * dist, t = m - r + p.Kt;
+            if (t < 0 || t > 2 * p.Kt + 1 || m < 0 || m >= p.M) continue;
+            const float dm = drow[m - rf];
+            acc = fmaf(__ldg(wh + t), dm, acc);
+            lo = fmaf(__ldg(wl + t), dm, lo);
+          }
+        }
+        const float dc = drow[r - rf];
+        lo = fmaf(__ldg(wl + p.Kt), dc, lo);
+        acc = fmaf(__ldg(wh + p.Kt), dc, acc + lo);
+      }
+      yv[k] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < SEG; ++k) out(a, s * SEG + k, yv[k]);
+}
+
+struct CurlArgs {
+  PhaseArgs ph[2];
+  float* b0;  // Step 1: b on E_z;  Step 2: b_x on H_x
+  float* b1;  // Step 2: b_y on H_y
+  int N;
+};
+
+// STEP 0: right-hand side of Step 1 on E_z; STEP 1: right-hand sides of Step 2 on H_x, H_y.
+template <int STEP>
+__global__ void __launch_bounds__(NT, 2) k_curl_tile(CurlArgs A) {
+  extern __shared__ float sm[];
+  float* dlt = sm;
+  float* dd = dlt + XROWS * XLP;
+  float* ys = dd + TB * DLP;
+  const int N = A.N;
+  const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
+  if (STEP == 0) {
+    // x-Pade of H_y: line = row j (c0 = j0), output node i = r + 1 (r0 = i0 - 1)
+    pade_phase(A.ph[0], j0, i0 - 1, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
+    __syncthreads();
+    // y-Pade of H_x: line = column i (c0 = i0), output node j = r + 1 (r0 = j0 - 1)
+    pade_phase(A.ph[1], i0, j0 - 1, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] -= v; });
+    __syncthreads();
+    for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
+      const int j = j0 + jj;
+      if (j > N) break;
+      for (int ii = threadIdx.x & 31; ii < TB; ii += 32) {
+        const int i = i0 + ii;
+        if (i > N) break;
+        const bool in = (i >= 1 && i <= N - 1 && j >= 1 && j <= N - 1);
+        A.b0[(size_t)j * (N + 1) + i] = in ? ys[jj * YSP + ii] : 0.0f;
+      }
+    }
+  } else {
+    // y-Pade of E for H_x: line = column i (c0 = i0), output half-row jh = r (r0 = j0)
+    pade_phase(A.ph[0], i0, j0, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] = v; });
+    __syncthreads();
+    for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
+      const int jh = j0 + jj;
+      if (jh >= N) break;
+      for (int ii = threadIdx.x & 31; ii < TB; ii += 32) {
+        const int i = i0 + ii;
+        if (i > N) break;
+        A.b0[(size_t)jh * (N + 1) + i] = (i >= 1 && i <= N - 1) ? -ys[jj * YSP + ii] : 0.0f;
+      }
+    }
+    __syncthreads();
+    // x-Pade of E for H_y: line = row j (c0 = j0), output half-column ih = r (r0 = i0)
+    pade_phase(A.ph[1], j0, i0, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
+    __syncthreads();
+    for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
+      const int j = j0 + jj;
+      if (j > N) break;
+      for (int ii = threadIdx.x & 31; ii < TB; ii += 32) {
+        const int ih = i0 + ii;
+        if (ih >= N) break;
+        A.b1[(size_t)j * N + ih] = (j >= 1 && j <= N - 1) ? ys[jj * YSP + ii] : 0.0f;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+struct SolveArgs {
+  const float* b[2];
+  float* hi[2];
+  float* lo[2];
+  int nx[2], ny[2], bcx[2], bcy[2];
+  int S;
+  float d_hi, d_lo, omega, s_hi, s_lo;
+};
+
+// (hi, lo) += (S_hi + S_lo) x with error-free transformations (see k_mixed.cu).
+__device__ __forceinline__ void ff_add_scaled_t(float& hi, float& lo, float x, float s_hi, float s_lo) {
+  const float p = __fmul_rn(s_hi, x);
+  float e = fmaf(s_hi, x, -p);
+  e = fmaf(s_lo, x, e);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float l = __fadd_rn(lo, __fadd_rn(err, e));
+  const float h2 = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h2, s));
+  hi = h2;
+}
+
+// Fill the even ghosts of the Neumann axes from the edge values (only tiles at such an edge).
+__device__ __forceinline__ void fill_ghosts(float* x, int gx0, int gy0, int nx, int ny, bool neu_x, bool neu_y) {
+  if (neu_x) {
+    const int lg0 = -1 - gx0, lg1 = nx - gx0;  // local columns of the ghosts gx = -1 and gx = nx
+    for (int ly = threadIdx.x; ly < RS; ly += NT) {
+      if (lg0 >= 0 && lg0 + 1 < RS) x[ly * RSP + lg0] = x[ly * RSP + lg0 + 1];
+      if (lg1 >= 1 && lg1 < RS) x[ly * RSP + lg1] = x[ly * RSP + lg1 - 1];
+    }
+  }
+  if (neu_y) {
+    const int lg0 = -1 - gy0, lg1 = ny - gy0;
+    for (int lx = threadIdx.x; lx < RS; lx += NT) {
+      if (lg0 >= 0 && lg0 + 1 < RS) x[lg0 * RSP + lx] = x[(lg0 + 1) * RSP + lx];
+      if (lg1 >= 1 && lg1 < RS) x[lg1 * RSP + lx] = x[(lg1 - 1) * RSP + lx];
+    }
+  }
+}
+
+// Region of RS x RS points = output tile (RS - 2H)^2 plus an H-cell halo, H = S - 1.  Warp w owns
+// columns 32 (w & 1) .. +31 and row strip w >> 1 of every sweep, so no warp straddles strips.
+__global__ void __launch_bounds__(NT, 3) k_solve_tile(SolveArgs A) {
+  extern __shared__ float sm[];
+  float* bs = sm;
+  float* xa = bs + RS * RSP;
+  float* xb = xa + RS * RSP;
+  const int f = blockIdx.z;
+  const int nx = f ? A.nx[1] : A.nx[0], ny = f ? A.ny[1] : A.ny[0];
+  const int bcx = f ? A.bcx[1] : A.bcx[0], bcy = f ? A.bcy[1] : A.bcy[0];
+  float* const shi = f ? A.hi[1] : A.hi[0];
+  float* const slo = f ? A.lo[1] : A.lo[0];
+  const float* b = f ? A.b[1] : A.b[0];
+  const int H = A.S - 1;
+  const int TS = RS - 2 * H;
+  const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+  if (tx0 >= nx || ty0 >= ny) return;
+  const int gx0 = tx0 - H, gy0 = ty0 - H;
+  // interior tile: the region holds only unknowns, so no boundary tests and no ghosts
+  const bool edge = !(gx0 >= 1 && gy0 >= 1 && gx0 + RS <= nx - 1 && gy0 + RS <= ny - 1);
+  const bool neu_x = edge && bcx == NEU, neu_y = edge && bcy == NEU;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // b and the first iterate x1 = omega b (0 off the unknowns)
+  for (int ly = warp; ly < RS; ly += NW) {
+    const int gy = gy0 + ly;
+    const bool row_ok = !edge || (gy >= 0 && gy < ny && interior(bcy, gy, ny));
+    const float* brow = b + (size_t)(row_ok ? gy : 0) * nx;
+#pragma unroll
+    for (int cc = 0; cc < RS / 32; ++cc) {
+      const int lx = lane + 32 * cc;
+      const int gx = gx0 + lx;
+      float v = 0.0f;
+      if (row_ok && (!edge || (gx >= 0 && gx < nx && interior(bcx, gx, nx)))) v = brow[gx];
+      bs[ly * RSP + lx] = v;
+      xa[ly * RSP + lx] = A.omega * v;
+    }
+  }
+  __syncthreads();
+  if (neu_x || neu_y) {
+    fill_ghosts(xa, gx0, gy0, nx, ny, neu_x, neu_y);
+    __syncthreads();
+  }
+  const int c = lane + 32 * (warp & 1);
+  const int st = warp >> 1;
+  const int gx = gx0 + c;
+  const bool col_unk = !edge || (gx >= 0 && gx < nx && interior(bcx, gx, nx));
+  float* xc = xa;
+  float* xn = xb;
+  for (int k = 1; k < A.S; ++k) {
+    const bool last = (k == A.S - 1);
+    const int rps = (RS - 2 * k + NW / 2 - 1) / (NW / 2);
+    const int ly0 = k + st * rps, ly1 = min(ly0 + rps, RS - k);
+    if (c >= k && c < RS - k && ly0 < ly1) {
+      const float* xcol = xc + c;
+      // window: rows ly-1 and ly at columns c-1, c, c+1, and their x-Laplacians
+      float a0 = xcol[(ly0 - 1) * RSP];
+      float b0 = xcol[ly0 * RSP];
+      float lxa = (xcol[(ly0 - 1) * RSP - 1] - a0) + (xcol[(ly0 - 1) * RSP + 1] - a0);
+      float lxb = (xcol[ly0 * RSP - 1] - b0) + (xcol[ly0 * RSP + 1] - b0);
+      for (int ly = ly0; ly < ly1; ++ly) {
+        const float cm = xcol[(ly + 1) * RSP - 1], c0v = xcol[(ly + 1) * RSP], cp = xcol[(ly + 1) * RSP + 1];
+        const float lxc = (cm - c0v) + (cp - c0v);
+        const int gy = gy0 + ly;
+        const bool unk = col_unk && (!edge || (gy >= 0 && gy < ny && interior(bcy, gy, ny)));
+        const float x = b0;
+        const float lyv = (a0 - x) + (c0v - x);
+        const float lxly = (lxa - lxb) + (lxc - lxb);
+        const float rest = -6.0f * (lxb + lyv) - lxly;
+        const float ph = __fmul_rn(A.d_hi, x);
+        const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
+        const float res = __fsub_rn(__fsub_rn(bs[ly * RSP + c], ph), pl) - rest;
+        const float corr = A.omega * res;
+        if (last) {
+          if (unk) {
+            const size_t gp = (size_t)gy * nx + gx;
+            float h = shi[gp], l = slo[gp];
+            ff_add_scaled_t(h, l, x, A.s_hi, A.s_lo);
+            ff_add_scaled_t(h, l, corr, A.s_hi, A.s_lo);
+            shi[gp] = h;
+            slo[gp] = l;
+          }
+        } else {
+          xn[ly * RSP + c] = unk ? x + corr : 0.0f;
+        }
+        a0 = b0;
+        lxa = lxb;
+        b0 = c0v;
+        lxb = lxc;
+      }
+    }
+    __syncthreads();
+    if (!last && (neu_x || neu_y)) {
+      fill_ghosts(xn, gx0, gy0, nx, ny, neu_x, neu_y);
+      __syncthreads();
+    }
+    float* t = xc;
+    xc = xn;
+    xn = t;
+  }
+  if (A.S == 1) {  // the first iterate is also the last: x = 0, correction omega b
+    for (int ly = warp; ly < RS; ly += NW) {
+      const int gy = ty0 + ly;
+#pragma unroll
+      for (int cc = 0; cc < RS / 32; ++cc) {
+        const int lx = lane + 32 * cc;
+        const int gx2 = tx0 + lx;
+        if (gx2 < nx && gy < ny && interior(bcx, gx2, nx) && interior(bcy, gy, ny)) {
+          const size_t gp = (size_t)gy * nx + gx2;
+          float h = shi[gp], l = slo[gp];
+          ff_add_scaled_t(h, l, xa[ly * RSP + lx], A.s_hi, A.s_lo);
+          shi[gp] = h;
+          slo[gp] = l;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Host side
+
+static PhaseArgs phase(const ms_grid* g, int src, int axis, int kind, float cb_hi, float cb_lo) {
+  const Shape& s = g->sh[src];
+  const PadeTable& t = g->pade32[kind];
+  PhaseArgs p;
+  p.hi = g->hi[src];
+  p.lo = g->lo[src];
+  p.snx = s.nx;
+  p.axis = axis;
+  p.M = t.M;
+  p.ghost_even = (axis == 0 ? s.bcx : s.bcy) == DIR;
+  p.n_across = axis == 0 ? s.ny : s.nx;
+  p.whi = t.d_whi;
+  p.wlo = t.d_wlo;
+  p.Kt = t.K;
+  p.Bt = t.B;
+  p.all_explicit = t.all_explicit;
+  p.cb_hi = cb_hi;
+  p.cb_lo = cb_lo;
+  return p;
+}
+
+size_t tiled_curl_smem() { return sizeof(float) * (size_t)(XROWS * XLP + TB * DLP + TB * YSP); }
+size_t tiled_solve_smem() { return sizeof(float) * (size_t)(3 * RS * RSP); }
+
+int tiled_configure() {
+  if (cudaFuncSetAttribute(k_curl_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_curl_smem()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_curl_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_curl_smem()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_solve_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_solve_smem()) !=
+          cudaSuccess)
+    return -1;
+  // interior Toeplitz row of A^{-1}: 24 (-rho) rho^|d| / (1 - rho^2) (rho < 0), split hi + lo
+  const long double rho = -11.0L + std::sqrt(120.0L);
+  float w[2 * KB + 2], wl[3];
+  for (int t = 0; t < 2 * KB + 2; ++t) {
+    const int d = t - KB;
+    long double v = 24.0L * (-rho) / (1.0L - rho * rho);
+    for (int k = 0; k < (d < 0 ? -d : d); ++k) v *= rho;
+    w[t] = (float)v;
+    if (d >= -1 && d <= 1) wl[d + 1] = (float)(v - (long double)w[t]);
+  }
+  if (cudaMemcpyToSymbol(c_w, w, sizeof w) != cudaSuccess || cudaMemcpyToSymbol(c_wl, wl, sizeof wl) != cudaSuccess)
+    return -1;
+  return 0;
+}
+
+void tiled_curl(ms_grid* g, int step, float cb_hi, float cb_lo, float* b0, float* b1) {
+  CurlArgs A;
+  A.N = g->N;
+  A.b0 = b0;
+  A.b1 = b1;
+  if (step == 0) {
+    A.ph[0] = phase(g, HY, 0, HALF_TO_NODE, cb_hi, cb_lo);
+    A.ph[1] = phase(g, HX, 1, HALF_TO_NODE, cb_hi, cb_lo);
+  } else {
+    A.ph[0] = phase(g, EZ, 1, NODE_TO_HALF, cb_hi, cb_lo);
+    A.ph[1] = phase(g, EZ, 0, NODE_TO_HALF, cb_hi, cb_lo);
+  }
+  const int nt = (g->N + 1 + TB - 1) / TB;
+  dim3 grid(nt, nt);
+  if (step == 0) k_curl_tile<0><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
+  else k_curl_tile<1><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
+}
+
+void tiled_solve(ms_grid* g, int nfields, const int* fields, const float* const* b, int S, float d_hi, float d_lo,
+                 float omega, float s_hi, float s_lo) {
+  SolveArgs A;
+  for (int k = 0; k < nfields; ++k) {
+    const Shape& s = g->sh[fields[k]];
+    A.b[k] = b[k];
+    A.hi[k] = g->hi[fields[k]];
+    A.lo[k] = g->lo[fields[k]];
+    A.nx[k] = s.nx;
+    A.ny[k] = s.ny;
+    A.bcx[k] = s.bcx;
+    A.bcy[k] = s.bcy;
+  }
+  A.S = S;
+  A.d_hi = d_hi;
+  A.d_lo = d_lo;
+  A.omega = omega;
+  A.s_hi = s_hi;
+  A.s_lo = s_lo;
+  const int TS = RS - 2 * (S - 1);
+  const int nt = (g->N + 1 + TS - 1) / TS;
+  dim3 grid(nt, nt, nfields);
+  k_solve_tile<<<grid, NT, tiled_solve_smem(), g->stream>>>(A);
+}
+
+}  // namespace ms

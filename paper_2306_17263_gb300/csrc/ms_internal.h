@@ -52,7 +52,7 @@ struct Graph {
 // Kernel kinds reported by ms_step_profiled.
 enum KernelKind {
   KK_FILTER64 = 0, KK_PADE64 = 1, KK_P1SWEEP64 = 2, KK_YEE64 = 3,
-  KK_FILTER32 = 4, KK_PADE32 = 5, KK_P1SWEEP32 = 6,
+  KK_FILTER32 = 4, KK_PADE32 = 5, KK_P1SWEEP32 = 6, KK_CURL32 = 7, KK_SOLVE32 = 8,
   KK_COUNT
 };
 const char* kernel_kind_name(int k);
