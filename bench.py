@@ -190,6 +190,56 @@ def run_reference(args, ws, rank):
 
 
 # ---------------------------------------------------------------------------------------
+def batched_leg(pkg, torch, steps: int = 64):
+    """512 cavities of sides 64..768 (4 seeded modes each) advanced by one launch per kernel;
+    the state (2.7 GB) is far larger than L2, so no flush is needed between steps."""
+    c = workloads.config4()
+    with pkg.Batch(c["sizes"], c["r"], stream="torch") as b:
+        count, cells, launches = b.info()
+        for k in range(count):
+            b.init_modes(k, c["modes"][k])
+        b.run(16)  # warm-up (also captures the graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        err = b.error_vs_exact(count - 1, c["modes"][count - 1])
+    return {"workload": "512 cavities, sides uniform in {64,96,...,768} (seed 0), 4 modes each, r=0.5, FP32_REFINED",
+            "cells_per_step": cells, "launches_per_step": launches, "steps": steps, "ms_per_step": ms,
+            "value": cells / (ms * 1e-3), "unit": "cell-updates/s",
+            "l2_rel_last_cavity": err[1]}
+
+
+def yee_leg(pkg, torch, modes, r, c4_l2_abs, c4_value, T=4000 * 0.5 / 2048):
+    """Plain second-order Yee (FP64) on the same modes and end time: its L2 error at three
+    resolutions, the fitted order, and the resolution and time-to-solution it would need to
+    reach the compact scheme's error (extrapolated from the measured error and rate)."""
+    errs, rates = [], []
+    for n in (512, 1024, 2048):
+        steps = int(round(T * n / r))
+        with pkg.Grid(n, r, scheme=pkg.SCHEME_YEE2, stream="torch") as g:
+            g.init_modes(modes)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.run(steps)
+            e1.record()
+            torch.cuda.synchronize()
+            rates.append(n * n * steps / (e0.elapsed_time(e1) * 1e-3))
+            errs.append(g.error_vs_exact(modes)[0])
+    order = math.log2(errs[1] / errs[2])
+    n_eq = 2048 * (errs[2] / c4_l2_abs) ** (1.0 / max(order, 1e-3))
+    # cost of a run to time T: n^2 cells x (T n / r) steps at the measured 2048^2 rate
+    t_yee = n_eq ** 3 * T / r / rates[2]
+    t_c4 = 2048 ** 3 * T / r / c4_value
+    return {"t": T, "l2_abs": dict(zip(("512", "1024", "2048"), errs)), "order": order,
+            "value_2048": rates[2], "unit": "cell-updates/s", "c4_l2_abs_2048": c4_l2_abs,
+            "n_for_equal_error": n_eq, "time_to_solution_s": {"yee_extrapolated": t_yee, "c4_measured": t_c4}}
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -325,6 +375,8 @@ def run_ours(args, ws, rank, local):
             line["fp64_gpu"] = {"value": N * N / (t64 / k64 * 1e-3), "unit": "cell-updates/s", "steps": k64,
                                 "ms_per_step": t64 / k64}
             g64.close()
+        line["batched"] = batched_leg(pkg, torch)
+        line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, l2_abs, value)
         # CPU oracle on a bounded sample of the workload (rank 0, one core)
         v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
         line["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",

@@ -209,6 +209,27 @@ ms_status ms_p1_solve_static(int n, double r, int field, const double* b, double
 /* Number of kernel launches one ms_step issues (for launch accounting). */
 ms_status ms_launches_per_step(ms_grid* g, int* launches);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches: many independent 2D cavities of uneven sizes advanced together.  Each cavity is the
+ * problem of ms_create_grid with n = n[b] cells per side; all share the rest of the descriptor
+ * (z_imp, r, precision, closure, scheme, stream).  Every kernel of a step is one launch for the
+ * whole batch (its blocks walk a list of (cavity, tile) entries), and ms_batch_run replays a
+ * captured CUDA graph.  Requires MS_FP32_REFINED and MS_SCHEME_C4 (MS_EUNSUPPORTED otherwise).
+ * Cavity indices are 0 .. count-1; the per-cavity calls behave like their ms_* counterparts. */
+typedef struct ms_batch ms_batch;
+ms_status ms_create_batch(const ms_grid_desc* desc, const int* n, int count, ms_batch** out);
+ms_status ms_batch_destroy(ms_batch* b);
+ms_status ms_batch_init_modes(ms_batch* b, int cavity, const ms_mode* modes, int nmodes);
+ms_status ms_batch_set_fields(ms_batch* b, int cavity, const double* const* comps, long step);
+ms_status ms_batch_get_fields(ms_batch* b, int cavity, double* const* comps);
+ms_status ms_batch_step(ms_batch* b);
+ms_status ms_batch_run(ms_batch* b, long nsteps);
+ms_status ms_batch_sync(ms_batch* b);
+ms_status ms_batch_error_vs_exact(ms_batch* b, int cavity, const ms_mode* modes, int nmodes, double* l2_abs,
+                                  double* l2_rel, double* max_abs, double* sum_abs);
+/* count: cavities; cells: sum of n[b]^2 (Yee cells advanced per step); launches: kernels per step. */
+ms_status ms_batch_info(ms_batch* b, int* count, long long* cells, int* launches);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* ms_last_error(void);
 

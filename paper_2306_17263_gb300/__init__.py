@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Grid", "MaxwellError", "load", "lib_path", "FP64", "FP32_REFINED", "CLOSURE_PAPER", "CLOSURE_REFLECT",
+__all__ = ["Grid", "Batch", "MaxwellError", "load", "lib_path", "FP64", "FP32_REFINED", "CLOSURE_PAPER", "CLOSURE_REFLECT",
            "SCHEME_C4", "SCHEME_YEE2", "OPS", "stability_limit"]
 
 FP64, FP32_REFINED = 0, 1
@@ -83,6 +83,16 @@ def load() -> ctypes.CDLL:
             "ms_apply_op": [V, I, PPD, PPD],
             "ms_launches_per_step": [V, ctypes.POINTER(I)],
             "ms_stability_limit": [I, PD],
+            "ms_create_batch": [ctypes.POINTER(_Desc), ctypes.POINTER(I), I, ctypes.POINTER(V)],
+            "ms_batch_destroy": [V],
+            "ms_batch_init_modes": [V, I, ctypes.POINTER(_Mode), I],
+            "ms_batch_set_fields": [V, I, PPD, L_],
+            "ms_batch_get_fields": [V, I, PPD],
+            "ms_batch_step": [V],
+            "ms_batch_run": [V, L_],
+            "ms_batch_sync": [V],
+            "ms_batch_error_vs_exact": [V, I, ctypes.POINTER(_Mode), I, PD, PD, PD, PD],
+            "ms_batch_info": [V, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I)],
             "ms_step_profiled": [V, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), PD, ctypes.POINTER(I)],
         }
         for name, args in sig.items():
@@ -247,3 +257,82 @@ class Grid:
         """Operator entry point on CUDA float64 tensors (see maxwell4.h, ms_apply_op)."""
         _check(load().ms_apply_op(self._h, OPS[op], _ptrs([t.data_ptr() for t in ins]),
                                   _ptrs([t.data_ptr() for t in outs])))
+
+
+class Batch:
+    """Many independent 2D TM_z cavities of uneven sizes advanced together (FP32_REFINED).
+
+    sizes: cells per side of each cavity; the other arguments are shared, as in Grid.
+    """
+
+    def __init__(self, sizes, r: float, z: float = 1.0, closure: int = CLOSURE_PAPER, stream=None):
+        L = load()
+        if stream == "torch":
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        sizes = [int(n) for n in sizes]
+        arr = (ctypes.c_int * len(sizes))(*sizes)
+        d = _Desc(2, 0, float(z), float(r), FP32_REFINED, int(closure), SCHEME_C4,
+                  ctypes.c_void_p(int(stream)) if stream else None)
+        h = ctypes.c_void_p()
+        _check(L.ms_create_batch(ctypes.byref(d), arr, len(sizes), ctypes.byref(h)))
+        self._h = h
+        self.sizes, self.r, self.z, self.closure = sizes, float(r), float(z), int(closure)
+
+    def shapes(self, cavity: int):
+        N = self.sizes[cavity]
+        return (N + 1, N + 1), (N, N + 1), (N + 1, N)
+
+    def close(self):
+        if self._h:
+            load().ms_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init_modes(self, cavity: int, modes):
+        arr, nm = _modes(modes)
+        _check(load().ms_batch_init_modes(self._h, int(cavity), arr, nm))
+
+    def set_fields(self, cavity: int, ez, hx, hy, step: int = 0):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ez, hx, hy)]
+        for a, s in zip(arrs, self.shapes(cavity)):
+            if a.shape != s:
+                raise ValueError(f"expected shape {s}, got {a.shape}")
+        _check(load().ms_batch_set_fields(self._h, int(cavity), _ptrs([a.ctypes.data for a in arrs]), int(step)))
+
+    def get_fields(self, cavity: int):
+        out = [np.zeros(s) for s in self.shapes(cavity)]
+        _check(load().ms_batch_get_fields(self._h, int(cavity), _ptrs([a.ctypes.data for a in out])))
+        return tuple(out)
+
+    def step(self):
+        _check(load().ms_batch_step(self._h))
+
+    def run(self, nsteps: int):
+        _check(load().ms_batch_run(self._h, int(nsteps)))
+
+    def sync(self):
+        _check(load().ms_batch_sync(self._h))
+
+    def error_vs_exact(self, cavity: int, modes):
+        arr, nm = _modes(modes)
+        out = [ctypes.c_double() for _ in range(4)]
+        _check(load().ms_batch_error_vs_exact(self._h, int(cavity), arr, nm, *[ctypes.byref(v) for v in out]))
+        return tuple(v.value for v in out)
+
+    def info(self):
+        """(cavities, cells advanced per step, kernel launches per step)."""
+        c, cells, nl = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        _check(load().ms_batch_info(self._h, ctypes.byref(c), ctypes.byref(cells), ctypes.byref(nl)))
+        return c.value, cells.value, nl.value

@@ -8,6 +8,7 @@
 
 #include "k_fp64.cuh"
 #include "k_mixed.cuh"
+#include "k_tiled.cuh"
 
 using namespace ms;
 
@@ -326,8 +327,16 @@ ms_status ms_stability_limit(int dim, double* rmax) {
   return MS_OK;
 }
 
+// shared64 != nullptr: the grid uses these six FP64 diagnostic planes (at least (n+1)^2 each,
+// owned by a batch) instead of allocating its own.
+static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64, ms_grid** out);
+
 ms_status ms_create_grid(const ms_grid_desc* d, ms_grid** out) {
   g_last_error.clear();
+  return create_grid_impl(d, nullptr, out);
+}
+
+static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64, ms_grid** out) {
   if (!out) return fail(MS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!d) return fail(MS_EINVAL, "desc is NULL");
@@ -395,7 +404,12 @@ ms_status ms_create_grid(const ms_grid_desc* d, ms_grid** out) {
   const size_t nmax = (size_t)(g->N + 1) * (g->N + 1);
   ms_status s = MS_OK;
   // FP64 scratch is used by the FP64 step and by the diagnostics of both precisions
-  for (int k = 0; k < 6 && s == MS_OK; ++k) s = dalloc(&g->s64[k], nmax);
+  if (shared64) {
+    for (int k = 0; k < 6; ++k) g->s64[k] = shared64[k];
+    g->shared64 = true;
+  } else {
+    for (int k = 0; k < 6 && s == MS_OK; ++k) s = dalloc(&g->s64[k], nmax);
+  }
   if (d->precision == MS_FP64) {
     for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->f64[f], g->sh[f].size());
   } else {
@@ -414,7 +428,7 @@ ms_status ms_create_grid(const ms_grid_desc* d, ms_grid** out) {
     if (g->hi[f]) cudaMemsetAsync(g->hi[f], 0, g->sh[f].size() * sizeof(float), g->stream);
     if (g->lo[f]) cudaMemsetAsync(g->lo[f], 0, g->sh[f].size() * sizeof(float), g->stream);
   }
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 6 && !g->shared64; ++k)
     if (g->s64[k]) cudaMemsetAsync(g->s64[k], 0, nmax * sizeof(double), g->stream);
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cleanup(fail(MS_ECUDA, std::string("create: ") + cudaGetErrorString(e)));
@@ -438,7 +452,7 @@ ms_status ms_destroy(ms_grid* g) {
     cudaFree(g->hi[f]);
     cudaFree(g->lo[f]);
   }
-  for (int k = 0; k < 6; ++k) cudaFree(g->s64[k]);
+  for (int k = 0; k < 6 && !g->shared64; ++k) cudaFree(g->s64[k]);
   for (int k = 0; k < 8; ++k) cudaFree(g->s32[k]);
   mixed_teardown(g);
   cudaFree(g->d_partial);
@@ -720,6 +734,190 @@ ms_status ms_apply_op(ms_grid* g, int op, const double* const* in, double* const
       return fail(MS_EINVAL, "unknown operator");
   }
   return check_launch("apply op");
+}
+
+}  // extern "C"
+
+// =======================================================================================
+// Batches of cavities
+
+struct ms_batch {
+  ms_grid_desc desc{};
+  std::vector<ms_grid*> cav;
+  double* s64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  ms::TiledBatch tb;
+  ms::Graph graph1, graphk;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  long long cells = 0;
+};
+
+namespace {
+
+bool valid_batch(ms_batch* b) { return b != nullptr && !b->cav.empty(); }
+
+ms_status batch_cavity(ms_batch* b, int cavity, ms_grid** g) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  if (cavity < 0 || cavity >= (int)b->cav.size()) return fail(MS_EINVAL, "cavity index out of range");
+  *g = b->cav[cavity];
+  return MS_OK;
+}
+
+ms_status batch_step_launch(ms_batch* b) {
+  tiled_batch_step(b->tb, b->stream);
+  return check_launch("batch step");
+}
+
+ms_status batch_capture(ms_batch* b, Graph* gr, int steps) {
+  if (gr->exec) return MS_OK;
+  MS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  ms_status st = MS_OK;
+  for (int k = 0; k < steps && st == MS_OK; ++k) st = batch_step_launch(b);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  if (st != MS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(MS_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&gr->exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(MS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  gr->graph = graph;
+  gr->steps = steps;
+  return MS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ms_status ms_batch_destroy(ms_batch* b) {
+  if (!b) return MS_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  free_graph(&b->graph1);
+  free_graph(&b->graphk);
+  tiled_batch_free(&b->tb);
+  for (ms_grid* g : b->cav) ms_destroy(g);
+  for (int k = 0; k < 6; ++k) cudaFree(b->s64[k]);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return MS_OK;
+}
+
+ms_status ms_create_batch(const ms_grid_desc* d, const int* n, int count, ms_batch** out) {
+  g_last_error.clear();
+  if (!out) return fail(MS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d || !n) return fail(MS_EINVAL, "desc or n is NULL");
+  if (count < 1 || count > (1 << 20)) return fail(MS_EINVAL, "count must be in [1, 2^20]");
+  if (d->precision != MS_FP32_REFINED || d->scheme != MS_SCHEME_C4)
+    return fail(MS_EUNSUPPORTED, "batches run the compact scheme in MS_FP32_REFINED");
+  int nmax = 0;
+  for (int c = 0; c < count; ++c) {
+    if (n[c] < 4 || n[c] > 32768) return fail(MS_EINVAL, "every n[b] must be in [4, 32768]");
+    nmax = n[c] > nmax ? n[c] : nmax;
+  }
+  ms_batch* b = new ms_batch();
+  b->desc = *d;
+  auto cleanup = [&](ms_status s) {
+    ms_batch_destroy(b);
+    return s;
+  };
+  if (d->stream) {
+    b->stream = (cudaStream_t)d->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(MS_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    b->own_stream = true;
+  }
+  const size_t plane = (size_t)(nmax + 1) * (nmax + 1);
+  for (int k = 0; k < 6; ++k) {
+    ms_status s = dalloc(&b->s64[k], plane);
+    if (s != MS_OK) return cleanup(s);
+  }
+  b->cav.reserve(count);
+  for (int c = 0; c < count; ++c) {
+    ms_grid_desc dc = *d;
+    dc.n = n[c];
+    dc.stream = b->stream;
+    ms_grid* g = nullptr;
+    ms_status s = create_grid_impl(&dc, b->s64, &g);
+    if (s != MS_OK) return cleanup(s);
+    b->cav.push_back(g);
+    b->cells += (long long)n[c] * n[c];
+  }
+  std::string err;
+  if (tiled_batch_build(b->cav.data(), count, &b->tb, &err) != 0) return cleanup(fail(MS_ENOMEM, err));
+  *out = b;
+  return MS_OK;
+}
+
+ms_status ms_batch_init_modes(ms_batch* b, int cavity, const ms_mode* modes, int nmodes) {
+  ms_grid* g;
+  MS_TRY(batch_cavity(b, cavity, &g));
+  return ms_init_modes(g, modes, nmodes);
+}
+
+ms_status ms_batch_set_fields(ms_batch* b, int cavity, const double* const* comps, long step) {
+  ms_grid* g;
+  MS_TRY(batch_cavity(b, cavity, &g));
+  return ms_set_fields(g, comps, step);
+}
+
+ms_status ms_batch_get_fields(ms_batch* b, int cavity, double* const* comps) {
+  ms_grid* g;
+  MS_TRY(batch_cavity(b, cavity, &g));
+  return ms_get_fields(g, comps);
+}
+
+ms_status ms_batch_error_vs_exact(ms_batch* b, int cavity, const ms_mode* modes, int nmodes, double* l2_abs,
+                                  double* l2_rel, double* max_abs, double* sum_abs) {
+  ms_grid* g;
+  MS_TRY(batch_cavity(b, cavity, &g));
+  return ms_error_vs_exact(g, modes, nmodes, l2_abs, l2_rel, max_abs, sum_abs);
+}
+
+ms_status ms_batch_step(ms_batch* b) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  MS_TRY(batch_step_launch(b));
+  for (ms_grid* g : b->cav) g->step += 1;
+  return MS_OK;
+}
+
+ms_status ms_batch_run(ms_batch* b, long nsteps) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  if (nsteps < 0) return fail(MS_EINVAL, "nsteps must be >= 0");
+  const int chunk = 16;
+  if (nsteps >= chunk) MS_TRY(batch_capture(b, &b->graphk, chunk));
+  if (nsteps % chunk) MS_TRY(batch_capture(b, &b->graph1, 1));
+  long left = nsteps;
+  while (left >= chunk) {
+    MS_CUDA(cudaGraphLaunch(b->graphk.exec, b->stream));
+    left -= chunk;
+  }
+  while (left > 0) {
+    MS_CUDA(cudaGraphLaunch(b->graph1.exec, b->stream));
+    left -= 1;
+  }
+  for (ms_grid* g : b->cav) g->step += nsteps;
+  return MS_OK;
+}
+
+ms_status ms_batch_sync(ms_batch* b) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  MS_CUDA(cudaStreamSynchronize(b->stream));
+  return MS_OK;
+}
+
+ms_status ms_batch_info(ms_batch* b, int* count, long long* cells, int* launches) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  if (count) *count = (int)b->cav.size();
+  if (cells) *cells = b->cells;
+  if (launches) *launches = 4;
+  return MS_OK;
 }
 
 }  // extern "C"

@@ -47,32 +47,46 @@ Split split(double v) {
 
 const char* mixed_last_error() { return g_mixed_err.c_str(); }
 
-ms_status step_mixed(ms_grid* g, int* nl) {
-  const double N1 = g->N + 1.0, Nd = g->N;
-  const double ne = N1 * N1, nh = Nd * N1;  // points of E_z and of each H component
+MixedConsts mixed_consts(const ms_grid* g) {
   const double c1h2 = g->c1 * g->h * g->h;
   const Split cb = split(12.0 * g->beta);
   const Split d = split(6.0 * c1h2);
-  const float omega = (float)(2.0 / (12.0 * c1h2 + 32.0));
   const Split sE = split(12.0 * g->Z / g->desc.r);
   const Split sH = split(12.0 / (g->desc.r * g->Z));
-  const int S = g->p1_sweeps32;
+  MixedConsts k;
+  k.cb_hi = cb.hi;
+  k.cb_lo = cb.lo;
+  k.d_hi = d.hi;
+  k.d_lo = d.lo;
+  k.omega = (float)(2.0 / (12.0 * c1h2 + 32.0));
+  k.sE_hi = sE.hi;
+  k.sE_lo = sE.lo;
+  k.sH_hi = sH.hi;
+  k.sH_lo = sH.lo;
+  k.S = g->p1_sweeps32;
+  return k;
+}
+
+ms_status step_mixed(ms_grid* g, int* nl) {
+  const double N1 = g->N + 1.0, Nd = g->N;
+  const double ne = N1 * N1, nh = Nd * N1;  // points of E_z and of each H component
+  const MixedConsts k = mixed_consts(g);
   // Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y) on E_z, then the E solve
   float* bE = g->s32[4];
-  tiled_curl(g, 0, cb.hi, cb.lo, bE, nullptr);
+  tiled_curl(g, 0, k.cb_hi, k.cb_lo, bE, nullptr);
   prof_mark(g, KK_CURL32, 4.0 * (4.0 * nh + ne));            // H_x, H_y (hi, lo) in; b out
   const int fe[1] = {EZ};
   const float* be[1] = {bE};
-  tiled_solve(g, 1, fe, be, S, d.hi, d.lo, omega, sE.hi, sE.lo);
+  tiled_solve(g, 1, fe, be, k.S, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo);
   prof_mark(g, KK_SOLVE32, 4.0 * (ne + 4.0 * ne));           // b in; E (hi, lo) read and written
   // Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x), then both H solves
   float* bx = g->s32[2];
   float* by = g->s32[3];
-  tiled_curl(g, 1, cb.hi, cb.lo, bx, by);
+  tiled_curl(g, 1, k.cb_hi, k.cb_lo, bx, by);
   prof_mark(g, KK_CURL32, 4.0 * (2.0 * ne + 2.0 * nh));      // E (hi, lo) in; b_x, b_y out
   const int fh[2] = {HX, HY};
   const float* bh[2] = {bx, by};
-  tiled_solve(g, 2, fh, bh, S, d.hi, d.lo, omega, sH.hi, sH.lo);
+  tiled_solve(g, 2, fh, bh, k.S, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo);
   prof_mark(g, KK_SOLVE32, 4.0 * (2.0 * nh + 8.0 * nh));     // b_x, b_y in; H (hi, lo) read and written
   *nl += 4;
   return MS_OK;
@@ -87,7 +101,8 @@ ms_status mixed_setup(ms_grid* g) {
       g_mixed_err = err;
       return MS_EINVAL;
     }
-    if (t.K > kTiledKMax || t.K < kTiledKFast) {
+    // the interior fast path needs K >= kTiledKFast; short lines store every row explicitly
+    if (t.K > kTiledKMax || (t.K < kTiledKFast && !t.all_explicit)) {
       g_mixed_err = "FP32 Pade band half-width outside the range the tile kernels hold";
       return MS_EUNSUPPORTED;
     }
@@ -121,8 +136,9 @@ ms_status mixed_setup(ms_grid* g) {
     g_mixed_err = "cannot configure shared memory of the tile kernels";
     return MS_ECUDA;
   }
+  // right-hand-side planes of the tile kernels: s32[4] (E_z), s32[2] (H_x), s32[3] (H_y)
   const size_t nmax = (size_t)(g->N + 1) * (g->N + 1);
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 2; k < 5; ++k) {
     if (cudaMalloc(&g->s32[k], nmax * sizeof(float) + 256) != cudaSuccess) {
       g_mixed_err = "cudaMalloc of FP32 scratch failed";
       return MS_ENOMEM;

@@ -24,6 +24,8 @@
 // boundary test, and the interior band of A^{-1} (the same Toeplitz row for every grid,
 // 24 (-rho) rho^|d| / (1 - rho^2), rho = -11 + sqrt(120)) is read from constant memory.
 #include <cmath>
+#include <string>
+#include <vector>
 
 #include "k_fp64.cuh"
 #include "k_tiled.cuh"
@@ -192,22 +194,27 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
   for (int k = 0; k < SEG; ++k) out(a, s * SEG + k, yv[k]);
 }
 
+}  // namespace
+
 struct CurlArgs {
   PhaseArgs ph[2];
   float* b0;  // Step 1: b on E_z;  Step 2: b_x on H_x
   float* b1;  // Step 2: b_y on H_y
   int N;
+  int ntiles;  // tiles per row of the cavity (batched launches)
 };
 
-// STEP 0: right-hand side of Step 1 on E_z; STEP 1: right-hand sides of Step 2 on H_x, H_y.
+namespace {
+
+// STEP 0: right-hand side of Step 1 on E_z; STEP 1: right-hand sides of Step 2 on H_x, H_y;
+// the tile with origin (i0, j0).
 template <int STEP>
-__global__ void __launch_bounds__(NT, 2) k_curl_tile(CurlArgs A) {
+__device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
   extern __shared__ float sm[];
   float* dlt = sm;
   float* dd = dlt + XROWS * XLP;
   float* ys = dd + TB * DLP;
   const int N = A.N;
-  const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
   if (STEP == 0) {
     // x-Pade of H_y: line = row j (c0 = j0), output node i = r + 1 (r0 = i0 - 1)
     pade_phase(A.ph[0], j0, i0 - 1, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
@@ -254,6 +261,33 @@ __global__ void __launch_bounds__(NT, 2) k_curl_tile(CurlArgs A) {
   }
 }
 
+template <int STEP>
+__global__ void __launch_bounds__(NT, 2) k_curl_tile(CurlArgs A) {
+  curl_body<STEP>(A, blockIdx.x * TB, blockIdx.y * TB);
+}
+
+// Words of a small argument struct copied from global to shared memory by the first warp.
+template <typename T>
+__device__ __forceinline__ void copy_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "argument structs are made of 4-byte words");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(T) / 4); k += NT) d[k] = s[k];
+  __syncthreads();
+}
+
+// Batched form: block b processes tile work[2b+1] of cavity work[2b].
+template <int STEP>
+__global__ void __launch_bounds__(NT, 2) k_curl_batch(const CurlArgs* __restrict__ args, const int* __restrict__ work) {
+  __shared__ CurlArgs sA;
+  const int cav = work[2 * blockIdx.x], t = work[2 * blockIdx.x + 1];
+  copy_args(&sA, args + cav);
+  const int nt = sA.ntiles;
+  curl_body<STEP>(sA, (t % nt) * TB, (t / nt) * TB);
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------------------
 struct SolveArgs {
   const float* b[2];
@@ -262,7 +296,10 @@ struct SolveArgs {
   int nx[2], ny[2], bcx[2], bcy[2];
   int S;
   float d_hi, d_lo, omega, s_hi, s_lo;
+  int ntiles;  // tiles per row of the cavity (batched launches)
 };
+
+namespace {
 
 // (hi, lo) += (S_hi + S_lo) x with error-free transformations (see k_mixed.cu).
 __device__ __forceinline__ void ff_add_scaled_t(float& hi, float& lo, float x, float s_hi, float s_lo) {
@@ -298,12 +335,11 @@ __device__ __forceinline__ void fill_ghosts(float* x, int gx0, int gy0, int nx, 
 
 // Region of RS x RS points = output tile (RS - 2H)^2 plus an H-cell halo, H = S - 1.  Warp w owns
 // columns 32 (w & 1) .. +31 and row strip w >> 1 of every sweep, so no warp straddles strips.
-__global__ void __launch_bounds__(NT, 3) k_solve_tile(SolveArgs A) {
+__device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, int tby) {
   extern __shared__ float sm[];
   float* bs = sm;
   float* xa = bs + RS * RSP;
   float* xb = xa + RS * RSP;
-  const int f = blockIdx.z;
   const int nx = f ? A.nx[1] : A.nx[0], ny = f ? A.ny[1] : A.ny[0];
   const int bcx = f ? A.bcx[1] : A.bcx[0], bcy = f ? A.bcy[1] : A.bcy[0];
   float* const shi = f ? A.hi[1] : A.hi[0];
@@ -311,7 +347,7 @@ __global__ void __launch_bounds__(NT, 3) k_solve_tile(SolveArgs A) {
   const float* b = f ? A.b[1] : A.b[0];
   const int H = A.S - 1;
   const int TS = RS - 2 * H;
-  const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+  const int tx0 = tbx * TS, ty0 = tby * TS;
   if (tx0 >= nx || ty0 >= ny) return;
   const int gx0 = tx0 - H, gy0 = ty0 - H;
   // interior tile: the region holds only unknowns, so no boundary tests and no ghosts
@@ -414,6 +450,17 @@ __global__ void __launch_bounds__(NT, 3) k_solve_tile(SolveArgs A) {
   }
 }
 
+__global__ void __launch_bounds__(NT, 3) k_solve_tile(SolveArgs A) { solve_body(A, blockIdx.z, blockIdx.x, blockIdx.y); }
+
+// Batched form: block b solves tile work[3b+2] of field slot work[3b+1] of cavity work[3b].
+__global__ void __launch_bounds__(NT, 3) k_solve_batch(const SolveArgs* __restrict__ args, const int* __restrict__ work) {
+  __shared__ SolveArgs sA;
+  const int cav = work[3 * blockIdx.x], f = work[3 * blockIdx.x + 1], t = work[3 * blockIdx.x + 2];
+  copy_args(&sA, args + cav);
+  const int nt = sA.ntiles;
+  solve_body(sA, f, t % nt, t / nt);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -440,16 +487,58 @@ static PhaseArgs phase(const ms_grid* g, int src, int axis, int kind, float cb_h
   return p;
 }
 
+static CurlArgs make_curl(const ms_grid* g, int step, float cb_hi, float cb_lo, float* b0, float* b1) {
+  CurlArgs A;
+  A.N = g->N;
+  A.b0 = b0;
+  A.b1 = b1;
+  A.ntiles = (g->N + 1 + TB - 1) / TB;
+  if (step == 0) {
+    A.ph[0] = phase(g, HY, 0, HALF_TO_NODE, cb_hi, cb_lo);
+    A.ph[1] = phase(g, HX, 1, HALF_TO_NODE, cb_hi, cb_lo);
+  } else {
+    A.ph[0] = phase(g, EZ, 1, NODE_TO_HALF, cb_hi, cb_lo);
+    A.ph[1] = phase(g, EZ, 0, NODE_TO_HALF, cb_hi, cb_lo);
+  }
+  return A;
+}
+
+static SolveArgs make_solve(const ms_grid* g, int nfields, const int* fields, const float* const* b, int S, float d_hi,
+                            float d_lo, float omega, float s_hi, float s_lo) {
+  SolveArgs A;
+  for (int k = 0; k < 2; ++k) {
+    const int f = fields[k < nfields ? k : 0];
+    const Shape& s = g->sh[f];
+    A.b[k] = b[k < nfields ? k : 0];
+    A.hi[k] = g->hi[f];
+    A.lo[k] = g->lo[f];
+    A.nx[k] = s.nx;
+    A.ny[k] = s.ny;
+    A.bcx[k] = s.bcx;
+    A.bcy[k] = s.bcy;
+  }
+  A.S = S;
+  A.d_hi = d_hi;
+  A.d_lo = d_lo;
+  A.omega = omega;
+  A.s_hi = s_hi;
+  A.s_lo = s_lo;
+  const int TS = RS - 2 * (S - 1);
+  A.ntiles = (g->N + 1 + TS - 1) / TS;
+  return A;
+}
+
 size_t tiled_curl_smem() { return sizeof(float) * (size_t)(XROWS * XLP + TB * DLP + TB * YSP); }
 size_t tiled_solve_smem() { return sizeof(float) * (size_t)(3 * RS * RSP); }
 
 int tiled_configure() {
-  if (cudaFuncSetAttribute(k_curl_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_curl_smem()) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_curl_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_curl_smem()) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_solve_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled_solve_smem()) !=
-          cudaSuccess)
+  const int cs = (int)tiled_curl_smem(), ss = (int)tiled_solve_smem();
+  if (cudaFuncSetAttribute(k_curl_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
+      cudaFuncSetAttribute(k_curl_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
+      cudaFuncSetAttribute(k_curl_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
+      cudaFuncSetAttribute(k_curl_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
+      cudaFuncSetAttribute(k_solve_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, ss) != cudaSuccess ||
+      cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, ss) != cudaSuccess)
     return -1;
   // interior Toeplitz row of A^{-1}: 24 (-rho) rho^|d| / (1 - rho^2) (rho < 0), split hi + lo
   const long double rho = -11.0L + std::sqrt(120.0L);
@@ -467,46 +556,89 @@ int tiled_configure() {
 }
 
 void tiled_curl(ms_grid* g, int step, float cb_hi, float cb_lo, float* b0, float* b1) {
-  CurlArgs A;
-  A.N = g->N;
-  A.b0 = b0;
-  A.b1 = b1;
-  if (step == 0) {
-    A.ph[0] = phase(g, HY, 0, HALF_TO_NODE, cb_hi, cb_lo);
-    A.ph[1] = phase(g, HX, 1, HALF_TO_NODE, cb_hi, cb_lo);
-  } else {
-    A.ph[0] = phase(g, EZ, 1, NODE_TO_HALF, cb_hi, cb_lo);
-    A.ph[1] = phase(g, EZ, 0, NODE_TO_HALF, cb_hi, cb_lo);
-  }
-  const int nt = (g->N + 1 + TB - 1) / TB;
-  dim3 grid(nt, nt);
+  const CurlArgs A = make_curl(g, step, cb_hi, cb_lo, b0, b1);
+  dim3 grid(A.ntiles, A.ntiles);
   if (step == 0) k_curl_tile<0><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
   else k_curl_tile<1><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
 }
 
 void tiled_solve(ms_grid* g, int nfields, const int* fields, const float* const* b, int S, float d_hi, float d_lo,
                  float omega, float s_hi, float s_lo) {
-  SolveArgs A;
-  for (int k = 0; k < nfields; ++k) {
-    const Shape& s = g->sh[fields[k]];
-    A.b[k] = b[k];
-    A.hi[k] = g->hi[fields[k]];
-    A.lo[k] = g->lo[fields[k]];
-    A.nx[k] = s.nx;
-    A.ny[k] = s.ny;
-    A.bcx[k] = s.bcx;
-    A.bcy[k] = s.bcy;
-  }
-  A.S = S;
-  A.d_hi = d_hi;
-  A.d_lo = d_lo;
-  A.omega = omega;
-  A.s_hi = s_hi;
-  A.s_lo = s_lo;
-  const int TS = RS - 2 * (S - 1);
-  const int nt = (g->N + 1 + TS - 1) / TS;
-  dim3 grid(nt, nt, nfields);
+  const SolveArgs A = make_solve(g, nfields, fields, b, S, d_hi, d_lo, omega, s_hi, s_lo);
+  dim3 grid(A.ntiles, A.ntiles, nfields);
   k_solve_tile<<<grid, NT, tiled_solve_smem(), g->stream>>>(A);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched launches: one work list of (cavity, tile) entries covers every cavity.
+
+int tiled_batch_build(ms_grid* const* cav, int count, TiledBatch* tb, std::string* err) {
+  std::vector<CurlArgs> curl(2 * (size_t)count);
+  std::vector<SolveArgs> solve(2 * (size_t)count);
+  std::vector<int> wc, we, wh;
+  for (int c = 0; c < count; ++c) {
+    ms_grid* g = cav[c];
+    const MixedConsts k = mixed_consts(g);
+    float* bE = g->s32[4];
+    float* bx = g->s32[2];
+    float* by = g->s32[3];
+    curl[c] = make_curl(g, 0, k.cb_hi, k.cb_lo, bE, nullptr);
+    curl[count + c] = make_curl(g, 1, k.cb_hi, k.cb_lo, bx, by);
+    const int fe[1] = {EZ};
+    const float* be[1] = {bE};
+    const int fh[2] = {HX, HY};
+    const float* bh[2] = {bx, by};
+    solve[c] = make_solve(g, 1, fe, be, k.S, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo);
+    solve[count + c] = make_solve(g, 2, fh, bh, k.S, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo);
+    const int ntc = curl[c].ntiles, nts = solve[c].ntiles;
+    for (int t = 0; t < ntc * ntc; ++t) {
+      wc.push_back(c);
+      wc.push_back(t);
+    }
+    for (int t = 0; t < nts * nts; ++t) {
+      we.insert(we.end(), {c, 0, t});
+      wh.insert(wh.end(), {c, 0, t});
+      wh.insert(wh.end(), {c, 1, t});
+    }
+  }
+  tb->n_curl = (int)(wc.size() / 2);
+  tb->n_solveE = (int)(we.size() / 3);
+  tb->n_solveH = (int)(wh.size() / 3);
+  tb->off_curl = 0;
+  tb->off_solveE = wc.size();
+  tb->off_solveH = wc.size() + we.size();
+  std::vector<int> work(wc);
+  work.insert(work.end(), we.begin(), we.end());
+  work.insert(work.end(), wh.begin(), wh.end());
+  if (cudaMalloc(&tb->d_curl, curl.size() * sizeof(CurlArgs)) != cudaSuccess ||
+      cudaMalloc(&tb->d_solve, solve.size() * sizeof(SolveArgs)) != cudaSuccess ||
+      cudaMalloc(&tb->d_work, work.size() * sizeof(int)) != cudaSuccess) {
+    *err = "cudaMalloc of the batch work lists failed";
+    return -1;
+  }
+  if (cudaMemcpy(tb->d_curl, curl.data(), curl.size() * sizeof(CurlArgs), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(tb->d_solve, solve.data(), solve.size() * sizeof(SolveArgs), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(tb->d_work, work.data(), work.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    *err = "copy of the batch work lists failed";
+    return -1;
+  }
+  tb->count = count;
+  return 0;
+}
+
+void tiled_batch_step(const TiledBatch& tb, cudaStream_t st) {
+  const size_t cs = tiled_curl_smem(), ss = tiled_solve_smem();
+  k_curl_batch<0><<<tb.n_curl, NT, cs, st>>>(tb.d_curl, tb.d_work + tb.off_curl);
+  k_solve_batch<<<tb.n_solveE, NT, ss, st>>>(tb.d_solve, tb.d_work + tb.off_solveE);
+  k_curl_batch<1><<<tb.n_curl, NT, cs, st>>>(tb.d_curl + tb.count, tb.d_work + tb.off_curl);
+  k_solve_batch<<<tb.n_solveH, NT, ss, st>>>(tb.d_solve + tb.count, tb.d_work + tb.off_solveH);
+}
+
+void tiled_batch_free(TiledBatch* tb) {
+  cudaFree(tb->d_curl);
+  cudaFree(tb->d_solve);
+  cudaFree(tb->d_work);
+  *tb = TiledBatch{};
 }
 
 }  // namespace ms

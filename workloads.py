@@ -42,3 +42,17 @@ def random_fields(n: int, seed: int):
     hx[:, 1:-1] = rng.standard_normal((n, n - 1))
     hy[1:-1, :] = rng.standard_normal((n - 1, n))
     return ez, hx, hy
+
+
+def config4(seed: int = 0):
+    """512 independent 2D TM_z cavities, r = 0.5, 1000 steps; side lengths uniform in
+    {64, 96, ..., 768}; each cavity has 4 modes with indices uniform in [1, 30] and N(0, 1)
+    amplitudes."""
+    rng = np.random.default_rng(seed)
+    sizes = [int(64 + 32 * k) for k in rng.integers(0, 23, size=512)]
+    modes = []
+    for _ in sizes:
+        mn = rng.integers(1, 31, size=(4, 2))
+        amp = rng.standard_normal(4)
+        modes.append([(int(a), int(b), float(c)) for (a, b), c in zip(mn, amp)])
+    return dict(sizes=sizes, r=0.5, modes=modes, steps=1000)
