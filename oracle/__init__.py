@@ -79,6 +79,14 @@ def lib() -> ctypes.CDLL:
             L.or2d_cg_solves.argtypes = [V]
             L.or2d_cg_solves.restype = ctypes.c_long
             L.or2d_sizeof.restype = ctypes.c_int
+            L.or_pade_line_T.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, D, D]
+            L.or2d_curl_h_to_e_T.argtypes = [V, D, D, D]
+            L.or2d_curl_e_to_h_T.argtypes = [V, D, D, D]
+            L.or2d_step_T.argtypes = [V, D, D, D]
+            L.or2d_taylor_h.argtypes = [V, D, D, D]
+            L.or2d_taylor_h_T.argtypes = [V, D, D, D]
+            L.or2d_misfit_grad.argtypes = [V, D, D, ctypes.c_int, D]
+            L.or2d_misfit_grad.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -94,6 +102,14 @@ def pade_line(f: np.ndarray, h: float, closure: int = CLOSURE_PAPER, kind: int =
     M = f.size - 1
     out = np.zeros(M)
     lib().or_pade_line(M, closure, kind, h, _p(f), _p(out))
+    return out
+
+
+def pade_line_T(g: np.ndarray, h: float, closure: int = CLOSURE_PAPER, kind: int = HALF_TO_NODE) -> np.ndarray:
+    """Transpose of pade_line: D1^T A^{-T} g / h, len(out) = len(g) + 1."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(g.size + 1)
+    lib().or_pade_line_T(g.size, closure, kind, h, _p(g), _p(out))
     return out
 
 
@@ -234,3 +250,30 @@ class Oracle2D:
     def cg_stats(self):
         L = lib()
         return L.or2d_cg_iters_total(self.g), L.or2d_cg_solves(self.g)
+
+    # -- adjoint (transpose) of the step, the Taylor initialisation and the misfit gradient --
+    def step_T(self, lez, lhx, lhy):
+        """Transpose of one full step, in place on the adjoint state (level n+1 -> n)."""
+        lib().or2d_step_T(self.g, _p(lez), _p(lhx), _p(lhy))
+
+    def taylor_h(self, ez0):
+        """H^{1/2} from E^0 with H^0 = 0 by the Taylor series of Sec. 5.1 (Eq. "talorh")."""
+        ez0 = np.ascontiguousarray(ez0, dtype=np.float64)
+        hx, hy = self.zeros(F_HX), self.zeros(F_HY)
+        lib().or2d_taylor_h(self.g, _p(ez0), _p(hx), _p(hy))
+        return hx, hy
+
+    def taylor_h_T(self, lhx, lhy):
+        lhx = np.ascontiguousarray(lhx, dtype=np.float64)
+        lhy = np.ascontiguousarray(lhy, dtype=np.float64)
+        out = self.zeros(F_EZ)
+        lib().or2d_taylor_h_T(self.g, _p(lhx), _p(lhy), _p(out))
+        return out
+
+    def misfit_grad(self, ez0, target, K, grad=True):
+        """L = (1/2) h^2 sum (E_z^K - target)^2 from (E^0, Taylor H^{1/2}) and dL/dE^0 (interior)."""
+        ez0 = np.ascontiguousarray(ez0, dtype=np.float64)
+        target = np.ascontiguousarray(target, dtype=np.float64)
+        g = self.zeros(F_EZ) if grad else None
+        L = lib().or2d_misfit_grad(self.g, _p(ez0), _p(target), int(K), _p(g) if grad else None)
+        return (L, g) if grad else L

@@ -565,3 +565,250 @@ void or2d_yee_step(const or_grid2d* g, double* ez, double* hx, double* hy) {
 long or2d_cg_iters_total(const or_grid2d* g) { return g->cg_iters_total; }
 long or2d_cg_solves(const or_grid2d* g) { return g->cg_solves; }
 int or2d_sizeof(void) { return (int)sizeof(or_grid2d); }
+
+/* ------------------------------------------------------------------ */
+/* Adjoint (transpose) of the step, for gradients of a misfit.  The step of Sec. 3.4 is linear
+ * in (E, H); its transpose is built from the transposes of its factors:
+ *   the filter and P1 are symmetric on the unknowns (Dirichlet zeros, even Neumann ghosts);
+ *   the Pade derivative fp = A^{-1} D1 f / h has the transpose D1^T A^{-T} g / h, with A^{-T}
+ *   applied by a banded solve of A^T z = g (A is not symmetric under the one-sided closure). */
+
+/* Solve (24 A)^T y = rhs (banded elimination on the transposed band, no pivoting: A^T is
+ * column diagonally dominant). */
+static void pade_solve24_T(int M, int closure, int kind, double* rhs, double* y) {
+  double* band = (double*)calloc((size_t)M * (2 * PB + 1), sizeof(double));
+  for (int i = 0; i < M; ++i) {
+    int col[4];
+    double val[4];
+    int n = pade_row(M, closure, kind, i, col, val);
+    /* entry (i, col) of 24A is entry (col, i) of the transpose */
+    for (int k = 0; k < n; ++k) band[(size_t)col[k] * (2 * PB + 1) + (i - col[k] + PB)] += val[k];
+  }
+  for (int k = 0; k < M; ++k) {
+    double piv = band[(size_t)k * (2 * PB + 1) + PB];
+    for (int i = k + 1; i <= k + PB && i < M; ++i) {
+      double* ri = band + (size_t)i * (2 * PB + 1);
+      double* rk = band + (size_t)k * (2 * PB + 1);
+      double a = ri[k - i + PB];
+      if (a == 0.0) continue;
+      double l = a / piv;
+      for (int j = k; j <= k + PB && j < M; ++j) ri[j - i + PB] -= l * rk[j - k + PB];
+      rhs[i] -= l * rhs[k];
+    }
+  }
+  for (int i = M - 1; i >= 0; --i) {
+    double* ri = band + (size_t)i * (2 * PB + 1);
+    double s = rhs[i];
+    for (int j = i + 1; j <= i + PB && j < M; ++j) s -= ri[j - i + PB] * y[j];
+    y[i] = s / ri[PB];
+  }
+  free(band);
+}
+
+/* Transpose of or_pade_line: g has M values, out receives M+1 values, out = D1^T A^{-T} g / h. */
+void or_pade_line_T(int M, int closure, int kind, double h, const double* g, double* out) {
+  double* rhs = (double*)malloc(sizeof(double) * M);
+  double* z = (double*)malloc(sizeof(double) * M);
+  for (int i = 0; i < M; ++i) rhs[i] = 24.0 * g[i];
+  pade_solve24_T(M, closure, kind, rhs, z);
+  /* (D1^T z)_k = z_{k-1} - z_k with z_{-1} = z_M = 0 */
+  for (int k = 0; k <= M; ++k) out[k] = ((k >= 1 ? z[k - 1] : 0.0) - (k < M ? z[k] : 0.0)) / h;
+  free(rhs);
+  free(z);
+}
+
+/* Transpose of pade_field: reads the dst-shaped array at the positions pade_field writes and
+ * accumulates into the src-shaped array (which it first zeroes). */
+static void pade_field_T(const or_grid2d* g, int fs, int fd, int axis, int kind, const double* dsrc, double* out) {
+  int snx, sny, sbx, sby, dnx, dny, dbx, dby;
+  field_dims(g, fs, &snx, &sny, &sbx, &sby);
+  field_dims(g, fd, &dnx, &dny, &dbx, &dby);
+  int N = g->N;
+  int M = (kind == HALF_TO_NODE) ? N - 1 : N;
+  int nl = (axis == 0) ? sny : snx;
+  double* gl = (double*)malloc(sizeof(double) * M);
+  double* o = (double*)malloc(sizeof(double) * (M + 1));
+  memset(out, 0, sizeof(double) * (size_t)snx * sny);
+  for (int l = 0; l < nl; ++l) {
+    for (int k = 0; k < M; ++k) {
+      int oo = (kind == HALF_TO_NODE) ? k + 1 : k;
+      gl[k] = (axis == 0) ? dsrc[(size_t)l * dnx + oo] : dsrc[(size_t)oo * dnx + l];
+    }
+    or_pade_line_T(M, g->closure, kind, g->h, gl, o);
+    for (int k = 0; k <= M; ++k) {
+      if (axis == 0) out[(size_t)l * snx + k] += o[k];
+      else out[(size_t)k * snx + l] += o[k];
+    }
+  }
+  free(gl);
+  free(o);
+}
+
+/* Transposes of the two right-hand-side curls (Sec. 3.4), on arrays whose Dirichlet
+ * boundary entries are zero. */
+void or2d_curl_h_to_e_T(const or_grid2d* g, const double* lR, double* lGx, double* lGy) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* mu = (double*)malloc(sizeof(double) * ne);
+  memcpy(mu, lR, sizeof(double) * ne);
+  zero_boundary(g, F_EZ, mu);
+  pade_field_T(g, F_HY, F_EZ, 0, HALF_TO_NODE, mu, lGy);
+  pade_field_T(g, F_HX, F_EZ, 1, HALF_TO_NODE, mu, lGx);
+  double s = g->kappa2 * g->Z;
+  for (int p = 0; p < ny_; ++p) lGy[p] *= s;
+  for (int p = 0; p < nx_; ++p) lGx[p] *= -s;
+  free(mu);
+}
+
+void or2d_curl_e_to_h_T(const or_grid2d* g, const double* lRx, const double* lRy, double* lGE) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* mx = (double*)malloc(sizeof(double) * nx_);
+  double* my = (double*)malloc(sizeof(double) * ny_);
+  double* t = (double*)malloc(sizeof(double) * ne);
+  memcpy(mx, lRx, sizeof(double) * nx_);
+  memcpy(my, lRy, sizeof(double) * ny_);
+  zero_boundary(g, F_HX, mx);
+  zero_boundary(g, F_HY, my);
+  double s = g->kappa2 / g->Z;
+  pade_field_T(g, F_EZ, F_HX, 1, NODE_TO_HALF, mx, lGE);
+  pade_field_T(g, F_EZ, F_HY, 0, NODE_TO_HALF, my, t);
+  for (int p = 0; p < ne; ++p) lGE[p] = s * (t[p] - lGE[p]);
+  free(mx);
+  free(my);
+  free(t);
+}
+
+/* Transpose of one full step: (lE, lHx, lHy) at level n+1 are replaced by the adjoint state at
+ * level n.  Reverse order of Sec. 3.4: adjoint of Step 2, then of Step 1. */
+void or2d_step_T(or_grid2d* g, double* lE, double* lHx, double* lHy) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* ux = (double*)malloc(sizeof(double) * nx_);
+  double* uy = (double*)malloc(sizeof(double) * ny_);
+  double* v = (double*)malloc(sizeof(double) * ne);
+  double* w = (double*)malloc(sizeof(double) * ne);
+  double* vx = (double*)malloc(sizeof(double) * nx_);
+  double* vy = (double*)malloc(sizeof(double) * ny_);
+  double* wx = (double*)malloc(sizeof(double) * nx_);
+  double* wy = (double*)malloc(sizeof(double) * ny_);
+  zero_boundary(g, F_EZ, lE);
+  zero_boundary(g, F_HX, lHx);
+  zero_boundary(g, F_HY, lHy);
+  /* Step 2: H += h_tau P1_H^{-1} curl_EH(F_E E)  =>  lE += h_tau F_E curl_EH^T(P1_H^{-1} lH) */
+  or2d_p1_solve_cg(g, F_HX, lHx, ux);
+  or2d_p1_solve_cg(g, F_HY, lHy, uy);
+  or2d_curl_e_to_h_T(g, ux, uy, v);
+  zero_boundary(g, F_EZ, v);
+  or2d_filter(g, F_EZ, v, w);
+  for (int p = 0; p < ne; ++p) lE[p] += g->ht * w[p];
+  /* Step 1: E += h_tau P1_E^{-1} curl_HE(F_H H)  =>  lH += h_tau F_H curl_HE^T(P1_E^{-1} lE) */
+  or2d_p1_solve_cg(g, F_EZ, lE, v);
+  or2d_curl_h_to_e_T(g, v, vx, vy);
+  zero_boundary(g, F_HX, vx);
+  zero_boundary(g, F_HY, vy);
+  or2d_filter(g, F_HX, vx, wx);
+  or2d_filter(g, F_HY, vy, wy);
+  for (int p = 0; p < nx_; ++p) lHx[p] += g->ht * wx[p];
+  for (int p = 0; p < ny_; ++p) lHy[p] += g->ht * wy[p];
+  free(ux);
+  free(uy);
+  free(v);
+  free(w);
+  free(vx);
+  free(vy);
+  free(wx);
+  free(wy);
+}
+
+/* Taylor initialisation of H^{1/2} from E^0 with H^0 = 0 (Sec. 5.1, Eq. "talorh"): with J = 0,
+ * d_t H = -Z^{-1} curl E = Z^{-1} (-d_y E, d_x E), d_tt H = 0 at t = 0 (it is the curl of d_t E,
+ * which vanishes with H), d_ttt H = Delta d_t H and d_tttt H = 0, so
+ *   H^{1/2} = Z^{-1} (t1 + (t1^3/6) Delta_h) c,  c = (-delta_y E^0, delta_x E^0),  t1 = h_tau / 2,
+ * with delta the node -> half-node Pade derivative of App. A.1. */
+void or2d_taylor_h(const or_grid2d* g, const double* ez, double* hx, double* hy) {
+  int nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* cx = (double*)malloc(sizeof(double) * nx_);
+  double* cy = (double*)malloc(sizeof(double) * ny_);
+  double* lx = (double*)malloc(sizeof(double) * nx_);
+  double* ly = (double*)malloc(sizeof(double) * ny_);
+  pade_field(g, F_EZ, F_HX, 1, NODE_TO_HALF, ez, cx); /* delta_y E */
+  pade_field(g, F_EZ, F_HY, 0, NODE_TO_HALF, ez, cy); /* delta_x E */
+  for (int p = 0; p < nx_; ++p) cx[p] = -cx[p];
+  zero_boundary(g, F_HX, cx);
+  zero_boundary(g, F_HY, cy);
+  or2d_laplacian(g, F_HX, cx, lx);
+  or2d_laplacian(g, F_HY, cy, ly);
+  double t1 = 0.5 * g->ht, c3 = t1 * t1 * t1 / 6.0;
+  for (int p = 0; p < nx_; ++p) hx[p] = (t1 * cx[p] + c3 * lx[p]) / g->Z;
+  for (int p = 0; p < ny_; ++p) hy[p] = (t1 * cy[p] + c3 * ly[p]) / g->Z;
+  zero_boundary(g, F_HX, hx);
+  zero_boundary(g, F_HY, hy);
+  free(cx);
+  free(cy);
+  free(lx);
+  free(ly);
+}
+
+/* Transpose of or2d_taylor_h: lez (output) = T^T (lhx, lhy). */
+void or2d_taylor_h_T(const or_grid2d* g, const double* lhx, const double* lhy, double* lez) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* ax = (double*)malloc(sizeof(double) * nx_);
+  double* ay = (double*)malloc(sizeof(double) * ny_);
+  double* lx = (double*)malloc(sizeof(double) * nx_);
+  double* ly = (double*)malloc(sizeof(double) * ny_);
+  double* t = (double*)malloc(sizeof(double) * ne);
+  memcpy(ax, lhx, sizeof(double) * nx_);
+  memcpy(ay, lhy, sizeof(double) * ny_);
+  zero_boundary(g, F_HX, ax);
+  zero_boundary(g, F_HY, ay);
+  or2d_laplacian(g, F_HX, ax, lx);
+  or2d_laplacian(g, F_HY, ay, ly);
+  double t1 = 0.5 * g->ht, c3 = t1 * t1 * t1 / 6.0;
+  for (int p = 0; p < nx_; ++p) ax[p] = (t1 * ax[p] + c3 * lx[p]) / g->Z;
+  for (int p = 0; p < ny_; ++p) ay[p] = (t1 * ay[p] + c3 * ly[p]) / g->Z;
+  zero_boundary(g, F_HX, ax);
+  zero_boundary(g, F_HY, ay);
+  /* curl_h^T: cx = -delta_y E -> -pade_T_y(ax); cy = delta_x E -> pade_T_x(ay) */
+  pade_field_T(g, F_EZ, F_HX, 1, NODE_TO_HALF, ax, lez);
+  pade_field_T(g, F_EZ, F_HY, 0, NODE_TO_HALF, ay, t);
+  for (int p = 0; p < ne; ++p) lez[p] = t[p] - lez[p];
+  zero_boundary(g, F_EZ, lez);
+  free(ax);
+  free(ay);
+  free(lx);
+  free(ly);
+  free(t);
+}
+
+/* Final-time misfit L = (1/2) h^2 sum_interior (E_z^K - target)^2 after K steps from
+ * (E^0, H^{1/2} = Taylor(E^0)), and its gradient with respect to the interior of E^0:
+ * the reverse pass applies the transposed step K times, then the transposed initialisation. */
+double or2d_misfit_grad(or_grid2d* g, const double* ez0, const double* target, int K, double* grad) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* ez = (double*)malloc(sizeof(double) * ne);
+  double* hx = (double*)malloc(sizeof(double) * nx_);
+  double* hy = (double*)malloc(sizeof(double) * ny_);
+  memcpy(ez, ez0, sizeof(double) * ne);
+  zero_boundary(g, F_EZ, ez);
+  or2d_taylor_h(g, ez, hx, hy);
+  for (int n = 0; n < K; ++n) or2d_step(g, ez, hx, hy);
+  /* d = E^K - target on the interior (boundary entries of target do not enter); lE = h^2 d */
+  double h2 = g->h * g->h, L = 0.0;
+  for (int p = 0; p < ne; ++p) ez[p] -= target[p];
+  zero_boundary(g, F_EZ, ez);
+  for (int p = 0; p < ne; ++p) {
+    L += ez[p] * ez[p];
+    ez[p] *= h2;
+  }
+  L *= 0.5 * h2;
+  memset(hx, 0, sizeof(double) * nx_);
+  memset(hy, 0, sizeof(double) * ny_);
+  if (grad) {
+    for (int n = 0; n < K; ++n) or2d_step_T(g, ez, hx, hy);
+    or2d_taylor_h_T(g, hx, hy, grad);
+    for (int p = 0; p < ne; ++p) grad[p] += ez[p];
+    zero_boundary(g, F_EZ, grad);
+  }
+  free(ez);
+  free(hx);
+  free(hy);
+  return L;
+}
