@@ -210,6 +210,45 @@ ms_status ms_p1_solve_static(int n, double r, int field, const double* b, double
 ms_status ms_launches_per_step(ms_grid* g, int* launches);
 
 /* ---------------------------------------------------------------------------------------
+ * Initial data that is not a cavity mode, and the reverse (adjoint) pass.
+ *
+ * ms_taylor_init sets E_z^0 = ez0 (boundary entries ignored, stored as zero) and H^{1/2} by the
+ * Taylor series of Sec. 5.1 (Eq. "talorh") with H^0 = 0 and J = 0:
+ *   H^{1/2} = Z^{-1} (t1 + (t1^3/6) Delta_h) (-delta_y E^0, delta_x E^0),  t1 = h_tau / 2,
+ * with delta the node -> half-node Pade derivative of App. A.1 and Delta_h the 5-point Laplacian
+ * with the ghost rules of Table "tab:bc" (the discrete reading of the continuous curl and
+ * Laplacian in the series).  The step counter is reset to 0.  ez0: (N+1)^2 FP64, host (or
+ * device for _device).
+ *
+ * The step is linear in the state, so a misfit L(E_z^K) has dL/dE_z^0 = T0^T (M^T)^K dL/dE_z^K,
+ * with M the matrix of one step (Sec. 3.4, Step 1 then Step 2) on the unknowns and T0 the
+ * map E^0 -> (E^0, H^{1/2}) above.  The paper has no reverse pass; this is its exact transpose:
+ *   Step 2^T:  u_H = P1_H^{-1} l_H,  l_E += h_tau F_E (kappa^2/Z) (delta_x^T u_y - delta_y^T u_x)
+ *   Step 1^T:  u_E = P1_E^{-1} l_E,  l_H += h_tau F_H kappa^2 Z (-delta_y^T u_E, delta_x^T u_E)
+ * (F the right-hand-side filter of Eq. "eq:ell", symmetric like P1 on the unknowns; delta^T
+ * the transpose of the truncated Pade band the forward kernels apply).  Because the step does
+ * not depend on the state, the reverse pass reads no forward trajectory: no checkpoints are
+ * stored and memory is that of one state.  The reverse pass computes in FP64 on both
+ * precisions (on an MS_FP32_REFINED grid it is the transpose of the exact step, which the
+ * refined forward reproduces to its stated accuracy).  It leaves the forward state untouched.
+ *
+ * ms_adjoint_run:  dL_dEz0 = T0^T (M^T)^nsteps (dL_dEzT, 0, 0): the gradient with respect to
+ *   E_z^0 of a loss of E_z after nsteps steps from ms_taylor_init data, given its gradient
+ *   dL_dEzT.  Both (N+1)^2 FP64; boundary entries of dL_dEzT are ignored and those of dL_dEz0
+ *   are zero.  Host arrays: synchronous.  _device: device arrays, asynchronous on the grid's
+ *   stream.
+ * ms_adjoint_steps: lam (3 arrays in the full layout of comps) <- (M^T)^nsteps lam, in place;
+ *   boundary entries are zeroed.  Host arrays: synchronous.  _device: asynchronous.
+ * ms_taylor_init_T: dEz0 = T0_H^T (l_Hx, l_Hy), the transpose of the H^{1/2} part of T0. */
+ms_status ms_taylor_init(ms_grid* g, const double* ez0);
+ms_status ms_taylor_init_device(ms_grid* g, const double* ez0);
+ms_status ms_adjoint_run(ms_grid* g, long nsteps, const double* dL_dEzT, double* dL_dEz0);
+ms_status ms_adjoint_run_device(ms_grid* g, long nsteps, const double* dL_dEzT, double* dL_dEz0);
+ms_status ms_adjoint_steps(ms_grid* g, long nsteps, double* const* lam);
+ms_status ms_adjoint_steps_device(ms_grid* g, long nsteps, double* const* lam);
+ms_status ms_taylor_init_T(ms_grid* g, const double* l_hx, const double* l_hy, double* dEz0);
+
+/* ---------------------------------------------------------------------------------------
  * Batches: many independent 2D cavities of uneven sizes advanced together.  Each cavity is the
  * problem of ms_create_grid with n = n[b] cells per side; all share the rest of the descriptor
  * (z_imp, r, precision, closure, scheme, stream).  Every kernel of a step is one launch for the

@@ -94,6 +94,13 @@ def load() -> ctypes.CDLL:
             "ms_batch_error_vs_exact": [V, I, ctypes.POINTER(_Mode), I, PD, PD, PD, PD],
             "ms_batch_info": [V, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I)],
             "ms_step_profiled": [V, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), PD, ctypes.POINTER(I)],
+            "ms_taylor_init": [V, V],
+            "ms_taylor_init_device": [V, V],
+            "ms_taylor_init_T": [V, V, V, V],
+            "ms_adjoint_run": [V, L_, V, V],
+            "ms_adjoint_run_device": [V, L_, V, V],
+            "ms_adjoint_steps": [V, L_, PPD],
+            "ms_adjoint_steps_device": [V, L_, PPD],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -257,6 +264,58 @@ class Grid:
         """Operator entry point on CUDA float64 tensors (see maxwell4.h, ms_apply_op)."""
         _check(load().ms_apply_op(self._h, OPS[op], _ptrs([t.data_ptr() for t in ins]),
                                   _ptrs([t.data_ptr() for t in outs])))
+
+    # -- non-mode initial data and the reverse pass (maxwell4.h, ms_taylor_init / ms_adjoint_*) --
+    def _host(self, a, shape):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != shape:
+            raise ValueError(f"expected shape {shape}, got {a.shape}")
+        return a
+
+    @staticmethod
+    def _dev(t, shape):
+        if tuple(t.shape) != shape or not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
+            raise ValueError(f"expected a contiguous CUDA float64 tensor of shape {shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def taylor_init(self, ez0):
+        """E_z^0 = ez0 and H^{1/2} by the Taylor series with H^0 = 0; step counter reset."""
+        a = self._host(ez0, self.shapes()[0])
+        _check(load().ms_taylor_init(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def taylor_init_device(self, ez0):
+        _check(load().ms_taylor_init_device(self._h, self._dev(ez0, self.shapes()[0])))
+
+    def taylor_init_T(self, l_hx, l_hy):
+        """Transpose of the map E^0 -> H^{1/2}: returns an (N+1)^2 array."""
+        _, sx, sy = self.shapes()
+        a, b = self._host(l_hx, sx), self._host(l_hy, sy)
+        out = np.zeros(self.shapes()[0])
+        _check(load().ms_taylor_init_T(self._h, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
+                                       out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def adjoint_run(self, nsteps: int, dL_dEzT):
+        """dL/dE_z^0 of a loss of E_z after nsteps steps from taylor_init data (host arrays)."""
+        a = self._host(dL_dEzT, self.shapes()[0])
+        out = np.zeros(self.shapes()[0])
+        _check(load().ms_adjoint_run(self._h, int(nsteps), a.ctypes.data_as(ctypes.c_void_p),
+                                     out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def adjoint_run_device(self, nsteps: int, dL_dEzT, dL_dEz0):
+        s = self.shapes()[0]
+        _check(load().ms_adjoint_run_device(self._h, int(nsteps), self._dev(dL_dEzT, s), self._dev(dL_dEz0, s)))
+
+    def adjoint_steps(self, nsteps: int, l_ez, l_hx, l_hy):
+        """(M^T)^nsteps applied to an adjoint state (host arrays); returns the new state."""
+        arrs = [self._host(a, s).copy() for a, s in zip((l_ez, l_hx, l_hy), self.shapes())]
+        _check(load().ms_adjoint_steps(self._h, int(nsteps), _ptrs([a.ctypes.data for a in arrs])))
+        return tuple(arrs)
+
+    def adjoint_steps_device(self, nsteps: int, l_ez, l_hx, l_hy):
+        ptrs = [self._dev(t, s).value for t, s in zip((l_ez, l_hx, l_hy), self.shapes())]
+        _check(load().ms_adjoint_steps_device(self._h, int(nsteps), _ptrs(ptrs)))
 
 
 class Batch:

@@ -90,6 +90,9 @@ void curl_eh64(ms_grid* g, const double* GE, double* Rx, double* Ry, int* nl) {
   *nl += 2;
 }
 
+}  // namespace
+
+namespace ms {
 // x = P1^{-1} b by Richardson sweeps; the last sweep writes `out` and, if upd != nullptr,
 // adds upd_scale * x to upd (the state update E += h_tau E*).
 void p1_solve64(ms_grid* g, int f, const double* b, double* out, double* upd, double upd_scale, int* nl) {
@@ -107,6 +110,9 @@ void p1_solve64(ms_grid* g, int f, const double* b, double* out, double* upd, do
   }
   *nl += S;
 }
+}  // namespace ms
+
+namespace {
 
 // H* = P1^{-1} R_H(E) for a given E (Step 2 without the update) into hxs, hys.
 void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, double* hx_upd, double* hy_upd, int* nl) {
@@ -441,6 +447,7 @@ ms_status ms_destroy(ms_grid* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   free_graph(&g->graph1);
   free_graph(&g->graphk);
+  adjoint_teardown(g);
   for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
   for (int k = 0; k < 2; ++k) {
     cudaFree(g->pade[k].d_w);

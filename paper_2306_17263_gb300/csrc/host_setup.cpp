@@ -9,7 +9,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "ms_internal.h"
+#include "k_fp64.cuh"
 
 namespace ms {
 
@@ -153,6 +153,9 @@ int build_pade_table(int M, int closure, int kind, double tol, PadeTable* t, std
   }
   t->M = M;
   t->K = K;
+  t->rows = M;
+  t->n_in = M + 1;
+  t->left = K;
   t->all_explicit = (2 * B >= M);
   if (t->all_explicit) B = M;
   t->B = B;
@@ -176,6 +179,42 @@ int build_pade_table(int M, int closure, int kind, double tol, PadeTable* t, std
     put(2 * B, mid);
   }
   return 0;
+}
+
+void build_pade_table_T(const PadeTable& f, PadeTable* t) {
+  const int M = f.M, K = f.K, rs = f.row_stride();
+  // entry (i, k) of the forward band: output i, input k
+  auto W = [&](int i, int k) {
+    if (i < 0 || i >= M) return 0.0;
+    const int d = k - i + K;
+    if (d < 0 || d > 2 * K + 1) return 0.0;
+    return pade_row_ptr(f.w.data(), i, M, K, f.B, f.all_explicit)[d];
+  };
+  // W^T row k reads W column k at rows k - K - 1 .. k + K; it is the reversed interior row as
+  // soon as all of those rows are interior rows of W, i.e. away from B + K + 1 rows of each end.
+  const int R = M + 1;
+  int B = f.B + K + 1;
+  t->M = M;
+  t->K = K;
+  t->rows = R;
+  t->n_in = M;
+  t->left = K + 1;
+  t->all_explicit = f.all_explicit || 2 * B >= R;
+  if (t->all_explicit) B = R;
+  t->B = B;
+  const int nrows = t->all_explicit ? R + 1 : 2 * B + 1;
+  t->w.assign((size_t)nrows * rs, 0.0);
+  auto put = [&](int slot, int k) {
+    for (int s = 0; s < rs; ++s) t->w[(size_t)slot * rs + s] = W(k - (K + 1) + s, k);
+  };
+  if (t->all_explicit) {
+    for (int k = 0; k < R; ++k) put(k, k);
+    put(R, R / 2);
+  } else {
+    for (int k = 0; k < B; ++k) put(k, k);
+    for (int k = 0; k < B; ++k) put(B + k, R - B + k);
+    put(2 * B, R / 2);
+  }
 }
 
 // Fourier symbol of one full step (Sec. 4): a mode is neutrally stable iff

@@ -29,15 +29,17 @@ __global__ void k_filter64(const double* __restrict__ u, double* __restrict__ G,
 }
 
 // ---------------------------------------------------------------------------------------
-// Pade derivative (App. A.1, delta = A^{-1} D1) applied as the explicit band of W = A^{-1} D1~:
-//   out[line, o] (+)= scale * sum_{t} W(i, t) in[line, i - K + t],  o = i + out_off.
+// Pade derivative (App. A.1, delta = A^{-1} D1) applied as the explicit band of W = A^{-1} D1~
+// (or of its transpose W^T in the reverse pass):
+//   out[line, o] (+)= scale * sum_{t} W(i, t) in[line, i - left + t],  o = i + out_off,
+// for the M output rows i of the table and inputs 0 .. n_in - 1.
 // AXIS 0: lines are rows (x contiguous); AXIS 1: lines are columns.  Every point of the
 // output array is written: outputs outside [out_off, out_off + M) or lines outside
 // [line_lo, line_hi) receive 0 (or are left unchanged when accumulating).
 template <int AXIS>
 __global__ void k_pade64(const double* __restrict__ in, double* __restrict__ out, int n_lines, int M, int in_ld,
                          int out_len, int out_ld, int out_off, int line_lo, int line_hi, const double* __restrict__ tab,
-                         int K, int B, int all_explicit, double scale, int accumulate) {
+                         int K, int B, int all_explicit, double scale, int accumulate, int n_in, int left) {
   int o, line;
   if (AXIS == 0) {
     o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,10 +54,10 @@ __global__ void k_pade64(const double* __restrict__ in, double* __restrict__ out
   double v = 0.0;
   if (i >= 0 && i < M && line >= line_lo && line < line_hi) {
     const double* w = pade_row_ptr(tab, i, M, K, B, all_explicit);
-    const int k0 = i - K;
+    const int k0 = i - left;
     for (int t = 0; t < 2 * K + 2; ++t) {
       const int k = k0 + t;
-      if (k < 0 || k > M) continue;
+      if (k < 0 || k >= n_in) continue;
       const double f = (AXIS == 0) ? in[(size_t)line * in_ld + k] : in[(size_t)k * in_ld + line];
       v = fma(w[t], f, v);
     }
@@ -165,13 +167,13 @@ void launch_pade64(int axis, const double* in, double* out, int n_lines, int in_
                    cudaStream_t st) {
   dim3 blk(32, 8);
   if (axis == 0) {
-    k_pade64<0><<<grid2(out_len, n_lines, blk), blk, 0, st>>>(in, out, n_lines, t.M, in_ld, out_len, out_ld, out_off,
-                                                              line_lo, line_hi, t.d_w, t.K, t.B, t.all_explicit, scale,
-                                                              accumulate);
+    k_pade64<0><<<grid2(out_len, n_lines, blk), blk, 0, st>>>(in, out, n_lines, t.rows, in_ld, out_len, out_ld,
+                                                              out_off, line_lo, line_hi, t.d_w, t.K, t.B,
+                                                              t.all_explicit, scale, accumulate, t.n_in, t.left);
   } else {
-    k_pade64<1><<<grid2(n_lines, out_len, blk), blk, 0, st>>>(in, out, n_lines, t.M, in_ld, out_len, out_ld, out_off,
-                                                              line_lo, line_hi, t.d_w, t.K, t.B, t.all_explicit, scale,
-                                                              accumulate);
+    k_pade64<1><<<grid2(n_lines, out_len, blk), blk, 0, st>>>(in, out, n_lines, t.rows, in_ld, out_len, out_ld,
+                                                              out_off, line_lo, line_hi, t.d_w, t.K, t.B,
+                                                              t.all_explicit, scale, accumulate, t.n_in, t.left);
   }
 }
 

@@ -33,6 +33,12 @@ void launch_p1_apply64(const double* x, double* out, const Shape& s, double c1h2
 void launch_yee_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
 void launch_yee_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);
 
+// x = P1^{-1} b for field f by the FP64 Richardson sweeps (scratch planes s64[3], s64[4]); the
+// last sweep writes `out` and, when upd != nullptr, adds upd_scale * x to upd (capi.cu).
+void p1_solve64(ms_grid* g, int f, const double* b, double* out, double* upd, double upd_scale, int* nl);
+// Reverse pass (adjoint.cu): releases the transposed tables, adjoint planes and graphs.
+void adjoint_teardown(ms_grid* g);
+
 // Diagnostics (k_diag.cu)
 void launch_mode_field(double* out, const Shape& s, const double* tab_x, const double* tab_y, const double* coef,
                        int nmodes, cudaStream_t st);

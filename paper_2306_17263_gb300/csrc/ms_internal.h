@@ -28,6 +28,10 @@ Shape field_shape(int N, int f);
 struct PadeTable {
   int M = 0, K = 0, B = 0;
   bool all_explicit = false;        // every row stored (short lines)
+  // Generic band form used by the FP64 kernel: `rows` outputs from `n_in` inputs, output i
+  // reading inputs i - left .. i - left + 2K + 1.  Forward tables: rows = M, n_in = M + 1,
+  // left = K.  Transposed tables (W^T, the reverse pass): rows = M + 1, n_in = M, left = K + 1.
+  int rows = 0, n_in = 0, left = 0;
   std::vector<double> w;             // (2B + 1) rows x (2K + 2)
   double* d_w = nullptr;             // device copy (FP64)
   float* d_whi = nullptr;            // device FP32 split: w = whi + wlo exactly to ~2^-48
@@ -37,6 +41,9 @@ struct PadeTable {
 // Build the table for M outputs, closure, kind; tail weights dropped sum below tol * row sum.
 int build_pade_table(int M, int closure, int kind, double tol, PadeTable* t, std::string* err,
                      bool of_differences = false);
+// Transpose W^T of a forward FP64 table, as the same truncated band: exact transpose of the
+// operator the forward kernels apply.
+void build_pade_table_T(const PadeTable& fwd, PadeTable* t);
 // Exact (untruncated) dense row i of W, for checks.
 void pade_dense_row(int M, int closure, int kind, int i, std::vector<double>* row);
 
@@ -110,5 +117,10 @@ struct ms_grid {
 
   ms::Graph graph1, graphk;
   int launches_per_step = 0;
+
+  // reverse pass (adjoint.cu): transposed FP64 Pade tables, adjoint state and scratch, graphs
+  ms::PadeTable padeT[2];
+  double* adj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  ms::Graph adj_graph1, adj_graphk;
   ms::Prof prof;
 };

@@ -56,3 +56,36 @@ def config4(seed: int = 0):
         amp = rng.standard_normal(4)
         modes.append([(int(a), int(b), float(c)) for (a, b), c in zip(mn, amp)])
     return dict(sizes=sizes, r=0.5, modes=modes, steps=1000)
+
+
+def sine_series_field(n: int, ell: float, seed: int, mmax: int = 96):
+    """Gaussian random field on the (n+1)^2 E_z nodes as a sine series
+    sum a_mn sin(m pi x) sin(n pi y), a_mn ~ N(0, 1) exp(-pi^2 (m^2 + n^2) ell^2 / 4), m, n <= mmax
+    (zero on the walls), normalised to unit RMS over the interior nodes."""
+    rng = np.random.default_rng(seed)
+    mc = min(mmax, n - 1)
+    k = np.arange(1, mc + 1)
+    env = np.exp(-np.pi ** 2 * (k[:, None] ** 2 + k[None, :] ** 2) * ell ** 2 / 4.0)
+    a = rng.standard_normal((mc, mc)) * env
+    # sin(k pi i / n) with the argument reduced exactly in integers
+    q = np.mod(np.outer(np.arange(n + 1), k), 2 * n)
+    s = np.sin(np.pi * q / n)
+    s[0, :] = 0.0
+    s[n, :] = 0.0
+    f = s @ a.T @ s.T  # f[j, i] = sum_mn a_mn sin(m pi x_i) sin(n pi y_j)
+    rms = np.sqrt(np.mean(f[1:-1, 1:-1] ** 2))
+    return f / rms
+
+
+def config5(seed: int = 0, n: int = 1024, steps: int = 2000):
+    """Reverse-pass workload: 2D TM_z, n x n cells, r = 0.5, `steps` steps.  E_z^0 is a Gaussian
+    random field of correlation length 0.05 (sine series, unit RMS), H^0 = 0 and H^{1/2} from the
+    Taylor series; the target is a 4-mode superposition (indices uniform in [1, 30], N(0, 1)
+    amplitudes) at the final time; 16 directions are further fields of the same law."""
+    rng = np.random.default_rng(seed)
+    seeds = rng.integers(0, 2 ** 31, size=18)
+    mn = rng.integers(1, 31, size=(4, 2))
+    amp = rng.standard_normal(4)
+    return dict(n=n, r=0.5, steps=steps, ell=0.05,
+                ez0_seed=int(seeds[0]), direction_seeds=[int(x) for x in seeds[2:18]],
+                target_modes=[(int(a), int(b), float(c)) for (a, b), c in zip(mn, amp)])
