@@ -123,10 +123,18 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_sources_hash():
+# source files that define each kernel kind reported by ms_step_profiled
+KIND_SOURCES = {
+    "curl32": ["k_tiled.cu", "k_tiled.cuh"], "solve32": ["k_tiled.cu", "k_tiled.cuh"],
+    "filter64": ["k_fp64.cu", "k_fp64.cuh"], "pade64": ["k_fp64.cu", "k_fp64.cuh"],
+    "p1sweep64": ["k_fp64.cu", "k_fp64.cuh"], "yee64": ["k_fp64.cu", "k_fp64.cuh"],
+}
+
+
+def kernel_sources_hash(kind: str):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_17263_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KIND_SOURCES.get(kind, []):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -134,17 +142,17 @@ def kernel_sources_hash():
 
 def ncu_traffic(kind: str):
     """DRAM bytes per launch of `kind` from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+    current sources of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("sources_sha") != kernel_sources_hash():
+    e = d.get(kind)
+    if not e or e.get("sources_sha") != kernel_sources_hash(kind):
         return None
-    v = d.get("per_launch_dram_bytes", {}).get(kind)
-    return float(v) if v is not None else None
+    return float(e["dram_bytes_per_launch"])
 
 
 # ---------------------------------------------------------------------------------------
@@ -211,6 +219,41 @@ def batched_leg(pkg, torch, steps: int = 64):
             "cells_per_step": cells, "launches_per_step": launches, "steps": steps, "ms_per_step": ms,
             "value": cells / (ms * 1e-3), "unit": "cell-updates/s",
             "l2_rel_last_cavity": err[1]}
+
+
+def reverse_leg(pkg, torch):
+    """Gradient workload: 1024^2 cells, 2000 steps, Taylor-initialised random field; the FP32_REFINED
+    forward run and the FP64 reverse pass (ms_adjoint_run_device), each timed with CUDA events."""
+    c = workloads.config5()
+    n, K = c["n"], c["steps"]
+    g = pkg.Grid(n, c["r"], precision=pkg.FP32_REFINED, stream="torch")
+    ez0 = torch.tensor(workloads.sine_series_field(n, c["ell"], c["ez0_seed"]), device="cuda")
+    lam = torch.zeros_like(ez0)
+    out = torch.empty_like(ez0)
+    lam[1:-1, 1:-1] = torch.tensor(workloads.sine_series_field(n, c["ell"], c["direction_seeds"][0]),
+                                   device="cuda")[1:-1, 1:-1]
+    g.taylor_init_device(ez0)
+    g.run(16)
+    g.adjoint_run_device(16, lam, out)  # builds the graphs and the transposed tables
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    g.taylor_init_device(ez0)
+    g.run(K)
+    ev[1].record()
+    ev[2].record()
+    g.adjoint_run_device(K, lam, out)
+    ev[3].record()
+    torch.cuda.synchronize()
+    fwd_ms, rev_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    g.close()
+    ok = bool(torch.isfinite(out).all().item())
+    return {"workload": "1024x1024 cells, 2000 steps, Gaussian random field E_z^0 (correlation length 0.05), "
+                        "H^(1/2) by Taylor series", "forward_precision": "fp32_refined", "reverse_precision": "fp64",
+            "forward_ms": fwd_ms, "reverse_ms": rev_ms,
+            "forward_value": n * n * K / (fwd_ms * 1e-3), "reverse_value": n * n * K / (rev_ms * 1e-3),
+            "unit": "cell-updates/s", "finite": ok,
+            "memory": "no trajectory stored: the step is linear, the reverse pass needs only the final adjoint"}
 
 
 def yee_leg(pkg, torch, modes, r, c4_l2_abs, c4_value, T=4000 * 0.5 / 2048):
@@ -376,6 +419,7 @@ def run_ours(args, ws, rank, local):
                                 "ms_per_step": t64 / k64}
             g64.close()
         line["batched"] = batched_leg(pkg, torch)
+        line["reverse_pass"] = reverse_leg(pkg, torch)
         line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, l2_abs, value)
         # CPU oracle on a bounded sample of the workload (rank 0, one core)
         v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
