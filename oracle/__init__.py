@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The CUDA library never uses it; the two share no code.
 
-The arithmetic lives in ``maxwell_oracle.c`` (plain C, FP64, single thread),
+The arithmetic lives in ``maxwell_oracle.c`` (2D) and ``maxwell_oracle3d.c`` (3D)
+(plain C, FP64, single thread),
 compiled on demand with gcc into ``oracle/_build/liboracle.so``.  This module
 only marshals numpy arrays to it.  Each wrapper names the passage of the paper
 its C routine follows.
@@ -20,7 +21,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "maxwell_oracle.c")
+_SRCS = [os.path.join(_HERE, "maxwell_oracle.c"), os.path.join(_HERE, "maxwell_oracle3d.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -34,11 +35,11 @@ HALF_TO_NODE, NODE_TO_HALF = 0, 1
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no fast-math) if it is missing or stale."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    stale = force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS)
     if stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -87,6 +88,25 @@ def lib() -> ctypes.CDLL:
             L.or2d_taylor_h_T.argtypes = [V, D, D, D]
             L.or2d_misfit_grad.argtypes = [V, D, D, ctypes.c_int, D]
             L.or2d_misfit_grad.restype = ctypes.c_double
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            L.or3d_sizeof.restype = ctypes.c_int
+            L.or3d_setup.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+            L.or3d_set_cg.argtypes = [V, ctypes.c_double, ctypes.c_int]
+            L.or3d_bc.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.or3d_bc.restype = ctypes.c_int
+            for name in ("or3d_laplacian", "or3d_filter", "or3d_p1_apply"):
+                getattr(L, name).argtypes = [V, ctypes.c_int, D, D]
+            L.or3d_p1_solve_cg.argtypes = [V, ctypes.c_int, D, D]
+            L.or3d_p1_solve_cg.restype = ctypes.c_int
+            L.or3d_curl_h_to_e.argtypes = [V, PP, PP]
+            L.or3d_curl_e_to_h.argtypes = [V, PP, PP]
+            L.or3d_step.argtypes = [V, PP]
+            L.or3d_exact.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, PP]
+            L.or3d_error.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, PP, D]
+            L.or3d_cg_iters_total.argtypes = [V]
+            L.or3d_cg_iters_total.restype = ctypes.c_long
+            L.or3d_cg_solves.argtypes = [V]
+            L.or3d_cg_solves.restype = ctypes.c_long
             _lib = L
     return _lib
 
@@ -277,3 +297,120 @@ class Oracle2D:
         g = self.zeros(F_EZ) if grad else None
         L = lib().or2d_misfit_grad(self.g, _p(ez0), _p(target), int(K), _p(g) if grad else None)
         return (L, g) if grad else L
+
+
+E_X, E_Y, E_Z, H_X, H_Y, H_Z = range(6)
+
+
+def _pp(arrs):
+    for a in arrs:
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+
+
+class Oracle3D:
+    """3D grid of the scheme: six components on the staggered unit cube (Eq. "eq:meshes"),
+    PEC walls, boundary types of Table "tab:bc".  Arrays are [z][y][x]."""
+
+    def __init__(self, N: int, r: float, Z: float = 1.0, closure: int = CLOSURE_PAPER):
+        L = lib()
+        self._buf = ctypes.create_string_buffer(L.or3d_sizeof())
+        self.g = ctypes.cast(self._buf, ctypes.c_void_p)
+        L.or3d_setup(self.g, int(N), float(r), float(Z), int(closure))
+        self.N, self.r, self.Z, self.closure = int(N), float(r), float(Z), int(closure)
+        self.h = 1.0 / N
+        self.ht = r * self.h
+        self.kappa2 = 24.0 / self.ht ** 2
+        self.beta = 1.0 + self.kappa2 * self.h ** 2 / 12.0
+        self.c1 = self.kappa2 * self.beta
+
+    @staticmethod
+    def bc(c: int, axis: int) -> int:
+        """0 = Dirichlet (nodes, wall zeros stored), 1 = Neumann (half-nodes, even ghosts)."""
+        return lib().or3d_bc(c, axis)
+
+    def shape(self, c: int):
+        """(nz, ny, nx) of component c."""
+        d = [self.N + 1 if self.bc(c, a) == 0 else self.N for a in range(3)]
+        return d[2], d[1], d[0]
+
+    def zeros(self, c: int) -> np.ndarray:
+        return np.zeros(self.shape(c))
+
+    def fields(self):
+        return [self.zeros(c) for c in range(6)]
+
+    def set_cg(self, tol: float, maxit: int = 200):
+        lib().or3d_set_cg(self.g, tol, maxit)
+
+    def _unary(self, name, c, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = self.zeros(c)
+        getattr(lib(), name)(self.g, c, _p(u), _p(out))
+        return out
+
+    def laplacian(self, c, u):
+        """Delta_h = D_xx + D_yy + D_zz with the component's boundary types."""
+        return self._unary("or3d_laplacian", c, u)
+
+    def filter(self, c, u):
+        """G = (1 + kappa^2 h^2/12) u + (h^2/12) Delta_h u (right side of Eq. "eq:ell")."""
+        return self._unary("or3d_filter", c, u)
+
+    def p1(self, c, x):
+        """P1 x = -(Delta_h + (h^2/6) Upsilon_h) x + c1 x (Definition "def:operatorsP")."""
+        return self._unary("or3d_p1_apply", c, x)
+
+    def p1_solve(self, c, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = self.zeros(c)
+        it = lib().or3d_p1_solve_cg(self.g, c, _p(b), _p(x))
+        return x, it
+
+    def curl_h_to_e(self, G):
+        """R_E = kappa^2 Z curl_h G_H (Step 1, Sec. 3.4); G = filtered (H_x, H_y, H_z)."""
+        G = [np.ascontiguousarray(a, dtype=np.float64) for a in G]
+        R = [self.zeros(c) for c in range(3)]
+        lib().or3d_curl_h_to_e(self.g, _pp(G), _pp(R))
+        return R
+
+    def curl_e_to_h(self, G):
+        """R_H = -(kappa^2/Z) curl_h G_E (Step 2, Sec. 3.4); G = filtered (E_x, E_y, E_z)."""
+        G = [np.ascontiguousarray(a, dtype=np.float64) for a in G]
+        R = [self.zeros(c) for c in range(3, 6)]
+        lib().or3d_curl_e_to_h(self.g, _pp(G), _pp(R))
+        return R
+
+    def step(self, f):
+        """One full step in place on f = [E_x, E_y, E_z, H_x, H_y, H_z] (Sec. 3.4)."""
+        lib().or3d_step(self.g, _pp(f))
+
+    def run(self, f, nsteps):
+        for _ in range(int(nsteps)):
+            self.step(f)
+
+    @staticmethod
+    def _modes(modes):
+        m = np.ascontiguousarray(np.asarray(modes, dtype=np.float64).reshape(-1, 6))
+        return m, m.shape[0]
+
+    def exact(self, modes, tE, tH):
+        """Exact cavity modes; rows (m, n, p, A_x, A_y, A_z) with A . (m, n, p) = 0."""
+        m, nm = self._modes(modes)
+        f = self.fields()
+        lib().or3d_exact(self.g, _p(m), nm, tE, tH, _pp(f))
+        return f
+
+    def init_modes(self, modes):
+        return self.exact(modes, 0.0, 0.5 * self.ht)
+
+    def error(self, modes, n, f):
+        """(L2 abs, L2 rel, max abs, sum |err|) of (E^n, H^{n+1/2}) against the exact modes."""
+        m, nm = self._modes(modes)
+        out = np.zeros(4)
+        lib().or3d_error(self.g, _p(m), nm, n * self.ht, (n + 0.5) * self.ht, _pp(f), _p(out))
+        return out
+
+    def cg_stats(self):
+        L = lib()
+        return L.or3d_cg_iters_total(self.g), L.or3d_cg_solves(self.g)

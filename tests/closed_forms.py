@@ -61,3 +61,51 @@ def mode_basis(N: int, kx: int, ky: int):
     hx[:, 0] = hx[:, -1] = 0.0
     hy[0, :] = hy[-1, :] = 0.0
     return ez, hx, hy
+
+
+def mode_step_matrix3(N: int, r: float, m: int, n: int, p: int, Z: float = 1.0) -> np.ndarray:
+    """Matrix of one full 3D step on the coefficients (e_x, e_y, e_z, h_x, h_y, h_z) of the mode
+    basis of mode_basis3 (sine on node axes, cosine on half-node axes), from the symbols of D_2,
+    P1 (with Upsilon_h), the filter and the Pade derivatives; curl_h as printed in Sec. 3.4."""
+    h = 1.0 / N
+    ht = r * h
+    k2 = 24.0 / ht ** 2
+    beta = 1.0 + k2 * h * h / 12.0
+    th = [math.pi * m * h, math.pi * n * h, math.pi * p * h]
+    mu = [-d2_symbol(t, h) for t in th]
+    filt = beta - (h * h / 12.0) * sum(mu)
+    p1 = k2 * beta + sum(mu) - (h * h / 6.0) * (mu[0] * mu[1] + mu[1] * mu[2] + mu[2] * mu[0])
+    g = k2 * filt / p1
+    dx, dy, dz = (pade_symbol(t, h) for t in th)
+    # d(half->node) cos -> -d sin, d(node->half) sin -> +d cos
+    S1 = np.eye(6)
+    S1[0, 4], S1[0, 5] = ht * Z * g * dz, -ht * Z * g * dy    # e_x += ht Z g (dz h_y - dy h_z)
+    S1[1, 5], S1[1, 3] = ht * Z * g * dx, -ht * Z * g * dz    # e_y += ht Z g (dx h_z - dz h_x)
+    S1[2, 3], S1[2, 4] = ht * Z * g * dy, -ht * Z * g * dx    # e_z += ht Z g (dy h_x - dx h_y)
+    S2 = np.eye(6)
+    c = ht * g / Z
+    S2[3, 1], S2[3, 2] = c * dz, -c * dy                       # h_x += (ht/Z) g (dz e_y - dy e_z)
+    S2[4, 2], S2[4, 0] = c * dx, -c * dz                       # h_y += (ht/Z) g (dx e_z - dz e_x)
+    S2[5, 0], S2[5, 1] = c * dy, -c * dx                       # h_z += (ht/Z) g (dy e_x - dx e_y)
+    return S2 @ S1
+
+
+def mode_basis3(N: int, m: int, n: int, p: int):
+    """Basis fields [z][y][x] of the six components for mode (m, n, p): on each axis a component
+    carries sin(theta i) on nodes (Dirichlet axes) and cos(theta (i + 1/2)) on half-nodes."""
+    h = 1.0 / N
+    th = [math.pi * m * h, math.pi * n * h, math.pi * p * h]
+    out = []
+    for c in range(6):
+        s = c % 3
+        node_axes = [a != s for a in range(3)] if c < 3 else [a == s for a in range(3)]
+        f1 = []
+        for a in range(3):
+            if node_axes[a]:
+                v = np.sin(th[a] * np.arange(N + 1))
+                v[0] = v[-1] = 0.0
+            else:
+                v = np.cos(th[a] * (np.arange(N) + 0.5))
+            f1.append(v)
+        out.append(np.einsum("k,j,i->kji", f1[2], f1[1], f1[0]))
+    return out
