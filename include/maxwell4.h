@@ -72,8 +72,8 @@ typedef enum { MS_CLOSURE_PAPER = 0, MS_CLOSURE_REFLECT = 1 } ms_closure;
 typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1 } ms_scheme;
 
 typedef struct {
-  int dim;          /* 2 (TM_z: E_z, H_x, H_y).  3 is reserved. */
-  int n;            /* cells per side of the unit square, h = 1/n; 4 <= n <= 32768 */
+  int dim;          /* 2 (TM_z: E_z, H_x, H_y) or 3 (six components, see below) */
+  int n;            /* cells per side of the unit square / cube, h = 1/n; 4 <= n <= 32768 (2D), 512 (3D) */
   double z_imp;     /* Z = sqrt(mu/epsilon) of Eq. "eq:maxwellv"; > 0 (1.0 in the paper) */
   double r;         /* CFL number h_tau / h, 0 < r < stability limit (Sec. 4) */
   int precision;    /* ms_precision */
@@ -92,10 +92,23 @@ typedef struct {
   double amp;
 } ms_mode;
 
+/* Three-dimensional grids (dim = 3): the six components of Eq. "eq:meshes" on the unit cube,
+ * host and device arrays in the layout [z][y][x] (x fastest), comps[0..5] = E_x, E_y, E_z, H_x,
+ * H_y, H_z.  A component has n+1 points along the axes on which it sits on nodes (Dirichlet,
+ * wall values zero) and n points along its half-node axes (Neumann), Table "tab:bc":
+ *   E_x (n, n+1, n+1)  E_y (n+1, n, n+1)  E_z (n+1, n+1, n)
+ *   H_x (n+1, n, n)    H_y (n, n+1, n)    H_z (n, n, n+1)      as (nx, ny, nz).
+ * One step is Step 1 / Step 2 of Sec. 3.4 with the full curl_h, the 7-point Delta_h and the
+ * 19-point P1 (Upsilon_h = D_zz D_xx + D_yy D_zz + D_xx D_yy).  ms_set_fields, ms_get_fields
+ * (and _device), ms_step, ms_run, ms_sync, ms_get_step, ms_step_profiled and
+ * ms_launches_per_step take 3D grids with six arrays; the mode calls are ms_init_modes3 and
+ * ms_error_vs_exact3; the other diagnostics, the operator entry points, batches and the reverse
+ * pass are 2D only (MS_EUNSUPPORTED, or MS_EINVAL for the 2D mode calls). */
+
 /* Create a grid.  Validates the descriptor (MS_EINVAL), rejects r at or above the exact
- * Fourier stability limit of the scheme (MS_ECFL; about 0.6895 in 2D, Sec. 4 gives the
- * sufficient bound 5/(6 sqrt 2)), allocates the state and all scratch on the device, and
- * zeroes the fields.  *out receives the handle; it is NULL on failure. */
+ * Fourier stability limit of the scheme (MS_ECFL; about 0.6895 in 2D and 0.5607 in 3D, Sec. 4
+ * gives the sufficient bounds 5/(6 sqrt 2) and 5/(6 sqrt 3)), allocates the state and all
+ * scratch on the device, and zeroes the fields.  *out receives the handle; it is NULL on failure. */
 ms_status ms_create_grid(const ms_grid_desc* desc, ms_grid** out);
 
 /* Release the grid's device memory and stream.  NULL is accepted. */
@@ -104,6 +117,25 @@ ms_status ms_destroy(ms_grid* g);
 /* Set E^0 and H^{1/2} to the exact superposition of nmodes cavity modes (Eq. "eq:data") at
  * t = 0 and t = h_tau/2, and reset the step counter to 0.  modes is a host array. */
 ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes);
+
+/* A cavity mode of the 3D problem (not in the paper; derived from Eq. "eq:maxwellv" with PEC
+ * walls): with (a, b, c) = pi (m, n, p) and w = |(a, b, c)|,
+ *   E = (ax cos(a x) sin(b y) sin(c z), ay sin(a x) cos(b y) sin(c z), az sin(a x) sin(b y) cos(c z)) cos(w t),
+ *   H = -(1/(Z w)) curl(E / cos(w t)) sin(w t),
+ * which needs (ax, ay, az) . (m, n, p) = 0 (MS_EINVAL otherwise) and m, n, p >= 1. */
+typedef struct {
+  int m, n, p;
+  double ax, ay, az;
+} ms_mode3;
+
+/* 3D grids: E^0 and H^{1/2} from a superposition of exact modes; step counter reset to 0.
+ * Synchronous. */
+ms_status ms_init_modes3(ms_grid* g, const ms_mode3* modes, int nmodes);
+
+/* 3D grids: error of the state against exact modes at t_E = n h_tau, t_H = (n + 1/2) h_tau
+ * over the six components (l2 with weight h^3), as ms_error_vs_exact.  Synchronous. */
+ms_status ms_error_vs_exact3(ms_grid* g, const ms_mode3* modes, int nmodes, double* l2_abs, double* l2_rel,
+                             double* max_abs, double* sum_abs);
 
 /* Copy host FP64 fields (layout above) to the device state and set the step counter to
  * `step` (E at step h_tau, H at (step + 1/2) h_tau).  Dirichlet boundary entries are ignored
@@ -170,7 +202,7 @@ ms_status ms_apply_op(ms_grid* g, int op, const double* const* in, double* const
 
 /* Largest CFL number r for which every Fourier mode of the scheme is neutrally stable
  * (Sec. 4: a mode is stable iff |h_tau lambda| <= 2 in sigma^2 - (2 - lambda^2 h_tau^2) sigma + 1 = 0),
- * computed from the symbols of the operators.  dim must be 2.  Needs no GPU. */
+ * computed from the symbols of the operators.  dim is 2 or 3.  Needs no GPU. */
 ms_status ms_stability_limit(int dim, double* rmax);
 
 /* Advance one step like ms_step, recording a CUDA event on the grid's stream after every

@@ -46,6 +46,11 @@ class _Mode(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("amp", ctypes.c_double)]
 
 
+class _Mode3(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("ax", ctypes.c_double),
+                ("ay", ctypes.c_double), ("az", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -94,6 +99,8 @@ def load() -> ctypes.CDLL:
             "ms_batch_error_vs_exact": [V, I, ctypes.POINTER(_Mode), I, PD, PD, PD, PD],
             "ms_batch_info": [V, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I)],
             "ms_step_profiled": [V, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), PD, ctypes.POINTER(I)],
+            "ms_init_modes3": [V, ctypes.POINTER(_Mode3), I],
+            "ms_error_vs_exact3": [V, ctypes.POINTER(_Mode3), I, PD, PD, PD, PD],
             "ms_taylor_init": [V, V],
             "ms_taylor_init_device": [V, V],
             "ms_taylor_init_T": [V, V, V, V],
@@ -127,6 +134,15 @@ def _modes(modes):
     return arr, len(modes)
 
 
+def _modes3(modes):
+    modes = list(modes)
+    arr = (_Mode3 * max(1, len(modes)))()
+    for k, (m, n, p, ax, ay, az) in enumerate(modes):
+        arr[k].m, arr[k].n, arr[k].p = int(m), int(n), int(p)
+        arr[k].ax, arr[k].ay, arr[k].az = float(ax), float(ay), float(az)
+    return arr, len(modes)
+
+
 def _ptrs(ptrs):
     return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
 
@@ -144,19 +160,21 @@ class Grid:
     precision: FP64 or FP32_REFINED; closure: CLOSURE_PAPER or CLOSURE_REFLECT;
     scheme: SCHEME_C4 (the paper's scheme) or SCHEME_YEE2 (plain Yee comparator).
     stream: a cudaStream_t handle (int), "torch" for torch's current stream, or None.
+    dim: 2 (E_z, H_x, H_y) or 3 (E_x, E_y, E_z, H_x, H_y, H_z on the unit cube, arrays [z][y][x]).
     """
 
     def __init__(self, n: int, r: float, z: float = 1.0, precision: int = FP64, closure: int = CLOSURE_PAPER,
-                 scheme: int = SCHEME_C4, stream=None):
+                 scheme: int = SCHEME_C4, stream=None, dim: int = 2):
         L = load()
         if stream == "torch":
             import torch
             stream = torch.cuda.current_stream().cuda_stream
-        d = _Desc(2, int(n), float(z), float(r), int(precision), int(closure), int(scheme),
+        d = _Desc(int(dim), int(n), float(z), float(r), int(precision), int(closure), int(scheme),
                   ctypes.c_void_p(int(stream)) if stream else None)
         h = ctypes.c_void_p()
         _check(L.ms_create_grid(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
+        self.dim = int(dim)
         self.n, self.r, self.z = int(n), float(r), float(z)
         self.precision, self.closure, self.scheme = int(precision), int(closure), int(scheme)
         self.h = 1.0 / n
@@ -165,6 +183,13 @@ class Grid:
     # ------------------------------------------------------------------
     def shapes(self):
         N = self.n
+        if self.dim == 3:
+            out = []
+            for c in range(6):
+                node = [(a != c % 3) if c < 3 else (a == c % 3) for a in range(3)]
+                nx, ny, nz = (N + 1 if q else N for q in node)
+                out.append((nz, ny, nx))
+            return tuple(out)
         return (N + 1, N + 1), (N, N + 1), (N + 1, N)
 
     def close(self):
@@ -186,12 +211,21 @@ class Grid:
 
     # ------------------------------------------------------------------
     def init_modes(self, modes):
+        """2D: rows (m, n, amp); 3D: rows (m, n, p, a_x, a_y, a_z) with a . (m, n, p) = 0."""
+        if self.dim == 3:
+            arr, nm = _modes3(modes)
+            _check(load().ms_init_modes3(self._h, arr, nm))
+            return
         arr, nm = _modes(modes)
         _check(load().ms_init_modes(self._h, arr, nm))
 
-    def set_fields(self, ez, hx, hy, step: int = 0):
-        """Host FP64 arrays (numpy) in the full staggered layout."""
-        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ez, hx, hy)]
+    def set_fields(self, *fields, step: int = 0):
+        """Host FP64 arrays (numpy) in the full staggered layout (3 in 2D, 6 in 3D)."""
+        if len(fields) == len(self.shapes()) + 1:  # trailing positional step
+            *fields, step = fields
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in fields]
+        if len(arrs) != len(self.shapes()):
+            raise ValueError(f"expected {len(self.shapes())} arrays")
         for a, s in zip(arrs, self.shapes()):
             if a.shape != s:
                 raise ValueError(f"expected shape {s}, got {a.shape}")
@@ -202,15 +236,21 @@ class Grid:
         _check(load().ms_get_fields(self._h, _ptrs([a.ctypes.data for a in out])))
         return tuple(out)
 
-    def set_fields_device(self, ez, hx, hy, step: int = 0):
+    def set_fields_device(self, *fields, step: int = 0):
         """torch CUDA float64 tensors (contiguous) in the full staggered layout."""
-        for t, s in zip((ez, hx, hy), self.shapes()):
+        if len(fields) == len(self.shapes()) + 1:
+            *fields, step = fields
+        if len(fields) != len(self.shapes()):
+            raise ValueError(f"expected {len(self.shapes())} tensors")
+        for t, s in zip(fields, self.shapes()):
             if tuple(t.shape) != s or not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
                 raise ValueError("expected contiguous CUDA float64 tensors of the staggered shapes")
-        _check(load().ms_set_fields_device(self._h, _ptrs([t.data_ptr() for t in (ez, hx, hy)]), int(step)))
+        _check(load().ms_set_fields_device(self._h, _ptrs([t.data_ptr() for t in fields]), int(step)))
 
-    def get_fields_device(self, ez, hx, hy):
-        _check(load().ms_get_fields_device(self._h, _ptrs([t.data_ptr() for t in (ez, hx, hy)])))
+    def get_fields_device(self, *fields):
+        if len(fields) != len(self.shapes()):
+            raise ValueError(f"expected {len(self.shapes())} tensors")
+        _check(load().ms_get_fields_device(self._h, _ptrs([t.data_ptr() for t in fields])))
 
     def step(self):
         _check(load().ms_step(self._h))
@@ -245,9 +285,10 @@ class Grid:
 
     def error_vs_exact(self, modes):
         """(l2_abs, l2_rel, max_abs, sum_abs) of the state against the exact modes."""
-        arr, nm = _modes(modes)
+        arr, nm = _modes3(modes) if self.dim == 3 else _modes(modes)
         out = [ctypes.c_double() for _ in range(4)]
-        _check(load().ms_error_vs_exact(self._h, arr, nm, *[ctypes.byref(v) for v in out]))
+        fn = load().ms_error_vs_exact3 if self.dim == 3 else load().ms_error_vs_exact
+        _check(fn(self._h, arr, nm, *[ctypes.byref(v) for v in out]))
         return tuple(v.value for v in out)
 
     def step_profiled(self, cap: int = 512):

@@ -182,6 +182,7 @@ bool valid(ms_grid* g) { return g != nullptr && g->N > 0; }
 
 ms_status check_grid(ms_grid* g) {
   if (!valid(g)) return afail(MS_EINVAL, "invalid grid");
+  if (g->g3) return afail(MS_EUNSUPPORTED, "the reverse pass is implemented for 2D grids");
   if (g->desc.scheme != MS_SCHEME_C4) return afail(MS_EUNSUPPORTED, "the reverse pass is for the compact scheme");
   return adjoint_setup(g);
 }

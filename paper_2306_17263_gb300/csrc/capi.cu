@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "grid3d.cuh"
 #include "k_fp64.cuh"
 #include "k_mixed.cuh"
 #include "k_tiled.cuh"
@@ -158,6 +159,7 @@ ms_status step64(ms_grid* g) {
 }
 
 ms_status step_any(ms_grid* g) {
+  if (g->g3) return step3d(g);
   if (g->desc.precision == MS_FP64) return step64(g);
   int nl = 0;
   ms_status s = step_mixed(g, &nl);
@@ -314,8 +316,9 @@ void prof_mark(ms_grid* g, int kind, double bytes) {
 }
 
 const char* kernel_kind_name(int k) {
-  static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64",
-                                        "filter32", "pade32", "p1sweep32", "curl32", "solve32"};
+  static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64", "filter32",
+                                        "pade32", "p1sweep32", "curl32", "solve32", "filter3d64",
+                                        "pade3d64", "sweep3d64", "dfilt3d32", "band3d32", "sweep3d32"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }
 
@@ -328,8 +331,8 @@ const char* ms_last_error(void) { return g_last_error.c_str(); }
 
 ms_status ms_stability_limit(int dim, double* rmax) {
   if (!rmax) return fail(MS_EINVAL, "rmax is NULL");
-  if (dim != 2) return fail(dim == 3 ? MS_EUNSUPPORTED : MS_EINVAL, "dim must be 2");
-  *rmax = stability_limit_2d();
+  if (dim != 2 && dim != 3) return fail(MS_EINVAL, "dim must be 2 or 3");
+  *rmax = dim == 2 ? stability_limit_2d() : stability_limit_3d();
   return MS_OK;
 }
 
@@ -346,7 +349,8 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   if (!out) return fail(MS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!d) return fail(MS_EINVAL, "desc is NULL");
-  if (d->dim != 2) return fail(d->dim == 3 ? MS_EUNSUPPORTED : MS_EINVAL, "dim must be 2 (3 is reserved)");
+  if (d->dim == 3 && !shared64) return create_grid3d(d, out);
+  if (d->dim != 2) return fail(MS_EINVAL, "dim must be 2 or 3 (batches: 2)");
   if (d->n < 4 || d->n > 32768) return fail(MS_EINVAL, "n must be in [4, 32768]");
   if (!(d->z_imp > 0.0) || !std::isfinite(d->z_imp)) return fail(MS_EINVAL, "z_imp must be positive");
   if (!(d->r > 0.0) || !std::isfinite(d->r)) return fail(MS_EINVAL, "r must be positive");
@@ -448,6 +452,7 @@ ms_status ms_destroy(ms_grid* g) {
   free_graph(&g->graph1);
   free_graph(&g->graphk);
   adjoint_teardown(g);
+  destroy_grid3d(g);
   for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
   for (int k = 0; k < 2; ++k) {
     cudaFree(g->pade[k].d_w);
@@ -472,6 +477,7 @@ ms_status ms_destroy(ms_grid* g) {
 
 ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes) {
   if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3) return fail(MS_EINVAL, "3D grids take ms_init_modes3");
   if (nmodes < 0 || (nmodes > 0 && !modes)) return fail(MS_EINVAL, "invalid modes");
   for (int m = 0; m < nmodes; ++m)
     if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
@@ -485,6 +491,11 @@ ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes) {
 
 ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step) {
   if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  if (g->g3) {
+    MS_TRY(set_fields3d(g, comps, 0));
+    g->step = step;
+    return MS_OK;
+  }
   for (int f = 0; f < 3; ++f)
     if (!comps[f]) return fail(MS_EINVAL, "NULL component");
   MS_TRY(store_state(g, comps));
@@ -494,6 +505,7 @@ ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step
 
 ms_status ms_get_fields_device(ms_grid* g, double* const* comps) {
   if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  if (g->g3) return get_fields3d(g, comps, 0);
   for (int f = 0; f < 3; ++f) {
     if (!comps[f]) return fail(MS_EINVAL, "NULL component");
     const size_t n = g->sh[f].size();
@@ -507,6 +519,11 @@ ms_status ms_get_fields_device(ms_grid* g, double* const* comps) {
 
 ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
   if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  if (g->g3) {
+    MS_TRY(set_fields3d(g, comps, 1));
+    g->step = step;
+    return MS_OK;
+  }
   double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
   for (int f = 0; f < 3; ++f) {
     if (!comps[f]) return fail(MS_EINVAL, "NULL component");
@@ -519,6 +536,7 @@ ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
 
 ms_status ms_get_fields(ms_grid* g, double* const* comps) {
   if (!valid_grid(g) || !comps) return fail(MS_EINVAL, "invalid argument");
+  if (g->g3) return get_fields3d(g, comps, 1);
   double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
   const double* view[3];
   for (int f = 0; f < 3; ++f)
@@ -610,6 +628,7 @@ ms_status ms_launches_per_step(ms_grid* g, int* launches) {
 
 ms_status ms_energy(ms_grid* g, double* W) {
   if (!valid_grid(g) || !W) return fail(MS_EINVAL, "invalid argument");
+  if (g->g3) return fail(MS_EUNSUPPORTED, "energy is implemented for 2D grids");
   if (g->desc.scheme != MS_SCHEME_C4) return fail(MS_EUNSUPPORTED, "energy is defined for the compact scheme");
   // FP64 view of the state in scratch slots that the H increment does not touch
   double* tmp[3] = {nullptr, nullptr, nullptr};
@@ -663,6 +682,7 @@ ms_status ms_energy(ms_grid* g, double* W) {
 
 ms_status ms_divergence(ms_grid* g, double* norm) {
   if (!valid_grid(g) || !norm) return fail(MS_EINVAL, "invalid argument");
+  if (g->g3) return fail(MS_EUNSUPPORTED, "the divergence is implemented for 2D grids");
   double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
   const double* view[3];
   MS_TRY(state64(g, tmp, view));
@@ -686,6 +706,7 @@ ms_status ms_divergence(ms_grid* g, double* norm) {
 ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double* l2_abs, double* l2_rel,
                             double* max_abs, double* sum_abs) {
   if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3) return fail(MS_EINVAL, "3D grids take ms_error_vs_exact3");
   if (nmodes < 0 || (nmodes > 0 && !modes)) return fail(MS_EINVAL, "invalid modes");
   for (int m = 0; m < nmodes; ++m)
     if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
@@ -711,7 +732,7 @@ ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double
 
 ms_status ms_apply_op(ms_grid* g, int op, const double* const* in, double* const* out) {
   if (!valid_grid(g) || !in || !out) return fail(MS_EINVAL, "invalid argument");
-  if (g->desc.precision != MS_FP64 || g->desc.scheme != MS_SCHEME_C4)
+  if (g->g3 || g->desc.precision != MS_FP64 || g->desc.scheme != MS_SCHEME_C4)
     return fail(MS_EUNSUPPORTED, "operator entry points need an FP64 compact-scheme grid");
   int nl = 0;
   const double c1h2 = g->c1 * g->h * g->h;
@@ -820,6 +841,7 @@ ms_status ms_create_batch(const ms_grid_desc* d, const int* n, int count, ms_bat
   *out = nullptr;
   if (!d || !n) return fail(MS_EINVAL, "desc or n is NULL");
   if (count < 1 || count > (1 << 20)) return fail(MS_EINVAL, "count must be in [1, 2^20]");
+  if (d->dim != 2) return fail(MS_EUNSUPPORTED, "batches hold 2D cavities");
   if (d->precision != MS_FP32_REFINED || d->scheme != MS_SCHEME_C4)
     return fail(MS_EUNSUPPORTED, "batches run the compact scheme in MS_FP32_REFINED");
   int nmax = 0;

@@ -1,0 +1,858 @@
+// Three-dimensional compact scheme: six components on the staggered unit cube (Eq. "eq:meshes"),
+// boundary types of Table "tab:bc", Step 1 / Step 2 of Sec. 3.4 with
+//   curl_h = [[0, -d_z, d_y], [d_z, 0, -d_x], [-d_y, d_x, 0]],
+// the 7-point filter of Eq. "eq:ell" (Delta_h = D_xx + D_yy + D_zz) and the 19-point
+// P1 = -(Delta_h + (h^2/6) Upsilon_h) + kappa^2 (1 + 2/r^2), Upsilon_h = D_zz D_xx + D_yy D_zz
+// + D_xx D_yy (Def. "def:operatorsP").  Every component is Dirichlet (stored wall zeros) along
+// the axes on which it sits on nodes and Neumann (even ghosts) along its half-node axes.
+//
+// MS_FP64: one operator per launch in FP64 (filter, Pade band along one axis, Richardson sweep).
+// MS_FP32_REFINED: the arithmetic of the 2D FP32 path (k_mixed.cu) carried to 3D: float-float
+// state; per Pade term one kernel forms the float-float first differences of the source state
+// along the line and filters them (d = 12 beta delta + L delta, the filter commuting with the
+// difference under the ghost rules), one kernel applies the A^{-1} band (farthest taps first)
+// and accumulates the right-hand side; the solve is the Richardson iteration on 6 h^2 P1 with
+// the exact two-product residual and the split last correction.
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "grid3d.cuh"
+#include "k_fp64.cuh"
+#include "k_tiled.cuh"
+
+namespace ms {
+
+Shape3 field_shape3(int N, int c) {
+  Shape3 s;
+  for (int a = 0; a < 3; ++a) {
+    const bool node = (c < 3) ? (a != c % 3) : (a == c % 3);
+    s.bc[a] = node ? DIR : NEU;
+    s.n[a] = node ? N + 1 : N;
+  }
+  return s;
+}
+
+struct Grid3D {
+  Shape3 sh[6];
+  double* f64[6] = {};
+  float* hi[6] = {};
+  float* lo[6] = {};
+  double* s64[7] = {};  // FP64: G[3], R, sweep ping-pong [2], solve output; FP32 grids use [0], [1]
+  float* s32[4] = {};   // FP32: differences, R, sweep ping-pong [2]
+  size_t nmax = 0;      // points of the largest component
+};
+
+namespace {
+
+thread_local std::string g_err3;
+
+ms_status fail3(ms_status s, const std::string& m) {
+  set_last_error(m.c_str());
+  return s;
+}
+
+#define MS3_CUDA(call)                                                                            \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail3(MS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define MS3_TRY(expr)           \
+  do {                          \
+    ms_status s_ = (expr);      \
+    if (s_ != MS_OK) return s_; \
+  } while (0)
+
+__device__ __forceinline__ bool unk3(const Shape3& s, int i, int j, int k) {
+  return interior(s.bc[0], i, s.n[0]) && interior(s.bc[1], j, s.n[1]) && interior(s.bc[2], k, s.n[2]);
+}
+
+__device__ __forceinline__ size_t at3(const Shape3& s, int i, int j, int k) {
+  return ((size_t)k * s.n[1] + j) * s.n[0] + i;
+}
+
+dim3 grid3(const Shape3& s, dim3 blk) {
+  return dim3((s.n[0] + blk.x - 1) / blk.x, (s.n[1] + blk.y - 1) / blk.y, s.n[2]);
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 kernels
+
+// G = beta u + (1/12) L u, L = h^2 Delta_h (7 points), 0 at wall points.
+__global__ void k_filter3d64(const double* __restrict__ u, double* __restrict__ G, Shape3 s, double beta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= s.n[0] || j >= s.n[1]) return;
+  const size_t p = at3(s, i, j, k);
+  if (!unk3(s, i, j, k)) {
+    G[p] = 0.0;
+    return;
+  }
+  const double c = u[p];
+  const double lap = (u[at3(s, clampi(i - 1, s.n[0]), j, k)] + u[at3(s, clampi(i + 1, s.n[0]), j, k)]) +
+                     (u[at3(s, i, clampi(j - 1, s.n[1]), k)] + u[at3(s, i, clampi(j + 1, s.n[1]), k)]) +
+                     (u[at3(s, i, j, clampi(k - 1, s.n[2]))] + u[at3(s, i, j, clampi(k + 1, s.n[2]))]) - 6.0 * c;
+  G[p] = beta * c + lap * (1.0 / 12.0);
+}
+
+// Pade band along AXIS (App. A.1): out[o] (+)= scale * sum_t W(r, t) in[r - left + t], r = o - out_off,
+// at every point of the output component; the two other coordinates are shared with the input.
+template <int AXIS>
+__global__ void k_pade3d64(const double* __restrict__ in, double* __restrict__ out, Shape3 so, Shape3 si,
+                           const double* __restrict__ tab, int rows, int n_in, int left, int K, int B,
+                           int all_explicit, int out_off, double scale, int accumulate) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (x >= so.n[0] || y >= so.n[1]) return;
+  const size_t po = at3(so, x, y, z);
+  const int o = AXIS == 0 ? x : (AXIS == 1 ? y : z);
+  const int r = o - out_off;
+  double v = 0.0;
+  if (r >= 0 && r < rows) {
+    const double* w = pade_row_ptr(tab, r, rows, K, B, all_explicit);
+    size_t base, stride;
+    if (AXIS == 0) {
+      base = at3(si, 0, y, z);
+      stride = 1;
+    } else if (AXIS == 1) {
+      base = at3(si, x, 0, z);
+      stride = (size_t)si.n[0];
+    } else {
+      base = at3(si, x, y, 0);
+      stride = (size_t)si.n[0] * si.n[1];
+    }
+    const int k0 = r - left;
+    for (int t = 0; t < 2 * K + 2; ++t) {
+      const int kk = k0 + t;
+      if (kk < 0 || kk >= n_in) continue;
+      v = fma(w[t], in[base + (size_t)kk * stride], v);
+    }
+    v *= scale;
+  }
+  out[po] = accumulate ? out[po] + v : v;
+}
+
+// One Richardson sweep for P~ x = bscale b, P~ = h^2 P1 = c1h2 - (Lx + Ly + Lz) - (1/6)(LxLy + LyLz + LzLx)
+// (19 points); first != 0: x_in = 0.  upd != nullptr: upd += upd_scale * x_out.
+__global__ void k_sweep3d64(const double* __restrict__ b, const double* __restrict__ xin, double* __restrict__ xout,
+                            Shape3 s, double c1h2, double omega, double bscale, int first, double* __restrict__ upd,
+                            double upd_scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= s.n[0] || j >= s.n[1]) return;
+  const size_t p = at3(s, i, j, k);
+  if (!unk3(s, i, j, k)) {
+    xout[p] = 0.0;
+    return;
+  }
+  double x;
+  if (first) {
+    x = omega * bscale * b[p];
+  } else {
+    const int im = clampi(i - 1, s.n[0]), ip = clampi(i + 1, s.n[0]);
+    const int jm = clampi(j - 1, s.n[1]), jp = clampi(j + 1, s.n[1]);
+    const int km = clampi(k - 1, s.n[2]), kp = clampi(k + 1, s.n[2]);
+    auto X = [&](int a, int bb, int c) { return xin[at3(s, a, bb, c)]; };
+    auto LX = [&](int bb, int c) { return X(im, bb, c) - 2.0 * X(i, bb, c) + X(ip, bb, c); };
+    auto LY = [&](int a, int c) { return X(a, jm, c) - 2.0 * X(a, j, c) + X(a, jp, c); };
+    const double c0 = X(i, j, k);
+    const double lx = LX(j, k), ly = LY(i, k);
+    const double lz = X(i, j, km) - 2.0 * c0 + X(i, j, kp);
+    const double lxly = LX(jm, k) - 2.0 * lx + LX(jp, k);
+    const double lxlz = LX(j, km) - 2.0 * lx + LX(j, kp);
+    const double lylz = LY(i, km) - 2.0 * ly + LY(i, kp);
+    const double px = c1h2 * c0 - (lx + ly + lz) - (lxly + lylz + lxlz) * (1.0 / 6.0);
+    x = c0 + omega * (bscale * b[p] - px);
+  }
+  xout[p] = x;
+  if (upd) upd[p] += upd_scale * x;
+}
+
+__global__ void k_zero_walls3d64(double* __restrict__ u, Shape3 s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= s.n[0] || j >= s.n[1]) return;
+  if (!unk3(s, i, j, k)) u[at3(s, i, j, k)] = 0.0;
+}
+
+// Superposition of separable modes: out = sum_q coef[q] tx[q][i] ty[q][j] tz[q][k].
+__global__ void k_mode_field3(double* __restrict__ out, Shape3 s, const double* __restrict__ tx,
+                              const double* __restrict__ ty, const double* __restrict__ tz,
+                              const double* __restrict__ coef, int nm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= s.n[0] || j >= s.n[1]) return;
+  double v = 0.0;
+  for (int q = 0; q < nm; ++q)
+    v += coef[q] * tx[(size_t)q * s.n[0] + i] * ty[(size_t)q * s.n[1] + j] * tz[(size_t)q * s.n[2] + k];
+  out[at3(s, i, j, k)] = unk3(s, i, j, k) ? v : 0.0;
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32_REFINED kernels
+
+// (hi, lo) += (s_hi + s_lo) x with error-free transformations (two-product by FMA, Knuth two-sum).
+__device__ __forceinline__ void ff_add_scaled3(float& hi, float& lo, float x, float s_hi, float s_lo) {
+  const float p = __fmul_rn(s_hi, x);
+  float e = fmaf(s_hi, x, -p);
+  e = fmaf(s_lo, x, e);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float l = __fadd_rn(lo, __fadd_rn(err, e));
+  const float h2 = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h2, s));
+  hi = h2;
+}
+
+// Filtered first differences along AXIS of a float-float source, written at the points of the
+// destination component (output o = m + out_off for difference m = 0 .. M-1):
+//   delta_m = (hi_{m+1} - hi_m) + (lo_{m+1} - lo_m),  d = 12 beta delta + L delta,
+// L the 7-point stencil with these ghost rules: along the line, zero differences beyond the ends
+// for a source that is Neumann along it (even ghosts of u) and even differences for a source
+// that is Dirichlet along it; across the line, the source's own rule (wall zeros / even ghosts).
+template <int AXIS>
+__global__ void k_dfilt3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 ss, float* __restrict__ d,
+                            Shape3 sd, int out_off, int M, int ghost_even, float cb_hi, float cb_lo) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (x >= sd.n[0] || y >= sd.n[1]) return;
+  const size_t pd = at3(sd, x, y, z);
+  const int m = (AXIS == 0 ? x : (AXIS == 1 ? y : z)) - out_off;
+  if (!unk3(sd, x, y, z) || m < 0 || m >= M) {
+    d[pd] = 0.0f;
+    return;
+  }
+  // difference at along-index mm and source coordinates (a, b, c) of the two other axes
+  auto delta = [&](int mm, int a, int b, int c) -> float {
+    if (mm < 0 || mm >= M) {
+      if (!ghost_even) return 0.0f;
+      mm = mm < 0 ? 0 : M - 1;
+    }
+    int i0 = a, j0 = b, k0 = c, i1 = a, j1 = b, k1 = c;
+    if (AXIS == 0) { i0 = mm; i1 = mm + 1; }
+    if (AXIS == 1) { j0 = mm; j1 = mm + 1; }
+    if (AXIS == 2) { k0 = mm; k1 = mm + 1; }
+    const size_t p0 = at3(ss, i0, j0, k0), p1 = at3(ss, i1, j1, k1);
+    return (hi[p1] - hi[p0]) + (lo[p1] - lo[p0]);
+  };
+  const int cx = clampi(x - 1, ss.n[0]), dx = clampi(x + 1, ss.n[0]);
+  const int cy = clampi(y - 1, ss.n[1]), dy = clampi(y + 1, ss.n[1]);
+  const int cz = clampi(z - 1, ss.n[2]), dz = clampi(z + 1, ss.n[2]);
+  float v, a1, a2, b1, b2, c1, c2;
+  v = delta(m, x, y, z);
+  a1 = delta(m - 1, x, y, z);
+  a2 = delta(m + 1, x, y, z);
+  if (AXIS == 0) {
+    b1 = delta(m, x, cy, z); b2 = delta(m, x, dy, z);
+    c1 = delta(m, x, y, cz); c2 = delta(m, x, y, dz);
+  } else if (AXIS == 1) {
+    b1 = delta(m, cx, y, z); b2 = delta(m, dx, y, z);
+    c1 = delta(m, x, y, cz); c2 = delta(m, x, y, dz);
+  } else {
+    b1 = delta(m, cx, y, z); b2 = delta(m, dx, y, z);
+    c1 = delta(m, x, cy, z); c2 = delta(m, x, dy, z);
+  }
+  const float lap = (((a1 - v) + (a2 - v)) + ((b1 - v) + (b2 - v))) + ((c1 - v) + (c2 - v));
+  d[pd] = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+}
+
+// y = A^{-1} d along AXIS (explicit FP32 hi + lo band rows, taps summed farthest first), then
+// R (+)= sign * y at the unknowns of the destination component.
+template <int AXIS>
+__global__ void k_band3d32(const float* __restrict__ d, float* __restrict__ R, Shape3 sd, int out_off, int M,
+                           const float* __restrict__ whi, const float* __restrict__ wlo, int K, int B,
+                           int all_explicit, float sign, int accumulate) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (x >= sd.n[0] || y >= sd.n[1]) return;
+  const size_t pd = at3(sd, x, y, z);
+  const int r = (AXIS == 0 ? x : (AXIS == 1 ? y : z)) - out_off;
+  if (!unk3(sd, x, y, z) || r < 0 || r >= M) {
+    if (!accumulate) R[pd] = 0.0f;
+    return;
+  }
+  const size_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? (size_t)sd.n[0] : (size_t)sd.n[0] * sd.n[1]);
+  const float* drow = d + pd - (size_t)r * stride;  // drow[m * stride] = d_m
+  const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
+  const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
+  float acc = 0.0f, lo = 0.0f;
+  for (int dist = K + 1; dist >= 1; --dist) {
+    for (int side = 1; side >= -1; side -= 2) {
+      const int m = r + side * dist, t = m - r + K;
+      if (t < 0 || t > 2 * K + 1 || m < 0 || m >= M) continue;
+      const float dm = drow[(size_t)m * stride];
+      acc = fmaf(__ldg(wh + t), dm, acc);
+      lo = fmaf(__ldg(wl + t), dm, lo);
+    }
+  }
+  const float dc = drow[(size_t)r * stride];
+  lo = fmaf(__ldg(wl + K), dc, lo);
+  acc = fmaf(__ldg(wh + K), dc, acc + lo);
+  R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
+}
+
+// One sweep of the FP32 Richardson iteration on 6 h^2 P1 x = b (6h^2 P1 = d - 6(Lx + Ly + Lz)
+// - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo).  first: x = omega b.  last: the state
+// (hi, lo) += s x + s corr (two separate error-free additions) instead of writing x.
+__global__ void k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin, float* __restrict__ xout,
+                            Shape3 s, float d_hi, float d_lo, float omega, int first, int last,
+                            float* __restrict__ shi, float* __restrict__ slo, float s_hi, float s_lo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= s.n[0] || j >= s.n[1]) return;
+  const size_t p = at3(s, i, j, k);
+  if (!unk3(s, i, j, k)) {
+    if (!last) xout[p] = 0.0f;
+    return;
+  }
+  if (first) {
+    const float x1 = omega * b[p];
+    if (last) {
+      float h = shi[p], l = slo[p];
+      ff_add_scaled3(h, l, x1, s_hi, s_lo);
+      shi[p] = h;
+      slo[p] = l;
+    } else {
+      xout[p] = x1;
+    }
+    return;
+  }
+  const int im = clampi(i - 1, s.n[0]), ip = clampi(i + 1, s.n[0]);
+  const int jm = clampi(j - 1, s.n[1]), jp = clampi(j + 1, s.n[1]);
+  const int km = clampi(k - 1, s.n[2]), kp = clampi(k + 1, s.n[2]);
+  auto X = [&](int a, int bb, int c) { return xin[at3(s, a, bb, c)]; };
+  auto LX = [&](int bb, int c) {
+    const float v = X(i, bb, c);
+    return (X(im, bb, c) - v) + (X(ip, bb, c) - v);
+  };
+  auto LY = [&](int a, int c) {
+    const float v = X(a, j, c);
+    return (X(a, jm, c) - v) + (X(a, jp, c) - v);
+  };
+  const float x = X(i, j, k);
+  const float lx = LX(j, k), ly = LY(i, k);
+  const float lz = (X(i, j, km) - x) + (X(i, j, kp) - x);
+  const float lxly = (LX(jm, k) - lx) + (LX(jp, k) - lx);
+  const float lxlz = (LX(j, km) - lx) + (LX(j, kp) - lx);
+  const float lylz = (LY(i, km) - ly) + (LY(i, kp) - ly);
+  const float rest = -6.0f * ((lx + ly) + lz) - ((lxly + lylz) + lxlz);
+  const float ph = __fmul_rn(d_hi, x);
+  const float pl = fmaf(d_lo, x, fmaf(d_hi, x, -ph));
+  const float res = __fsub_rn(__fsub_rn(b[p], ph), pl) - rest;
+  const float corr = omega * res;
+  if (last) {
+    float h = shi[p], l = slo[p];
+    ff_add_scaled3(h, l, x, s_hi, s_lo);
+    ff_add_scaled3(h, l, corr, s_hi, s_lo);
+    shi[p] = h;
+    slo[p] = l;
+  } else {
+    xout[p] = x + corr;
+  }
+}
+
+__global__ void k_split3(const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const float h = (float)v[p];
+  hi[p] = h;
+  lo[p] = (float)(v[p] - (double)h);
+}
+
+__global__ void k_join3(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ v, size_t n) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  v[p] = (double)hi[p] + (double)lo[p];
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers
+
+const dim3 kBlk(32, 8, 1);
+
+void filter3d64(ms_grid* g, int c, const double* u, double* G) {
+  const Shape3& s = g->g3->sh[c];
+  k_filter3d64<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(u, G, s, g->beta);
+  prof_mark(g, KK_FILTER3D64, 16.0 * (double)s.size());
+}
+
+// out (+)= scale * delta_axis(in), in of component cs, out of component cd
+void pade3d64(ms_grid* g, int axis, int cs, int cd, const double* in, double* out, double scale, int accumulate) {
+  const Shape3& si = g->g3->sh[cs];
+  const Shape3& so = g->g3->sh[cd];
+  const int kind = (si.bc[axis] == NEU) ? HALF_TO_NODE : NODE_TO_HALF;
+  const PadeTable& t = g->pade[kind];
+  const int off = (kind == HALF_TO_NODE) ? 1 : 0;
+  const dim3 grd = grid3(so, kBlk);
+  if (axis == 0)
+    k_pade3d64<0><<<grd, kBlk, 0, g->stream>>>(in, out, so, si, t.d_w, t.rows, t.n_in, t.left, t.K, t.B,
+                                                t.all_explicit, off, scale, accumulate);
+  else if (axis == 1)
+    k_pade3d64<1><<<grd, kBlk, 0, g->stream>>>(in, out, so, si, t.d_w, t.rows, t.n_in, t.left, t.K, t.B,
+                                                t.all_explicit, off, scale, accumulate);
+  else
+    k_pade3d64<2><<<grd, kBlk, 0, g->stream>>>(in, out, so, si, t.d_w, t.rows, t.n_in, t.left, t.K, t.B,
+                                                t.all_explicit, off, scale, accumulate);
+  prof_mark(g, KK_PADE3D64, 8.0 * ((double)si.size() + (accumulate ? 2.0 : 1.0) * (double)so.size()));
+}
+
+// x = P1^{-1} b for component c; the last sweep adds upd_scale * x to upd.
+void solve3d64(ms_grid* g, int c, const double* b, double* upd, double upd_scale, int* nl) {
+  const Shape3& s = g->g3->sh[c];
+  const double c1h2 = g->c1 * g->h * g->h, om = 2.0 / (2.0 * c1h2 + 16.0 / 3.0), h2 = g->h * g->h;
+  double* buf[2] = {g->g3->s64[4], g->g3->s64[5]};
+  const double* xin = nullptr;
+  for (int k = 0; k < g->p1_sweeps; ++k) {
+    const bool last = (k == g->p1_sweeps - 1);
+    double* xo = last ? g->g3->s64[6] : buf[k & 1];
+    k_sweep3d64<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(b, xin, xo, s, c1h2, om, h2, k == 0, last ? upd : nullptr,
+                                                         upd_scale);
+    prof_mark(g, KK_SWEEP3D64, 8.0 * (double)s.size() * ((k == 0 ? 2 : 3) + (last ? 2 : 0)));
+    xin = xo;
+  }
+  *nl += g->p1_sweeps;
+}
+
+ms_status step3d64(ms_grid* g) {
+  Grid3D* G3 = g->g3;
+  int nl = 0;
+  double** G = G3->s64;  // G[0..2]
+  double* R = G3->s64[3];
+  const double s_he = g->kappa2 * g->Z / g->h, s_eh = g->kappa2 / (g->Z * g->h);
+  // Step 1: R_e = kappa^2 Z (d_{e+1} G_{e+2} - d_{e+2} G_{e+1}) on E_e, P1 E* = R, E += h_tau E*
+  for (int c = 0; c < 3; ++c) filter3d64(g, 3 + c, G3->f64[3 + c], G[c]);
+  nl += 3;
+  for (int e = 0; e < 3; ++e) {
+    const int p1 = (e + 1) % 3, p2 = (e + 2) % 3;
+    pade3d64(g, p1, 3 + p2, e, G[p2], R, s_he, 0);
+    pade3d64(g, p2, 3 + p1, e, G[p1], R, -s_he, 1);
+    nl += 2;
+    solve3d64(g, e, R, G3->f64[e], g->ht, &nl);
+  }
+  // Step 2: R_h = -(kappa^2/Z)(d_{h+1} G_{E,h+2} - d_{h+2} G_{E,h+1}) on H_h
+  for (int c = 0; c < 3; ++c) filter3d64(g, c, G3->f64[c], G[c]);
+  nl += 3;
+  for (int hc = 0; hc < 3; ++hc) {
+    const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
+    pade3d64(g, p1, p2, 3 + hc, G[p2], R, -s_eh, 0);
+    pade3d64(g, p2, p1, 3 + hc, G[p1], R, s_eh, 1);
+    nl += 2;
+    solve3d64(g, 3 + hc, R, G3->f64[3 + hc], g->ht, &nl);
+  }
+  g->launches_per_step = nl;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("3D FP64 step: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+// FP32_REFINED: one Pade term y = A^{-1} D1 G~ of source component cs along axis, added with
+// `sign` into R on component cd.
+void term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, float sign, int accumulate) {
+  Grid3D* G3 = g->g3;
+  const Shape3& ss = G3->sh[cs];
+  const Shape3& sd = G3->sh[cd];
+  const int kind = (ss.bc[axis] == NEU) ? HALF_TO_NODE : NODE_TO_HALF;
+  const PadeTable& t = g->pade32[kind];
+  const int off = (kind == HALF_TO_NODE) ? 1 : 0;
+  const int ghost_even = (ss.bc[axis] == DIR);
+  float* d = G3->s32[0];
+  float* R = G3->s32[1];
+  const dim3 grd = grid3(sd, kBlk);
+  if (axis == 0)
+    k_dfilt3d32<0><<<grd, kBlk, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, d, sd, off, t.M, ghost_even, cb_hi, cb_lo);
+  else if (axis == 1)
+    k_dfilt3d32<1><<<grd, kBlk, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, d, sd, off, t.M, ghost_even, cb_hi, cb_lo);
+  else
+    k_dfilt3d32<2><<<grd, kBlk, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, d, sd, off, t.M, ghost_even, cb_hi, cb_lo);
+  // state hi + lo in, d out
+  prof_mark(g, KK_DFILT3D32, 4.0 * (2.0 * (double)ss.size() + (double)sd.size()));
+  if (axis == 0)
+    k_band3d32<0><<<grd, kBlk, 0, g->stream>>>(d, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign,
+                                                accumulate);
+  else if (axis == 1)
+    k_band3d32<1><<<grd, kBlk, 0, g->stream>>>(d, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign,
+                                                accumulate);
+  else
+    k_band3d32<2><<<grd, kBlk, 0, g->stream>>>(d, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign,
+                                                accumulate);
+  // d in, R out (read too when accumulating)
+  prof_mark(g, KK_BAND3D32, 4.0 * (double)sd.size() * (accumulate ? 3.0 : 2.0));
+}
+
+void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_hi, float s_lo, int S, int* nl) {
+  Grid3D* G3 = g->g3;
+  const Shape3& s = G3->sh[c];
+  const float* b = G3->s32[1];
+  float* buf[2] = {G3->s32[2], G3->s32[3]};
+  const float* xin = nullptr;
+  for (int k = 0; k < S; ++k) {
+    const bool last = (k == S - 1);
+    float* xo = buf[k & 1];
+    k_sweep3d32<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, k == 0, last, G3->hi[c],
+                                                         G3->lo[c], s_hi, s_lo);
+    prof_mark(g, KK_SWEEP3D32, 4.0 * (double)s.size() * ((k == 0 ? 1.0 : 2.0) + (last ? 4.0 : 1.0)));
+    xin = xo;
+  }
+  *nl += S;
+}
+
+ms_status step3d32(ms_grid* g) {
+  const MixedConsts k = mixed_consts(g);
+  int nl = 0;
+  for (int e = 0; e < 3; ++e) {
+    const int p1 = (e + 1) % 3, p2 = (e + 2) % 3;
+    term3d32(g, p1, 3 + p2, e, k.cb_hi, k.cb_lo, 1.0f, 0);
+    term3d32(g, p2, 3 + p1, e, k.cb_hi, k.cb_lo, -1.0f, 1);
+    nl += 4;
+    solve3d32(g, e, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo, k.S, &nl);
+  }
+  for (int hc = 0; hc < 3; ++hc) {
+    const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
+    term3d32(g, p1, p2, 3 + hc, k.cb_hi, k.cb_lo, -1.0f, 0);
+    term3d32(g, p2, p1, 3 + hc, k.cb_hi, k.cb_lo, 1.0f, 1);
+    nl += 4;
+    solve3d32(g, 3 + hc, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo, k.S, &nl);
+  }
+  g->launches_per_step = nl;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("3D FP32 step: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+// Largest |h_tau lambda|^2 / 4 over the 3D Fourier symbol at CFL number r (units h = 1).
+double max_amp2_3d(double r) {
+  const double k2 = 24.0 / (r * r), beta = 1.0 + 2.0 / (r * r);
+  const int n = 48;
+  std::vector<double> mu(n), dd(n);
+  for (int a = 0; a < n; ++a) {
+    const double t = M_PI * (a + 1) / n;
+    mu[a] = 4.0 * std::sin(t / 2) * std::sin(t / 2);
+    const double d = 2.0 * std::sin(t / 2) * 12.0 / (11.0 + std::cos(t));
+    dd[a] = d * d;
+  }
+  double worst = 0.0;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int c = 0; c < n; ++c) {
+        const double s1 = mu[a] + mu[b] + mu[c], s2 = mu[a] * mu[b] + mu[b] * mu[c] + mu[c] * mu[a];
+        const double gg = k2 * (beta - s1 / 12.0) / (k2 * beta + s1 - s2 / 6.0);
+        const double v = r * r * gg * gg * (dd[a] + dd[b] + dd[c]);
+        if (v > worst) worst = v;
+      }
+  return worst;
+}
+
+template <typename T>
+ms_status alloc3(T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 256);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail3(MS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return MS_OK;
+}
+
+ms_status store3(ms_grid* g, int c, const double* dev) {
+  Grid3D* G3 = g->g3;
+  const Shape3& s = G3->sh[c];
+  if (g->desc.precision == MS_FP64) {
+    if (dev != G3->f64[c])
+      MS3_CUDA(cudaMemcpyAsync(G3->f64[c], dev, s.size() * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    k_zero_walls3d64<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(G3->f64[c], s);
+  } else {
+    double* tmp = G3->s64[0];
+    if (dev != tmp) MS3_CUDA(cudaMemcpyAsync(tmp, dev, s.size() * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    k_zero_walls3d64<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(tmp, s);
+    k_split3<<<(unsigned)((s.size() + 255) / 256), 256, 0, g->stream>>>(tmp, G3->hi[c], G3->lo[c], s.size());
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("store: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+// FP64 view of component c: the FP64 array, or hi + lo joined into dst.
+const double* view3(ms_grid* g, int c, double* dst) {
+  Grid3D* G3 = g->g3;
+  if (g->desc.precision == MS_FP64) return G3->f64[c];
+  const size_t n = G3->sh[c].size();
+  k_join3<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(G3->hi[c], G3->lo[c], dst, n);
+  return dst;
+}
+
+// Exact modes (component c) into out, t_E / t_H (see the oracle's mode: sine on node axes,
+// cosine on half axes; H = -(1/(Z omega)) curl(E shape) sin(omega t)).
+ms_status exact3(ms_grid* g, const ms_mode3* modes, int nm, double tE, double tH, int c, double* out) {
+  const int N = g->N;
+  const Shape3& s = g->g3->sh[c];
+  std::vector<double> host;
+  const size_t ox = 0, oy = (size_t)nm * s.n[0], oz = oy + (size_t)nm * s.n[1], oc = oz + (size_t)nm * s.n[2];
+  host.assign(oc + nm, 0.0);
+  auto sin_node = [&](int k, int i) {
+    if (i == 0 || i == N) return 0.0;
+    long q = ((long)k * i) % (2L * N);
+    return std::sin(M_PI * (double)q / N);
+  };
+  auto cos_half = [&](int k, int i) {
+    long q = ((long)k * (2L * i + 1)) % (4L * N);
+    return std::cos(M_PI * (double)q / (2.0 * N));
+  };
+  for (int q = 0; q < nm; ++q) {
+    const int kk[3] = {modes[q].m, modes[q].n, modes[q].p};
+    const size_t off[3] = {ox, oy, oz};
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < s.n[a]; ++i)
+        host[off[a] + (size_t)q * s.n[a] + i] = (s.bc[a] == DIR) ? sin_node(kk[a], i) : cos_half(kk[a], i);
+    const double a = M_PI * kk[0], b = M_PI * kk[1], cc = M_PI * kk[2];
+    const double w = std::sqrt(a * a + b * b + cc * cc);
+    const double Ax = modes[q].ax, Ay = modes[q].ay, Az = modes[q].az;
+    const double ce = std::cos(w * tE), sh = -std::sin(w * tH) / (g->Z * w);
+    const double amp[6] = {Ax * ce, Ay * ce, Az * ce, sh * (Az * b - Ay * cc), sh * (Ax * cc - Az * a),
+                           sh * (Ay * a - Ax * b)};
+    host[oc + q] = amp[c];
+  }
+  if (host.size() > g->modetab_cap) {
+    cudaFree(g->d_modetab);
+    g->d_modetab = nullptr;
+    g->modetab_cap = 0;
+    MS3_TRY(alloc3(&g->d_modetab, host.size()));
+    g->modetab_cap = host.size();
+  }
+  MS3_CUDA(cudaMemcpyAsync(g->d_modetab, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  k_mode_field3<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(out, s, g->d_modetab + ox, g->d_modetab + oy,
+                                                         g->d_modetab + oz, g->d_modetab + oc, nm);
+  MS3_CUDA(cudaGetLastError());
+  MS3_CUDA(cudaStreamSynchronize(g->stream));  // the host table is released on return
+  return MS_OK;
+}
+
+ms_status check_modes3(const ms_mode3* modes, int nm) {
+  if (nm < 0 || (nm > 0 && !modes)) return fail3(MS_EINVAL, "invalid modes");
+  for (int q = 0; q < nm; ++q) {
+    const ms_mode3& m = modes[q];
+    if (m.m < 1 || m.n < 1 || m.p < 1) return fail3(MS_EINVAL, "mode indices must be >= 1");
+    const double dot = m.ax * m.m + m.ay * m.n + m.az * m.p;
+    const double scale = std::fabs(m.ax * m.m) + std::fabs(m.ay * m.n) + std::fabs(m.az * m.p);
+    if (std::fabs(dot) > 1e-12 * (scale > 0 ? scale : 1.0))
+      return fail3(MS_EINVAL, "mode polarisation must satisfy A . (m, n, p) = 0 (divergence-free E)");
+  }
+  return MS_OK;
+}
+
+}  // namespace
+
+double stability_limit_3d() {
+  static double cached = 0.0;
+  if (cached > 0.0) return cached;
+  double lo = 0.3, hi = 1.0;
+  for (int it = 0; it < 50; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (max_amp2_3d(mid) <= 4.0) lo = mid;
+    else hi = mid;
+  }
+  cached = lo;
+  return cached;
+}
+
+ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
+  if (d->n < 4 || d->n > 512) return fail3(MS_EINVAL, "3D grids need 4 <= n <= 512");
+  if (!(d->z_imp > 0.0) || !std::isfinite(d->z_imp)) return fail3(MS_EINVAL, "z_imp must be positive");
+  if (!(d->r > 0.0) || !std::isfinite(d->r)) return fail3(MS_EINVAL, "r must be positive");
+  if (d->precision != MS_FP64 && d->precision != MS_FP32_REFINED) return fail3(MS_EINVAL, "unknown precision");
+  if (d->closure != MS_CLOSURE_PAPER && d->closure != MS_CLOSURE_REFLECT) return fail3(MS_EINVAL, "unknown closure");
+  if (d->scheme != MS_SCHEME_C4) return fail3(MS_EUNSUPPORTED, "3D grids run the compact scheme only");
+  const double rmax = stability_limit_3d();
+  if (d->r >= rmax) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "r = %.6g is at or above the stability limit %.6g of the 3D scheme", d->r, rmax);
+    return fail3(MS_ECFL, buf);
+  }
+  ms_grid* g = new ms_grid();
+  g->g3 = new Grid3D();
+  Grid3D* G3 = g->g3;
+  g->desc = *d;
+  g->N = d->n;
+  g->Z = d->z_imp;
+  g->h = 1.0 / d->n;
+  g->ht = d->r * g->h;
+  g->kappa2 = 24.0 / (g->ht * g->ht);
+  g->beta = 1.0 + g->kappa2 * g->h * g->h / 12.0;
+  g->c1 = g->kappa2 * g->beta;
+  auto cleanup = [&](ms_status s) {
+    ms_destroy(g);
+    return s;
+  };
+  for (int c = 0; c < 6; ++c) {
+    G3->sh[c] = field_shape3(g->N, c);
+    if (G3->sh[c].size() > G3->nmax) G3->nmax = G3->sh[c].size();
+  }
+  if (d->stream) {
+    g->stream = (cudaStream_t)d->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail3(MS_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    g->own_stream = true;
+  }
+  std::string err;
+  const double c1h2 = g->c1 * g->h * g->h;
+  const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
+  ms_status s = MS_OK;
+  if (d->precision == MS_FP64) {
+    for (int kind = 0; kind < 2 && s == MS_OK; ++kind) {
+      const int M = (kind == HALF_TO_NODE) ? g->N - 1 : g->N;
+      PadeTable& t = g->pade[kind];
+      if (build_pade_table(M, d->closure, kind, 1e-18, &t, &err) != 0) return cleanup(fail3(MS_EINVAL, err));
+      s = alloc3(&t.d_w, t.w.size());
+      if (s == MS_OK && cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = fail3(MS_ECUDA, "copy of Pade tables failed");
+    }
+    int S = (int)std::ceil(std::log(1e-17) / std::log(rho));
+    g->p1_sweeps = S < 1 ? 1 : (S > 64 ? 64 : S);
+    for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->f64[c], G3->sh[c].size());
+    for (int k = 0; k < 7 && s == MS_OK; ++k) s = alloc3(&G3->s64[k], G3->nmax);
+  } else {
+    for (int kind = 0; kind < 2 && s == MS_OK; ++kind) {
+      const int M = (kind == HALF_TO_NODE) ? g->N - 1 : g->N;
+      PadeTable& t = g->pade32[kind];
+      if (build_pade_table(M, d->closure, kind, 1e-12, &t, &err, /*of_differences=*/true) != 0)
+        return cleanup(fail3(MS_EINVAL, err));
+      std::vector<float> whi(t.w.size()), wlo(t.w.size());
+      for (size_t q = 0; q < t.w.size(); ++q) {
+        whi[q] = (float)t.w[q];
+        wlo[q] = (float)(t.w[q] - (double)whi[q]);
+      }
+      s = alloc3(&t.d_whi, whi.size());
+      if (s == MS_OK) s = alloc3(&t.d_wlo, wlo.size());
+      if (s == MS_OK && (cudaMemcpy(t.d_whi, whi.data(), whi.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemcpy(t.d_wlo, wlo.data(), wlo.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess))
+        s = fail3(MS_ECUDA, "copy of FP32 Pade tables failed");
+    }
+    int S = (int)std::ceil(std::log(1e-10) / std::log(rho));
+    g->p1_sweeps32 = S < 1 ? 1 : S;
+    if (g->p1_sweeps32 > 8) s = fail3(MS_EUNSUPPORTED, "CFL number too close to the stability limit for the FP32 solve");
+    for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->hi[c], G3->sh[c].size());
+    for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->lo[c], G3->sh[c].size());
+    for (int k = 0; k < 4 && s == MS_OK; ++k) s = alloc3(&G3->s32[k], G3->nmax);
+    for (int k = 0; k < 2 && s == MS_OK; ++k) s = alloc3(&G3->s64[k], G3->nmax);
+  }
+  if (s == MS_OK) s = alloc3(&g->d_result, 8);
+  if (s == MS_OK) {
+    const int b = reduce_blocks(G3->nmax);
+    s = alloc3(&g->d_partial, (size_t)b * 4);
+    g->partial_cap = b;
+  }
+  if (s != MS_OK) return cleanup(s);
+  for (int c = 0; c < 6; ++c) {
+    const size_t n = G3->sh[c].size();
+    if (G3->f64[c]) cudaMemsetAsync(G3->f64[c], 0, n * sizeof(double), g->stream);
+    if (G3->hi[c]) cudaMemsetAsync(G3->hi[c], 0, n * sizeof(float), g->stream);
+    if (G3->lo[c]) cudaMemsetAsync(G3->lo[c], 0, n * sizeof(float), g->stream);
+  }
+  for (int k = 0; k < 7; ++k)
+    if (G3->s64[k]) cudaMemsetAsync(G3->s64[k], 0, G3->nmax * sizeof(double), g->stream);
+  for (int k = 0; k < 4; ++k)
+    if (G3->s32[k]) cudaMemsetAsync(G3->s32[k], 0, G3->nmax * sizeof(float), g->stream);
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cleanup(fail3(MS_ECUDA, std::string("create: ") + cudaGetErrorString(e)));
+  *out = g;
+  return MS_OK;
+}
+
+void destroy_grid3d(ms_grid* g) {
+  Grid3D* G3 = g->g3;
+  if (!G3) return;
+  for (int c = 0; c < 6; ++c) {
+    cudaFree(G3->f64[c]);
+    cudaFree(G3->hi[c]);
+    cudaFree(G3->lo[c]);
+  }
+  for (int k = 0; k < 7; ++k) cudaFree(G3->s64[k]);
+  for (int k = 0; k < 4; ++k) cudaFree(G3->s32[k]);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(g->pade32[k].d_whi);
+    cudaFree(g->pade32[k].d_wlo);
+    g->pade32[k].d_whi = g->pade32[k].d_wlo = nullptr;
+  }
+  delete G3;
+  g->g3 = nullptr;
+}
+
+ms_status step3d(ms_grid* g) { return g->desc.precision == MS_FP64 ? step3d64(g) : step3d32(g); }
+
+ms_status set_fields3d(ms_grid* g, const double* const* comps, int host) {
+  for (int c = 0; c < 6; ++c)
+    if (!comps[c]) return fail3(MS_EINVAL, "NULL component");
+  Grid3D* G3 = g->g3;
+  for (int c = 0; c < 6; ++c) {
+    const size_t n = G3->sh[c].size();
+    if (host) {
+      double* tmp = G3->s64[0];
+      MS3_CUDA(cudaMemcpyAsync(tmp, comps[c], n * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+      MS3_TRY(store3(g, c, tmp));
+    } else {
+      MS3_TRY(store3(g, c, comps[c]));
+    }
+  }
+  if (host) MS3_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status get_fields3d(ms_grid* g, double* const* comps, int host) {
+  for (int c = 0; c < 6; ++c)
+    if (!comps[c]) return fail3(MS_EINVAL, "NULL component");
+  Grid3D* G3 = g->g3;
+  for (int c = 0; c < 6; ++c) {
+    const size_t n = G3->sh[c].size();
+    if (g->desc.precision == MS_FP64) {
+      MS3_CUDA(cudaMemcpyAsync(comps[c], G3->f64[c], n * sizeof(double),
+                               host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream));
+    } else if (host) {
+      const double* v = view3(g, c, G3->s64[0]);
+      MS3_CUDA(cudaMemcpyAsync(comps[c], v, n * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+      MS3_CUDA(cudaStreamSynchronize(g->stream));  // s64[0] is reused by the next component
+    } else {
+      view3(g, c, comps[c]);
+    }
+  }
+  MS3_CUDA(cudaGetLastError());
+  if (host) MS3_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+}  // namespace ms
+
+using namespace ms;
+
+extern "C" {
+
+ms_status ms_init_modes3(ms_grid* g, const ms_mode3* modes, int nmodes) {
+  if (!g || !g->g3) return fail3(MS_EINVAL, "ms_init_modes3 needs a 3D grid");
+  MS3_TRY(check_modes3(modes, nmodes));
+  double* tmp = g->g3->s64[1];
+  for (int c = 0; c < 6; ++c) {
+    MS3_TRY(exact3(g, modes, nmodes, 0.0, 0.5 * g->ht, c, tmp));
+    MS3_TRY(store3(g, c, tmp));
+  }
+  g->step = 0;
+  MS3_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status ms_error_vs_exact3(ms_grid* g, const ms_mode3* modes, int nmodes, double* l2_abs, double* l2_rel,
+                             double* max_abs, double* sum_abs) {
+  if (!g || !g->g3) return fail3(MS_EINVAL, "ms_error_vs_exact3 needs a 3D grid");
+  MS3_TRY(check_modes3(modes, nmodes));
+  Grid3D* G3 = g->g3;
+  const double tE = g->step * g->ht, tH = (g->step + 0.5) * g->ht;
+  for (int c = 0; c < 6; ++c) {
+    const size_t n = G3->sh[c].size();
+    MS3_TRY(exact3(g, modes, nmodes, tE, tH, c, G3->s64[1]));
+    const double* v = view3(g, c, G3->s64[0]);
+    launch_err_reduce(v, G3->s64[1], n, g->d_partial, reduce_blocks(n), g->d_result, c > 0, g->stream);
+  }
+  double r[4];
+  MS3_CUDA(cudaMemcpyAsync(r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  MS3_CUDA(cudaStreamSynchronize(g->stream));
+  const double h3 = g->h * g->h * g->h;
+  if (l2_abs) *l2_abs = std::sqrt(h3 * r[0]);
+  if (l2_rel) *l2_rel = r[1] > 0.0 ? std::sqrt(r[0] / r[1]) : 0.0;
+  if (max_abs) *max_abs = r[2];
+  if (sum_abs) *sum_abs = r[3];
+  return MS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,28 @@
+// Three-dimensional grids (six components) behind the same C ABI (grid3d.cu).
+#pragma once
+
+#include "ms_internal.h"
+
+namespace ms {
+
+// One 3D component in the full staggered layout [z][y][x] (Eq. "eq:meshes"): n[a] points and the
+// boundary type bc[a] along axis a (Table "tab:bc": Dirichlet on node axes, Neumann on half axes).
+struct Shape3 {
+  int n[3];
+  int bc[3];
+  __host__ __device__ size_t size() const { return (size_t)n[0] * n[1] * n[2]; }
+};
+Shape3 field_shape3(int N, int c);
+
+struct Grid3D;
+
+// 3D counterparts of the grid life cycle and state access, dispatched from capi.cu.
+ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out);
+void destroy_grid3d(ms_grid* g);
+ms_status step3d(ms_grid* g);
+// comps: 6 arrays (E_x, E_y, E_z, H_x, H_y, H_z); host != 0: host memory, synchronous.
+ms_status set_fields3d(ms_grid* g, const double* const* comps, int host);
+ms_status get_fields3d(ms_grid* g, double* const* comps, int host);
+double stability_limit_3d();
+
+}  // namespace ms

@@ -60,6 +60,7 @@ struct Graph {
 enum KernelKind {
   KK_FILTER64 = 0, KK_PADE64 = 1, KK_P1SWEEP64 = 2, KK_YEE64 = 3,
   KK_FILTER32 = 4, KK_PADE32 = 5, KK_P1SWEEP32 = 6, KK_CURL32 = 7, KK_SOLVE32 = 8,
+  KK_FILTER3D64 = 9, KK_PADE3D64 = 10, KK_SWEEP3D64 = 11, KK_DFILT3D32 = 12, KK_BAND3D32 = 13, KK_SWEEP3D32 = 14,
   KK_COUNT
 };
 const char* kernel_kind_name(int k);
@@ -77,6 +78,7 @@ struct Prof {
 
 struct ms_grid;
 namespace ms {
+struct Grid3D;  // six-component state of a 3D grid (grid3d.cu)
 // Record an event after a launch of the given kind when the grid is being profiled.
 void prof_mark(ms_grid* g, int kind, double bytes = 0.0);
 // Set the message returned by ms_last_error on this thread.
@@ -122,5 +124,8 @@ struct ms_grid {
   ms::PadeTable padeT[2];
   double* adj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ms::Graph adj_graph1, adj_graphk;
+
+  // 3D grids (desc.dim == 3): components, scratch and kernels live in grid3d.cu
+  ms::Grid3D* g3 = nullptr;
   ms::Prof prof;
 };

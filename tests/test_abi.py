@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import paper_2306_17263_gb300 as pkg
-from closed_forms import mode_step_matrix
+from closed_forms import mode_step_matrix, mode_step_matrix3
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "maxwell4.h")
 
@@ -35,7 +35,8 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("kw,status", [
-    (dict(dim=1), -1), (dict(dim=3), -7), (dict(n=3), -1), (dict(n=40000), -1), (dict(z_imp=0.0), -1),
+    (dict(dim=1), -1), (dict(dim=3, r=0.58), -2), (dict(dim=3, n=600, r=0.4), -1),
+    (dict(dim=3, r=0.4, scheme=1), -7), (dict(dim=3, r=0.4, precision=7), -1), (dict(n=3), -1), (dict(n=40000), -1), (dict(z_imp=0.0), -1),
     (dict(r=-0.1), -1), (dict(r=float("nan")), -1), (dict(precision=5), -1), (dict(closure=9), -1),
     (dict(scheme=4), -1), (dict(r=0.70), -2), (dict(r=1 / math.sqrt(2)), -2),
     (dict(scheme=1, r=0.75), -2), (dict(scheme=1, precision=1), -7),
@@ -67,5 +68,18 @@ def test_stability_limit_matches_mode_recurrence():
     def amp(r):
         return max(np.max(np.abs(np.linalg.eigvals(mode_step_matrix(N, r, kx, ky))))
                    for kx in (N - 1, N - 2) for ky in (N - 1, N - 2))
+    assert amp(rmax * 0.999) < 1 + 1e-9
+    assert amp(rmax * 1.003) > 1 + 1e-6
+
+
+def test_stability_limit_3d_matches_mode_recurrence():
+    """3D: the exported limit agrees with the closed-form 6x6 per-mode step matrix."""
+    rmax = pkg.stability_limit(3)
+    assert 5 / (6 * math.sqrt(3)) < rmax < 0.6
+    N = 512
+
+    def amp(r):
+        return max(np.max(np.abs(np.linalg.eigvals(mode_step_matrix3(N, r, a, b, c))))
+                   for a in (N - 1, N - 3) for b in (N - 1, N - 3) for c in (N - 1, N - 3))
     assert amp(rmax * 0.999) < 1 + 1e-9
     assert amp(rmax * 1.003) > 1 + 1e-6

@@ -89,3 +89,38 @@ def config5(seed: int = 0, n: int = 1024, steps: int = 2000):
     return dict(n=n, r=0.5, steps=steps, ell=0.05,
                 ez0_seed=int(seeds[0]), direction_seeds=[int(x) for x in seeds[2:18]],
                 target_modes=[(int(a), int(b), float(c)) for (a, b), c in zip(mn, amp)])
+
+
+def mode3(m: int, n: int, p: int, amp: float):
+    """3D cavity mode with polarisation amp (-n, m, 0) / max(m, n) (divergence-free; the largest
+    component has magnitude |amp|)."""
+    s = amp / max(m, n)
+    return (int(m), int(n), int(p), -n * s, m * s, 0.0)
+
+
+def config3(seed: int = 0):
+    """3D six-component cavity, 256^3 cells, r = 0.4, 500 steps: mode (2, 3, 1) with unit
+    amplitude plus one mode with (m, n, p) uniform in [1, 16] and an N(0, 1) amplitude."""
+    rng = np.random.default_rng(seed)
+    mnp = rng.integers(1, 17, size=3)
+    amp = float(rng.standard_normal())
+    return dict(n=256, r=0.4, steps=500, modes=[mode3(2, 3, 1, 1.0), mode3(*[int(v) for v in mnp], amp)])
+
+
+def random_fields3(n: int, seed: int):
+    """Random 3D staggered fields (E_x, E_y, E_z, H_x, H_y, H_z), [z][y][x], with zero values at
+    the walls of every component's node axes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(6):
+        node = [(a != c % 3) if c < 3 else (a == c % 3) for a in range(3)]
+        nx, ny, nz = (n + 1 if q else n for q in node)
+        f = rng.standard_normal((nz, ny, nx))
+        if node[0]:
+            f[:, :, 0] = f[:, :, -1] = 0.0
+        if node[1]:
+            f[:, 0, :] = f[:, -1, :] = 0.0
+        if node[2]:
+            f[0, :, :] = f[-1, :, :] = 0.0
+        out.append(f)
+    return out
