@@ -127,6 +127,8 @@ def measured_peaks():
 KIND_SOURCES = {
     "curl32": ["k_tiled.cu", "k_tiled.cuh"], "solve32": ["k_tiled.cu", "k_tiled.cuh"],
     "filter64": ["k_fp64.cu", "k_fp64.cuh"], "pade64": ["k_fp64.cu", "k_fp64.cuh"],
+    "dfilt3d32": ["grid3d.cu", "grid3d.cuh"], "band3d32": ["grid3d.cu", "grid3d.cuh"],
+    "sweep3d32": ["grid3d.cu", "grid3d.cuh"],
     "p1sweep64": ["k_fp64.cu", "k_fp64.cuh"], "yee64": ["k_fp64.cu", "k_fp64.cuh"],
 }
 
@@ -254,6 +256,37 @@ def reverse_leg(pkg, torch):
             "forward_value": n * n * K / (fwd_ms * 1e-3), "reverse_value": n * n * K / (rev_ms * 1e-3),
             "unit": "cell-updates/s", "finite": ok,
             "memory": "no trajectory stored: the step is linear, the reverse pass needs only the final adjoint"}
+
+
+def leg_3d(pkg, torch):
+    """3D six-component workload: 256^3 cells, r = 0.4, 500 steps, 2 seeded modes, FP32_REFINED
+    (every step timed with CUDA events; the 6-component state, 0.8 GB, exceeds L2), plus 20 FP64
+    steps for the FP64-vs-refined comparison."""
+    c = workloads.config3()
+    n, r, modes, K = c["n"], c["r"], c["modes"], c["steps"]
+    out = {"workload": "3D PEC cube 256^3 cells, modes (2,3,1) + one seeded mode (indices in [1,16]), r=0.4",
+           "unit": "cell-updates/s", "l2": "state 0.8 GB > L2; no flush"}
+    for prec, steps, key in ((pkg.FP32_REFINED, K, "fp32_refined"), (pkg.FP64, 20, "fp64")):
+        g = pkg.Grid(n, r, precision=prec, dim=3, stream="torch")
+        g.init_modes(modes)
+        for _ in range(3):
+            g.step_profiled()
+        g.init_modes(modes)
+        total, per = 0.0, {}
+        for _ in range(steps):
+            for kind, ms, nbytes in g.step_profiled():
+                total += ms
+                a = per.setdefault(kind, [0, 0.0, 0.0])
+                a[0] += 1
+                a[1] += ms
+                a[2] += nbytes
+        l2_abs, l2_rel, _, _ = g.error_vs_exact(modes)
+        kinds = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / total, "GBps": v[2] / (v[1] * 1e-3) / 1e9}
+                 for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])}
+        out[key] = {"steps": steps, "ms_per_step": total / steps, "value": n ** 3 * steps / (total * 1e-3),
+                    "l2_abs": l2_abs, "l2_rel": l2_rel, "launches_per_step": g.launches_per_step, "kernels": kinds}
+        g.close()
+    return out
 
 
 def yee_leg(pkg, torch, modes, r, c4_l2_abs, c4_value, T=4000 * 0.5 / 2048):
@@ -420,6 +453,7 @@ def run_ours(args, ws, rank, local):
             g64.close()
         line["batched"] = batched_leg(pkg, torch)
         line["reverse_pass"] = reverse_leg(pkg, torch)
+        line["three_d"] = leg_3d(pkg, torch)
         line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, l2_abs, value)
         # CPU oracle on a bounded sample of the workload (rank 0, one core)
         v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
