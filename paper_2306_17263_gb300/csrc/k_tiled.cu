@@ -75,7 +75,45 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
   // the whole strip lies inside the lines and needs no ghost: no per-element tests
   const bool inside = (mb >= 0) && (mb + XL <= p.M) && (c0 >= 1) && (c0 + TB + 1 <= p.n_across);
   // 1) raw differences delta on lines c0-1 .. c0+TB, along m in [mb, mb + XL)
-  if (p.axis == 0) {
+  if (inside) {
+    // block-uniform path: fixed trip counts, constant offsets, every load of a thread in flight
+    // before its first use
+    if (p.axis == 0) {
+      const size_t base = (size_t)(c0 - 1) * p.snx + mb + lane;
+      const float* hb = p.hi + base;
+      const float* lb = p.lo + base;
+      float* db = dlt + lane;
+#pragma unroll 2
+      for (int a = warp; a < XROWS; a += NW) {
+        const float* hr = hb + (size_t)a * p.snx;
+        const float* lr = lb + (size_t)a * p.snx;
+#pragma unroll
+        for (int cc = 0; cc < (XL + 31) / 32; ++cc)
+          if (32 * cc + 32 <= XL || lane + 32 * cc < XL)
+            db[a * XLP + 32 * cc] = (hr[32 * cc + 1] - hr[32 * cc]) + (lr[32 * cc + 1] - lr[32 * cc]);
+      }
+    } else {
+      // lines a = lane, lane + 32 (lanes along x); the two last lines with lanes along m
+      const size_t base = (size_t)mb * p.snx + (c0 - 1) + lane;
+      const float* hb = p.hi + base;
+      const float* lb = p.lo + base;
+      const size_t sn = (size_t)p.snx;
+#pragma unroll 2
+      for (int q = warp; q < XL; q += NW) {
+        const float* hr = hb + (size_t)q * sn;
+        const float* lr = lb + (size_t)q * sn;
+        const float v0 = (hr[sn] - hr[0]) + (lr[sn] - lr[0]);
+        const float v1 = (hr[sn + 32] - hr[32]) + (lr[sn + 32] - lr[32]);
+        dlt[lane * XLP + q] = v0;
+        dlt[(lane + 32) * XLP + q] = v1;
+      }
+      for (int idx = threadIdx.x; idx < (XROWS - 64) * XL; idx += NT) {
+        const int e = idx / XL, q = idx - e * XL;
+        const size_t g0 = (size_t)(mb + q) * sn + (c0 - 1) + 64 + e;
+        dlt[(64 + e) * XLP + q] = (p.hi[g0 + sn] - p.hi[g0]) + (p.lo[g0 + sn] - p.lo[g0]);
+      }
+    }
+  } else if (p.axis == 0) {
     for (int a = warp; a < XROWS; a += NW) {
       const int c = c0 - 1 + a;
       const bool line_ok = c >= 0 && c < p.n_across;
@@ -122,6 +160,23 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
   }
   __syncthreads();
   // 2) filtered differences d = 12 beta delta + L delta on lines c0 .. c0+TB-1, m in [mb+1, mb+1+DL)
+  if (inside) {
+#pragma unroll
+    for (int it = 0; it < TB / NW; ++it) {
+      const int a = warp + it * NW;
+      const float* r1 = dlt + (a + 1) * XLP + 1 + lane;
+      float* o = dd + a * DLP + lane;
+#pragma unroll
+      for (int cc = 0; cc < (DL + 31) / 32; ++cc) {
+        if (32 * cc + 32 <= DL || lane + 32 * cc < DL) {
+          const int q = 32 * cc;
+          const float x = r1[q];
+          const float lap = ((r1[q - 1] - x) + (r1[q + 1] - x)) + ((r1[q - XLP] - x) + (r1[q + XLP] - x));
+          o[q] = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
+        }
+      }
+    }
+  } else
   for (int a = warp; a < TB; a += NW) {
     const int c = c0 + a;
     const bool line_ok = inside || (c >= 1 && c <= p.n_across - 2);
