@@ -38,7 +38,8 @@ constexpr int KB = kTiledKFast;      // band half-width of the interior fast pat
 constexpr int KMAX = kTiledKMax;     // largest band half-width of the explicit end rows
 constexpr int NT = 512;              // threads per block
 constexpr int NW = NT / 32;          // warps per block
-constexpr int SEG = 8;               // outputs per thread along a line
+constexpr int SEG = 4;               // outputs per band segment along a line
+constexpr int NSEG = TB / SEG / (NW / 2);  // band segments per thread
 constexpr int DL = TB + 2 * KMAX + 2;  // filtered differences held per line
 constexpr int DLP = DL | 1;            // odd row pitch: conflict-free across lanes
 constexpr int XL = DL + 2;             // raw differences per line (one more on each side)
@@ -193,10 +194,12 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
     }
   }
   __syncthreads();
-  // 3) band of A^{-1}: lane -> line, warp -> (line half, segment of SEG outputs)
+  // 3) band of A^{-1}: lane -> line, warp -> (line half, NSEG segments of SEG outputs)
   const int a = lane + 32 * (warp & 1);
-  const int s = warp >> 1;
-  const int rf = r0 + s * SEG;  // first output of this thread
+#pragma unroll 1
+  for (int sg = 0; sg < NSEG; ++sg) {
+  const int s = (warp >> 1) + (NW / 2) * sg;
+  const int rf = r0 + s * SEG;  // first output of this segment
   const float* drow = dd + a * DLP + (rf - (mb + 1));  // drow[j] = d_{rf + j}
   float yv[SEG];
   const bool fast = !p.all_explicit && rf >= p.Bt && rf + SEG - 1 < p.M - p.Bt;
@@ -247,6 +250,7 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
   }
 #pragma unroll
   for (int k = 0; k < SEG; ++k) out(a, s * SEG + k, yv[k]);
+  }
 }
 
 }  // namespace
@@ -317,7 +321,7 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
 }
 
 template <int STEP>
-__global__ void __launch_bounds__(NT, 2) k_curl_tile(CurlArgs A) {
+__global__ void __launch_bounds__(NT, 3) k_curl_tile(CurlArgs A) {
   curl_body<STEP>(A, blockIdx.x * TB, blockIdx.y * TB);
 }
 
@@ -333,7 +337,7 @@ __device__ __forceinline__ void copy_args(T* dst, const T* src) {
 
 // Batched form: block b processes tile work[2b+1] of cavity work[2b].
 template <int STEP>
-__global__ void __launch_bounds__(NT, 2) k_curl_batch(const CurlArgs* __restrict__ args, const int* __restrict__ work) {
+__global__ void __launch_bounds__(NT, 3) k_curl_batch(const CurlArgs* __restrict__ args, const int* __restrict__ work) {
   __shared__ CurlArgs sA;
   const int cav = work[2 * blockIdx.x], t = work[2 * blockIdx.x + 1];
   copy_args(&sA, args + cav);
@@ -388,6 +392,73 @@ __device__ __forceinline__ void fill_ghosts(float* x, int gx0, int gy0, int nx, 
   }
 }
 
+// Sweeps 1 .. S-1 of one region (see solve_body); EDGE: the region touches a wall, so points
+// off the unknowns are masked and Neumann ghosts refilled after every sweep.
+template <bool EDGE>
+__device__ __forceinline__ void solve_sweeps(const SolveArgs& A, const float* bs, float* xa, float* xb, int gx0,
+                                             int gy0, int nx, int ny, int bcx, int bcy, float* shi, float* slo,
+                                             bool neu_x, bool neu_y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane + 32 * (warp & 1);
+  const int st = warp >> 1;
+  const int gx = gx0 + c;
+  const bool col_unk = !EDGE || (gx >= 0 && gx < nx && interior(bcx, gx, nx));
+  float* xc = xa;
+  float* xn = xb;
+  for (int k = 1; k < A.S; ++k) {
+    const bool last = (k == A.S - 1);
+    const int rps = (RS - 2 * k + NW / 2 - 1) / (NW / 2);
+    const int ly0 = k + st * rps, ly1 = min(ly0 + rps, RS - k);
+    if (c >= k && c < RS - k && ly0 < ly1) {
+      const float* xcol = xc + c;
+      // window: rows ly-1 and ly at columns c-1, c, c+1, and their x-Laplacians
+      float a0 = xcol[(ly0 - 1) * RSP];
+      float b0 = xcol[ly0 * RSP];
+      float lxa = (xcol[(ly0 - 1) * RSP - 1] - a0) + (xcol[(ly0 - 1) * RSP + 1] - a0);
+      float lxb = (xcol[ly0 * RSP - 1] - b0) + (xcol[ly0 * RSP + 1] - b0);
+#pragma unroll 2
+      for (int ly = ly0; ly < ly1; ++ly) {
+        const float cm = xcol[(ly + 1) * RSP - 1], c0v = xcol[(ly + 1) * RSP], cp = xcol[(ly + 1) * RSP + 1];
+        const float lxc = (cm - c0v) + (cp - c0v);
+        const int gy = gy0 + ly;
+        const bool unk = col_unk && (!EDGE || (gy >= 0 && gy < ny && interior(bcy, gy, ny)));
+        const float x = b0;
+        const float lyv = (a0 - x) + (c0v - x);
+        const float lxly = (lxa - lxb) + (lxc - lxb);
+        const float rest = -6.0f * (lxb + lyv) - lxly;
+        const float ph = __fmul_rn(A.d_hi, x);
+        const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
+        const float res = __fsub_rn(__fsub_rn(bs[ly * RSP + c], ph), pl) - rest;
+        const float corr = A.omega * res;
+        if (last) {
+          if (unk) {
+            const size_t gp = (size_t)gy * nx + gx;
+            float h = shi[gp], l = slo[gp];
+            ff_add_scaled_t(h, l, x, A.s_hi, A.s_lo);
+            ff_add_scaled_t(h, l, corr, A.s_hi, A.s_lo);
+            shi[gp] = h;
+            slo[gp] = l;
+          }
+        } else {
+          xn[ly * RSP + c] = unk ? x + corr : 0.0f;
+        }
+        a0 = b0;
+        lxa = lxb;
+        b0 = c0v;
+        lxb = lxc;
+      }
+    }
+    __syncthreads();
+    if (EDGE && !last && (neu_x || neu_y)) {
+      fill_ghosts(xn, gx0, gy0, nx, ny, neu_x, neu_y);
+      __syncthreads();
+    }
+    float* t = xc;
+    xc = xn;
+    xn = t;
+  }
+}
+
 // Region of RS x RS points = output tile (RS - 2H)^2 plus an H-cell halo, H = S - 1.  Warp w owns
 // columns 32 (w & 1) .. +31 and row strip w >> 1 of every sweep, so no warp straddles strips.
 __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, int tby) {
@@ -429,63 +500,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
     fill_ghosts(xa, gx0, gy0, nx, ny, neu_x, neu_y);
     __syncthreads();
   }
-  const int c = lane + 32 * (warp & 1);
-  const int st = warp >> 1;
-  const int gx = gx0 + c;
-  const bool col_unk = !edge || (gx >= 0 && gx < nx && interior(bcx, gx, nx));
-  float* xc = xa;
-  float* xn = xb;
-  for (int k = 1; k < A.S; ++k) {
-    const bool last = (k == A.S - 1);
-    const int rps = (RS - 2 * k + NW / 2 - 1) / (NW / 2);
-    const int ly0 = k + st * rps, ly1 = min(ly0 + rps, RS - k);
-    if (c >= k && c < RS - k && ly0 < ly1) {
-      const float* xcol = xc + c;
-      // window: rows ly-1 and ly at columns c-1, c, c+1, and their x-Laplacians
-      float a0 = xcol[(ly0 - 1) * RSP];
-      float b0 = xcol[ly0 * RSP];
-      float lxa = (xcol[(ly0 - 1) * RSP - 1] - a0) + (xcol[(ly0 - 1) * RSP + 1] - a0);
-      float lxb = (xcol[ly0 * RSP - 1] - b0) + (xcol[ly0 * RSP + 1] - b0);
-      for (int ly = ly0; ly < ly1; ++ly) {
-        const float cm = xcol[(ly + 1) * RSP - 1], c0v = xcol[(ly + 1) * RSP], cp = xcol[(ly + 1) * RSP + 1];
-        const float lxc = (cm - c0v) + (cp - c0v);
-        const int gy = gy0 + ly;
-        const bool unk = col_unk && (!edge || (gy >= 0 && gy < ny && interior(bcy, gy, ny)));
-        const float x = b0;
-        const float lyv = (a0 - x) + (c0v - x);
-        const float lxly = (lxa - lxb) + (lxc - lxb);
-        const float rest = -6.0f * (lxb + lyv) - lxly;
-        const float ph = __fmul_rn(A.d_hi, x);
-        const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
-        const float res = __fsub_rn(__fsub_rn(bs[ly * RSP + c], ph), pl) - rest;
-        const float corr = A.omega * res;
-        if (last) {
-          if (unk) {
-            const size_t gp = (size_t)gy * nx + gx;
-            float h = shi[gp], l = slo[gp];
-            ff_add_scaled_t(h, l, x, A.s_hi, A.s_lo);
-            ff_add_scaled_t(h, l, corr, A.s_hi, A.s_lo);
-            shi[gp] = h;
-            slo[gp] = l;
-          }
-        } else {
-          xn[ly * RSP + c] = unk ? x + corr : 0.0f;
-        }
-        a0 = b0;
-        lxa = lxb;
-        b0 = c0v;
-        lxb = lxc;
-      }
-    }
-    __syncthreads();
-    if (!last && (neu_x || neu_y)) {
-      fill_ghosts(xn, gx0, gy0, nx, ny, neu_x, neu_y);
-      __syncthreads();
-    }
-    float* t = xc;
-    xc = xn;
-    xn = t;
-  }
+  if (edge) solve_sweeps<true>(A, bs, xa, xb, gx0, gy0, nx, ny, bcx, bcy, shi, slo, neu_x, neu_y);
+  else solve_sweeps<false>(A, bs, xa, xb, gx0, gy0, nx, ny, bcx, bcy, shi, slo, false, false);
   if (A.S == 1) {  // the first iterate is also the last: x = 0, correction omega b
     for (int ly = warp; ly < RS; ly += NW) {
       const int gy = ty0 + ly;
