@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64"])
     p.add_argument("--closure", default="paper", choices=["paper", "reflect"])
     p.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
+    p.add_argument("--only-3d", type=int, default=None, metavar="STEPS",
+                   help="run only the 3D leg (FP32_REFINED, STEPS steps) and print its JSON (profiling)")
     return p.parse_args()
 
 
@@ -258,7 +260,7 @@ def reverse_leg(pkg, torch):
             "memory": "no trajectory stored: the step is linear, the reverse pass needs only the final adjoint"}
 
 
-def leg_3d(pkg, torch):
+def leg_3d(pkg, torch, steps32=None, with_fp64=True):
     """3D six-component workload: 256^3 cells, r = 0.4, 500 steps, 2 seeded modes, FP32_REFINED
     (every step timed with CUDA events; the 6-component state, 0.8 GB, exceeds L2), plus 20 FP64
     steps for the FP64-vs-refined comparison."""
@@ -266,7 +268,8 @@ def leg_3d(pkg, torch):
     n, r, modes, K = c["n"], c["r"], c["modes"], c["steps"]
     out = {"workload": "3D PEC cube 256^3 cells, modes (2,3,1) + one seeded mode (indices in [1,16]), r=0.4",
            "unit": "cell-updates/s", "l2": "state 0.8 GB > L2; no flush"}
-    for prec, steps, key in ((pkg.FP32_REFINED, K, "fp32_refined"), (pkg.FP64, 20, "fp64")):
+    legs = [(pkg.FP32_REFINED, steps32 or K, "fp32_refined")] + ([(pkg.FP64, 20, "fp64")] if with_fp64 else [])
+    for prec, steps, key in legs:
         g = pkg.Grid(n, r, precision=prec, dim=3, stream="torch")
         g.init_modes(modes)
         for _ in range(3):
@@ -470,6 +473,14 @@ def run_ours(args, ws, rank, local):
 def main():
     args = parse()
     ws, rank, local = dist_info()
+    if args.only_3d is not None:
+        import torch
+
+        import paper_2306_17263_gb300 as pkg
+        torch.cuda.set_device(local)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        print(json.dumps(leg_3d(pkg, torch, steps32=args.only_3d, with_fp64=False)), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     return run_ours(args, ws, rank, local)

@@ -202,88 +202,96 @@ __device__ __forceinline__ void ff_add_scaled3(float& hi, float& lo, float x, fl
   hi = h2;
 }
 
+// Interior row of A^{-1} at offsets -KB3 .. KB3+1 (hi) and the lo parts of offsets -1, 0, 1: the
+// same Toeplitz row for every grid, 24 (-rho) rho^|d| / (1 - rho^2), rho = -11 + sqrt(120).
+constexpr int KB3 = 7;
+__constant__ float c_w3[2 * KB3 + 2];
+__constant__ float c_wl3[3];
+
 // Filtered first differences along AXIS of a float-float source, written at the points of the
 // destination component (output o = m + out_off for difference m = 0 .. M-1):
 //   delta_m = (hi_{m+1} - hi_m) + (lo_{m+1} - lo_m),  d = 12 beta delta + L delta,
 // L the 7-point stencil with these ghost rules: along the line, zero differences beyond the ends
 // for a source that is Neumann along it (even ghosts of u) and even differences for a source
 // that is Dirichlet along it; across the line, the source's own rule (wall zeros / even ghosts).
+// Indices are 32-bit (n <= 512: at most 513^3 points per component).
 template <int AXIS>
 __global__ void k_dfilt3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 ss, float* __restrict__ d,
                             Shape3 sd, int out_off, int M, int ghost_even, float cb_hi, float cb_lo) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
   if (x >= sd.n[0] || y >= sd.n[1]) return;
-  const size_t pd = at3(sd, x, y, z);
+  const int pd = (z * sd.n[1] + y) * sd.n[0] + x;
   const int m = (AXIS == 0 ? x : (AXIS == 1 ? y : z)) - out_off;
   if (!unk3(sd, x, y, z) || m < 0 || m >= M) {
     d[pd] = 0.0f;
     return;
   }
-  // difference at along-index mm and source coordinates (a, b, c) of the two other axes
-  auto delta = [&](int mm, int a, int b, int c) -> float {
-    if (mm < 0 || mm >= M) {
-      if (!ghost_even) return 0.0f;
-      mm = mm < 0 ? 0 : M - 1;
-    }
-    int i0 = a, j0 = b, k0 = c, i1 = a, j1 = b, k1 = c;
-    if (AXIS == 0) { i0 = mm; i1 = mm + 1; }
-    if (AXIS == 1) { j0 = mm; j1 = mm + 1; }
-    if (AXIS == 2) { k0 = mm; k1 = mm + 1; }
-    const size_t p0 = at3(ss, i0, j0, k0), p1 = at3(ss, i1, j1, k1);
-    return (hi[p1] - hi[p0]) + (lo[p1] - lo[p0]);
-  };
-  const int cx = clampi(x - 1, ss.n[0]), dx = clampi(x + 1, ss.n[0]);
-  const int cy = clampi(y - 1, ss.n[1]), dy = clampi(y + 1, ss.n[1]);
-  const int cz = clampi(z - 1, ss.n[2]), dz = clampi(z + 1, ss.n[2]);
-  float v, a1, a2, b1, b2, c1, c2;
-  v = delta(m, x, y, z);
-  a1 = delta(m - 1, x, y, z);
-  a2 = delta(m + 1, x, y, z);
-  if (AXIS == 0) {
-    b1 = delta(m, x, cy, z); b2 = delta(m, x, dy, z);
-    c1 = delta(m, x, y, cz); c2 = delta(m, x, y, dz);
-  } else if (AXIS == 1) {
-    b1 = delta(m, cx, y, z); b2 = delta(m, dx, y, z);
-    c1 = delta(m, x, y, cz); c2 = delta(m, x, y, dz);
-  } else {
-    b1 = delta(m, cx, y, z); b2 = delta(m, dx, y, z);
-    c1 = delta(m, x, cy, z); c2 = delta(m, x, dy, z);
-  }
+  const int st[3] = {1, ss.n[0], ss.n[0] * ss.n[1]};
+  const int sa = st[AXIS];
+  const int cx = AXIS == 0 ? m : x, cy = AXIS == 1 ? m : y, cz = AXIS == 2 ? m : z;
+  const int ps = (cz * ss.n[1] + cy) * ss.n[0] + cx;  // source index of difference m
+  auto delta = [&](int q) { return (hi[q + sa] - hi[q]) + (lo[q + sa] - lo[q]); };
+  const float v = delta(ps);
+  const float a1 = m > 0 ? delta(ps - sa) : (ghost_even ? v : 0.0f);
+  const float a2 = m < M - 1 ? delta(ps + sa) : (ghost_even ? v : 0.0f);
+  // the two other axes in increasing order, neighbours clamped (even ghosts on Neumann axes)
+  constexpr int P1 = AXIS == 0 ? 1 : 0, P2 = AXIS == 2 ? 1 : 2;
+  const int u1 = P1 == 0 ? x : y, u2 = P2 == 1 ? y : z;
+  const int m1 = u1 > 0 ? -st[P1] : 0, p1 = u1 < ss.n[P1] - 1 ? st[P1] : 0;
+  const int m2 = u2 > 0 ? -st[P2] : 0, p2 = u2 < ss.n[P2] - 1 ? st[P2] : 0;
+  const float b1 = delta(ps + m1), b2 = delta(ps + p1);
+  const float c1 = delta(ps + m2), c2 = delta(ps + p2);
   const float lap = (((a1 - v) + (a2 - v)) + ((b1 - v) + (b2 - v))) + ((c1 - v) + (c2 - v));
   d[pd] = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
 }
 
-// y = A^{-1} d along AXIS (explicit FP32 hi + lo band rows, taps summed farthest first), then
-// R (+)= sign * y at the unknowns of the destination component.
+// y = A^{-1} d along AXIS, then R (+)= sign * y at the unknowns of the destination component.
+// Rows away from the line ends use the interior row from constant memory (taps -KB3 .. KB3+1);
+// the end rows use the explicit FP32 hi + lo table rows.  Taps are summed farthest first (see
+// the 2D curl tile for why the order matters).
 template <int AXIS>
 __global__ void k_band3d32(const float* __restrict__ d, float* __restrict__ R, Shape3 sd, int out_off, int M,
                            const float* __restrict__ whi, const float* __restrict__ wlo, int K, int B,
                            int all_explicit, float sign, int accumulate) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
   if (x >= sd.n[0] || y >= sd.n[1]) return;
-  const size_t pd = at3(sd, x, y, z);
+  const int pd = (z * sd.n[1] + y) * sd.n[0] + x;
   const int r = (AXIS == 0 ? x : (AXIS == 1 ? y : z)) - out_off;
   if (!unk3(sd, x, y, z) || r < 0 || r >= M) {
     if (!accumulate) R[pd] = 0.0f;
     return;
   }
-  const size_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? (size_t)sd.n[0] : (size_t)sd.n[0] * sd.n[1]);
-  const float* drow = d + pd - (size_t)r * stride;  // drow[m * stride] = d_m
-  const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
-  const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
-  float acc = 0.0f, lo = 0.0f;
-  for (int dist = K + 1; dist >= 1; --dist) {
-    for (int side = 1; side >= -1; side -= 2) {
-      const int m = r + side * dist, t = m - r + K;
-      if (t < 0 || t > 2 * K + 1 || m < 0 || m >= M) continue;
-      const float dm = drow[(size_t)m * stride];
-      acc = fmaf(__ldg(wh + t), dm, acc);
-      lo = fmaf(__ldg(wl + t), dm, lo);
+  const int stride = AXIS == 0 ? 1 : (AXIS == 1 ? sd.n[0] : sd.n[0] * sd.n[1]);
+  const float* dc = d + pd;  // dc[t * stride] = d_{r + t}
+  float acc;
+  if (!all_explicit && r >= B && r < M - B && r >= KB3 && r + KB3 + 1 < M) {
+    acc = c_w3[2 * KB3 + 1] * dc[(KB3 + 1) * stride];
+#pragma unroll
+    for (int dist = KB3; dist >= 1; --dist) {
+      acc = fmaf(c_w3[KB3 + dist], dc[dist * stride], acc);
+      acc = fmaf(c_w3[KB3 - dist], dc[-dist * stride], acc);
     }
+    acc = fmaf(c_wl3[0], dc[-stride], acc);
+    acc = fmaf(c_wl3[2], dc[stride], acc);
+    acc = fmaf(c_wl3[1], dc[0], acc);
+    acc = fmaf(c_w3[KB3], dc[0], acc);
+  } else {
+    const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
+    const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
+    float lo = 0.0f;
+    acc = 0.0f;
+    for (int dist = K + 1; dist >= 1; --dist) {
+      for (int side = 1; side >= -1; side -= 2) {
+        const int mm = r + side * dist, t = mm - r + K;
+        if (t < 0 || t > 2 * K + 1 || mm < 0 || mm >= M) continue;
+        const float dm = dc[(mm - r) * stride];
+        acc = fmaf(__ldg(wh + t), dm, acc);
+        lo = fmaf(__ldg(wl + t), dm, lo);
+      }
+    }
+    lo = fmaf(__ldg(wl + K), dc[0], lo);
+    acc = fmaf(__ldg(wh + K), dc[0], acc + lo);
   }
-  const float dc = drow[(size_t)r * stride];
-  lo = fmaf(__ldg(wl + K), dc, lo);
-  acc = fmaf(__ldg(wh + K), dc, acc + lo);
   R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
 }
 
@@ -294,8 +302,9 @@ __global__ void k_sweep3d32(const float* __restrict__ b, const float* __restrict
                             Shape3 s, float d_hi, float d_lo, float omega, int first, int last,
                             float* __restrict__ shi, float* __restrict__ slo, float s_hi, float s_lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
-  if (i >= s.n[0] || j >= s.n[1]) return;
-  const size_t p = at3(s, i, j, k);
+  const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
+  if (i >= n0 || j >= n1) return;
+  const int p = (k * n1 + j) * n0 + i;
   if (!unk3(s, i, j, k)) {
     if (!last) xout[p] = 0.0f;
     return;
@@ -312,24 +321,26 @@ __global__ void k_sweep3d32(const float* __restrict__ b, const float* __restrict
     }
     return;
   }
-  const int im = clampi(i - 1, s.n[0]), ip = clampi(i + 1, s.n[0]);
-  const int jm = clampi(j - 1, s.n[1]), jp = clampi(j + 1, s.n[1]);
-  const int km = clampi(k - 1, s.n[2]), kp = clampi(k + 1, s.n[2]);
-  auto X = [&](int a, int bb, int c) { return xin[at3(s, a, bb, c)]; };
-  auto LX = [&](int bb, int c) {
-    const float v = X(i, bb, c);
-    return (X(im, bb, c) - v) + (X(ip, bb, c) - v);
+  // neighbour offsets, clamped on Neumann axes (even ghosts); Dirichlet neighbours are stored zeros
+  const int sz = n0 * n1;
+  const int xm = i > 0 ? -1 : 0, xp = i < n0 - 1 ? 1 : 0;
+  const int ym = j > 0 ? -n0 : 0, yp = j < n1 - 1 ? n0 : 0;
+  const int zm = k > 0 ? -sz : 0, zp = k < n2 - 1 ? sz : 0;
+  const float* X = xin + p;
+  auto LX = [&](int o) {
+    const float v = X[o];
+    return (X[o + xm] - v) + (X[o + xp] - v);
   };
-  auto LY = [&](int a, int c) {
-    const float v = X(a, j, c);
-    return (X(a, jm, c) - v) + (X(a, jp, c) - v);
+  auto LY = [&](int o) {
+    const float v = X[o];
+    return (X[o + ym] - v) + (X[o + yp] - v);
   };
-  const float x = X(i, j, k);
-  const float lx = LX(j, k), ly = LY(i, k);
-  const float lz = (X(i, j, km) - x) + (X(i, j, kp) - x);
-  const float lxly = (LX(jm, k) - lx) + (LX(jp, k) - lx);
-  const float lxlz = (LX(j, km) - lx) + (LX(j, kp) - lx);
-  const float lylz = (LY(i, km) - ly) + (LY(i, kp) - ly);
+  const float x = X[0];
+  const float lx = LX(0), ly = LY(0);
+  const float lz = (X[zm] - x) + (X[zp] - x);
+  const float lxly = (LX(ym) - lx) + (LX(yp) - lx);
+  const float lxlz = (LX(zm) - lx) + (LX(zp) - lx);
+  const float lylz = (LY(zm) - ly) + (LY(zp) - ly);
   const float rest = -6.0f * ((lx + ly) + lz) - ((lxly + lylz) + lxlz);
   const float ph = __fmul_rn(d_hi, x);
   const float pl = fmaf(d_lo, x, fmaf(d_hi, x, -ph));
@@ -537,6 +548,22 @@ double max_amp2_3d(double r) {
   return worst;
 }
 
+// Interior row of A^{-1} in closed form (long double), split hi + lo, into constant memory.
+int upload_band_row() {
+  const long double rho = -11.0L + std::sqrt(120.0L);
+  float w[2 * KB3 + 2], wl[3];
+  for (int t = 0; t < 2 * KB3 + 2; ++t) {
+    const int dd = t - KB3;
+    long double v = 24.0L * (-rho) / (1.0L - rho * rho);
+    for (int q = 0; q < (dd < 0 ? -dd : dd); ++q) v *= rho;
+    w[t] = (float)v;
+    if (dd >= -1 && dd <= 1) wl[dd + 1] = (float)(v - (long double)w[t]);
+  }
+  if (cudaMemcpyToSymbol(c_w3, w, sizeof w) != cudaSuccess || cudaMemcpyToSymbol(c_wl3, wl, sizeof wl) != cudaSuccess)
+    return -1;
+  return 0;
+}
+
 template <typename T>
 ms_status alloc3(T** p, size_t n) {
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 256);
@@ -721,6 +748,7 @@ ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
                          cudaMemcpy(t.d_wlo, wlo.data(), wlo.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess))
         s = fail3(MS_ECUDA, "copy of FP32 Pade tables failed");
     }
+    if (s == MS_OK && upload_band_row() != 0) s = fail3(MS_ECUDA, "cannot upload the interior band row");
     int S = (int)std::ceil(std::log(1e-10) / std::log(rho));
     g->p1_sweeps32 = S < 1 ? 1 : S;
     if (g->p1_sweeps32 > 8) s = fail3(MS_EUNSUPPORTED, "CFL number too close to the stability limit for the FP32 solve");
