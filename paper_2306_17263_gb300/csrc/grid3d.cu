@@ -296,10 +296,11 @@ __global__ void k_band3d32(const float* __restrict__ d, float* __restrict__ R, S
 }
 
 // One sweep of the FP32 Richardson iteration on 6 h^2 P1 x = b (6h^2 P1 = d - 6(Lx + Ly + Lz)
-// - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo).  first: x = omega b.  last: the state
-// (hi, lo) += s x + s corr (two separate error-free additions) instead of writing x.
+// - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo), x_{k+1} = x_k + omega (b - 6 h^2 P1 x_k) from
+// x_1 = omega b.  first: the sweep from x_1, read as omega b.  last: the state (hi, lo) += s x +
+// s corr (two separate error-free additions) instead of writing x.  single: S = 1, state += s omega b.
 __global__ void k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin, float* __restrict__ xout,
-                            Shape3 s, float d_hi, float d_lo, float omega, int first, int last,
+                            Shape3 s, float d_hi, float d_lo, float omega, int first, int last, int single,
                             float* __restrict__ shi, float* __restrict__ slo, float s_hi, float s_lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
   const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
@@ -309,35 +310,33 @@ __global__ void k_sweep3d32(const float* __restrict__ b, const float* __restrict
     if (!last) xout[p] = 0.0f;
     return;
   }
-  if (first) {
-    const float x1 = omega * b[p];
-    if (last) {
-      float h = shi[p], l = slo[p];
-      ff_add_scaled3(h, l, x1, s_hi, s_lo);
-      shi[p] = h;
-      slo[p] = l;
-    } else {
-      xout[p] = x1;
-    }
+  if (single) {  // one iterate in all: x = omega b
+    float h = shi[p], l = slo[p];
+    ff_add_scaled3(h, l, omega * b[p], s_hi, s_lo);
+    shi[p] = h;
+    slo[p] = l;
     return;
   }
-  // neighbour offsets, clamped on Neumann axes (even ghosts); Dirichlet neighbours are stored zeros
+  // neighbour offsets, clamped on Neumann axes (even ghosts); Dirichlet neighbours are stored zeros.
+  // first: the iterate x_1 = omega b (zero off the unknowns, like b) is formed from b on the fly.
   const int sz = n0 * n1;
   const int xm = i > 0 ? -1 : 0, xp = i < n0 - 1 ? 1 : 0;
   const int ym = j > 0 ? -n0 : 0, yp = j < n1 - 1 ? n0 : 0;
   const int zm = k > 0 ? -sz : 0, zp = k < n2 - 1 ? sz : 0;
-  const float* X = xin + p;
+  const float* X0 = (first ? b : xin) + p;
+  const float sc = first ? omega : 1.0f;
+  auto X = [&](int o) { return first ? sc * X0[o] : X0[o]; };
   auto LX = [&](int o) {
-    const float v = X[o];
-    return (X[o + xm] - v) + (X[o + xp] - v);
+    const float v = X(o);
+    return (X(o + xm) - v) + (X(o + xp) - v);
   };
   auto LY = [&](int o) {
-    const float v = X[o];
-    return (X[o + ym] - v) + (X[o + yp] - v);
+    const float v = X(o);
+    return (X(o + ym) - v) + (X(o + yp) - v);
   };
-  const float x = X[0];
+  const float x = X(0);
   const float lx = LX(0), ly = LY(0);
-  const float lz = (X[zm] - x) + (X[zp] - x);
+  const float lz = (X(zm) - x) + (X(zp) - x);
   const float lxly = (LX(ym) - lx) + (LX(yp) - lx);
   const float lxlz = (LX(zm) - lx) + (LX(zp) - lx);
   const float lylz = (LY(zm) - ly) + (LY(zp) - ly);
@@ -490,16 +489,18 @@ void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_h
   const Shape3& s = G3->sh[c];
   const float* b = G3->s32[1];
   float* buf[2] = {G3->s32[2], G3->s32[3]};
+  // launch k (k = 1 .. S-1, or one launch when S = 1) produces iterate k + 1 from iterate k
   const float* xin = nullptr;
-  for (int k = 0; k < S; ++k) {
-    const bool last = (k == S - 1);
+  const int L = S > 1 ? S - 1 : 1;
+  for (int k = 0; k < L; ++k) {
+    const bool last = (k == L - 1);
     float* xo = buf[k & 1];
-    k_sweep3d32<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, k == 0, last, G3->hi[c],
-                                                         G3->lo[c], s_hi, s_lo);
+    k_sweep3d32<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, k == 0, last, S == 1,
+                                                         G3->hi[c], G3->lo[c], s_hi, s_lo);
     prof_mark(g, KK_SWEEP3D32, 4.0 * (double)s.size() * ((k == 0 ? 1.0 : 2.0) + (last ? 4.0 : 1.0)));
     xin = xo;
   }
-  *nl += S;
+  *nl += L;
 }
 
 ms_status step3d32(ms_grid* g) {
