@@ -292,6 +292,32 @@ def leg_3d(pkg, torch, steps32=None, with_fp64=True):
     return out
 
 
+def wavenumber_mae(pkg, k: int, scheme, N: int = 64, r: float = 0.5, T: float = 4.0 / math.sqrt(2.0)):
+    """Mean absolute error of Sec. 5.1 for the single mode k_x = k_y = k at h = 1/N after
+    round(T / h_tau) steps: the sum of |u - u_exact| over all stored points and steps, divided by
+    3 n_steps N^2; per-step sums from ms_error_vs_exact."""
+    modes = [(k, k, 1.0)]
+    with pkg.Grid(N, r, precision=pkg.FP64, scheme=scheme) as g:
+        g.init_modes(modes)
+        K = int(round(T / g.ht))
+        acc = 0.0
+        for _ in range(K):
+            g.step()
+            acc += g.error_vs_exact(modes)[3]
+    return acc / (3.0 * K * N * N), K
+
+
+def wavenumber_leg(pkg):
+    """Error against wavenumber at h = 1/64 (the setting of Fig. "fig:error(k)": k_x = k_y = k,
+    T = 4/sqrt(2), Z = 1), points per wavelength 2N/k from 64 (k = 2) to 2.56 (k = 50); compact
+    scheme and plain Yee, FP64."""
+    ks = list(range(2, 51, 2))
+    c4 = [wavenumber_mae(pkg, k, pkg.SCHEME_C4)[0] for k in ks]
+    yee = [wavenumber_mae(pkg, k, pkg.SCHEME_YEE2)[0] for k in ks]
+    return {"N": 64, "r": 0.5, "T": 4.0 / math.sqrt(2.0), "k": ks, "ppw": [128.0 / k for k in ks],
+            "mae_c4": c4, "mae_yee": yee}
+
+
 def yee_leg(pkg, torch, modes, r, c4_l2_abs, c4_value, T=4000 * 0.5 / 2048):
     """Plain second-order Yee (FP64) on the same modes and end time: its L2 error at three
     resolutions, the fitted order, and the resolution and time-to-solution it would need to
@@ -457,6 +483,7 @@ def run_ours(args, ws, rank, local):
         line["batched"] = batched_leg(pkg, torch)
         line["reverse_pass"] = reverse_leg(pkg, torch)
         line["three_d"] = leg_3d(pkg, torch)
+        line["error_vs_wavenumber"] = wavenumber_leg(pkg)
         line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, l2_abs, value)
         # CPU oracle on a bounded sample of the workload (rank 0, one core)
         v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
