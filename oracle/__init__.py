@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
             L.or2d_taylor_h_T.argtypes = [V, D, D, D]
             L.or2d_misfit_grad.argtypes = [V, D, D, ctypes.c_int, D]
             L.or2d_misfit_grad.restype = ctypes.c_double
+            L.or_nc_line.argtypes = [ctypes.c_int, ctypes.c_double, D, D]
+            L.or2d_nc_step.argtypes = [V, D, D, D]
             PP = ctypes.POINTER(ctypes.c_void_p)
             L.or3d_sizeof.restype = ctypes.c_int
             L.or3d_setup.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -130,6 +132,15 @@ def pade_line_T(g: np.ndarray, h: float, closure: int = CLOSURE_PAPER, kind: int
     g = np.ascontiguousarray(g, dtype=np.float64)
     out = np.zeros(g.size + 1)
     lib().or_pade_line_T(g.size, closure, kind, h, _p(g), _p(out))
+    return out
+
+
+def nc_line(f: np.ndarray, h: float) -> np.ndarray:
+    """Fourth-order staggered first derivative of the NC comparator (Sec. 5.2, stencil K4 with
+    a = 0, one-sided fourth-order differences at the ends): len(out) = len(f) - 1."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(f.size - 1)
+    lib().or_nc_line(f.size, h, _p(f), _p(out))
     return out
 
 
@@ -224,6 +235,10 @@ class Oracle2D:
     def yee_step(self, ez, hx, hy):
         """One plain second-order Yee step in place (Sec. 5.2, stencil S with c = 1)."""
         lib().or2d_yee_step(self.g, _p(ez), _p(hx), _p(hy))
+
+    def nc_step(self, ez, hx, hy):
+        """One step of the non-compact fourth-order comparator NC in place (Sec. 5.2, K4, a = 0)."""
+        lib().or2d_nc_step(self.g, _p(ez), _p(hx), _p(hy))
 
     @staticmethod
     def _modes(modes):

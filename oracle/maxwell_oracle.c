@@ -20,7 +20,9 @@
  *   - the time step (Step 1 then Step 2): Sec. 3.4;
  *   - conjugate-gradient solves of the SPD systems: Sec. 3.2 and Sec. 6;
  *   - exact PEC cavity modes and the mean absolute error: Sec. 5.1, Eq. "eq:data";
- *   - Yee updating rules with the second-order stencil (c=1): Sec. 5.2.
+ *   - Yee updating rules with the second-order stencil (c=1): Sec. 5.2;
+ *   - the non-compact fourth-order comparator NC (stencil K4, a = 0, one-sided
+ *     fourth-order differences at the line ends): Sec. 5.2, Eq. "eq:K4".
  *
  * Readings of points the paper leaves open (all listed in the design notes):
  *   - the third rows of Step 1 / Step 2 are E_z and H_z (the printed E_y, H_y
@@ -811,4 +813,69 @@ double or2d_misfit_grad(or_grid2d* g, const double* ez0, const double* target, i
   free(hx);
   free(hy);
   return L;
+}
+
+/* ------------------------------------------------------------------ */
+/* Non-compact fourth-order comparator NC (Sec. 5.2): the leapfrog updating rules of the Yee
+ * scheme with the stencil K4 of Eq. "eq:K4" at a = 0, i.e. the first derivative on a staggered
+ * line
+ *   D u_i = (9/8 (u_{i+1/2} - u_{i-1/2}) - 1/24 (u_{i+3/2} - u_{i-3/2})) / h,
+ * and, where that stencil would leave the line, the standard fourth-order one-sided staggered
+ * difference: at the first output, from the first four inputs at offsets -1/2, 1/2, 3/2, 5/2,
+ *   D u = (-23 u_0 + 21 u_1 + 3 u_2 - u_3) / (24 h),
+ * and its mirror image at the last output.  The weights are the unique ones exact for cubics
+ * (Taylor expansion), which a test checks. */
+
+/* Derivative of one staggered line of nin values: out[k] (k = 0 .. nin-2) sits between inputs k
+ * and k+1 (N half-node values give the N-1 interior nodes; N+1 node values give the N half-nodes). */
+void or_nc_line(int nin, double h, const double* f, double* out) {
+  int nout = nin - 1; /* both kinds: one output between each pair of neighbouring inputs */
+  for (int k = 0; k < nout; ++k) {
+    /* inputs straddling output k: f[k] (left, offset -1/2) and f[k+1] (right, +1/2) */
+    double v;
+    if (k >= 1 && k + 2 < nin) {
+      v = (9.0 / 8.0) * (f[k + 1] - f[k]) - (1.0 / 24.0) * (f[k + 2] - f[k - 1]);
+    } else if (k == 0) {
+      v = (-23.0 * f[0] + 21.0 * f[1] + 3.0 * f[2] - f[3]) / 24.0;
+    } else {
+      int m = nin - 1; /* last input, offset +1/2 of the last output */
+      v = (23.0 * f[m] - 21.0 * f[m - 1] - 3.0 * f[m - 2] + f[m - 3]) / 24.0;
+    }
+    out[k] = v / h;
+  }
+}
+
+/* One NC step in place (leapfrog as or2d_yee_step, derivatives by or_nc_line):
+ *   E_z += h_tau Z (D_x H_y - D_y H_x);  H_x -= (h_tau/Z) D_y E_z;  H_y += (h_tau/Z) D_x E_z. */
+void or2d_nc_step(const or_grid2d* g, double* ez, double* hx, double* hy) {
+  int N = g->N;
+  double* f = (double*)malloc(sizeof(double) * (N + 1));
+  double* d = (double*)malloc(sizeof(double) * (N + 1));
+  double ce = g->ht * g->Z, ch = g->ht / g->Z;
+  /* E_z: rows j = 1..N-1, D_x H_y (H_y row j has N half-node values) */
+  for (int j = 1; j < N; ++j) {
+    for (int i = 0; i < N; ++i) f[i] = hy[(size_t)j * N + i];
+    or_nc_line(N, g->h, f, d);
+    for (int i = 1; i < N; ++i) ez[(size_t)j * (N + 1) + i] += ce * d[i - 1];
+  }
+  /* columns i = 1..N-1, D_y H_x (H_x column i has N half-node values) */
+  for (int i = 1; i < N; ++i) {
+    for (int j = 0; j < N; ++j) f[j] = hx[(size_t)j * (N + 1) + i];
+    or_nc_line(N, g->h, f, d);
+    for (int j = 1; j < N; ++j) ez[(size_t)j * (N + 1) + i] -= ce * d[j - 1];
+  }
+  /* H_x: columns i = 1..N-1, D_y E_z (N+1 node values) -> N half-nodes */
+  for (int i = 1; i < N; ++i) {
+    for (int j = 0; j <= N; ++j) f[j] = ez[(size_t)j * (N + 1) + i];
+    or_nc_line(N + 1, g->h, f, d);
+    for (int j = 0; j < N; ++j) hx[(size_t)j * (N + 1) + i] -= ch * d[j];
+  }
+  /* H_y: rows j = 1..N-1, D_x E_z */
+  for (int j = 1; j < N; ++j) {
+    for (int i = 0; i <= N; ++i) f[i] = ez[(size_t)j * (N + 1) + i];
+    or_nc_line(N + 1, g->h, f, d);
+    for (int i = 0; i < N; ++i) hy[(size_t)j * N + i] += ch * d[i];
+  }
+  free(f);
+  free(d);
 }
