@@ -310,12 +310,13 @@ def wavenumber_mae(pkg, k: int, scheme, N: int = 64, r: float = 0.5, T: float = 
 def wavenumber_leg(pkg):
     """Error against wavenumber at h = 1/64 (the setting of Fig. "fig:error(k)": k_x = k_y = k,
     T = 4/sqrt(2), Z = 1), points per wavelength 2N/k from 64 (k = 2) to 2.56 (k = 50); compact
-    scheme and plain Yee, FP64."""
+    scheme, the non-compact fourth-order comparator NC and plain Yee, FP64."""
     ks = list(range(2, 51, 2))
     c4 = [wavenumber_mae(pkg, k, pkg.SCHEME_C4)[0] for k in ks]
     yee = [wavenumber_mae(pkg, k, pkg.SCHEME_YEE2)[0] for k in ks]
+    nc = [wavenumber_mae(pkg, k, pkg.SCHEME_NC4)[0] for k in ks]
     return {"N": 64, "r": 0.5, "T": 4.0 / math.sqrt(2.0), "k": ks, "ppw": [128.0 / k for k in ks],
-            "mae_c4": c4, "mae_yee": yee}
+            "mae_c4": c4, "mae_nc": nc, "mae_yee": yee}
 
 
 def yee_leg(pkg, torch, modes, r, c4_l2_abs, c4_value, T=4000 * 0.5 / 2048):

@@ -67,9 +67,12 @@ typedef enum { MS_FP64 = 0, MS_FP32_REFINED = 1 } ms_precision;
 typedef enum { MS_CLOSURE_PAPER = 0, MS_CLOSURE_REFLECT = 1 } ms_closure;
 
 /* Time-stepping scheme.  MS_SCHEME_C4 is the paper's compact scheme (Sec. 3.4);
- * MS_SCHEME_YEE2 is the plain second-order Yee update (Sec. 5.2, stencil S with c = 1),
- * kept as a same-hardware comparator. */
-typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1 } ms_scheme;
+ * MS_SCHEME_YEE2 is the plain second-order Yee update (Sec. 5.2, stencil S with c = 1);
+ * MS_SCHEME_NC4 is the paper's non-compact fourth-order comparator NC (Sec. 5.2, stencil K4 of
+ * Eq. "eq:K4" with a = 0: the (9/8, -1/24) staggered difference, the standard fourth-order
+ * one-sided difference (-23, 21, 3, -1)/24 at the line ends, leapfrog in time).  The two
+ * comparators run in FP64 on 2D grids; NC needs r < 1 / (sqrt 2 (9/8 + 1/24)) = 0.606. */
+typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1, MS_SCHEME_NC4 = 2 } ms_scheme;
 
 typedef struct {
   int dim;          /* 2 (TM_z: E_z, H_x, H_y) or 3 (six components, see below) */

@@ -140,6 +140,15 @@ ms_status step64(ms_grid* g) {
     g->launches_per_step = 2;
     return check_launch("yee step");
   }
+  if (g->desc.scheme == MS_SCHEME_NC4) {
+    const double ne = (double)g->sh[EZ].size(), nh = (double)g->sh[HX].size();
+    launch_nc_e64(ez, hx, hy, g->N, g->ht * g->Z, g->stream);
+    prof_mark(g, KK_NC64, 8.0 * (2 * ne + 2 * nh));
+    launch_nc_h64(ez, hx, hy, g->N, g->ht / g->Z, g->stream);
+    prof_mark(g, KK_NC64, 8.0 * (ne + 4 * nh));
+    g->launches_per_step = 2;
+    return check_launch("nc step");
+  }
   // Step 1: G = (beta + (h^2/12) Delta_h) H, R = kappa^2 Z curl_h G, P1 E* = R, E += h_tau E*
   double* Gx = g->s64[0];
   double* Gy = g->s64[1];
@@ -318,7 +327,8 @@ void prof_mark(ms_grid* g, int kind, double bytes) {
 const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64", "filter32",
                                         "pade32", "p1sweep32", "curl32", "solve32", "filter3d64",
-                                        "pade3d64", "sweep3d64", "dfilt3d32", "band3d32", "sweep3d32"};
+                                        "pade3d64", "sweep3d64", "dfilt3d32", "band3d32", "sweep3d32",
+                                        "nc64"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }
 
@@ -356,9 +366,10 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   if (!(d->r > 0.0) || !std::isfinite(d->r)) return fail(MS_EINVAL, "r must be positive");
   if (d->precision != MS_FP64 && d->precision != MS_FP32_REFINED) return fail(MS_EINVAL, "unknown precision");
   if (d->closure != MS_CLOSURE_PAPER && d->closure != MS_CLOSURE_REFLECT) return fail(MS_EINVAL, "unknown closure");
-  if (d->scheme != MS_SCHEME_C4 && d->scheme != MS_SCHEME_YEE2) return fail(MS_EINVAL, "unknown scheme");
-  if (d->scheme == MS_SCHEME_YEE2 && d->precision != MS_FP64)
-    return fail(MS_EUNSUPPORTED, "the Yee comparator runs in FP64 only");
+  if (d->scheme != MS_SCHEME_C4 && d->scheme != MS_SCHEME_YEE2 && d->scheme != MS_SCHEME_NC4)
+    return fail(MS_EINVAL, "unknown scheme");
+  if (d->scheme != MS_SCHEME_C4 && d->precision != MS_FP64)
+    return fail(MS_EUNSUPPORTED, "the Yee and NC comparators run in FP64 only");
   if (d->scheme == MS_SCHEME_C4) {
     const double rmax = stability_limit_2d();
     if (d->r >= rmax) {
@@ -366,8 +377,10 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
       snprintf(buf, sizeof buf, "r = %.6g is at or above the stability limit %.6g of the 2D scheme", d->r, rmax);
       return fail(MS_ECFL, buf);
     }
-  } else if (d->r * std::sqrt(2.0) >= 1.0) {
+  } else if (d->scheme == MS_SCHEME_YEE2 && d->r * std::sqrt(2.0) >= 1.0) {
     return fail(MS_ECFL, "Yee scheme requires r < 1/sqrt(2)");
+  } else if (d->scheme == MS_SCHEME_NC4 && d->r * std::sqrt(2.0) * (9.0 / 8.0 + 1.0 / 24.0) >= 1.0) {
+    return fail(MS_ECFL, "NC scheme requires r < 1/(sqrt(2) (9/8 + 1/24))");
   }
   ms_grid* g = new ms_grid();
   g->desc = *d;
@@ -392,7 +405,8 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   }
   // Pade tables (FP64 truncation 1e-18 of the row's absolute sum)
   std::string err;
-  for (int kind = 0; kind < 2; ++kind) {
+  // (the Yee and NC comparators use no Pade tables)
+  for (int kind = 0; kind < 2 && d->scheme == MS_SCHEME_C4; ++kind) {
     const int M = (kind == HALF_TO_NODE) ? g->N - 1 : g->N;
     if (build_pade_table(M, d->closure, kind, 1e-18, &g->pade[kind], &err) != 0) return cleanup(fail(MS_EINVAL, err));
     PadeTable& t = g->pade[kind];
@@ -683,6 +697,7 @@ ms_status ms_energy(ms_grid* g, double* W) {
 ms_status ms_divergence(ms_grid* g, double* norm) {
   if (!valid_grid(g) || !norm) return fail(MS_EINVAL, "invalid argument");
   if (g->g3) return fail(MS_EUNSUPPORTED, "the divergence is implemented for 2D grids");
+  if (g->desc.scheme != MS_SCHEME_C4) return fail(MS_EUNSUPPORTED, "the Pade divergence is defined for the compact scheme");
   double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
   const double* view[3];
   MS_TRY(state64(g, tmp, view));

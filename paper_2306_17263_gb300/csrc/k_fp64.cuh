@@ -32,6 +32,9 @@ void launch_p1_sweep64(const double* b, const double* xin, double* xout, const S
 void launch_p1_apply64(const double* x, double* out, const Shape& s, double c1h2, double out_scale, cudaStream_t st);
 void launch_yee_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
 void launch_yee_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);
+// Non-compact fourth-order comparator NC (k_nc.cu)
+void launch_nc_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
+void launch_nc_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);
 
 // x = P1^{-1} b for field f by the FP64 Richardson sweeps (scratch planes s64[3], s64[4]); the
 // last sweep writes `out` and, when upd != nullptr, adds upd_scale * x to upd (capi.cu).

@@ -123,3 +123,21 @@ def test_full_size_reflect_closed_form(precision, steps):
     scale = max(float(np.abs(w).max()) for w in want)
     tol = 1e-10 if precision == pkg.FP64 else 2e-6
     assert worst <= tol * scale, worst / scale
+
+
+def test_full_size_fp32_refined_within_fp64_discretisation_error():
+    """256^3 cells, 500 steps, PAPER closure: the FP32_REFINED state is within 2x the FP64 path's
+    error against the exact modes and closer to the FP64 state than FP64 is to the exact modes
+    (the FP64 path is the oracle's parity-pinned stand-in at this size)."""
+    c = workloads.config3()
+    n, r, modes, K = c["n"], c["r"], c["modes"], c["steps"]
+    out = {}
+    for prec in (pkg.FP64, pkg.FP32_REFINED):
+        with pkg.Grid(n, r, precision=prec, dim=3) as g:
+            g.init_modes(modes)
+            g.run(K)
+            out[prec] = (g.get_fields(), g.error_vs_exact(modes)[0])
+    (f64, e64), (f32, e32) = out[pkg.FP64], out[pkg.FP32_REFINED]
+    diff = np.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(f32, f64)) / n ** 3)
+    assert e32 <= 2 * e64, (e32, e64)
+    assert diff <= e64, (diff, e64)
