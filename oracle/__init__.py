@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             L.or2d_misfit_grad.restype = ctypes.c_double
             L.or_nc_line.argtypes = [ctypes.c_int, ctypes.c_double, D, D]
             L.or2d_nc_step.argtypes = [V, D, D, D]
+            L.or2d_step_tracked.argtypes = [V, D, D, D, D]
             PP = ctypes.POINTER(ctypes.c_void_p)
             L.or3d_sizeof.restype = ctypes.c_int
             L.or3d_setup.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -235,6 +236,11 @@ class Oracle2D:
     def yee_step(self, ez, hx, hy):
         """One plain second-order Yee step in place (Sec. 5.2, stencil S with c = 1)."""
         lib().or2d_yee_step(self.g, _p(ez), _p(hx), _p(hy))
+
+    def step_tracked(self, ez, hx, hy, de):
+        """One step of the tracked-Delta-E variant in place (Sec. 3.4 as printed: DE advanced by
+        Eq. "eq:mhe", Step 2 filtered with it as in Eq. "eq:helm2")."""
+        lib().or2d_step_tracked(self.g, _p(ez), _p(hx), _p(hy), _p(de))
 
     def nc_step(self, ez, hx, hy):
         """One step of the non-compact fourth-order comparator NC in place (Sec. 5.2, K4, a = 0)."""

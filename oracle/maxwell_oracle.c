@@ -879,3 +879,52 @@ void or2d_nc_step(const or_grid2d* g, double* ez, double* hx, double* hy) {
   free(f);
   free(d);
 }
+
+/* ------------------------------------------------------------------ */
+/* Tracked-Delta-E variant: the literal Step 1 / Step 2 of Sec. 3.4.  Besides E and H it carries
+ * DE, a fourth-order approximation of Delta E_z on the E grid.  After Step 1 it is advanced
+ * with the modified Helmholtz equation of Eq. "eq:mhe" (with J = 0),
+ *   DE^{n+1} = DE^n + kappa^2 (E^{n+1} - E^n) - Z (24/h_tau) curl_h H^{n+1/2},
+ * curl_h H = delta_x H_y - delta_y H_x the unfiltered Pade curl (App. A.1), and Step 2 filters E
+ * with it in the form of Eq. "eq:helm2": G_E = (1 + kappa^2 h^2/12) E + (h^2/12) DE.  DE is 0 on
+ * the PEC nodes (Delta E_z = d_tt E_z = 0 there, Table "tab:bc_terms"). */
+void or2d_step_tracked(or_grid2d* g, double* ez, double* hx, double* hy, double* de) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* Gx = (double*)malloc(sizeof(double) * nx_);
+  double* Gy = (double*)malloc(sizeof(double) * ny_);
+  double* R = (double*)malloc(sizeof(double) * ne);
+  double* C = (double*)malloc(sizeof(double) * ne);
+  double* Es = (double*)malloc(sizeof(double) * ne);
+  double* GE = (double*)malloc(sizeof(double) * ne);
+  double* Rx = (double*)malloc(sizeof(double) * nx_);
+  double* Ry = (double*)malloc(sizeof(double) * ny_);
+  double* Hs = (double*)malloc(sizeof(double) * (nx_ > ny_ ? nx_ : ny_));
+  /* Step 1, as in or2d_step */
+  or2d_filter(g, F_HX, hx, Gx);
+  or2d_filter(g, F_HY, hy, Gy);
+  or2d_curl_h_to_e(g, Gx, Gy, R);
+  or2d_p1_solve_cg(g, F_EZ, R, Es);
+  for (int p = 0; p < ne; ++p) ez[p] += g->ht * Es[p];
+  /* DE += kappa^2 h_tau E* - Z (24/h_tau) curl_h H; or2d_curl_h_to_e gives kappa^2 Z curl_h H */
+  or2d_curl_h_to_e(g, hx, hy, C);
+  for (int p = 0; p < ne; ++p) de[p] += g->kappa2 * g->ht * Es[p] - (24.0 / g->ht) * C[p] / g->kappa2;
+  zero_boundary(g, F_EZ, de);
+  /* Step 2 with G_E = beta E + (h^2/12) DE */
+  double h2_12 = g->h * g->h / 12.0;
+  for (int p = 0; p < ne; ++p) GE[p] = g->beta * ez[p] + h2_12 * de[p];
+  zero_boundary(g, F_EZ, GE);
+  or2d_curl_e_to_h(g, GE, Rx, Ry);
+  or2d_p1_solve_cg(g, F_HX, Rx, Hs);
+  for (int p = 0; p < nx_; ++p) hx[p] += g->ht * Hs[p];
+  or2d_p1_solve_cg(g, F_HY, Ry, Hs);
+  for (int p = 0; p < ny_; ++p) hy[p] += g->ht * Hs[p];
+  free(Gx);
+  free(Gy);
+  free(R);
+  free(C);
+  free(Es);
+  free(GE);
+  free(Rx);
+  free(Ry);
+  free(Hs);
+}

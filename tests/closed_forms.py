@@ -109,3 +109,31 @@ def mode_basis3(N: int, m: int, n: int, p: int):
             f1.append(v)
         out.append(np.einsum("k,j,i->kji", f1[2], f1[1], f1[0]))
     return out
+
+
+def mode_step_matrix_tracked(N: int, r: float, kx: int, ky: int, Z: float = 1.0) -> np.ndarray:
+    """One step of the tracked-Delta-E variant on the coefficients (e, a, b, q) of the mode basis
+    (q: the tracked Delta E on the E_z basis): Step 1 as in mode_step_matrix, then
+    q' = q + kappa^2 (e' - e) - Z kappa^2 h_tau (d_y a - d_x b) (Eq. "eq:mhe" with the unfiltered
+    Pade curl), and Step 2 with G_E = beta e' + (h^2/12) q' (Eq. "eq:helm2")."""
+    h = 1.0 / N
+    ht = r * h
+    k2 = 24.0 / ht ** 2
+    beta = 1.0 + k2 * h * h / 12.0
+    tx, ty = math.pi * kx * h, math.pi * ky * h
+    mx, my = -d2_symbol(tx, h), -d2_symbol(ty, h)
+    filt = beta - (h * h / 12.0) * (mx + my)
+    p1 = k2 * beta + mx + my - (h * h / 6.0) * mx * my
+    g = k2 * filt / p1
+    dx, dy = pade_symbol(tx, h), pade_symbol(ty, h)
+    S1 = np.eye(4)
+    S1[0, 1], S1[0, 2] = ht * Z * g * dy, -ht * Z * g * dx
+    # q' = q + k2 (e' - e) - Z k2 ht (dy a - dx b), with e' - e = ht Z g (dy a - dx b)
+    c = k2 * ht * Z * (g - 1.0)
+    S1[3, 1], S1[3, 2] = c * dy, -c * dx
+    S2 = np.eye(4)
+    w = ht * k2 / (Z * p1)  # H* = -(k2/Z) curl(G_E) / p1
+    # G_E = beta e + (h^2/12) q
+    S2[1, 0], S2[1, 3] = -w * dy * beta, -w * dy * h * h / 12.0
+    S2[2, 0], S2[2, 3] = w * dx * beta, w * dx * h * h / 12.0
+    return S2 @ S1
