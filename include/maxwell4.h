@@ -71,8 +71,13 @@ typedef enum { MS_CLOSURE_PAPER = 0, MS_CLOSURE_REFLECT = 1 } ms_closure;
  * MS_SCHEME_NC4 is the paper's non-compact fourth-order comparator NC (Sec. 5.2, stencil K4 of
  * Eq. "eq:K4" with a = 0: the (9/8, -1/24) staggered difference, the standard fourth-order
  * one-sided difference (-23, 21, 3, -1)/24 at the line ends, leapfrog in time).  The two
- * comparators run in FP64 on 2D grids; NC needs r < 1 / (sqrt 2 (9/8 + 1/24)) = 0.606. */
-typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1, MS_SCHEME_NC4 = 2 } ms_scheme;
+ * comparators run in FP64 on 2D grids; NC needs r < 1 / (sqrt 2 (9/8 + 1/24)) = 0.606.
+ * MS_SCHEME_C4_DE is the compact scheme in the form Step 1 / Step 2 print it: Delta E_z is
+ * carried as state DE, advanced after Step 1 by Eq. "eq:mhe" (DE += kappa^2 (E^{n+1} - E^n)
+ * - Z (24/h_tau) curl_h H^{n+1/2}), and Step 2 filters E with it (Eq. "eq:helm2") instead of
+ * with Delta_h E.  FP64, 2D.  DE starts as the exact Delta E of the modes (ms_init_modes) or as
+ * Delta_h E^0 (ms_set_fields); it is internal state, not returned by ms_get_fields. */
+typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1, MS_SCHEME_NC4 = 2, MS_SCHEME_C4_DE = 3 } ms_scheme;
 
 typedef struct {
   int dim;          /* 2 (TM_z: E_z, H_x, H_y) or 3 (six components, see below) */

@@ -17,11 +17,11 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Grid", "Batch", "MaxwellError", "load", "lib_path", "FP64", "FP32_REFINED", "CLOSURE_PAPER", "CLOSURE_REFLECT",
-           "SCHEME_C4", "SCHEME_YEE2", "SCHEME_NC4", "OPS", "stability_limit"]
+           "SCHEME_C4", "SCHEME_YEE2", "SCHEME_NC4", "SCHEME_C4_DE", "OPS", "stability_limit"]
 
 FP64, FP32_REFINED = 0, 1
 CLOSURE_PAPER, CLOSURE_REFLECT = 0, 1
-SCHEME_C4, SCHEME_YEE2, SCHEME_NC4 = 0, 1, 2
+SCHEME_C4, SCHEME_YEE2, SCHEME_NC4, SCHEME_C4_DE = 0, 1, 2, 3
 OPS = {
     "filter_ez": 0, "filter_hx": 1, "filter_hy": 2, "curl_he": 3, "curl_eh": 4,
     "p1_ez": 5, "p1_hx": 6, "p1_hy": 7, "p1solve_ez": 8, "p1solve_hx": 9, "p1solve_hy": 10,
@@ -159,7 +159,8 @@ class Grid:
 
     precision: FP64 or FP32_REFINED; closure: CLOSURE_PAPER or CLOSURE_REFLECT;
     scheme: SCHEME_C4 (the paper's scheme), SCHEME_YEE2 (plain Yee comparator) or SCHEME_NC4
-    (the paper's non-compact fourth-order comparator NC).
+    (the paper's non-compact fourth-order comparator NC) or SCHEME_C4_DE (the compact scheme with
+    Delta E tracked as in Step 1 / Step 2 as printed).
     stream: a cudaStream_t handle (int), "torch" for torch's current stream, or None.
     dim: 2 (E_z, H_x, H_y) or 3 (E_x, E_y, E_z, H_x, H_y, H_z on the unit cube, arrays [z][y][x]).
     """

@@ -128,6 +128,35 @@ void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, doubl
   p1_solve64(g, HY, Ry, hys, hy_upd, g->ht, nl);
 }
 
+// The step as printed in Sec. 3.4 (MS_SCHEME_C4_DE): Step 1 as in step64, then DE advanced by
+// Eq. "eq:mhe" with the unfiltered Pade curl of H, and Step 2 with G_E = beta E + (h^2/12) DE.
+ms_status step64_tracked(ms_grid* g) {
+  int nl = 0;
+  double *ez = g->f64[EZ], *hx = g->f64[HX], *hy = g->f64[HY];
+  double* Gx = g->s64[0];
+  double* Gy = g->s64[1];
+  double* R = g->s64[2];
+  launch_filter64(hx, Gx, g->sh[HX], g->beta, g->stream);
+  prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[HX].size());
+  launch_filter64(hy, Gy, g->sh[HY], g->beta, g->stream);
+  prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[HY].size());
+  nl += 2;
+  curl_he64(g, Gx, Gy, R, &nl);
+  p1_solve64(g, EZ, R, g->s64[5], ez, g->ht, &nl);  // E* in s64[5], E += h_tau E*
+  curl_he64(g, hx, hy, g->s64[0], &nl);              // kappa^2 Z curl_h H (unfiltered)
+  double* GE = g->s64[1];
+  launch_de_update64(g->de64, g->s64[5], g->s64[0], ez, GE, g->N, g->ht, g->kappa2, g->beta, g->h, g->stream);
+  prof_mark(g, KK_FILTER64, 8.0 * 6.0 * (double)g->sh[EZ].size());
+  nl += 1;
+  double* Rx = g->s64[0];
+  double* Ry = g->s64[2];
+  curl_eh64(g, GE, Rx, Ry, &nl);
+  p1_solve64(g, HX, Rx, g->s64[5], hx, g->ht, &nl);
+  p1_solve64(g, HY, Ry, g->s64[5], hy, g->ht, &nl);
+  g->launches_per_step = nl;
+  return check_launch("fp64 tracked step");
+}
+
 ms_status step64(ms_grid* g) {
   int nl = 0;
   double *ez = g->f64[EZ], *hx = g->f64[HX], *hy = g->f64[HY];
@@ -149,6 +178,7 @@ ms_status step64(ms_grid* g) {
     g->launches_per_step = 2;
     return check_launch("nc step");
   }
+  if (g->desc.scheme == MS_SCHEME_C4_DE) return step64_tracked(g);
   // Step 1: G = (beta + (h^2/12) Delta_h) H, R = kappa^2 Z curl_h G, P1 E* = R, E += h_tau E*
   double* Gx = g->s64[0];
   double* Gy = g->s64[1];
@@ -366,11 +396,13 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   if (!(d->r > 0.0) || !std::isfinite(d->r)) return fail(MS_EINVAL, "r must be positive");
   if (d->precision != MS_FP64 && d->precision != MS_FP32_REFINED) return fail(MS_EINVAL, "unknown precision");
   if (d->closure != MS_CLOSURE_PAPER && d->closure != MS_CLOSURE_REFLECT) return fail(MS_EINVAL, "unknown closure");
-  if (d->scheme != MS_SCHEME_C4 && d->scheme != MS_SCHEME_YEE2 && d->scheme != MS_SCHEME_NC4)
+  if (d->scheme != MS_SCHEME_C4 && d->scheme != MS_SCHEME_YEE2 && d->scheme != MS_SCHEME_NC4 &&
+      d->scheme != MS_SCHEME_C4_DE)
     return fail(MS_EINVAL, "unknown scheme");
   if (d->scheme != MS_SCHEME_C4 && d->precision != MS_FP64)
-    return fail(MS_EUNSUPPORTED, "the Yee and NC comparators run in FP64 only");
-  if (d->scheme == MS_SCHEME_C4) {
+    return fail(MS_EUNSUPPORTED, "the tracked-Delta-E variant and the Yee and NC comparators run in FP64 only");
+  const bool compact = d->scheme == MS_SCHEME_C4 || d->scheme == MS_SCHEME_C4_DE;
+  if (compact) {
     const double rmax = stability_limit_2d();
     if (d->r >= rmax) {
       char buf[160];
@@ -406,7 +438,7 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   // Pade tables (FP64 truncation 1e-18 of the row's absolute sum)
   std::string err;
   // (the Yee and NC comparators use no Pade tables)
-  for (int kind = 0; kind < 2 && d->scheme == MS_SCHEME_C4; ++kind) {
+  for (int kind = 0; kind < 2 && compact; ++kind) {
     const int M = (kind == HALF_TO_NODE) ? g->N - 1 : g->N;
     if (build_pade_table(M, d->closure, kind, 1e-18, &g->pade[kind], &err) != 0) return cleanup(fail(MS_EINVAL, err));
     PadeTable& t = g->pade[kind];
@@ -436,6 +468,10 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   }
   if (d->precision == MS_FP64) {
     for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->f64[f], g->sh[f].size());
+    if (s == MS_OK && d->scheme == MS_SCHEME_C4_DE) {
+      s = dalloc(&g->de64, g->sh[EZ].size());
+      if (s == MS_OK) cudaMemsetAsync(g->de64, 0, g->sh[EZ].size() * sizeof(double), g->stream);
+    }
   } else {
     for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->hi[f], g->sh[f].size());
     for (int f = 0; f < 3 && s == MS_OK; ++f) s = dalloc(&g->lo[f], g->sh[f].size());
@@ -478,6 +514,7 @@ ms_status ms_destroy(ms_grid* g) {
     cudaFree(g->hi[f]);
     cudaFree(g->lo[f]);
   }
+  cudaFree(g->de64);
   for (int k = 0; k < 6 && !g->shared64; ++k) cudaFree(g->s64[k]);
   for (int k = 0; k < 8; ++k) cudaFree(g->s32[k]);
   mixed_teardown(g);
@@ -495,6 +532,13 @@ ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes) {
   if (nmodes < 0 || (nmodes > 0 && !modes)) return fail(MS_EINVAL, "invalid modes");
   for (int m = 0; m < nmodes; ++m)
     if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
+  if (g->de64) {
+    // Delta E of a mode is -pi^2 (m^2 + n^2) E: the exact E_z field of the rescaled amplitudes
+    std::vector<ms_mode> lap(modes, modes + nmodes);
+    for (ms_mode& m : lap) m.amp *= -M_PI * M_PI * ((double)m.m * m.m + (double)m.n * m.n);
+    double* dd[3] = {g->de64, g->s64[0], g->s64[1]};
+    MS_TRY(exact_fields64(g, lap.data(), nmodes, 0.0, 0.5 * g->ht, dd));
+  }
   double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
   MS_TRY(exact_fields64(g, modes, nmodes, 0.0, 0.5 * g->ht, dst));
   MS_TRY(store_state(g, dst));
@@ -513,8 +557,9 @@ ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step
   for (int f = 0; f < 3; ++f)
     if (!comps[f]) return fail(MS_EINVAL, "NULL component");
   MS_TRY(store_state(g, comps));
+  if (g->de64) launch_lap_e64(g->f64[EZ], g->de64, g->N, g->h, g->stream);  // DE^0 = Delta_h E^0
   g->step = step;
-  return MS_OK;
+  return check_launch("set fields");
 }
 
 ms_status ms_get_fields_device(ms_grid* g, double* const* comps) {
@@ -544,8 +589,9 @@ ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
     MS_CUDA(cudaMemcpyAsync(dst[f], comps[f], g->sh[f].size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
   }
   MS_TRY(store_state(g, dst));
+  if (g->de64) launch_lap_e64(g->f64[EZ], g->de64, g->N, g->h, g->stream);  // DE^0 = Delta_h E^0
   g->step = step;
-  return MS_OK;
+  return check_launch("set fields");
 }
 
 ms_status ms_get_fields(ms_grid* g, double* const* comps) {
@@ -697,7 +743,8 @@ ms_status ms_energy(ms_grid* g, double* W) {
 ms_status ms_divergence(ms_grid* g, double* norm) {
   if (!valid_grid(g) || !norm) return fail(MS_EINVAL, "invalid argument");
   if (g->g3) return fail(MS_EUNSUPPORTED, "the divergence is implemented for 2D grids");
-  if (g->desc.scheme != MS_SCHEME_C4) return fail(MS_EUNSUPPORTED, "the Pade divergence is defined for the compact scheme");
+  if (g->desc.scheme != MS_SCHEME_C4 && g->desc.scheme != MS_SCHEME_C4_DE)
+    return fail(MS_EUNSUPPORTED, "the Pade divergence is defined for the compact scheme");
   double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
   const double* view[3];
   MS_TRY(state64(g, tmp, view));

@@ -32,6 +32,11 @@ void launch_p1_sweep64(const double* b, const double* xin, double* xout, const S
 void launch_p1_apply64(const double* x, double* out, const Shape& s, double c1h2, double out_scale, cudaStream_t st);
 void launch_yee_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
 void launch_yee_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);
+// Tracked-Delta-E variant (k_tracked.cu): DE += kappa^2 h_tau E* - (24/h_tau) c / kappa^2 with
+// c = kappa^2 Z curl_h H, then G_E = beta E + (h^2/12) DE; and DE = Delta_h E for initial data.
+void launch_de_update64(double* de, const double* es, const double* c, const double* e, double* ge, int N, double ht,
+                        double k2, double beta, double h, cudaStream_t st);
+void launch_lap_e64(const double* e, double* de, int N, double h, cudaStream_t st);
 // Non-compact fourth-order comparator NC (k_nc.cu)
 void launch_nc_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
 void launch_nc_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);

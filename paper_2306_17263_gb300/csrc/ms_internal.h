@@ -104,6 +104,7 @@ struct ms_grid {
 
   // FP64 state and scratch
   double* f64[3] = {nullptr, nullptr, nullptr};   // E_z, H_x, H_y
+  double* de64 = nullptr;                          // tracked Delta E_z (MS_SCHEME_C4_DE)
   double* s64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool shared64 = false;  // s64 planes belong to a batch
   // FP32 hi/lo state (MS_FP32_REFINED)

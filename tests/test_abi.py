@@ -40,7 +40,8 @@ def _desc(**kw):
     (dict(r=-0.1), -1), (dict(r=float("nan")), -1), (dict(precision=5), -1), (dict(closure=9), -1),
     (dict(scheme=4), -1), (dict(r=0.70), -2), (dict(r=1 / math.sqrt(2)), -2),
     (dict(scheme=1, r=0.75), -2), (dict(scheme=1, precision=1), -7),
-    (dict(scheme=2, r=0.61), -2), (dict(scheme=2, precision=1), -7), (dict(scheme=3), -1),
+    (dict(scheme=2, r=0.61), -2), (dict(scheme=2, precision=1), -7), (dict(scheme=4), -1),
+    (dict(scheme=3, precision=1), -7), (dict(scheme=3, r=0.70), -2),
 ])
 def test_descriptor_validation(kw, status):
     L = pkg.load()
