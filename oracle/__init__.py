@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
             L.or_nc_line.argtypes = [ctypes.c_int, ctypes.c_double, D, D]
             L.or2d_nc_step.argtypes = [V, D, D, D]
             L.or2d_step_tracked.argtypes = [V, D, D, D, D]
+            L.or2d_step_src.argtypes = [V, D, D, D, D, ctypes.c_int, ctypes.c_long]
+            L.or2d_exact_driven.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D, D]
             PP = ctypes.POINTER(ctypes.c_void_p)
             L.or3d_sizeof.restype = ctypes.c_int
             L.or3d_setup.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -241,6 +243,24 @@ class Oracle2D:
         """One step of the tracked-Delta-E variant in place (Sec. 3.4 as printed: DE advanced by
         Eq. "eq:mhe", Step 2 filtered with it as in Eq. "eq:helm2")."""
         lib().or2d_step_tracked(self.g, _p(ez), _p(hx), _p(hy), _p(de))
+
+    @staticmethod
+    def _src(src):
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.float64).reshape(-1, 4))
+        return a, a.shape[0]
+
+    def step_src(self, ez, hx, hy, src, n):
+        """Step n (E^n -> E^{n+1}) with current sources J_z = a sin(m pi x) sin(n pi y) sin(w t),
+        rows (m, n, a, w): P(J) and curl d_t J added to the right-hand sides of Eq. "eq:mh"."""
+        s, ns = self._src(src)
+        lib().or2d_step_src(self.g, _p(ez), _p(hx), _p(hy), _p(s), ns, int(n))
+
+    def exact_driven(self, src, tE, tH):
+        """Exact particular solution driven by the sources (E at tE, H at tH)."""
+        s, ns = self._src(src)
+        ez, hx, hy = self.zeros(F_EZ), self.zeros(F_HX), self.zeros(F_HY)
+        lib().or2d_exact_driven(self.g, _p(s), ns, tE, tH, _p(ez), _p(hx), _p(hy))
+        return ez, hx, hy
 
     def nc_step(self, ez, hx, hy):
         """One step of the non-compact fourth-order comparator NC in place (Sec. 5.2, K4, a = 0)."""

@@ -928,3 +928,102 @@ void or2d_step_tracked(or_grid2d* g, double* ez, double* hx, double* hy, double*
   free(Ry);
   free(Hs);
 }
+
+/* ------------------------------------------------------------------ */
+/* Current sources J = J_z z (2D TM_z, so div J = 0), a superposition of driven sine modes
+ *   J_z = a sin(m pi x) sin(n pi y) sin(w t),  src rows (m, n, a, w),
+ * which vanish on the walls with all the derivatives the Neumann data of Sec. 3.3 involve, so the
+ * even ghosts of Cor. "cor:ghost_cor" stay exact.  The modified Helmholtz equations of Eq. "eq:mh"
+ * gain, from the Taylor expansion of Sec. 3.1 written out with Faraday's and Ampere's laws,
+ *   E:  P(J) = Z (-kappa^2 J + grad div J - d_tt J) = -Z (kappa^2 - w^2) J   at t^{n+1/2},
+ *   H:  + curl d_t J = (d_y d_t J_z, -d_x d_t J_z)                            at t^{n+1},
+ * each passed through the right-hand-side filter of Eq. "eq:ell" with the exact Laplacian of
+ * the source (the form of Eq. "eq:helm2"): factor beta - (h^2/12) pi^2 (m^2 + n^2). */
+static void add_sources_e(const or_grid2d* g, const double* src, int nsrc, double t, double* R) {
+  int N = g->N;
+  double pi = M_PI, h = g->h;
+  for (int q = 0; q < nsrc; ++q) {
+    double m = src[4 * q], n = src[4 * q + 1], a = src[4 * q + 2], w = src[4 * q + 3];
+    double filt = g->beta - (h * h / 12.0) * pi * pi * (m * m + n * n);
+    double amp = -g->Z * (g->kappa2 - w * w) * filt * a * sin(w * t);
+    for (int j = 1; j < N; ++j)
+      for (int i = 1; i < N; ++i) R[(size_t)j * (N + 1) + i] += amp * sin(pi * m * i * h) * sin(pi * n * j * h);
+  }
+}
+
+static void add_sources_h(const or_grid2d* g, const double* src, int nsrc, double t, double* Rx, double* Ry) {
+  int N = g->N;
+  double pi = M_PI, h = g->h;
+  for (int q = 0; q < nsrc; ++q) {
+    double m = src[4 * q], n = src[4 * q + 1], a = src[4 * q + 2], w = src[4 * q + 3];
+    double filt = g->beta - (h * h / 12.0) * pi * pi * (m * m + n * n);
+    double c = filt * a * w * cos(w * t);
+    for (int j = 0; j < N; ++j) /* H_x at (x_i, y_{j+1/2}): d_y d_t J_z */
+      for (int i = 1; i < N; ++i)
+        Rx[(size_t)j * (N + 1) + i] += c * pi * n * sin(pi * m * i * h) * cos(pi * n * (j + 0.5) * h);
+    for (int j = 1; j < N; ++j) /* H_y at (x_{i+1/2}, y_j): -d_x d_t J_z */
+      for (int i = 0; i < N; ++i)
+        Ry[(size_t)j * N + i] -= c * pi * m * cos(pi * m * (i + 0.5) * h) * sin(pi * n * j * h);
+  }
+}
+
+/* One full step with sources: or2d_step with P(J)^{n+1/2} added to the E right-hand side and
+ * curl d_t J^{n+1} to the H right-hand sides; n is the index of the step (E^n -> E^{n+1}). */
+void or2d_step_src(or_grid2d* g, double* ez, double* hx, double* hy, const double* src, int nsrc, long n) {
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* Gx = (double*)malloc(sizeof(double) * nx_);
+  double* Gy = (double*)malloc(sizeof(double) * ny_);
+  double* R = (double*)malloc(sizeof(double) * ne);
+  double* Es = (double*)malloc(sizeof(double) * ne);
+  double* GE = (double*)malloc(sizeof(double) * ne);
+  double* Rx = (double*)malloc(sizeof(double) * nx_);
+  double* Ry = (double*)malloc(sizeof(double) * ny_);
+  double* Hs = (double*)malloc(sizeof(double) * (nx_ > ny_ ? nx_ : ny_));
+  or2d_filter(g, F_HX, hx, Gx);
+  or2d_filter(g, F_HY, hy, Gy);
+  or2d_curl_h_to_e(g, Gx, Gy, R);
+  add_sources_e(g, src, nsrc, (n + 0.5) * g->ht, R);
+  or2d_p1_solve_cg(g, F_EZ, R, Es);
+  for (int p = 0; p < ne; ++p) ez[p] += g->ht * Es[p];
+  or2d_filter(g, F_EZ, ez, GE);
+  or2d_curl_e_to_h(g, GE, Rx, Ry);
+  add_sources_h(g, src, nsrc, (n + 1.0) * g->ht, Rx, Ry);
+  or2d_p1_solve_cg(g, F_HX, Rx, Hs);
+  for (int p = 0; p < nx_; ++p) hx[p] += g->ht * Hs[p];
+  or2d_p1_solve_cg(g, F_HY, Ry, Hs);
+  for (int p = 0; p < ny_; ++p) hy[p] += g->ht * Hs[p];
+  free(Gx);
+  free(Gy);
+  free(R);
+  free(Es);
+  free(GE);
+  free(Rx);
+  free(Ry);
+  free(Hs);
+}
+
+/* Exact driven solution for the sources above (particular solution, w^2 != pi^2 (m^2 + n^2)):
+ *   E_z = A cos(w t) sin(m pi x) sin(n pi y),  A = Z a w / (w^2 - pi^2 (m^2 + n^2)),
+ *   H_x = -(A n pi / (Z w)) sin(w t) sin(m pi x) cos(n pi y),  H_y = (A m pi / (Z w)) sin(w t) cos(m pi x) sin(n pi y),
+ * from Faraday's law and d_tt E_z = Delta E_z - Z d_t J_z. */
+void or2d_exact_driven(const or_grid2d* g, const double* src, int nsrc, double tE, double tH, double* ez, double* hx,
+                       double* hy) {
+  int N = g->N;
+  double h = g->h, pi = M_PI;
+  memset(ez, 0, sizeof(double) * (N + 1) * (N + 1));
+  memset(hx, 0, sizeof(double) * N * (N + 1));
+  memset(hy, 0, sizeof(double) * N * (N + 1));
+  for (int q = 0; q < nsrc; ++q) {
+    double m = src[4 * q], n = src[4 * q + 1], a = src[4 * q + 2], w = src[4 * q + 3];
+    double A = g->Z * a * w / (w * w - pi * pi * (m * m + n * n));
+    double ce = A * cos(w * tE), sh = A * sin(w * tH) / (g->Z * w);
+    for (int j = 1; j < N; ++j)
+      for (int i = 1; i < N; ++i) ez[(size_t)j * (N + 1) + i] += ce * sin(pi * m * i * h) * sin(pi * n * j * h);
+    for (int j = 0; j < N; ++j)
+      for (int i = 1; i < N; ++i)
+        hx[(size_t)j * (N + 1) + i] += -sh * pi * n * sin(pi * m * i * h) * cos(pi * n * (j + 0.5) * h);
+    for (int j = 1; j < N; ++j)
+      for (int i = 0; i < N; ++i)
+        hy[(size_t)j * N + i] += sh * pi * m * cos(pi * m * (i + 0.5) * h) * sin(pi * n * j * h);
+  }
+}

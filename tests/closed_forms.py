@@ -137,3 +137,30 @@ def mode_step_matrix_tracked(N: int, r: float, kx: int, ky: int, Z: float = 1.0)
     S2[1, 0], S2[1, 3] = -w * dy * beta, -w * dy * h * h / 12.0
     S2[2, 0], S2[2, 3] = w * dx * beta, w * dx * h * h / 12.0
     return S2 @ S1
+
+
+def mode_step_forced(N, r, m, n, Z, src_amp, w, step):
+    """Affine per-mode step (M, f) of the scheme with the current source
+    J_z = src_amp sin(m pi x) sin(n pi y) sin(w t) on the coefficients (e, a, b) of mode_basis:
+    v_{step+1} = M v_step + f, with P(J) = -Z (kappa^2 - w^2) J at t^{n+1/2} added to Step 1 and
+    curl d_t J at t^{n+1} to Step 2, both filtered with the exact Laplacian of the source."""
+    h = 1.0 / N
+    ht = r * h
+    k2 = 24.0 / ht ** 2
+    beta = 1.0 + k2 * h * h / 12.0
+    tx, ty = math.pi * m * h, math.pi * n * h
+    mx, my = -d2_symbol(tx, h), -d2_symbol(ty, h)
+    filt = beta - (h * h / 12.0) * (mx + my)
+    p1 = k2 * beta + mx + my - (h * h / 6.0) * mx * my
+    g = k2 * filt / p1
+    dx, dy = pade_symbol(tx, h), pade_symbol(ty, h)
+    fj = beta - (h * h / 12.0) * math.pi ** 2 * (m * m + n * n)
+    th, tn = (step + 0.5) * ht, (step + 1.0) * ht
+    se = -Z * (k2 - w * w) * fj * src_amp * math.sin(w * th)
+    shx = fj * src_amp * w * math.pi * n * math.cos(w * tn)
+    shy = fj * src_amp * w * math.pi * m * math.cos(w * tn)
+    S1 = np.array([[1.0, ht * Z * g * dy, -ht * Z * g * dx], [0, 1, 0], [0, 0, 1]])
+    f1 = np.array([ht * se / p1, 0.0, 0.0])
+    S2 = np.array([[1.0, 0, 0], [-(ht / Z) * g * dy, 1, 0], [(ht / Z) * g * dx, 0, 1]])
+    f2 = np.array([0.0, ht * shx / p1, -ht * shy / p1])
+    return S2 @ S1, S2 @ f1 + f2
