@@ -250,6 +250,36 @@ ms_status ms_p1_solve_static(int n, double r, int field, const double* b, double
 ms_status ms_launches_per_step(ms_grid* g, int* launches);
 
 /* ---------------------------------------------------------------------------------------
+ * Current sources (2D TM_z, J = J_z z, so div J = 0 and rho stays 0): a superposition of driven
+ * sine modes
+ *   J_z = amp sin(pi m x) sin(pi n y) sin(omega t),  m, n >= 1,
+ * which vanish on the walls with every derivative the Neumann data of Sec. 3.3 involve, so the
+ * boundary treatment of the homogeneous scheme stays exact.  The modified Helmholtz equations of
+ * Eq. "eq:mh" gain, from the Taylor expansion of Sec. 3.1 written out with Faraday's and Ampere's
+ * laws, P(J) = Z (-kappa^2 J + grad div J - d_tt J) at t^{n+1/2} on the E side and curl d_t J at
+ * t^{n+1} on the H side, each through the right-hand-side filter of Eq. "eq:ell" with the exact
+ * Laplacian of the source.  (The printed P(J) of Eq. "eq:pj" and the J term of the H expansion
+ * differ from this derivation; the derived form is the fourth-order one.)
+ *
+ * ms_set_sources: replaces the grid's sources (nsrc = 0 removes them); 2D MS_SCHEME_C4 grids in
+ *   either precision (MS_EUNSUPPORTED otherwise); at most 64 sources.  The step index that fixes
+ *   the source time is kept on the device, so ms_run's captured graphs stay valid.
+ * ms_init_driven: E^0, H^{1/2} = the exact particular solution the sources drive (omega^2 must
+ *   differ from pi^2 (m^2 + n^2)):
+ *     E_z = A cos(omega t) sin(pi m x) sin(pi n y),  A = Z amp omega / (omega^2 - pi^2 (m^2 + n^2)),
+ *     H_x = -(A pi n / (Z omega)) sin(omega t) sin(pi m x) cos(pi n y),
+ *     H_y =  (A pi m / (Z omega)) sin(omega t) cos(pi m x) sin(pi n y);  step counter 0.
+ * ms_error_vs_driven: as ms_error_vs_exact against that solution at t_E = n h_tau, t_H = (n+1/2) h_tau. */
+typedef struct {
+  int m, n;
+  double amp, omega;
+} ms_source;
+ms_status ms_set_sources(ms_grid* g, const ms_source* src, int nsrc);
+ms_status ms_init_driven(ms_grid* g, const ms_source* src, int nsrc);
+ms_status ms_error_vs_driven(ms_grid* g, const ms_source* src, int nsrc, double* l2_abs, double* l2_rel,
+                             double* max_abs, double* sum_abs);
+
+/* ---------------------------------------------------------------------------------------
  * Initial data that is not a cavity mode, and the reverse (adjoint) pass.
  *
  * ms_taylor_init sets E_z^0 = ez0 (boundary entries ignored, stored as zero) and H^{1/2} by the

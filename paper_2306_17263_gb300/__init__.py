@@ -46,6 +46,10 @@ class _Mode(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("amp", ctypes.c_double)]
 
 
+class _Source(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("amp", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
 class _Mode3(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("az", ctypes.c_double)]
@@ -100,6 +104,9 @@ def load() -> ctypes.CDLL:
             "ms_batch_info": [V, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I)],
             "ms_step_profiled": [V, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), PD, ctypes.POINTER(I)],
             "ms_init_modes3": [V, ctypes.POINTER(_Mode3), I],
+            "ms_set_sources": [V, ctypes.POINTER(_Source), I],
+            "ms_init_driven": [V, ctypes.POINTER(_Source), I],
+            "ms_error_vs_driven": [V, ctypes.POINTER(_Source), I, PD, PD, PD, PD],
             "ms_error_vs_exact3": [V, ctypes.POINTER(_Mode3), I, PD, PD, PD, PD],
             "ms_taylor_init": [V, V],
             "ms_taylor_init_device": [V, V],
@@ -141,6 +148,14 @@ def _modes3(modes):
         arr[k].m, arr[k].n, arr[k].p = int(m), int(n), int(p)
         arr[k].ax, arr[k].ay, arr[k].az = float(ax), float(ay), float(az)
     return arr, len(modes)
+
+
+def _sources(src):
+    src = list(src)
+    arr = (_Source * max(1, len(src)))()
+    for k, (m, n, a, w) in enumerate(src):
+        arr[k].m, arr[k].n, arr[k].amp, arr[k].omega = int(m), int(n), float(a), float(w)
+    return arr, len(src)
 
 
 def _ptrs(ptrs):
@@ -307,6 +322,23 @@ class Grid:
         """Operator entry point on CUDA float64 tensors (see maxwell4.h, ms_apply_op)."""
         _check(load().ms_apply_op(self._h, OPS[op], _ptrs([t.data_ptr() for t in ins]),
                                   _ptrs([t.data_ptr() for t in outs])))
+
+    # -- current sources J_z = amp sin(pi m x) sin(pi n y) sin(omega t) (maxwell4.h, ms_set_sources) --
+    def set_sources(self, src):
+        """Rows (m, n, amp, omega); an empty list removes the sources."""
+        arr, ns = _sources(src)
+        _check(load().ms_set_sources(self._h, arr, ns))
+
+    def init_driven(self, src):
+        """E^0, H^{1/2} = the exact particular solution driven by the sources."""
+        arr, ns = _sources(src)
+        _check(load().ms_init_driven(self._h, arr, ns))
+
+    def error_vs_driven(self, src):
+        arr, ns = _sources(src)
+        out = [ctypes.c_double() for _ in range(4)]
+        _check(load().ms_error_vs_driven(self._h, arr, ns, *[ctypes.byref(v) for v in out]))
+        return tuple(v.value for v in out)
 
     # -- non-mode initial data and the reverse pass (maxwell4.h, ms_taylor_init / ms_adjoint_*) --
     def _host(self, a, shape):

@@ -116,7 +116,8 @@ void p1_solve64(ms_grid* g, int f, const double* b, double* out, double* upd, do
 namespace {
 
 // H* = P1^{-1} R_H(E) for a given E (Step 2 without the update) into hxs, hys.
-void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, double* hx_upd, double* hy_upd, int* nl) {
+void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, double* hx_upd, double* hy_upd, int* nl,
+                   bool with_sources = false) {
   double* GE = g->s64[0];
   double* Rx = g->s64[1];
   double* Ry = g->s64[2];
@@ -124,6 +125,11 @@ void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, doubl
   prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[EZ].size());
   *nl += 1;
   curl_eh64(g, GE, Rx, Ry, nl);
+  if (with_sources && g->nsrc) {
+    launch_src_h64(g, Rx, Ry, 1.0);
+    prof_mark(g, KK_SRC, 8.0 * 2.0 * (double)g->sh[HX].size());
+    *nl += 1;
+  }
   p1_solve64(g, HX, Rx, hxs, hx_upd, g->ht, nl);
   p1_solve64(g, HY, Ry, hys, hy_upd, g->ht, nl);
 }
@@ -189,10 +195,20 @@ ms_status step64(ms_grid* g) {
   prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[HY].size());
   nl += 2;
   curl_he64(g, Gx, Gy, R, &nl);
+  if (g->nsrc) {
+    launch_src_e64(g, R, 1.0);
+    prof_mark(g, KK_SRC, 16.0 * (double)g->sh[EZ].size());
+    nl += 1;
+  }
   // the solve's result lands in s64[5]; the last sweep also performs E += h_tau E*
   p1_solve64(g, EZ, R, g->s64[5], ez, g->ht, &nl);
   // Step 2 on E^{n+1}
-  h_increment64(g, ez, g->s64[5], g->s64[5], hx, hy, &nl);
+  h_increment64(g, ez, g->s64[5], g->s64[5], hx, hy, &nl, true);
+  if (g->nsrc) {
+    launch_tick(g);
+    prof_mark(g, KK_SRC, 0.0);
+    nl += 1;
+  }
   g->launches_per_step = nl;
   return check_launch("fp64 step");
 }
@@ -246,7 +262,8 @@ ms_status ensure_partial(ms_grid* g, size_t n) {
 
 // 1D tables of the separable cavity modes on the three grids (Eq. "eq:data").
 // Per field: [tab_x (nm x nx)] [tab_y (nm x ny)] [coef (nm)].
-ms_status exact_fields64(ms_grid* g, const ms_mode* modes, int nm, double tE, double tH, double* out[3]) {
+ms_status exact_fields64(ms_grid* g, const ms_mode* modes, int nm, double tE, double tH, double* out[3],
+                         const double* wover = nullptr) {
   const int N = g->N;
   const double pi = M_PI;
   std::vector<double> host;
@@ -272,7 +289,7 @@ ms_status exact_fields64(ms_grid* g, const ms_mode* modes, int nm, double tE, do
   };
   for (int m = 0; m < nm; ++m) {
     const int kx = modes[m].m, ky = modes[m].n;
-    const double A = modes[m].amp, w = pi * std::sqrt((double)kx * kx + (double)ky * ky);
+    const double A = modes[m].amp, w = wover ? wover[m] : pi * std::sqrt((double)kx * kx + (double)ky * ky);
     // E_z
     for (int i = 0; i <= N; ++i) host[offs[EZ][0] + (size_t)m * (N + 1) + i] = sin_node(kx, i);
     for (int j = 0; j <= N; ++j) host[offs[EZ][1] + (size_t)m * (N + 1) + j] = sin_node(ky, j);
@@ -335,6 +352,38 @@ ms_status store_state(ms_grid* g, const double* const* src) {
 
 bool valid_grid(ms_grid* g) { return g != nullptr && g->N > 0; }
 
+// The device copy of the step index read by the source kernels (sources only).
+ms_status sync_step(ms_grid* g) {
+  if (g->d_step) MS_CUDA(cudaMemcpyAsync(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice, g->stream));
+  return MS_OK;
+}
+
+ms_status check_sources(ms_grid* g, const ms_source* src, int nsrc, bool need_off_resonance) {
+  if (nsrc < 0 || nsrc > 64 || (nsrc > 0 && !src)) return fail(MS_EINVAL, "invalid sources (0 <= nsrc <= 64)");
+  for (int q = 0; q < nsrc; ++q) {
+    if (src[q].m < 1 || src[q].n < 1) return fail(MS_EINVAL, "source indices must be >= 1");
+    if (!std::isfinite(src[q].amp) || !std::isfinite(src[q].omega)) return fail(MS_EINVAL, "non-finite source");
+    const double w2 = M_PI * M_PI * ((double)src[q].m * src[q].m + (double)src[q].n * src[q].n);
+    if (need_off_resonance && std::fabs(src[q].omega * src[q].omega - w2) <= 1e-12 * w2)
+      return fail(MS_EINVAL, "the driven solution needs omega^2 != pi^2 (m^2 + n^2)");
+    if (need_off_resonance && src[q].omega == 0.0) return fail(MS_EINVAL, "the driven solution needs omega != 0");
+  }
+  (void)g;
+  return MS_OK;
+}
+
+// The driven solution as a mode superposition with its own frequencies (ms_init_driven).
+void driven_modes(ms_grid* g, const ms_source* src, int nsrc, std::vector<ms_mode>* modes, std::vector<double>* w) {
+  modes->resize(nsrc);
+  w->resize(nsrc);
+  for (int q = 0; q < nsrc; ++q) {
+    const double om = src[q].omega;
+    const double w2 = M_PI * M_PI * ((double)src[q].m * src[q].m + (double)src[q].n * src[q].n);
+    (*modes)[q] = ms_mode{src[q].m, src[q].n, g->Z * src[q].amp * om / (om * om - w2)};
+    (*w)[q] = om;
+  }
+}
+
 }  // namespace
 
 namespace ms {
@@ -358,7 +407,7 @@ const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64", "filter32",
                                         "pade32", "p1sweep32", "curl32", "solve32", "filter3d64",
                                         "pade3d64", "sweep3d64", "dfilt3d32", "band3d32", "sweep3d32",
-                                        "nc64"};
+                                        "nc64", "source"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }
 
@@ -515,6 +564,9 @@ ms_status ms_destroy(ms_grid* g) {
     cudaFree(g->lo[f]);
   }
   cudaFree(g->de64);
+  cudaFree(g->d_src);
+  cudaFree(g->d_srctab);
+  cudaFree(g->d_step);
   for (int k = 0; k < 6 && !g->shared64; ++k) cudaFree(g->s64[k]);
   for (int k = 0; k < 8; ++k) cudaFree(g->s32[k]);
   mixed_teardown(g);
@@ -543,6 +595,7 @@ ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes) {
   MS_TRY(exact_fields64(g, modes, nmodes, 0.0, 0.5 * g->ht, dst));
   MS_TRY(store_state(g, dst));
   g->step = 0;
+  MS_TRY(sync_step(g));
   MS_CUDA(cudaStreamSynchronize(g->stream));
   return MS_OK;
 }
@@ -559,6 +612,7 @@ ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step
   MS_TRY(store_state(g, comps));
   if (g->de64) launch_lap_e64(g->f64[EZ], g->de64, g->N, g->h, g->stream);  // DE^0 = Delta_h E^0
   g->step = step;
+  MS_TRY(sync_step(g));
   return check_launch("set fields");
 }
 
@@ -591,6 +645,7 @@ ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
   MS_TRY(store_state(g, dst));
   if (g->de64) launch_lap_e64(g->f64[EZ], g->de64, g->N, g->h, g->stream);  // DE^0 = Delta_h E^0
   g->step = step;
+  MS_TRY(sync_step(g));
   return check_launch("set fields");
 }
 
@@ -774,6 +829,78 @@ ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double
     if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
   double* ex[3] = {g->s64[0], g->s64[1], g->s64[2]};
   MS_TRY(exact_fields64(g, modes, nmodes, g->step * g->ht, (g->step + 0.5) * g->ht, ex));
+  double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  const double* view[3];
+  MS_TRY(state64(g, tmp, view));
+  for (int f = 0; f < 3; ++f) {
+    const size_t n = g->sh[f].size();
+    launch_err_reduce(view[f], ex[f], n, g->d_partial, reduce_blocks(n), g->d_result, f > 0, g->stream);
+  }
+  MS_TRY(check_launch("error reduce"));
+  double r[4];
+  MS_CUDA(cudaMemcpyAsync(r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  if (l2_abs) *l2_abs = std::sqrt(g->h * g->h * r[0]);
+  if (l2_rel) *l2_rel = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
+  if (max_abs) *max_abs = r[2];
+  if (sum_abs) *sum_abs = r[3];
+  return MS_OK;
+}
+
+ms_status ms_set_sources(ms_grid* g, const ms_source* src, int nsrc) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3 || g->desc.scheme != MS_SCHEME_C4)
+    return fail(MS_EUNSUPPORTED, "sources are implemented for 2D grids of the compact scheme");
+  MS_TRY(check_sources(g, src, nsrc, false));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  cudaFree(g->d_src);
+  cudaFree(g->d_srctab);
+  g->d_src = nullptr;
+  g->d_srctab = nullptr;
+  g->nsrc = 0;
+  free_graph(&g->graph1);  // the captured steps do not contain the source launches
+  free_graph(&g->graphk);
+  g->launches_per_step = 0;
+  if (nsrc == 0) return MS_OK;
+  std::vector<unsigned char> blob;
+  std::vector<double> tabs;
+  build_sources(g, src, nsrc, &blob, &tabs);
+  MS_TRY(dalloc((unsigned char**)&g->d_src, blob.size()));
+  MS_TRY(dalloc(&g->d_srctab, tabs.size()));
+  if (!g->d_step) MS_TRY(dalloc(&g->d_step, 1));
+  MS_CUDA(cudaMemcpy(g->d_src, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  MS_CUDA(cudaMemcpy(g->d_srctab, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice));
+  MS_CUDA(cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice));
+  g->nsrc = nsrc;
+  return MS_OK;
+}
+
+ms_status ms_init_driven(ms_grid* g, const ms_source* src, int nsrc) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3) return fail(MS_EUNSUPPORTED, "driven solutions are implemented for 2D grids");
+  MS_TRY(check_sources(g, src, nsrc, true));
+  std::vector<ms_mode> modes;
+  std::vector<double> w;
+  driven_modes(g, src, nsrc, &modes, &w);
+  double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
+  MS_TRY(exact_fields64(g, modes.data(), nsrc, 0.0, 0.5 * g->ht, dst, w.data()));
+  MS_TRY(store_state(g, dst));
+  g->step = 0;
+  MS_TRY(sync_step(g));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status ms_error_vs_driven(ms_grid* g, const ms_source* src, int nsrc, double* l2_abs, double* l2_rel,
+                             double* max_abs, double* sum_abs) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3) return fail(MS_EUNSUPPORTED, "driven solutions are implemented for 2D grids");
+  MS_TRY(check_sources(g, src, nsrc, true));
+  std::vector<ms_mode> modes;
+  std::vector<double> w;
+  driven_modes(g, src, nsrc, &modes, &w);
+  double* ex[3] = {g->s64[0], g->s64[1], g->s64[2]};
+  MS_TRY(exact_fields64(g, modes.data(), nsrc, g->step * g->ht, (g->step + 0.5) * g->ht, ex, w.data()));
   double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};
   const double* view[3];
   MS_TRY(state64(g, tmp, view));

@@ -37,6 +37,15 @@ void launch_yee_h64(const double* ez, double* hx, double* hy, int N, double c_h,
 void launch_de_update64(double* de, const double* es, const double* c, const double* e, double* ge, int N, double ht,
                         double k2, double beta, double h, cudaStream_t st);
 void launch_lap_e64(const double* e, double* de, int N, double h, cudaStream_t st);
+// Current sources (k_src.cu): host tables and constants; launches that add P(J) to an E right-hand
+// side and curl d_t J to the H right-hand sides (scaled by `scale`), and the device step tick.
+int build_sources(ms_grid* g, const ms_source* src, int nsrc, std::vector<unsigned char>* dev_blob,
+                  std::vector<double>* tabs);
+void launch_src_e64(ms_grid* g, double* R, double scale);
+void launch_src_h64(ms_grid* g, double* Rx, double* Ry, double scale);
+void launch_src_e32(ms_grid* g, float* R, double scale);
+void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale);
+void launch_tick(ms_grid* g);
 // Non-compact fourth-order comparator NC (k_nc.cu)
 void launch_nc_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
 void launch_nc_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);

@@ -26,6 +26,7 @@
 #include <cmath>
 #include <string>
 
+#include "k_fp64.cuh"
 #include "k_mixed.cuh"
 #include "k_tiled.cuh"
 
@@ -75,6 +76,13 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   float* bE = g->s32[4];
   tiled_curl(g, 0, k.cb_hi, k.cb_lo, bE, nullptr);
   prof_mark(g, KK_CURL32, 4.0 * (4.0 * nh + ne));            // H_x, H_y (hi, lo) in; b out
+  // sources in the units of b: 6 h^2 P1 x = b with E += (12 Z / r) x, so b = (h^3 r^2 / (2 Z)) R
+  const double hr2 = g->h * g->h * g->h * g->desc.r * g->desc.r;
+  if (g->nsrc) {
+    launch_src_e32(g, bE, hr2 / (2.0 * g->Z));
+    prof_mark(g, KK_SRC, 8.0 * ne);
+    *nl += 1;
+  }
   const int fe[1] = {EZ};
   const float* be[1] = {bE};
   tiled_solve(g, 1, fe, be, k.S, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo);
@@ -84,10 +92,20 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   float* by = g->s32[3];
   tiled_curl(g, 1, k.cb_hi, k.cb_lo, bx, by);
   prof_mark(g, KK_CURL32, 4.0 * (2.0 * ne + 2.0 * nh));      // E (hi, lo) in; b_x, b_y out
+  if (g->nsrc) {  // H += (12 / (r Z)) x, so b = (h^3 r^2 Z / 2) R
+    launch_src_h32(g, bx, by, hr2 * g->Z / 2.0);
+    prof_mark(g, KK_SRC, 16.0 * nh);
+    *nl += 1;
+  }
   const int fh[2] = {HX, HY};
   const float* bh[2] = {bx, by};
   tiled_solve(g, 2, fh, bh, k.S, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo);
   prof_mark(g, KK_SOLVE32, 4.0 * (2.0 * nh + 8.0 * nh));     // b_x, b_y in; H (hi, lo) read and written
+  if (g->nsrc) {
+    launch_tick(g);
+    prof_mark(g, KK_SRC, 0.0);
+    *nl += 1;
+  }
   *nl += 4;
   return MS_OK;
 }

@@ -61,7 +61,7 @@ enum KernelKind {
   KK_FILTER64 = 0, KK_PADE64 = 1, KK_P1SWEEP64 = 2, KK_YEE64 = 3,
   KK_FILTER32 = 4, KK_PADE32 = 5, KK_P1SWEEP32 = 6, KK_CURL32 = 7, KK_SOLVE32 = 8,
   KK_FILTER3D64 = 9, KK_PADE3D64 = 10, KK_SWEEP3D64 = 11, KK_DFILT3D32 = 12, KK_BAND3D32 = 13, KK_SWEEP3D32 = 14,
-  KK_NC64 = 15,
+  KK_NC64 = 15, KK_SRC = 16,
   KK_COUNT
 };
 const char* kernel_kind_name(int k);
@@ -126,6 +126,12 @@ struct ms_grid {
   ms::PadeTable padeT[2];
   double* adj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ms::Graph adj_graph1, adj_graphk;
+
+  // current sources (k_src.cu): per-source constants, sine/cosine tables, device step index
+  int nsrc = 0;
+  void* d_src = nullptr;
+  double* d_srctab = nullptr;
+  long* d_step = nullptr;
 
   // 3D grids (desc.dim == 3): components, scratch and kernels live in grid3d.cu
   ms::Grid3D* g3 = nullptr;
