@@ -583,7 +583,9 @@ static CurlArgs make_curl(const ms_grid* g, int step, float cb_hi, float cb_lo, 
   A.N = g->N;
   A.b0 = b0;
   A.b1 = b1;
-  A.ntiles = (g->N + 1 + TB - 1) / TB;
+  // every output off the walls has both indices <= N - 1, so tiles cover 0 .. N-1 only; the
+  // right-hand-side planes are zeroed at set-up and their wall entries are never written
+  A.ntiles = (g->N + TB - 1) / TB;
   if (step == 0) {
     A.ph[0] = phase(g, HY, 0, HALF_TO_NODE, cb_hi, cb_lo);
     A.ph[1] = phase(g, HX, 1, HALF_TO_NODE, cb_hi, cb_lo);
