@@ -57,6 +57,23 @@ def dist_info():
     return ws, rank, local
 
 
+def job_step_ms(ms_local: float, dist, device) -> float:
+    """The job's time per step: the slowest rank's (max over ranks); replicas run in lock step
+    between the barriers that bracket the timed region."""
+    if dist is None:
+        return ms_local
+    import torch
+
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, cells_per_rank: int, ms_step: float) -> float:
+    """Whole-job cell-updates/s: every rank advances its own replica of cells_per_rank cells."""
+    return ws * cells_per_rank / (ms_step * 1e-3)
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi every 200 ms while running."""
 
@@ -404,12 +421,8 @@ def run_ours(args, ws, rank, local):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     barrier()
-    ms_step = total_ms / K
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ws * N * N / (ms_step * 1e-3)
+    ms_step = job_step_ms(total_ms / K, dist, "cuda")
+    value = job_value(ws, N * N, ms_step)
 
     l2_abs, l2_rel, max_abs, _ = g.error_vs_exact(modes)
 
