@@ -339,6 +339,16 @@ ms_status ms_batch_error_vs_exact(ms_batch* b, int cavity, const ms_mode* modes,
 /* count: cavities; cells: sum of n[b]^2 (Yee cells advanced per step); launches: kernels per step. */
 ms_status ms_batch_info(ms_batch* b, int* count, long long* cells, int* launches);
 
+/* Checkpoint / resume (the paper has none).  ms_save writes the grid's state (the fields in their
+ * working representation: FP64 arrays, or the exact FP32 hi and lo arrays of MS_FP32_REFINED, plus
+ * the tracked Delta E_z of MS_SCHEME_C4_DE), its step counter and its descriptor to `path`;
+ * ms_load restores them into a grid created with the same dim, n, precision, closure, scheme,
+ * z_imp and r (MS_EINVAL otherwise, or for a file that is not a checkpoint), so a resumed run is
+ * bit-identical to an uninterrupted one.  Sources are configuration, not state, and are not
+ * saved.  Little-endian raw format described in ckpt.cu.  Synchronous; not for batch cavities. */
+ms_status ms_save(ms_grid* g, const char* path);
+ms_status ms_load(ms_grid* g, const char* path);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* ms_last_error(void);
 

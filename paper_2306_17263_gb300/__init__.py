@@ -104,6 +104,8 @@ def load() -> ctypes.CDLL:
             "ms_batch_info": [V, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I)],
             "ms_step_profiled": [V, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), PD, ctypes.POINTER(I)],
             "ms_init_modes3": [V, ctypes.POINTER(_Mode3), I],
+            "ms_save": [V, ctypes.c_char_p],
+            "ms_load": [V, ctypes.c_char_p],
             "ms_set_sources": [V, ctypes.POINTER(_Source), I],
             "ms_init_driven": [V, ctypes.POINTER(_Source), I],
             "ms_error_vs_driven": [V, ctypes.POINTER(_Source), I, PD, PD, PD, PD],
@@ -322,6 +324,13 @@ class Grid:
         """Operator entry point on CUDA float64 tensors (see maxwell4.h, ms_apply_op)."""
         _check(load().ms_apply_op(self._h, OPS[op], _ptrs([t.data_ptr() for t in ins]),
                                   _ptrs([t.data_ptr() for t in outs])))
+
+    # -- checkpoint / resume (maxwell4.h, ms_save / ms_load) --
+    def save(self, path: str):
+        _check(load().ms_save(self._h, os.fsencode(path)))
+
+    def load_state(self, path: str):
+        _check(load().ms_load(self._h, os.fsencode(path)))
 
     # -- current sources J_z = amp sin(pi m x) sin(pi n y) sin(omega t) (maxwell4.h, ms_set_sources) --
     def set_sources(self, src):

@@ -800,6 +800,17 @@ void destroy_grid3d(ms_grid* g) {
   g->g3 = nullptr;
 }
 
+int state_arrays3d(ms_grid* g, double** f64, float** hi, float** lo, size_t* n) {
+  Grid3D* G3 = g->g3;
+  for (int c = 0; c < 6; ++c) {
+    f64[c] = G3->f64[c];
+    hi[c] = G3->hi[c];
+    lo[c] = G3->lo[c];
+    n[c] = G3->sh[c].size();
+  }
+  return 6;
+}
+
 ms_status step3d(ms_grid* g) { return g->desc.precision == MS_FP64 ? step3d64(g) : step3d32(g); }
 
 ms_status set_fields3d(ms_grid* g, const double* const* comps, int host) {
