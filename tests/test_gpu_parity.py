@@ -244,3 +244,21 @@ def test_full_size_reflect_matches_closed_form(prec):
         assert l2([a - b for a, b in zip(got, ref)]) <= disc
         assert l2([a - e for a, e in zip(got, ex)]) <= 2 * disc
     assert l2_rel < 1e-4
+
+
+@pytest.mark.parametrize("N,r,Z,steps", [(129, 0.5, 1.0, 12), (150, 5 / (6 * math.sqrt(2)), 1.6, 10),
+                                         (191, 0.45, 0.7, 8)])
+@pytest.mark.parametrize("closure", [pkg.CLOSURE_PAPER, pkg.CLOSURE_REFLECT])
+def test_mixed_multi_tile_ragged_sizes_close_to_oracle(N, r, Z, steps, closure):
+    """FP32_REFINED tile kernels over several curl tiles (64) and solve regions (64 - 2(S-1)) with
+    ragged last tiles, against the oracle on random fields (FP32 noise ~1e-7 per step)."""
+    init = workloads.random_fields(N, seed=2000 + N)
+    o = oracle.Oracle2D(N, r, Z=Z, closure=closure)
+    ref = [a.copy() for a in init]
+    o.run(*ref, steps)
+    with pkg.Grid(N, r, z=Z, precision=pkg.FP32_REFINED, closure=closure) as g:
+        g.set_fields(*init)
+        g.run(steps)
+        got = g.get_fields()
+    cat = lambda fs: np.concatenate([np.ravel(a) for a in fs])
+    assert np.linalg.norm(cat(got) - cat(ref)) <= 2e-6 * np.linalg.norm(cat(ref))
