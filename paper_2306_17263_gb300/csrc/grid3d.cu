@@ -295,6 +295,154 @@ __global__ void k_band3d32(const float* __restrict__ d, float* __restrict__ R, S
   R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
 }
 
+// One Pade term fused: the filtered differences of the difference-filter kernel above and the
+// A^{-1} band of the band kernel, on a tile of TO destination points along AXIS times NPL lines
+// along the in-tile transverse axis P, at one coordinate of the other transverse axis Q.  The
+// differences of the centre Q plane go to shared memory with a one-line halo in P and K3H + 1
+// points along the line; the Q neighbours of the filter come from global memory; the band reads
+// shared memory.  Every destination point of the tile is written (walls included).  The filter
+// sums its neighbours in the order of k_dfilt3d32 (along, then P, then Q), so d is the same.
+constexpr int T3O = 64;          // destination points along the line per tile
+constexpr int K3H = 13;          // band reach held in shared memory (table half-width <= 12)
+constexpr int D3L = T3O + 2 * K3H;       // filtered differences per line
+constexpr int D3P = D3L | 1;
+constexpr int X3L = D3L + 2;             // raw differences per line
+constexpr int X3P = X3L | 1;
+
+template <int AXIS>
+struct TermGeo {
+  static constexpr int P = AXIS == 0 ? 1 : 0;          // in-tile transverse axis
+  static constexpr int Q = AXIS == 2 ? 1 : 2;          // the other transverse axis
+  static constexpr int NPL = AXIS == 0 ? 8 : 32;       // lines per tile
+};
+
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 ss,
+                                                  float* __restrict__ R, Shape3 sd, int out_off, int M, int ghost_even,
+                                                  float cb_hi, float cb_lo, const float* __restrict__ whi,
+                                                  const float* __restrict__ wlo, int K, int B, int all_explicit,
+                                                  float sign, int accumulate) {
+  using G = TermGeo<AXIS>;
+  constexpr int P = G::P, Q = G::Q, NPL = G::NPL;
+  __shared__ float dlt[(NPL + 2) * X3P];
+  __shared__ float dd[NPL * D3P];
+  // tile coordinates: along (destination) o0, lines p0 .. p0+NPL-1, transverse q
+  int o0, p0, q;
+  if (AXIS == 0) { o0 = blockIdx.x * T3O; p0 = blockIdx.y * NPL; q = blockIdx.z; }
+  else if (AXIS == 1) { p0 = blockIdx.x * NPL; o0 = blockIdx.y * T3O; q = blockIdx.z; }
+  else { p0 = blockIdx.x * NPL; q = blockIdx.y; o0 = blockIdx.z * T3O; }
+  const int r0 = o0 - out_off;  // difference / band index of the first destination point
+  const int st[3] = {1, ss.n[0], ss.n[0] * ss.n[1]};
+  const int sdt[3] = {1, sd.n[0], sd.n[0] * sd.n[1]};
+  const int nA = sd.n[AXIS], nP = sd.n[P], nQ = sd.n[Q];
+  const bool q_wall = sd.bc[Q] == DIR && (q == 0 || q == nQ - 1);
+  // source index of difference m on source line (p, q): along index m, transverse p, q
+  auto src_index = [&](int m, int p, int qq) { return m * st[AXIS] + p * st[P] + qq * st[Q]; };
+  auto delta_at = [&](int idx) { return (hi[idx + st[AXIS]] - hi[idx]) + (lo[idx + st[AXIS]] - lo[idx]); };
+  auto p_line = [&](int p) -> int {  // source line for transverse P index p (-1: zero line)
+    if (p >= 0 && p < nP) return p;
+    if (ss.bc[P] == NEU) return p < 0 ? 0 : nP - 1;
+    return -1;
+  };
+  if (!q_wall) {
+    // 1) raw differences of the centre plane: lines p0-1 .. p0+NPL, m = r0 - K3H - 1 + j
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < (NPL + 2) * X3L; idx += blockDim.x) {
+      int pl, j;
+      if (AXIS == 0) { pl = idx / X3L; j = idx - pl * X3L; }
+      else { j = idx / (NPL + 2); pl = idx - j * (NPL + 2); }
+      int m = r0 - K3H - 1 + j;
+      const int pp = p_line(p0 - 1 + pl);
+      float v = 0.0f;
+      if (pp >= 0) {
+        bool zero = false;
+        if (m < 0 || m >= M) {
+          if (!ghost_even || m < -1 || m > M) zero = true;
+          else m = m < 0 ? 0 : M - 1;
+        }
+        if (!zero) v = delta_at(src_index(m, pp, q));
+      }
+      dlt[pl * X3P + j] = v;
+    }
+    __syncthreads();
+    // 2) filtered differences d = 12 beta delta + L delta on lines p0 .. p0+NPL-1
+    const int qm = q > 0 ? q - 1 : (ss.bc[Q] == NEU ? 0 : -1);
+    const int qp = q < nQ - 1 ? q + 1 : (ss.bc[Q] == NEU ? nQ - 1 : -1);
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < NPL * D3L; idx += blockDim.x) {
+      int pl, j;
+      if (AXIS == 0) { pl = idx / D3L; j = idx - pl * D3L; }
+      else { j = idx / NPL; pl = idx - j * NPL; }
+      const int m = r0 - K3H + j;
+      const int p = p0 + pl;
+      float out = 0.0f;
+      const bool p_unk = p < nP && interior(sd.bc[P], p, nP);
+      if (p_unk && m >= 0 && m < M) {
+        const float* c = dlt + (pl + 1) * X3P + j + 1;
+        const float v = c[0];
+        const float a1 = c[-1], a2 = c[1];
+        const float b1 = c[-X3P], b2 = c[X3P];
+        const float c1 = qm >= 0 ? delta_at(src_index(m, p, qm)) : 0.0f;
+        const float c2 = qp >= 0 ? delta_at(src_index(m, p, qp)) : 0.0f;
+        const float lap = (((a1 - v) + (a2 - v)) + ((b1 - v) + (b2 - v))) + ((c1 - v) + (c2 - v));
+        out = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+      }
+      dd[pl * D3P + j] = out;
+    }
+    __syncthreads();
+  }
+  // 3) band y = A^{-1} d and R (+)= sign y at every destination point of the tile
+  for (int idx = threadIdx.x; idx < NPL * T3O; idx += blockDim.x) {
+    int pl, o;
+    if (AXIS == 0) { pl = idx / T3O; o = idx - pl * T3O; }
+    else { o = idx / NPL; pl = idx - o * NPL; }
+    const int od = o0 + o, p = p0 + pl;
+    if (od >= nA || p >= nP) continue;
+    int coord[3];
+    coord[AXIS] = od;
+    coord[P] = p;
+    coord[Q] = q;
+    const int pd = coord[0] * sdt[0] + coord[1] * sdt[1] + coord[2] * sdt[2];
+    const int r = od - out_off;
+    const bool unk = !q_wall && interior(sd.bc[AXIS], od, nA) && interior(sd.bc[P], p, nP) && r >= 0 && r < M;
+    if (!unk) {
+      if (!accumulate) R[pd] = 0.0f;
+      continue;
+    }
+    const float* dc = dd + pl * D3P + (r - r0 + K3H);  // dc[t] = d_{r + t}
+    float acc;
+    if (!all_explicit && r >= B && r < M - B && r >= KB3 && r + KB3 + 1 < M) {
+      acc = c_w3[2 * KB3 + 1] * dc[KB3 + 1];
+#pragma unroll
+      for (int dist = KB3; dist >= 1; --dist) {
+        acc = fmaf(c_w3[KB3 + dist], dc[dist], acc);
+        acc = fmaf(c_w3[KB3 - dist], dc[-dist], acc);
+      }
+      acc = fmaf(c_wl3[0], dc[-1], acc);
+      acc = fmaf(c_wl3[2], dc[1], acc);
+      acc = fmaf(c_wl3[1], dc[0], acc);
+      acc = fmaf(c_w3[KB3], dc[0], acc);
+    } else {
+      const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
+      const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
+      float lo2 = 0.0f;
+      acc = 0.0f;
+      for (int dist = K + 1; dist >= 1; --dist) {
+        for (int side = 1; side >= -1; side -= 2) {
+          const int mm = r + side * dist, t = mm - r + K;
+          if (t < 0 || t > 2 * K + 1 || mm < 0 || mm >= M) continue;
+          const float dm = dc[mm - r];
+          acc = fmaf(__ldg(wh + t), dm, acc);
+          lo2 = fmaf(__ldg(wl + t), dm, lo2);
+        }
+      }
+      lo2 = fmaf(__ldg(wl + K), dc[0], lo2);
+      acc = fmaf(__ldg(wh + K), dc[0], acc + lo2);
+    }
+    R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
+  }
+}
+
 // One sweep of the FP32 Richardson iteration on 6 h^2 P1 x = b (6h^2 P1 = d - 6(Lx + Ly + Lz)
 // - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo), x_{k+1} = x_k + omega (b - 6 h^2 P1 x_k) from
 // x_1 = omega b.  first: the sweep from x_1, read as omega b.  last: the state (hi, lo) += s x +
@@ -452,7 +600,8 @@ ms_status step3d64(ms_grid* g) {
 
 // FP32_REFINED: one Pade term y = A^{-1} D1 G~ of source component cs along axis, added with
 // `sign` into R on component cd.
-void term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, float sign, int accumulate) {
+// Returns the number of launches issued.
+int term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, float sign, int accumulate) {
   Grid3D* G3 = g->g3;
   const Shape3& ss = G3->sh[cs];
   const Shape3& sd = G3->sh[cd];
@@ -460,6 +609,28 @@ void term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, fl
   const PadeTable& t = g->pade32[kind];
   const int off = (kind == HALF_TO_NODE) ? 1 : 0;
   const int ghost_even = (ss.bc[axis] == DIR);
+  if (t.K + 1 <= K3H) {
+    // fused difference-filter and band in one tiled kernel
+    const int nA = sd.n[axis];
+    const int ta = (nA + T3O - 1) / T3O;
+    float* R = G3->s32[1];
+    if (axis == 0) {
+      dim3 grd(ta, (sd.n[1] + 7) / 8, sd.n[2]);
+      k_term3d32<0><<<grd, 256, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, R, sd, off, t.M, ghost_even, cb_hi, cb_lo,
+                                                 t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
+    } else if (axis == 1) {
+      dim3 grd((sd.n[0] + 31) / 32, ta, sd.n[2]);
+      k_term3d32<1><<<grd, 256, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, R, sd, off, t.M, ghost_even, cb_hi, cb_lo,
+                                                 t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
+    } else {
+      dim3 grd((sd.n[0] + 31) / 32, sd.n[1], ta);
+      k_term3d32<2><<<grd, 256, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, R, sd, off, t.M, ghost_even, cb_hi, cb_lo,
+                                                 t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
+    }
+    // state hi + lo in, R out (read too when accumulating)
+    prof_mark(g, KK_DFILT3D32, 4.0 * (2.0 * (double)ss.size() + (accumulate ? 2.0 : 1.0) * (double)sd.size()));
+    return 1;
+  }
   float* d = G3->s32[0];
   float* R = G3->s32[1];
   const dim3 grd = grid3(sd, kBlk);
@@ -482,6 +653,7 @@ void term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, fl
                                                 accumulate);
   // d in, R out (read too when accumulating)
   prof_mark(g, KK_BAND3D32, 4.0 * (double)sd.size() * (accumulate ? 3.0 : 2.0));
+  return 2;
 }
 
 void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_hi, float s_lo, int S, int* nl) {
@@ -508,16 +680,14 @@ ms_status step3d32(ms_grid* g) {
   int nl = 0;
   for (int e = 0; e < 3; ++e) {
     const int p1 = (e + 1) % 3, p2 = (e + 2) % 3;
-    term3d32(g, p1, 3 + p2, e, k.cb_hi, k.cb_lo, 1.0f, 0);
-    term3d32(g, p2, 3 + p1, e, k.cb_hi, k.cb_lo, -1.0f, 1);
-    nl += 4;
+    nl += term3d32(g, p1, 3 + p2, e, k.cb_hi, k.cb_lo, 1.0f, 0);
+    nl += term3d32(g, p2, 3 + p1, e, k.cb_hi, k.cb_lo, -1.0f, 1);
     solve3d32(g, e, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo, k.S, &nl);
   }
   for (int hc = 0; hc < 3; ++hc) {
     const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
-    term3d32(g, p1, p2, 3 + hc, k.cb_hi, k.cb_lo, -1.0f, 0);
-    term3d32(g, p2, p1, 3 + hc, k.cb_hi, k.cb_lo, 1.0f, 1);
-    nl += 4;
+    nl += term3d32(g, p1, p2, 3 + hc, k.cb_hi, k.cb_lo, -1.0f, 0);
+    nl += term3d32(g, p2, p1, 3 + hc, k.cb_hi, k.cb_lo, 1.0f, 1);
     solve3d32(g, 3 + hc, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo, k.S, &nl);
   }
   g->launches_per_step = nl;
