@@ -344,7 +344,77 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
     if (ss.bc[P] == NEU) return p < 0 ? 0 : nP - 1;
     return -1;
   };
-  if (!q_wall) {
+  // Tiles whose transverse lines and neighbours are all in range (the along-line ends are handled
+  // per element): warp-structured loops with one base address per row.
+  const bool inner = !q_wall && p0 - 1 >= 0 && p0 + NPL + 1 <= nP && q >= 1 && q + 1 <= nQ - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW3 = 8;
+  if (inner) {
+    const int sa = st[AXIS], sq = st[Q];
+    // difference at along index m on the line whose difference-0 index is `line`: ghost rules of
+    // k_dfilt3d32 at the ends
+    auto delta_m = [&](int line, int m) -> float {
+      if (m < 0 || m >= M) {
+        if (!ghost_even || m < -1 || m > M) return 0.0f;
+        m = m < 0 ? 0 : M - 1;
+      }
+      return delta_at(line + m * sa);
+    };
+    if (AXIS == 0) {
+      for (int pl = warp; pl < NPL + 2; pl += NW3) {
+        const int line = src_index(0, p0 - 1 + pl, q);
+#pragma unroll
+        for (int cc = 0; cc < (X3L + 31) / 32; ++cc) {
+          const int j = lane + 32 * cc;
+          if (32 * cc + 32 <= X3L || j < X3L) dlt[pl * X3P + j] = delta_m(line, r0 - K3H - 1 + j);
+        }
+      }
+      __syncthreads();
+      const int pl = warp;
+      const int line = src_index(0, p0 + pl, q);
+      const float* cbase = dlt + (pl + 1) * X3P + 1;
+#pragma unroll
+      for (int cc = 0; cc < (D3L + 31) / 32; ++cc) {
+        const int j = lane + 32 * cc;
+        if (32 * cc + 32 <= D3L || j < D3L) {
+          const int m = r0 - K3H + j;
+          float out = 0.0f;
+          if (m >= 0 && m < M) {
+            const float* c = cbase + j;
+            const float v = c[0];
+            const int at = line + m * sa;
+            const float lap = (((c[-1] - v) + (c[1] - v)) + ((c[-X3P] - v) + (c[X3P] - v))) +
+                              ((delta_at(at - sq) - v) + (delta_at(at + sq) - v));
+            out = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+          }
+          dd[pl * D3P + j] = out;
+        }
+      }
+    } else {
+      const int line0 = src_index(0, p0 - 1, q);
+      for (int j = warp; j < X3L; j += NW3) {
+        const int m = r0 - K3H - 1 + j;
+        dlt[lane * X3P + j] = delta_m(line0 + lane, m);
+        if (lane < 2) dlt[(32 + lane) * X3P + j] = delta_m(line0 + 32 + lane, m);
+      }
+      __syncthreads();
+      const int line = src_index(0, p0, q) + lane;
+      for (int j = warp; j < D3L; j += NW3) {
+        const int m = r0 - K3H + j;
+        float out = 0.0f;
+        if (m >= 0 && m < M) {
+          const float* c = dlt + (lane + 1) * X3P + j + 1;
+          const float v = c[0];
+          const int at = line + m * sa;
+          const float lap = (((c[-1] - v) + (c[1] - v)) + ((c[-X3P] - v) + (c[X3P] - v))) +
+                            ((delta_at(at - sq) - v) + (delta_at(at + sq) - v));
+          out = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+        }
+        dd[lane * D3P + j] = out;
+      }
+    }
+    __syncthreads();
+  } else if (!q_wall) {
     // 1) raw differences of the centre plane: lines p0-1 .. p0+NPL, m = r0 - K3H - 1 + j
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < (NPL + 2) * X3L; idx += blockDim.x) {
@@ -392,6 +462,70 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
     __syncthreads();
   }
   // 3) band y = A^{-1} d and R (+)= sign y at every destination point of the tile
+  auto band_row = [&](const float* dc, int r) -> float {  // dc[t] = d_{r + t}
+    if (!all_explicit && r >= B && r < M - B && r >= KB3 && r + KB3 + 1 < M) {
+      float acc = c_w3[2 * KB3 + 1] * dc[KB3 + 1];
+#pragma unroll
+      for (int dist = KB3; dist >= 1; --dist) {
+        acc = fmaf(c_w3[KB3 + dist], dc[dist], acc);
+        acc = fmaf(c_w3[KB3 - dist], dc[-dist], acc);
+      }
+      acc = fmaf(c_wl3[0], dc[-1], acc);
+      acc = fmaf(c_wl3[2], dc[1], acc);
+      acc = fmaf(c_wl3[1], dc[0], acc);
+      return fmaf(c_w3[KB3], dc[0], acc);
+    }
+    const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
+    const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
+    float acc = 0.0f, lo2 = 0.0f;
+    for (int dist = K + 1; dist >= 1; --dist) {
+      for (int side = 1; side >= -1; side -= 2) {
+        const int mm = r + side * dist, t = mm - r + K;
+        if (t < 0 || t > 2 * K + 1 || mm < 0 || mm >= M) continue;
+        const float dm = dc[mm - r];
+        acc = fmaf(__ldg(wh + t), dm, acc);
+        lo2 = fmaf(__ldg(wl + t), dm, lo2);
+      }
+    }
+    lo2 = fmaf(__ldg(wl + K), dc[0], lo2);
+    return fmaf(__ldg(wh + K), dc[0], acc + lo2);
+  };
+  if (inner) {  // every transverse line of the tile is an unknown line
+    if (AXIS == 0) {
+      const int pl = warp;
+      const int pd0 = (p0 + pl) * sdt[1] + q * sdt[2];
+#pragma unroll
+      for (int cc = 0; cc < T3O / 32; ++cc) {
+        const int od = o0 + lane + 32 * cc;
+        if (od >= nA) continue;
+        const int r = od - out_off, pd = pd0 + od;
+        if (!interior(sd.bc[AXIS], od, nA) || r < 0 || r >= M) {
+          if (!accumulate) R[pd] = 0.0f;
+          continue;
+        }
+        const float y = band_row(dd + pl * D3P + (r - r0 + K3H), r);
+        R[pd] = accumulate ? R[pd] + sign * y : sign * y;
+      }
+    } else {
+      for (int o = warp; o < T3O; o += NW3) {
+        const int od = o0 + o;
+        if (od >= nA) break;
+        int coord[3];
+        coord[AXIS] = od;
+        coord[P] = p0 + lane;
+        coord[Q] = q;
+        const int pd = coord[0] * sdt[0] + coord[1] * sdt[1] + coord[2] * sdt[2];
+        const int r = od - out_off;
+        if (!interior(sd.bc[AXIS], od, nA) || r < 0 || r >= M) {
+          if (!accumulate) R[pd] = 0.0f;
+          continue;
+        }
+        const float y = band_row(dd + lane * D3P + (r - r0 + K3H), r);
+        R[pd] = accumulate ? R[pd] + sign * y : sign * y;
+      }
+    }
+    return;
+  }
   for (int idx = threadIdx.x; idx < NPL * T3O; idx += blockDim.x) {
     int pl, o;
     if (AXIS == 0) { pl = idx / T3O; o = idx - pl * T3O; }
@@ -409,36 +543,7 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
       if (!accumulate) R[pd] = 0.0f;
       continue;
     }
-    const float* dc = dd + pl * D3P + (r - r0 + K3H);  // dc[t] = d_{r + t}
-    float acc;
-    if (!all_explicit && r >= B && r < M - B && r >= KB3 && r + KB3 + 1 < M) {
-      acc = c_w3[2 * KB3 + 1] * dc[KB3 + 1];
-#pragma unroll
-      for (int dist = KB3; dist >= 1; --dist) {
-        acc = fmaf(c_w3[KB3 + dist], dc[dist], acc);
-        acc = fmaf(c_w3[KB3 - dist], dc[-dist], acc);
-      }
-      acc = fmaf(c_wl3[0], dc[-1], acc);
-      acc = fmaf(c_wl3[2], dc[1], acc);
-      acc = fmaf(c_wl3[1], dc[0], acc);
-      acc = fmaf(c_w3[KB3], dc[0], acc);
-    } else {
-      const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
-      const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
-      float lo2 = 0.0f;
-      acc = 0.0f;
-      for (int dist = K + 1; dist >= 1; --dist) {
-        for (int side = 1; side >= -1; side -= 2) {
-          const int mm = r + side * dist, t = mm - r + K;
-          if (t < 0 || t > 2 * K + 1 || mm < 0 || mm >= M) continue;
-          const float dm = dc[mm - r];
-          acc = fmaf(__ldg(wh + t), dm, acc);
-          lo2 = fmaf(__ldg(wl + t), dm, lo2);
-        }
-      }
-      lo2 = fmaf(__ldg(wl + K), dc[0], lo2);
-      acc = fmaf(__ldg(wh + K), dc[0], acc + lo2);
-    }
+    const float acc = band_row(dd + pl * D3P + (r - r0 + K3H), r);
     R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
   }
 }
