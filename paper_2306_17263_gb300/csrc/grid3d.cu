@@ -552,61 +552,120 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
 // - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo), x_{k+1} = x_k + omega (b - 6 h^2 P1 x_k) from
 // x_1 = omega b.  first: the sweep from x_1, read as omega b.  last: the state (hi, lo) += s x +
 // s corr (two separate error-free additions) instead of writing x.  single: S = 1, state += s omega b.
-__global__ void k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin, float* __restrict__ xout,
-                            Shape3 s, float d_hi, float d_lo, float omega, int first, int last, int single,
-                            float* __restrict__ shi, float* __restrict__ slo, float s_hi, float s_lo) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+// A block takes a tile of SWX x SWY points and marches SWZ planes along z.  The iterate on planes
+// z-1, z, z+1 over the tile with a one-point halo in x and y sits in a ring in shared memory; the
+// next plane is fetched into registers while the current one is computed.  Halo indices are
+// clamped: the even ghosts of a Neumann axis; on a Dirichlet axis the clamped values are seen only
+// by wall points, which are not updated.
+constexpr int SWX = 32, SWY = 8, SWZ = 16;
+constexpr int SWXP = SWX + 2, SWYP = SWY + 2;
+
+__global__ void __launch_bounds__(256) k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin,
+                                                   float* __restrict__ xout, Shape3 s, float d_hi, float d_lo,
+                                                   float omega, int first, int last, int single,
+                                                   float* __restrict__ shi, float* __restrict__ slo, float s_hi,
+                                                   float s_lo) {
+  __shared__ float xs[3][SWYP][SWXP];
   const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
-  if (i >= n0 || j >= n1) return;
-  const int p = (k * n1 + j) * n0 + i;
-  if (!unk3(s, i, j, k)) {
-    if (!last) xout[p] = 0.0f;
-    return;
-  }
-  if (single) {  // one iterate in all: x = omega b
-    float h = shi[p], l = slo[p];
-    ff_add_scaled3(h, l, omega * b[p], s_hi, s_lo);
-    shi[p] = h;
-    slo[p] = l;
-    return;
-  }
-  // neighbour offsets, clamped on Neumann axes (even ghosts); Dirichlet neighbours are stored zeros.
-  // first: the iterate x_1 = omega b (zero off the unknowns, like b) is formed from b on the fly.
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * SWX + tx, j = blockIdx.y * SWY + ty;
+  const int k0 = blockIdx.z * SWZ, k1 = min(k0 + SWZ, n2);
+  const bool inside = i < n0 && j < n1;
   const int sz = n0 * n1;
-  const int xm = i > 0 ? -1 : 0, xp = i < n0 - 1 ? 1 : 0;
-  const int ym = j > 0 ? -n0 : 0, yp = j < n1 - 1 ? n0 : 0;
-  const int zm = k > 0 ? -sz : 0, zp = k < n2 - 1 ? sz : 0;
-  const float* X0 = (first ? b : xin) + p;
-  const float sc = first ? omega : 1.0f;
-  auto X = [&](int o) { return first ? sc * X0[o] : X0[o]; };
-  auto LX = [&](int o) {
-    const float v = X(o);
-    return (X(o + xm) - v) + (X(o + xp) - v);
-  };
-  auto LY = [&](int o) {
-    const float v = X(o);
-    return (X(o + ym) - v) + (X(o + yp) - v);
-  };
-  const float x = X(0);
-  const float lx = LX(0), ly = LY(0);
-  const float lz = (X(zm) - x) + (X(zp) - x);
-  const float lxly = (LX(ym) - lx) + (LX(yp) - lx);
-  const float lxlz = (LX(zm) - lx) + (LX(zp) - lx);
-  const float lylz = (LY(zm) - ly) + (LY(zp) - ly);
-  const float rest = -6.0f * ((lx + ly) + lz) - ((lxly + lylz) + lxlz);
-  const float ph = __fmul_rn(d_hi, x);
-  const float pl = fmaf(d_lo, x, fmaf(d_hi, x, -ph));
-  const float res = __fsub_rn(__fsub_rn(b[p], ph), pl) - rest;
-  const float corr = omega * res;
-  if (last) {
-    float h = shi[p], l = slo[p];
-    ff_add_scaled3(h, l, x, s_hi, s_lo);
-    ff_add_scaled3(h, l, corr, s_hi, s_lo);
-    shi[p] = h;
-    slo[p] = l;
-  } else {
-    xout[p] = x + corr;
+  if (single) {  // one iterate in all: x = omega b
+    if (!inside) return;
+    for (int k = k0; k < k1; ++k) {
+      const int p = k * sz + j * n0 + i;
+      if (!unk3(s, i, j, k)) continue;
+      float h = shi[p], l = slo[p];
+      ff_add_scaled3(h, l, omega * b[p], s_hi, s_lo);
+      shi[p] = h;
+      slo[p] = l;
+    }
+    return;
   }
+  const float* X0 = first ? b : xin;
+  const float sc = first ? omega : 1.0f;
+  // plane loader: warp w stages rows w and w + 8 (< SWYP) of the tile with halo, lanes along x
+  const int warp = ty, lane = tx;
+  const int ia = clampi(blockIdx.x * SWX + lane - 1, n0);
+  const int ib = clampi(blockIdx.x * SWX + SWX - 1 + lane, n0);  // columns SWX, SWX + 1 (lanes 0, 1)
+  const int ja = clampi(blockIdx.y * SWY + warp - 1, n1);
+  const int jb = clampi(blockIdx.y * SWY + warp + SWY - 1, n1);   // row warp + 8 (warps 0, 1)
+  const bool row_b = warp + SWY < SWYP, col_b = lane < 2;
+  float ra = 0.0f, rb = 0.0f, rc = 0.0f, rd = 0.0f;
+  auto fetch = [&](int kk) {
+    const int base = clampi(kk, n2) * sz;
+    ra = X0[base + ja * n0 + ia];
+    if (col_b) rb = X0[base + ja * n0 + ib];
+    if (row_b) {
+      rc = X0[base + jb * n0 + ia];
+      if (col_b) rd = X0[base + jb * n0 + ib];
+    }
+  };
+  auto stage = [&](int kk) {
+    float(*pl)[SWXP] = xs[(kk + 3) % 3];
+    pl[warp][lane] = first ? sc * ra : ra;
+    if (col_b) pl[warp][SWX + lane] = first ? sc * rb : rb;
+    if (row_b) {
+      pl[warp + SWY][lane] = first ? sc * rc : rc;
+      if (col_b) pl[warp + SWY][SWX + lane] = first ? sc * rd : rd;
+    }
+  };
+  fetch(k0 - 1);
+  stage(k0 - 1);
+  fetch(k0);
+  stage(k0);
+  fetch(k0 + 1);
+  for (int k = k0; k < k1; ++k) {
+    stage(k + 1);
+    __syncthreads();
+    if (k + 1 < k1) fetch(k + 2);
+    if (inside) {
+      const int p = k * sz + j * n0 + i;
+      if (!unk3(s, i, j, k)) {
+        if (!last) xout[p] = 0.0f;
+      } else {
+        const int c0 = tx + 1, r0 = ty + 1;
+        const float(*Zm)[SWXP] = xs[(k + 2) % 3];
+        const float(*Z0)[SWXP] = xs[k % 3];
+        const float(*Zp)[SWXP] = xs[(k + 1) % 3];
+        auto LX = [&](const float(*Pl)[SWXP], int r) {
+          const float v = Pl[r][c0];
+          return (Pl[r][c0 - 1] - v) + (Pl[r][c0 + 1] - v);
+        };
+        auto LY = [&](const float(*Pl)[SWXP]) {
+          const float v = Pl[r0][c0];
+          return (Pl[r0 - 1][c0] - v) + (Pl[r0 + 1][c0] - v);
+        };
+        const float x = Z0[r0][c0];
+        const float lx = LX(Z0, r0), ly = LY(Z0);
+        const float lz = (Zm[r0][c0] - x) + (Zp[r0][c0] - x);
+        const float lxly = (LX(Z0, r0 - 1) - lx) + (LX(Z0, r0 + 1) - lx);
+        const float lxlz = (LX(Zm, r0) - lx) + (LX(Zp, r0) - lx);
+        const float lylz = (LY(Zm) - ly) + (LY(Zp) - ly);
+        const float rest = -6.0f * ((lx + ly) + lz) - ((lxly + lylz) + lxlz);
+        const float ph = __fmul_rn(d_hi, x);
+        const float pl = fmaf(d_lo, x, fmaf(d_hi, x, -ph));
+        const float res = __fsub_rn(__fsub_rn(b[p], ph), pl) - rest;
+        const float corr = omega * res;
+        if (last) {
+          float h = shi[p], l = slo[p];
+          ff_add_scaled3(h, l, x, s_hi, s_lo);
+          ff_add_scaled3(h, l, corr, s_hi, s_lo);
+          shi[p] = h;
+          slo[p] = l;
+        } else {
+          xout[p] = x + corr;
+        }
+      }
+    }
+    __syncthreads();  // the slot of plane k - 1 is staged again as plane k + 2
+  }
+}
+
+dim3 sweep_grid3(const Shape3& s) {
+  return dim3((s.n[0] + SWX - 1) / SWX, (s.n[1] + SWY - 1) / SWY, (s.n[2] + SWZ - 1) / SWZ);
 }
 
 __global__ void k_split3(const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
@@ -772,7 +831,7 @@ void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_h
   for (int k = 0; k < L; ++k) {
     const bool last = (k == L - 1);
     float* xo = buf[k & 1];
-    k_sweep3d32<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, k == 0, last, S == 1,
+    k_sweep3d32<<<sweep_grid3(s), dim3(SWX, SWY, 1), 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, k == 0, last, S == 1,
                                                          G3->hi[c], G3->lo[c], s_hi, s_lo);
     prof_mark(g, KK_SWEEP3D32, 4.0 * (double)s.size() * ((k == 0 ? 1.0 : 2.0) + (last ? 4.0 : 1.0)));
     xin = xo;
