@@ -48,6 +48,8 @@ constexpr int XROWS = TB + 2;          // lines of raw differences (one more on 
 constexpr int YSP = TB + 1;
 constexpr int RS = 64;                     // solve region edge (output tile + 2 x halo)
 constexpr int RSP = RS + 1;
+constexpr int MAXR = (RS + NW / 2 - 1) / (NW / 2);  // rows of a sweep strip, at most
+constexpr int PF = 4;                                // state rows fetched ahead in the last sweep
 
 // interior row of A^{-1} at offsets -KB .. KB+1 (hi), and the lo parts of offsets -1, 0, 1
 __constant__ float c_w[2 * KB + 2];
@@ -408,6 +410,50 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
   float lxa = fmaf(-2.0f, a0, xcol[(ly0 - 1) * RSP - 1] + xcol[(ly0 - 1) * RSP + 1]);
   float lxb = fmaf(-2.0f, b0, xcol[ly0 * RSP - 1] + xcol[ly0 * RSP + 1]);
   size_t gp = (size_t)(gy0 + ly0) * nx + gx;
+  if (LAST) {
+    // the state of PF rows at a time is fetched before the first of them is updated
+#pragma unroll
+    for (int t0 = 0; t0 < MAXR; t0 += PF) {
+      float ph_[PF], pl_[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int ly = ly0 + t0 + u;
+        const bool unk =
+            ly < ly1 && (!EDGE || (col_unk && gy0 + ly >= 0 && gy0 + ly < ny && interior(bcy, gy0 + ly, ny)));
+        ph_[u] = unk ? shi[gp + (size_t)(t0 + u) * nx] : 0.0f;
+        pl_[u] = unk ? slo[gp + (size_t)(t0 + u) * nx] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int ly = ly0 + t0 + u;
+        if (ly >= ly1) break;
+        const float* row = xcol + (ly + 1) * RSP;
+        const float cm = row[-1], c0v = row[0], cp = row[1];
+        const float lxc = fmaf(-2.0f, c0v, cm + cp);
+        const float x = b0;
+        const float lyv = fmaf(-2.0f, x, a0 + c0v);
+        const float lxly = fmaf(-2.0f, lxb, lxa + lxc);
+        const float rest = fmaf(-6.0f, lxb + lyv, -lxly);
+        const float ph = __fmul_rn(A.d_hi, x);
+        const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
+        const float res = __fsub_rn(__fsub_rn(bs[ly * RSP + c], ph), pl) - rest;
+        const float corr = A.omega * res;
+        const bool unk = !EDGE || (col_unk && gy0 + ly >= 0 && gy0 + ly < ny && interior(bcy, gy0 + ly, ny));
+        if (unk) {
+          float h = ph_[u], l = pl_[u];
+          ff_add_scaled_t(h, l, x, A.s_hi, A.s_lo);
+          ff_add_scaled_t(h, l, corr, A.s_hi, A.s_lo);
+          shi[gp + (size_t)(t0 + u) * nx] = h;
+          slo[gp + (size_t)(t0 + u) * nx] = l;
+        }
+        a0 = b0;
+        lxa = lxb;
+        b0 = c0v;
+        lxb = lxc;
+      }
+    }
+    return;
+  }
 #pragma unroll 3
   for (int ly = ly0; ly < ly1; ++ly) {
     const float* row = xcol + (ly + 1) * RSP;
@@ -501,6 +547,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
   const bool neu_x = edge && bcx == NEU, neu_y = edge && bcy == NEU;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // b and the first iterate x1 = omega b (0 off the unknowns)
+#pragma unroll
   for (int ly = warp; ly < RS; ly += NW) {
     const int gy = gy0 + ly;
     const bool row_ok = !edge || (gy >= 0 && gy < ny && interior(bcy, gy, ny));
