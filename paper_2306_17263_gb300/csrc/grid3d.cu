@@ -550,107 +550,103 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
 
 // One sweep of the FP32 Richardson iteration on 6 h^2 P1 x = b (6h^2 P1 = d - 6(Lx + Ly + Lz)
 // - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo), x_{k+1} = x_k + omega (b - 6 h^2 P1 x_k) from
-// x_1 = omega b.  first: the sweep from x_1, read as omega b.  last: the state (hi, lo) += s x +
-// s corr (two separate error-free additions) instead of writing x.  single: S = 1, state += s omega b.
+// x_1 = omega b.  FIRST: the sweep from x_1, read as omega b.  LAST: the state (hi, lo) += s x +
+// s corr (two separate error-free additions) instead of writing x.
 // A block takes a tile of SWX x SWY points and marches SWZ planes along z.  The iterate on planes
 // z-1, z, z+1 over the tile with a one-point halo in x and y sits in a ring in shared memory; the
-// next plane is fetched into registers while the current one is computed.  Halo indices are
-// clamped: the even ghosts of a Neumann axis; on a Dirichlet axis the clamped values are seen only
-// by wall points, which are not updated.
+// next plane is fetched into registers, and the per-point operands (b, the state) of the next
+// plane too, while the current one is computed.  Halo indices are clamped: the even ghosts of a
+// Neumann axis; on a Dirichlet axis the clamped values are seen only by wall points, which are not
+// updated.
 constexpr int SWX = 32, SWY = 8, SWZ = 16;
 constexpr int SWXP = SWX + 2, SWYP = SWY + 2;
 
-__global__ void __launch_bounds__(256) k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin,
-                                                   float* __restrict__ xout, Shape3 s, float d_hi, float d_lo,
-                                                   float omega, int first, int last, int single,
-                                                   float* __restrict__ shi, float* __restrict__ slo, float s_hi,
-                                                   float s_lo) {
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(256, 8) k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin,
+                                                      float* __restrict__ xout, Shape3 s, float d_hi, float d_lo,
+                                                      float omega, float* __restrict__ shi, float* __restrict__ slo,
+                                                      float s_hi, float s_lo) {
   __shared__ float xs[3][SWYP][SWXP];
   const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = blockIdx.x * SWX + tx, j = blockIdx.y * SWY + ty;
   const int k0 = blockIdx.z * SWZ, k1 = min(k0 + SWZ, n2);
   const bool inside = i < n0 && j < n1;
+  const bool unk_xy = inside && interior(s.bc[0], i, n0) && interior(s.bc[1], j, n1);
+  const int bcz = s.bc[2];
   const int sz = n0 * n1;
-  if (single) {  // one iterate in all: x = omega b
-    if (!inside) return;
-    for (int k = k0; k < k1; ++k) {
-      const int p = k * sz + j * n0 + i;
-      if (!unk3(s, i, j, k)) continue;
-      float h = shi[p], l = slo[p];
-      ff_add_scaled3(h, l, omega * b[p], s_hi, s_lo);
-      shi[p] = h;
-      slo[p] = l;
-    }
-    return;
-  }
-  const float* X0 = first ? b : xin;
-  const float sc = first ? omega : 1.0f;
-  // plane loader: warp w stages rows w and w + 8 (< SWYP) of the tile with halo, lanes along x
-  const int warp = ty, lane = tx;
-  const int ia = clampi(blockIdx.x * SWX + lane - 1, n0);
-  const int ib = clampi(blockIdx.x * SWX + SWX - 1 + lane, n0);  // columns SWX, SWX + 1 (lanes 0, 1)
-  const int ja = clampi(blockIdx.y * SWY + warp - 1, n1);
-  const int jb = clampi(blockIdx.y * SWY + warp + SWY - 1, n1);   // row warp + 8 (warps 0, 1)
-  const bool row_b = warp + SWY < SWYP, col_b = lane < 2;
-  float ra = 0.0f, rb = 0.0f, rc = 0.0f, rd = 0.0f;
+  const float* X0 = FIRST ? b : xin;
+  // plane loader: thread t stages elements t and t + 256 (< SWYP * SWXP) of the tile with halo,
+  // at global offsets fixed for the whole march
+  const int t1 = ty * SWX + tx, t2 = t1 + SWX * SWY;
+  const bool has2 = t2 < SWYP * SWXP;
+  auto plane_off = [&](int e) {
+    const int row = e / SWXP, col = e - row * SWXP;
+    return clampi(blockIdx.y * SWY + row - 1, n1) * n0 + clampi(blockIdx.x * SWX + col - 1, n0);
+  };
+  const int o1 = plane_off(t1), o2 = plane_off(has2 ? t2 : t1);
+  float ra = 0.0f, rb = 0.0f;
   auto fetch = [&](int kk) {
-    const int base = clampi(kk, n2) * sz;
-    ra = X0[base + ja * n0 + ia];
-    if (col_b) rb = X0[base + ja * n0 + ib];
-    if (row_b) {
-      rc = X0[base + jb * n0 + ia];
-      if (col_b) rd = X0[base + jb * n0 + ib];
+    const float* P = X0 + clampi(kk, n2) * sz;
+    ra = P[o1];
+    if (has2) rb = P[o2];
+  };
+  auto stage = [&](float(*pl)[SWXP]) {
+    float* f = &pl[0][0];
+    f[t1] = FIRST ? omega * ra : ra;
+    if (has2) f[t2] = FIRST ? omega * rb : rb;
+  };
+  // per-point operands of the next plane
+  float bq = 0.0f, hq = 0.0f, lq = 0.0f;
+  auto fetch_pt = [&](int p) {
+    bq = b[p];
+    if (LAST) {
+      hq = shi[p];
+      lq = slo[p];
     }
   };
-  auto stage = [&](int kk) {
-    float(*pl)[SWXP] = xs[(kk + 3) % 3];
-    pl[warp][lane] = first ? sc * ra : ra;
-    if (col_b) pl[warp][SWX + lane] = first ? sc * rb : rb;
-    if (row_b) {
-      pl[warp + SWY][lane] = first ? sc * rc : rc;
-      if (col_b) pl[warp + SWY][SWX + lane] = first ? sc * rd : rd;
-    }
-  };
+  float(*Zm)[SWXP] = xs[0];
+  float(*Z0)[SWXP] = xs[1];
+  float(*Zp)[SWXP] = xs[2];
   fetch(k0 - 1);
-  stage(k0 - 1);
+  stage(Zm);
   fetch(k0);
-  stage(k0);
+  stage(Z0);
   fetch(k0 + 1);
-  for (int k = k0; k < k1; ++k) {
-    stage(k + 1);
+  int p = k0 * sz + j * n0 + i;
+  if (inside) fetch_pt(p);
+  const int c0 = tx + 1, r0 = ty + 1;
+  for (int k = k0; k < k1; ++k, p += sz) {
+    stage(Zp);
     __syncthreads();
     if (k + 1 < k1) fetch(k + 2);
+    const float bc = bq, hc = hq, lc = lq;
+    if (inside && k + 1 < k1) fetch_pt(p + sz);
     if (inside) {
-      const int p = k * sz + j * n0 + i;
-      if (!unk3(s, i, j, k)) {
-        if (!last) xout[p] = 0.0f;
+      if (!(unk_xy && interior(bcz, k, n2))) {
+        if (!LAST) xout[p] = 0.0f;
       } else {
-        const int c0 = tx + 1, r0 = ty + 1;
-        const float(*Zm)[SWXP] = xs[(k + 2) % 3];
-        const float(*Z0)[SWXP] = xs[k % 3];
-        const float(*Zp)[SWXP] = xs[(k + 1) % 3];
-        auto LX = [&](const float(*Pl)[SWXP], int r) {
-          const float v = Pl[r][c0];
-          return (Pl[r][c0 - 1] - v) + (Pl[r][c0 + 1] - v);
+        // second differences as a + b - 2 v: the residual's dominant term d x is an exact
+        // two-product, so the rounding of these sums is far below an ulp of the residual
+        auto LX = [&](const float(*Pl)[SWXP], int rr) {
+          return fmaf(-2.0f, Pl[rr][c0], Pl[rr][c0 - 1] + Pl[rr][c0 + 1]);
         };
         auto LY = [&](const float(*Pl)[SWXP]) {
-          const float v = Pl[r0][c0];
-          return (Pl[r0 - 1][c0] - v) + (Pl[r0 + 1][c0] - v);
+          return fmaf(-2.0f, Pl[r0][c0], Pl[r0 - 1][c0] + Pl[r0 + 1][c0]);
         };
         const float x = Z0[r0][c0];
         const float lx = LX(Z0, r0), ly = LY(Z0);
-        const float lz = (Zm[r0][c0] - x) + (Zp[r0][c0] - x);
-        const float lxly = (LX(Z0, r0 - 1) - lx) + (LX(Z0, r0 + 1) - lx);
-        const float lxlz = (LX(Zm, r0) - lx) + (LX(Zp, r0) - lx);
-        const float lylz = (LY(Zm) - ly) + (LY(Zp) - ly);
-        const float rest = -6.0f * ((lx + ly) + lz) - ((lxly + lylz) + lxlz);
+        const float lz = fmaf(-2.0f, x, Zm[r0][c0] + Zp[r0][c0]);
+        const float lxly = fmaf(-2.0f, lx, LX(Z0, r0 - 1) + LX(Z0, r0 + 1));
+        const float lxlz = fmaf(-2.0f, lx, LX(Zm, r0) + LX(Zp, r0));
+        const float lylz = fmaf(-2.0f, ly, LY(Zm) + LY(Zp));
+        const float rest = fmaf(-6.0f, (lx + ly) + lz, -((lxly + lylz) + lxlz));
         const float ph = __fmul_rn(d_hi, x);
         const float pl = fmaf(d_lo, x, fmaf(d_hi, x, -ph));
-        const float res = __fsub_rn(__fsub_rn(b[p], ph), pl) - rest;
+        const float res = __fsub_rn(__fsub_rn(bc, ph), pl) - rest;
         const float corr = omega * res;
-        if (last) {
-          float h = shi[p], l = slo[p];
+        if (LAST) {
+          float h = hc, l = lc;
           ff_add_scaled3(h, l, x, s_hi, s_lo);
           ff_add_scaled3(h, l, corr, s_hi, s_lo);
           shi[p] = h;
@@ -661,7 +657,23 @@ __global__ void __launch_bounds__(256) k_sweep3d32(const float* __restrict__ b, 
       }
     }
     __syncthreads();  // the slot of plane k - 1 is staged again as plane k + 2
+    float(*t)[SWXP] = Zm;
+    Zm = Z0;
+    Z0 = Zp;
+    Zp = t;
   }
+}
+
+// S = 1: the single iterate x = omega b is the correction, state += s omega b.
+__global__ void k_single3d32(const float* __restrict__ b, Shape3 s, float omega, float* __restrict__ shi,
+                             float* __restrict__ slo, float s_hi, float s_lo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= s.n[0] || j >= s.n[1] || !unk3(s, i, j, k)) return;
+  const int p = (k * s.n[1] + j) * s.n[0] + i;
+  float h = shi[p], l = slo[p];
+  ff_add_scaled3(h, l, omega * b[p], s_hi, s_lo);
+  shi[p] = h;
+  slo[p] = l;
 }
 
 dim3 sweep_grid3(const Shape3& s) {
@@ -831,8 +843,19 @@ void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_h
   for (int k = 0; k < L; ++k) {
     const bool last = (k == L - 1);
     float* xo = buf[k & 1];
-    k_sweep3d32<<<sweep_grid3(s), dim3(SWX, SWY, 1), 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, k == 0, last, S == 1,
-                                                         G3->hi[c], G3->lo[c], s_hi, s_lo);
+    const dim3 grd = sweep_grid3(s), blk(SWX, SWY, 1);
+    float* hi = G3->hi[c];
+    float* lo = G3->lo[c];
+    if (S == 1)
+      k_single3d32<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(b, s, omega, hi, lo, s_hi, s_lo);
+    else if (k == 0 && last)
+      k_sweep3d32<true, true><<<grd, blk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, hi, lo, s_hi, s_lo);
+    else if (k == 0)
+      k_sweep3d32<true, false><<<grd, blk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, hi, lo, s_hi, s_lo);
+    else if (last)
+      k_sweep3d32<false, true><<<grd, blk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, hi, lo, s_hi, s_lo);
+    else
+      k_sweep3d32<false, false><<<grd, blk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, hi, lo, s_hi, s_lo);
     prof_mark(g, KK_SWEEP3D32, 4.0 * (double)s.size() * ((k == 0 ? 1.0 : 2.0) + (last ? 4.0 : 1.0)));
     xin = xo;
   }

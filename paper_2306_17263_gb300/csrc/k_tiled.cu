@@ -409,8 +409,8 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
   float b0 = xcol[ly0 * RSP];
   float lxa = fmaf(-2.0f, a0, xcol[(ly0 - 1) * RSP - 1] + xcol[(ly0 - 1) * RSP + 1]);
   float lxb = fmaf(-2.0f, b0, xcol[ly0 * RSP - 1] + xcol[ly0 * RSP + 1]);
-  size_t gp = (size_t)(gy0 + ly0) * nx + gx;
-  if (LAST) {
+  if constexpr (LAST) {
+    const size_t gp = (size_t)(gy0 + ly0) * nx + gx;
     // the state of PF rows at a time is fetched before the first of them is updated
 #pragma unroll
     for (int t0 = 0; t0 < MAXR; t0 += PF) {
@@ -452,8 +452,7 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
         lxb = lxc;
       }
     }
-    return;
-  }
+  } else {
 #pragma unroll 3
   for (int ly = ly0; ly < ly1; ++ly) {
     const float* row = xcol + (ly + 1) * RSP;
@@ -472,22 +471,12 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
       const int gy = gy0 + ly;
       unk = col_unk && gy >= 0 && gy < ny && interior(bcy, gy, ny);
     }
-    if (LAST) {
-      if (unk) {
-        float h = shi[gp], l = slo[gp];
-        ff_add_scaled_t(h, l, x, A.s_hi, A.s_lo);
-        ff_add_scaled_t(h, l, corr, A.s_hi, A.s_lo);
-        shi[gp] = h;
-        slo[gp] = l;
-      }
-      gp += nx;
-    } else {
-      xn[ly * RSP + c] = unk ? x + corr : 0.0f;
-    }
+    xn[ly * RSP + c] = unk ? x + corr : 0.0f;
     a0 = b0;
     lxa = lxb;
     b0 = c0v;
     lxb = lxc;
+  }
   }
 }
 
