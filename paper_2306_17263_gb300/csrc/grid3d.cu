@@ -391,27 +391,73 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
         }
       }
     } else {
-      const int line0 = src_index(0, p0 - 1, q);
-      for (int j = warp; j < X3L; j += NW3) {
-        const int m = r0 - K3H - 1 + j;
-        dlt[lane * X3P + j] = delta_m(line0 + lane, m);
-        if (lane < 2) dlt[(32 + lane) * X3P + j] = delta_m(line0 + 32 + lane, m);
+      // lanes across the lines, warp w along a contiguous run of the line: each source row is read
+      // once per run and its hi / lo kept for the next difference; the along-line ends (ghosts)
+      // are split off, so the sliding loops carry no range tests
+      const int mb = r0 - K3H - 1;  // m of raw column 0
+      {
+        constexpr int RJ = (X3L + NW3 - 1) / NW3;
+        const int ja = warp * RJ, jb = min(ja + RJ, X3L);
+        const int ca = max(ja, min(jb, -mb)), cb = max(ca, min(jb, M - mb));
+        const int line = src_index(0, p0 - 1, q) + lane;
+        float* row = dlt + lane * X3P;
+        for (int j = ja; j < ca; ++j) row[j] = delta_m(line, mb + j);
+        if (ca < cb) {
+          const float* hp = hi + line + (mb + ca) * sa;
+          const float* lp = lo + line + (mb + ca) * sa;
+          float h0 = hp[0], l0 = lp[0];
+#pragma unroll 4
+          for (int j = ca; j < cb; ++j) {
+            hp += sa;
+            lp += sa;
+            const float h1 = *hp, l1 = *lp;
+            row[j] = (h1 - h0) + (l1 - l0);
+            h0 = h1;
+            l0 = l1;
+          }
+        }
+        for (int j = cb; j < jb; ++j) row[j] = delta_m(line, mb + j);
+      }
+      for (int idx = threadIdx.x; idx < 2 * X3L; idx += blockDim.x) {  // the last two lines
+        const int e = idx >= X3L, j = idx - e * X3L;
+        dlt[(32 + e) * X3P + j] = delta_m(src_index(0, p0 + 31 + e, q), mb + j);
       }
       __syncthreads();
-      const int line = src_index(0, p0, q) + lane;
-      for (int j = warp; j < D3L; j += NW3) {
-        const int m = r0 - K3H + j;
-        float out = 0.0f;
-        if (m >= 0 && m < M) {
-          const float* c = dlt + (lane + 1) * X3P + j + 1;
-          const float v = c[0];
-          const int at = line + m * sa;
-          const float lap = (((c[-1] - v) + (c[1] - v)) + ((c[-X3P] - v) + (c[X3P] - v))) +
-                            ((delta_at(at - sq) - v) + (delta_at(at + sq) - v));
-          out = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+      const int mf = r0 - K3H;  // m of filtered column 0
+      constexpr int RD = (D3L + NW3 - 1) / NW3;
+      const int ja = warp * RD, jb = min(ja + RD, D3L);
+      const int ca = max(ja, min(jb, -mf)), cb = max(ca, min(jb, M - mf));
+      float* out = dd + lane * D3P;
+      for (int j = ja; j < ca; ++j) out[j] = 0.0f;
+      if (ca < cb) {
+        // Q neighbours (lines q - 1 and q + 1) slide along the line the same way
+        const int at0 = src_index(0, p0, q) + lane + (mf + ca) * sa;
+        const float* hm = hi + at0 - sq;
+        const float* lm = lo + at0 - sq;
+        const float* hq = hi + at0 + sq;
+        const float* lq = lo + at0 + sq;
+        float hm0 = hm[0], lm0 = lm[0], hq0 = hq[0], lq0 = lq[0];
+        const float* c = dlt + (lane + 1) * X3P + 1;
+#pragma unroll 2
+        for (int j = ca; j < cb; ++j) {
+          hm += sa;
+          lm += sa;
+          hq += sa;
+          lq += sa;
+          const float hm1 = *hm, lm1 = *lm, hq1 = *hq, lq1 = *lq;
+          const float c1 = (hm1 - hm0) + (lm1 - lm0);
+          const float c2 = (hq1 - hq0) + (lq1 - lq0);
+          const float v = c[j];
+          const float lap = (((c[j - 1] - v) + (c[j + 1] - v)) + ((c[j - X3P] - v) + (c[j + X3P] - v))) +
+                            ((c1 - v) + (c2 - v));
+          out[j] = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+          hm0 = hm1;
+          lm0 = lm1;
+          hq0 = hq1;
+          lq0 = lq1;
         }
-        dd[lane * D3P + j] = out;
       }
+      for (int j = cb; j < jb; ++j) out[j] = 0.0f;
     }
     __syncthreads();
   } else if (!q_wall) {
