@@ -24,7 +24,7 @@
  *   - the non-compact fourth-order comparator NC (stencil K4, a = 0, one-sided
  *     fourth-order differences at the line ends): Sec. 5.2, Eq. "eq:K4".
  *
- * Readings of points the paper leaves open (all listed in the design notes):
+ * Readings of points the paper leaves open:
  *   - the third rows of Step 1 / Step 2 are E_z and H_z (the printed E_y, H_y
  *     rows are typos);
  *   - the Laplacian inside the right-hand-side filter is Delta_h for both

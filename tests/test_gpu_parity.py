@@ -1,9 +1,9 @@
 """Parity of the CUDA path with the FP64 CPU oracle (GB300 only).
 
-Tolerances (written here, derived in the design notes):
+Tolerances:
   - FP64 path: relative L2 difference <= 1e-12 after the whole run;
   - FP32_REFINED path: within 2x the oracle's own error against the exact modes and closer to
-    the oracle than the oracle is to the exact modes (the spec criterion); on random
+    the oracle than the oracle is to the exact modes (the mixed-path criterion); on random
     fields, relative L2 difference <= 2e-6.
 Inputs come from workloads.py (seeded); expected values come only from oracle/ or from the
 closed forms in tests/closed_forms.py, which are pinned to the oracle by test_oracle_pins.py.
