@@ -323,9 +323,33 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
   }
 }
 
+// Launch order of the tiles of an nt x nt grid: the boundary ring first, then the interior.  Ring
+// tiles take the general paths (line ends, ghost lines, explicit Pade rows) and run about twice as
+// long as interior tiles; started first, they no longer form the tail of the launch.
+__host__ __device__ __forceinline__ void ring_first_tile(int b, int nt, int* tx, int* ty) {
+  const int ring = nt > 1 ? 4 * (nt - 1) : 1;
+  if (b >= ring) {  // interior tiles, row by row
+    const int k = b - ring, w = nt - 2;
+    *tx = 1 + k % w;
+    *ty = 1 + k / w;
+  } else if (b < nt) {  // first row
+    *tx = b;
+    *ty = 0;
+  } else if (b < 2 * nt) {  // last row
+    *tx = b - nt;
+    *ty = nt - 1;
+  } else {  // first and last columns, rows 1 .. nt-2
+    const int k = b - 2 * nt;
+    *tx = (k & 1) ? nt - 1 : 0;
+    *ty = 1 + (k >> 1);
+  }
+}
+
 template <int STEP>
 __global__ void __launch_bounds__(NT, 3) k_curl_tile(CurlArgs A) {
-  curl_body<STEP>(A, blockIdx.x * TB, blockIdx.y * TB);
+  int tx, ty;
+  ring_first_tile(blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, &tx, &ty);
+  curl_body<STEP>(A, tx * TB, ty * TB);
 }
 
 // Words of a small argument struct copied from global to shared memory by the first warp.
