@@ -117,48 +117,74 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
       }
     }
   } else if (p.axis == 0) {
+    // strip at a line end or with lines past the array: the ghost rule per element, zero lines
+    // past the array; rows unrolled by two and chunks unrolled so the loads are in flight together
+#pragma unroll 2
     for (int a = warp; a < XROWS; a += NW) {
       const int c = c0 - 1 + a;
       const bool line_ok = c >= 0 && c < p.n_across;
       const float* hr = p.hi + (size_t)(line_ok ? c : 0) * p.snx;
       const float* lr = p.lo + (size_t)(line_ok ? c : 0) * p.snx;
-      for (int q = lane; q < XL; q += 32) {
-        const int m = mb + q;
-        float v = 0.0f;
-        if (inside) {
-          v = (hr[m + 1] - hr[m]) + (lr[m + 1] - lr[m]);
-        } else if (line_ok) {
-          int mm = m;
-          bool zero = false;
-          if (m < 0 || m >= p.M) {
-            if (!p.ghost_even || m < -1 || m > p.M) zero = true;
-            else mm = (m < 0) ? 0 : p.M - 1;
+#pragma unroll
+      for (int cc = 0; cc < (XL + 31) / 32; ++cc) {
+        const int q = lane + 32 * cc;
+        if (32 * cc + 32 <= XL || q < XL) {
+          const int m = mb + q;
+          float v = 0.0f;
+          if (line_ok) {
+            int mm = m;
+            bool zero = false;
+            if (m < 0 || m >= p.M) {
+              if (!p.ghost_even || m < -1 || m > p.M) zero = true;
+              else mm = (m < 0) ? 0 : p.M - 1;
+            }
+            if (!zero) v = (hr[mm + 1] - hr[mm]) + (lr[mm + 1] - lr[mm]);
           }
-          if (!zero) v = (hr[mm + 1] - hr[mm]) + (lr[mm + 1] - lr[mm]);
+          dlt[a * XLP + q] = v;
         }
-        dlt[a * XLP + q] = v;
       }
     }
   } else {
+    // same for lines along y: lanes across the lines (zero past the array, load index clamped
+    // into it), warp along the rows with the ghost rule per row; rows unrolled by two
+    const int ca = c0 - 1 + lane, cb = c0 + 31 + lane;
+    const bool va = ca >= 0 && ca < p.n_across, vb = cb >= 0 && cb < p.n_across;
+    const int ka = va ? ca : 0, kb = vb ? cb : 0;
+    const size_t sn = (size_t)p.snx;
+#pragma unroll 2
     for (int q = warp; q < XL; q += NW) {
-      const int m = mb + q;
-      int mm = m;
+      int m = mb + q;
       bool zero = false;
-      if (!inside && (m < 0 || m >= p.M)) {
+      if (m < 0 || m >= p.M) {
         if (!p.ghost_even || m < -1 || m > p.M) zero = true;
-        else mm = (m < 0) ? 0 : p.M - 1;
+        else m = (m < 0) ? 0 : p.M - 1;
       }
-      const size_t row0 = (size_t)(zero ? 0 : mm) * p.snx;
+      const size_t row0 = (size_t)(zero ? 0 : m) * sn;
       const float* h0 = p.hi + row0;
       const float* l0 = p.lo + row0;
-      const float* h1 = h0 + p.snx;
-      const float* l1 = l0 + p.snx;
-      for (int a = lane; a < XROWS; a += 32) {
-        const int c = c0 - 1 + a;
-        float v = 0.0f;
-        if (!zero && (inside || (c >= 0 && c < p.n_across))) v = (h1[c] - h0[c]) + (l1[c] - l0[c]);
-        dlt[a * XLP + q] = v;
+      float v0 = 0.0f, v1 = 0.0f;
+      if (!zero) {
+        v0 = (h0[sn + ka] - h0[ka]) + (l0[sn + ka] - l0[ka]);
+        v1 = (h0[sn + kb] - h0[kb]) + (l0[sn + kb] - l0[kb]);
       }
+      dlt[lane * XLP + q] = va ? v0 : 0.0f;
+      dlt[(lane + 32) * XLP + q] = vb ? v1 : 0.0f;
+    }
+    for (int idx = threadIdx.x; idx < (XROWS - 64) * XL; idx += NT) {  // the last two lines
+      const int e = idx / XL, q = idx - e * XL;
+      const int c = c0 + 63 + e;
+      int m = mb + q;
+      bool zero = !(c >= 0 && c < p.n_across);
+      if (!zero && (m < 0 || m >= p.M)) {
+        if (!p.ghost_even || m < -1 || m > p.M) zero = true;
+        else m = (m < 0) ? 0 : p.M - 1;
+      }
+      float v = 0.0f;
+      if (!zero) {
+        const size_t g0 = (size_t)m * sn + c;
+        v = (p.hi[g0 + sn] - p.hi[g0]) + (p.lo[g0 + sn] - p.lo[g0]);
+      }
+      dlt[(64 + e) * XLP + q] = v;
     }
   }
   __syncthreads();
