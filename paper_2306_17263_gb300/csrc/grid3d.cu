@@ -296,7 +296,7 @@ __global__ void k_band3d32(const float* __restrict__ d, float* __restrict__ R, S
 }
 
 // One Pade term fused: the filtered differences of the difference-filter kernel above and the
-// A^{-1} band of the band kernel, on a tile of TO destination points along AXIS times NPL lines
+// A^{-1} band of the band kernel, on a tile of T3O destination points along AXIS times NPL lines
 // along the in-tile transverse axis P, at one coordinate of the other transverse axis Q.  The
 // differences of the centre Q plane go to shared memory with a one-line halo in P and K3H + 1
 // points along the line; the Q neighbours of the filter come from global memory; the band reads
