@@ -59,3 +59,36 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
 
     assert bench.run_reference(A(), 2, 1) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
+    """Rank 0 prints one JSON line with the contract's keys; the oracle loop itself is replaced by
+    a stub here (its timing is what the line reports, not what this test checks)."""
+    import json
+
+    import bench
+
+    calls = []
+
+    def fake_rate(n, steps, modes, time_budget=None):
+        calls.append((n, steps))
+        return 1.0e6, steps, 0.5
+
+    monkeypatch.setattr(bench, "oracle_rate", fake_rate)
+
+    class A:
+        steps, warmup, gpus = 4, 1, 1
+
+    assert bench.run_reference(A(), 1, 0) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] == 1.0e6 and d["steps"] == 4 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert "workload" in d["config"]
+    # one warm-up call, then the timed call, both on the same sample size
+    assert [c[1] for c in calls] == [1, 4] and calls[0][0] == calls[1][0]
