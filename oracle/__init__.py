@@ -108,6 +108,10 @@ def lib() -> ctypes.CDLL:
             L.or3d_step.argtypes = [V, PP]
             L.or3d_exact.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, PP]
             L.or3d_error.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, PP, D]
+            L.or3d_energy.argtypes = [V, PP]
+            L.or3d_energy.restype = ctypes.c_double
+            L.or3d_divergence.argtypes = [V, PP, D]
+            L.or3d_divergence.restype = ctypes.c_double
             L.or3d_cg_iters_total.argtypes = [V]
             L.or3d_cg_iters_total.restype = ctypes.c_long
             L.or3d_cg_solves.argtypes = [V]
@@ -451,6 +455,16 @@ class Oracle3D:
         out = np.zeros(4)
         lib().or3d_error(self.g, _p(m), nm, n * self.ht, (n + 0.5) * self.ht, _pp(f), _p(out))
         return out
+
+    def energy(self, f):
+        """W^n = Z^-1 ||E^n||^2 + Z <H^{n-1/2}, H^{n+1/2}> (h^3-weighted) of the six components."""
+        return lib().or3d_energy(self.g, _pp(f))
+
+    def divergence(self, f):
+        """(||div_h H||_h, div field on the N^3 cell centres) with node->half-node Pade derivatives."""
+        div = np.zeros((self.N, self.N, self.N))
+        nrm = lib().or3d_divergence(self.g, _pp(f), _p(div))
+        return nrm, div
 
     def cg_stats(self):
         L = lib()

@@ -378,5 +378,80 @@ void or3d_error(const or_grid3d* g, const double* modes, int nmodes, double tE, 
   out[3] = s1;
 }
 
+/* Discrete energy W^n = Z^{-1} ||E^n||^2 + Z <H^{n-1/2}, H^{n+1/2}> with h^3-weighted sums over
+ * the stored points (wall values are zero): the 3D form of the leapfrog invariant of the 2D
+ * diagnostic (the paper is silent on a discrete energy; Sec. 4 writes the scheme as a leapfrog).
+ * f holds E^n and H^{n+1/2}; H^{n-1/2} = H^{n+1/2} - h_tau H*, with H* = P1^{-1} R_H(E^n) the
+ * Step 2 increment (Sec. 3.4). */
+double or3d_energy(or_grid3d* g, const double* const* f) {
+  double* G[3];
+  double* R[3];
+  double* X[3];
+  for (int q = 0; q < 3; ++q) {
+    long n = or3d_field_size(g, 3 + q) > or3d_field_size(g, q) ? or3d_field_size(g, 3 + q) : or3d_field_size(g, q);
+    G[q] = (double*)malloc(sizeof(double) * n);
+    R[q] = (double*)malloc(sizeof(double) * n);
+    X[q] = (double*)malloc(sizeof(double) * n);
+  }
+  for (int q = 0; q < 3; ++q) or3d_filter(g, q, f[q], G[q]);
+  or3d_curl_e_to_h(g, (const double* const*)G, R);
+  for (int q = 0; q < 3; ++q) or3d_p1_solve_cg(g, 3 + q, R[q], X[q]);
+  double se = 0.0, sh = 0.0;
+  for (int q = 0; q < 3; ++q) {
+    long n = or3d_field_size(g, q);
+    for (long p = 0; p < n; ++p) se += f[q][p] * f[q][p];
+    n = or3d_field_size(g, 3 + q);
+    for (long p = 0; p < n; ++p) sh += (f[3 + q][p] - g->ht * X[q][p]) * f[3 + q][p];
+  }
+  for (int q = 0; q < 3; ++q) {
+    free(G[q]);
+    free(R[q]);
+    free(X[q]);
+  }
+  return g->h * g->h * g->h * (se / g->Z + g->Z * sh);
+}
+
+/* Pade divergence of H on the N^3 cell centres: div_h H = d_x H_x + d_y H_y + d_z H_z, each a
+ * node -> half-node derivative of App. A.1 along its own axis (the 3D form of the 2D
+ * diagnostic).  Returns sqrt(h^3 sum div^2); div_out (N^3, [z][y][x]) may be NULL. */
+double or3d_divergence(const or_grid3d* g, const double* const* f, double* div_out) {
+  const int N = g->N;
+  const long nc = (long)N * N * N;
+  double* div = div_out ? div_out : (double*)malloc(sizeof(double) * nc);
+  double* line = (double*)malloc(sizeof(double) * (N + 1));
+  double* dl = (double*)malloc(sizeof(double) * N);
+  for (long p = 0; p < nc; ++p) div[p] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    int d[3];
+    or3d_dims(g, 3 + a, d); /* d[a] = N + 1 nodes along a, N half points across */
+    const double* u = f[3 + a];
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j) {
+        /* the line along axis a through centre indices (j, k) of the two other axes */
+        for (int t = 0; t <= N; ++t) {
+          int c[3];
+          c[a] = t;
+          c[(a + 1) % 3] = j;
+          c[(a + 2) % 3] = k;
+          line[t] = u[((long)c[2] * d[1] + c[1]) * d[0] + c[0]];
+        }
+        or_pade_line(N, g->closure, P_NODE_TO_HALF, g->h, line, dl);
+        for (int t = 0; t < N; ++t) {
+          int c[3];
+          c[a] = t;
+          c[(a + 1) % 3] = j;
+          c[(a + 2) % 3] = k;
+          div[((long)c[2] * N + c[1]) * N + c[0]] += dl[t];
+        }
+      }
+  }
+  double s = 0.0;
+  for (long p = 0; p < nc; ++p) s += div[p] * div[p];
+  free(line);
+  free(dl);
+  if (!div_out) free(div);
+  return sqrt(g->h * g->h * g->h * s);
+}
+
 long or3d_cg_iters_total(const or_grid3d* g) { return g->cg_iters_total; }
 long or3d_cg_solves(const or_grid3d* g) { return g->cg_solves; }

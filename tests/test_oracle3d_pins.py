@@ -180,3 +180,51 @@ def test_fourth_order_convergence_paper_closure():
         errs.append(o.error(modes, K, f)[0])
     rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     assert rates[1] > 3.6, (errs, rates)
+
+
+# --------------------------------------------------------------------------
+# Diagnostics: discrete energy and Pade divergence of H in 3D
+
+@pytest.mark.parametrize("closure", [CLOSURE_PAPER, CLOSURE_REFLECT])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_energy_and_divergence_reduce_to_2d(closure, axis):
+    """For fields independent of one coordinate, the 3D energy and the norm of the 3D divergence
+    equal those of the pinned 2D oracle on the cross-section (h^3 sums over N copies)."""
+    N, r, Z = 9, 0.4, 1.3
+    o2 = oracle.Oracle2D(N, r, Z=Z, closure=closure)
+    o3 = oracle.Oracle3D(N, r, Z=Z, closure=closure)
+    s2 = list(workloads.random_fields(N, seed=80 + axis))
+    f, _ = _extrude(s2, N, axis)
+    W2, W3 = o2.energy(*s2), o3.energy(f)
+    assert abs(W3 - W2) <= 1e-12 * abs(W2)
+    d2, d3 = o2.divergence(s2[1], s2[2])[0], o3.divergence(f)[0]
+    assert abs(d3 - d2) <= 1e-12 * d2
+
+
+def test_reflect_energy_and_divergence_conserved_3d():
+    """REFLECT closure: the leapfrog invariant and the Pade divergence of H are conserved to
+    round-off by the six-component step (random fields, far from divergence-free)."""
+    N = 7
+    o = oracle.Oracle3D(N, 0.45, Z=1.4, closure=CLOSURE_REFLECT)
+    f = list(workloads.random_fields3(N, seed=5))
+    W0 = o.energy(f)
+    d0, div0 = o.divergence(f)
+    assert d0 > 1.0
+    for _ in range(8):
+        o.step(f)
+    assert abs(o.energy(f) - W0) < 1e-12 * W0
+    d1, div1 = o.divergence(f)
+    assert np.max(np.abs(div1 - div0)) < 1e-10 * np.max(np.abs(div0))
+
+
+def test_paper_closure_energy_bounded_3d():
+    """PAPER closure: W is not an exact invariant, but stays in a narrow band for cavity modes."""
+    N = 16
+    o = oracle.Oracle3D(N, 0.4, closure=CLOSURE_PAPER)
+    f = o.init_modes([workloads.mode3(2, 3, 1, 1.0), workloads.mode3(1, 2, 2, 0.7)])
+    W = [o.energy(f)]
+    for _ in range(4):
+        o.run(f, 8)
+        W.append(o.energy(f))
+    W = np.array(W)
+    assert (W.max() - W.min()) / W[0] < 1e-3
