@@ -171,15 +171,18 @@ ms_status ms_sync(ms_grid* g);
 ms_status ms_get_step(ms_grid* g, long* step);
 
 /* Discrete energy at the current state, FP64 reductions:
- *   W^n = Z^{-1} h^2 sum E^n.E^n + Z h^2 sum H^{n-1/2}.H^{n+1/2},
+ *   W^n = Z^{-1} h^d sum E^n.E^n + Z h^d sum H^{n-1/2}.H^{n+1/2}   (d = 2 or 3; all components),
  * with H^{n-1/2} = H^{n+1/2} - h_tau H*(E^n) recomputed on the device.  This is the
  * leapfrog invariant of the scheme in the form of Sec. 4, Eq. "eq:eh" (the paper states
  * no discrete energy); exact under MS_CLOSURE_REFLECT, bounded under MS_CLOSURE_PAPER.
- * Synchronous. */
+ * 3D grids: MS_FP64 only (MS_EUNSUPPORTED for MS_FP32_REFINED; copy the state into an FP64
+ * grid with ms_get_fields / ms_set_fields).  Synchronous. */
 ms_status ms_energy(ms_grid* g, double* W);
 
-/* L2 norm sqrt(h^2 sum div^2) of the Pade divergence of H on the n x n cell centres,
- * div_h H = delta_x H_x + delta_y H_y (node-to-half-node derivatives of App. A.1). Synchronous. */
+/* L2 norm sqrt(h^d sum div^2) of the Pade divergence of H on the n^d cell centres,
+ * div_h H = delta_x H_x + delta_y H_y (+ delta_z H_z in 3D), node-to-half-node derivatives of
+ * App. A.1 along each component's own axis.  3D grids: MS_FP64 only, as ms_energy.
+ * Synchronous. */
 ms_status ms_divergence(ms_grid* g, double* norm);
 
 /* Error of the current state against a superposition of exact modes at t_E = n h_tau,

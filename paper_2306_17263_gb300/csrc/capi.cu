@@ -743,7 +743,7 @@ ms_status ms_launches_per_step(ms_grid* g, int* launches) {
 
 ms_status ms_energy(ms_grid* g, double* W) {
   if (!valid_grid(g) || !W) return fail(MS_EINVAL, "invalid argument");
-  if (g->g3) return fail(MS_EUNSUPPORTED, "energy is implemented for 2D grids");
+  if (g->g3) return energy3d(g, W);
   if (g->desc.scheme != MS_SCHEME_C4) return fail(MS_EUNSUPPORTED, "energy is defined for the compact scheme");
   // FP64 view of the state in scratch slots that the H increment does not touch
   double* tmp[3] = {nullptr, nullptr, nullptr};
@@ -797,7 +797,7 @@ ms_status ms_energy(ms_grid* g, double* W) {
 
 ms_status ms_divergence(ms_grid* g, double* norm) {
   if (!valid_grid(g) || !norm) return fail(MS_EINVAL, "invalid argument");
-  if (g->g3) return fail(MS_EUNSUPPORTED, "the divergence is implemented for 2D grids");
+  if (g->g3) return divergence3d(g, norm);
   if (g->desc.scheme != MS_SCHEME_C4 && g->desc.scheme != MS_SCHEME_C4_DE)
     return fail(MS_EUNSUPPORTED, "the Pade divergence is defined for the compact scheme");
   double* tmp[3] = {g->s64[3], g->s64[4], g->s64[5]};

@@ -1256,6 +1256,75 @@ ms_status get_fields3d(ms_grid* g, double* const* comps, int host) {
   return MS_OK;
 }
 
+// Discrete energy of a 3D FP64 grid: W = h^3 [Z^-1 sum E.E + Z (sum H.H - h_tau sum H*.H)], H* the
+// Step 2 increment that the current E gives (P1^{-1} of the H right-hand side), computed with the
+// step's own filter, Pade and sweep kernels but not added to H.
+ms_status energy3d(ms_grid* g, double* W) {
+  Grid3D* G3 = g->g3;
+  if (g->desc.precision != MS_FP64)
+    return fail3(MS_EUNSUPPORTED, "the energy of a 3D grid is computed on the FP64 path (copy the state into an FP64 grid)");
+  double** G = G3->s64;  // G[0..2]: filtered E
+  double* R = G3->s64[3];
+  const double* X = G3->s64[6];  // the last sweep's iterate
+  const double s_eh = g->kappa2 / (g->Z * g->h);
+  int nl = 0;
+  for (int c = 0; c < 3; ++c) {
+    filter3d64(g, c, G3->f64[c], G[c]);
+    const size_t n = G3->sh[c].size();
+    launch_dot(G3->f64[c], G3->f64[c], n, g->d_partial, reduce_blocks(n), g->d_result, 0, c > 0, g->stream);
+  }
+  for (int hc = 0; hc < 3; ++hc) {
+    const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
+    pade3d64(g, p1, p2, 3 + hc, G[p2], R, -s_eh, 0);
+    pade3d64(g, p2, p1, 3 + hc, G[p1], R, s_eh, 1);
+    solve3d64(g, 3 + hc, R, nullptr, 0.0, &nl);
+    const size_t n = G3->sh[3 + hc].size();
+    const double* H = G3->f64[3 + hc];
+    launch_dot(H, H, n, g->d_partial, reduce_blocks(n), g->d_result, 1, hc > 0, g->stream);
+    launch_dot(X, H, n, g->d_partial, reduce_blocks(n), g->d_result, 2, hc > 0, g->stream);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("3D energy: ") + cudaGetErrorString(e));
+  double r[3];
+  MS3_CUDA(cudaMemcpyAsync(r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  MS3_CUDA(cudaStreamSynchronize(g->stream));
+  *W = g->h * g->h * g->h * (r[0] / g->Z + g->Z * (r[1] - g->ht * r[2]));
+  return MS_OK;
+}
+
+// Pade divergence of H on the N^3 cell centres of a 3D FP64 grid: div_h H = sum_a delta_a H_a, each
+// a node -> half-node derivative along its own axis; *norm = sqrt(h^3 sum div^2).
+ms_status divergence3d(ms_grid* g, double* norm) {
+  Grid3D* G3 = g->g3;
+  if (g->desc.precision != MS_FP64)
+    return fail3(MS_EUNSUPPORTED, "the divergence of a 3D grid is computed on the FP64 path (copy the state into an FP64 grid)");
+  const int N = g->N;
+  Shape3 sc;  // cell centres: N points on every axis, no walls
+  for (int a = 0; a < 3; ++a) {
+    sc.n[a] = N;
+    sc.bc[a] = NEU;
+  }
+  double* div = G3->s64[0];
+  const PadeTable& t = g->pade[NODE_TO_HALF];
+  const dim3 grd = grid3(sc, kBlk);
+  const double sc_h = 1.0 / g->h;
+  k_pade3d64<0><<<grd, kBlk, 0, g->stream>>>(G3->f64[3], div, sc, G3->sh[3], t.d_w, t.rows, t.n_in, t.left, t.K,
+                                              t.B, t.all_explicit, 0, sc_h, 0);
+  k_pade3d64<1><<<grd, kBlk, 0, g->stream>>>(G3->f64[4], div, sc, G3->sh[4], t.d_w, t.rows, t.n_in, t.left, t.K,
+                                              t.B, t.all_explicit, 0, sc_h, 1);
+  k_pade3d64<2><<<grd, kBlk, 0, g->stream>>>(G3->f64[5], div, sc, G3->sh[5], t.d_w, t.rows, t.n_in, t.left, t.K,
+                                              t.B, t.all_explicit, 0, sc_h, 1);
+  const size_t n = sc.size();
+  launch_dot(div, div, n, g->d_partial, reduce_blocks(n), g->d_result, 0, 0, g->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("3D divergence: ") + cudaGetErrorString(e));
+  double r;
+  MS3_CUDA(cudaMemcpyAsync(&r, g->d_result, sizeof r, cudaMemcpyDeviceToHost, g->stream));
+  MS3_CUDA(cudaStreamSynchronize(g->stream));
+  *norm = std::sqrt(g->h * g->h * g->h * r);
+  return MS_OK;
+}
+
 }  // namespace ms
 
 using namespace ms;

@@ -24,6 +24,10 @@ ms_status step3d(ms_grid* g);
 ms_status set_fields3d(ms_grid* g, const double* const* comps, int host);
 ms_status get_fields3d(ms_grid* g, double* const* comps, int host);
 double stability_limit_3d();
+// Diagnostics of a 3D FP64 grid (MS_EUNSUPPORTED for FP32_REFINED grids): the discrete energy and
+// the norm of the Pade divergence of H on the cell centres.
+ms_status energy3d(ms_grid* g, double* W);
+ms_status divergence3d(ms_grid* g, double* norm);
 // Device arrays of the state of a 3D grid: component c has n[c] points in f64[c] (MS_FP64) or in
 // hi[c] + lo[c] (MS_FP32_REFINED; the other pointers are NULL).  Returns the component count (6).
 int state_arrays3d(ms_grid* g, double** f64, float** hi, float** lo, size_t* n);

@@ -141,3 +141,43 @@ def test_full_size_fp32_refined_within_fp64_discretisation_error():
     diff = np.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(f32, f64)) / n ** 3)
     assert e32 <= 2 * e64, (e32, e64)
     assert diff <= e64, (diff, e64)
+
+
+# --------------------------------------------------------------------------
+# Diagnostics: discrete energy and Pade divergence of H (FP64 3D grids)
+
+@pytest.mark.parametrize("closure", [pkg.CLOSURE_PAPER, pkg.CLOSURE_REFLECT])
+@pytest.mark.parametrize("n", [8, 13])
+def test_fp64_energy_and_divergence_match_oracle(closure, n):
+    r, Z, steps = 0.4, 1.3, 2
+    init = workloads.random_fields3(n, seed=700 + n)
+    o = oracle.Oracle3D(n, r, Z=Z, closure=closure)
+    ref = [a.copy() for a in init]
+    with pkg.Grid(n, r, z=Z, closure=closure, dim=3) as g:
+        g.set_fields(*init)
+        for k in range(steps + 1):
+            W, d = g.energy(), g.divergence()
+            assert abs(W - o.energy(ref)) <= 1e-12 * abs(o.energy(ref)), k
+            d_ref = o.divergence(ref)[0]
+            assert abs(d - d_ref) <= 1e-12 * d_ref, k
+            g.step()
+            o.step(ref)
+
+
+def test_fp64_reflect_energy_and_divergence_conserved():
+    n, r = 12, 0.45
+    with pkg.Grid(n, r, closure=pkg.CLOSURE_REFLECT, dim=3) as g:
+        g.set_fields(*workloads.random_fields3(n, seed=9))
+        W0, d0 = g.energy(), g.divergence()
+        g.run(20)
+        assert abs(g.energy() - W0) <= 1e-12 * W0
+        assert abs(g.divergence() - d0) <= 1e-10 * d0
+
+
+def test_fp32_3d_energy_is_unsupported():
+    with pkg.Grid(8, 0.4, precision=pkg.FP32_REFINED, dim=3) as g:
+        g.set_fields(*workloads.random_fields3(8, seed=3))
+        with pytest.raises(Exception, match="FP64"):
+            g.energy()
+        with pytest.raises(Exception, match="FP64"):
+            g.divergence()
