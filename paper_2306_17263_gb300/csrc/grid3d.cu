@@ -850,7 +850,7 @@ int term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, flo
                                                  t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
     }
     // state hi + lo in, R out (read too when accumulating)
-    prof_mark(g, KK_DFILT3D32, 4.0 * (2.0 * (double)ss.size() + (accumulate ? 2.0 : 1.0) * (double)sd.size()));
+    prof_mark(g, KK_TERM3D32, 4.0 * (2.0 * (double)ss.size() + (accumulate ? 2.0 : 1.0) * (double)sd.size()));
     return 1;
   }
   float* d = G3->s32[0];
