@@ -19,6 +19,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -153,12 +154,20 @@ KIND_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """C/CUDA source without comments and blank lines (so that a comment edit keeps the hash)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", l).rstrip() for l in text.splitlines()]
+    return "\n".join(l for l in lines if l.strip())
+
+
 def kernel_sources_hash(kind: str):
+    """Hash of the code (not the comments) of the files that define a kernel kind."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_17263_gb300", "csrc")
     for f in KIND_SOURCES.get(kind, []):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

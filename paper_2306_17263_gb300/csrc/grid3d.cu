@@ -8,11 +8,13 @@
 //
 // MS_FP64: one operator per launch in FP64 (filter, Pade band along one axis, Richardson sweep).
 // MS_FP32_REFINED: the arithmetic of the 2D FP32 path (k_mixed.cu) carried to 3D: float-float
-// state; per Pade term one kernel forms the float-float first differences of the source state
-// along the line and filters them (d = 12 beta delta + L delta, the filter commuting with the
-// difference under the ghost rules), one kernel applies the A^{-1} band (farthest taps first)
-// and accumulates the right-hand side; the solve is the Richardson iteration on 6 h^2 P1 with
-// the exact two-product residual and the split last correction.
+// state; per Pade term one tile kernel (k_term3d32) forms the float-float first differences of
+// the source state along the line, filters them (d = 12 beta delta + L delta, the filter
+// commuting with the difference under the ghost rules) and applies the A^{-1} band (farthest
+// taps first), accumulating the right-hand side (a difference-filter kernel and a band kernel
+// take over for tables wider than the tile holds); the solve (k_sweep3d32) is the Richardson
+// iteration on 6 h^2 P1 with the exact two-product residual and the split last correction,
+// each sweep one launch that marches tiles along z.
 #include <cmath>
 #include <cstdio>
 #include <string>

@@ -19,6 +19,10 @@
 // wall, filter zero there) has even differences (delta_{-1} = delta_0, delta_M = delta_{M-1}).
 // Across the line every source is Dirichlet with stored zeros.
 //
+// Launch order: the curl launches the boundary ring of tiles first (those take the general paths
+// and run about twice as long); the solve runs its tiles in row order, so neighbouring tiles
+// that share halo rows run together.
+//
 // Instruction budget: both kernels are bound by issue, not by DRAM, so loops have constant
 // strides and 32-bit offsets, tiles away from the walls take block-uniform paths without any
 // boundary test, and the interior band of A^{-1} (the same Toeplitz row for every grid,
