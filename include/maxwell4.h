@@ -175,13 +175,14 @@ ms_status ms_get_step(ms_grid* g, long* step);
  * with H^{n-1/2} = H^{n+1/2} - h_tau H*(E^n) recomputed on the device.  This is the
  * leapfrog invariant of the scheme in the form of Sec. 4, Eq. "eq:eh" (the paper states
  * no discrete energy); exact under MS_CLOSURE_REFLECT, bounded under MS_CLOSURE_PAPER.
- * 3D grids: MS_FP64 only (MS_EUNSUPPORTED for MS_FP32_REFINED; copy the state into an FP64
- * grid with ms_get_fields / ms_set_fields).  Synchronous. */
+ * 3D grids are evaluated in FP64; an MS_FP32_REFINED 3D grid joins its float-float state into
+ * FP64 copies and, on its first call, allocates the FP64 tables and scratch this needs (kept
+ * until ms_destroy).  Synchronous. */
 ms_status ms_energy(ms_grid* g, double* W);
 
 /* L2 norm sqrt(h^d sum div^2) of the Pade divergence of H on the n^d cell centres,
  * div_h H = delta_x H_x + delta_y H_y (+ delta_z H_z in 3D), node-to-half-node derivatives of
- * App. A.1 along each component's own axis.  3D grids: MS_FP64 only, as ms_energy.
+ * App. A.1 along each component's own axis.  3D grids are evaluated in FP64, as ms_energy.
  * Synchronous. */
 ms_status ms_divergence(ms_grid* g, double* norm);
 

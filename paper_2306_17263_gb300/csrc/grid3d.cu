@@ -43,6 +43,7 @@ struct Grid3D {
   float* lo[6] = {};
   double* s64[7] = {};  // FP64: G[3], R, sweep ping-pong [2], solve output; FP32 grids use [0], [1]
   float* s32[4] = {};   // FP32: differences, R, sweep ping-pong [2]
+  double* dview[6] = {};  // FP32_REFINED grids: FP64 copy of the state for the diagnostics
   size_t nmax = 0;      // points of the largest component
 };
 
@@ -1193,6 +1194,7 @@ void destroy_grid3d(ms_grid* g) {
     cudaFree(G3->f64[c]);
     cudaFree(G3->hi[c]);
     cudaFree(G3->lo[c]);
+    cudaFree(G3->dview[c]);
   }
   for (int k = 0; k < 7; ++k) cudaFree(G3->s64[k]);
   for (int k = 0; k < 4; ++k) cudaFree(G3->s32[k]);
@@ -1258,22 +1260,58 @@ ms_status get_fields3d(ms_grid* g, double* const* comps, int host) {
   return MS_OK;
 }
 
-// Discrete energy of a 3D FP64 grid: W = h^3 [Z^-1 sum E.E + Z (sum H.H - h_tau sum H*.H)], H* the
-// Step 2 increment that the current E gives (P1^{-1} of the H right-hand side), computed with the
+// FP64 components for the diagnostics.  An FP64 grid gives its state; an FP32_REFINED grid joins
+// its float-float state into FP64 copies, and on the first call builds what the FP64 kernels need
+// (FP64 Pade tables, the FP64 sweep count, FP64 scratch), kept until the grid is destroyed.
+ms_status diag_view3d(ms_grid* g, double** f) {
+  Grid3D* G3 = g->g3;
+  if (g->desc.precision == MS_FP64) {
+    for (int c = 0; c < 6; ++c) f[c] = G3->f64[c];
+    return MS_OK;
+  }
+  std::string err;
+  for (int kind = 0; kind < 2; ++kind) {
+    PadeTable& t = g->pade[kind];
+    if (t.d_w) continue;
+    const int M = (kind == HALF_TO_NODE) ? g->N - 1 : g->N;
+    if (build_pade_table(M, g->desc.closure, kind, 1e-18, &t, &err) != 0) return fail3(MS_EINVAL, err);
+    MS3_TRY(alloc3(&t.d_w, t.w.size()));
+    if (cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail3(MS_ECUDA, "copy of Pade tables failed");
+  }
+  if (!g->p1_sweeps) {
+    const double c1h2 = g->c1 * g->h * g->h;
+    const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
+    const int S = (int)std::ceil(std::log(1e-17) / std::log(rho));
+    g->p1_sweeps = S < 1 ? 1 : (S > 64 ? 64 : S);
+  }
+  for (int k = 0; k < 7; ++k)
+    if (!G3->s64[k]) MS3_TRY(alloc3(&G3->s64[k], G3->nmax));
+  for (int c = 0; c < 6; ++c) {
+    const size_t n = G3->sh[c].size();
+    if (!G3->dview[c]) MS3_TRY(alloc3(&G3->dview[c], n));
+    k_join3<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(G3->hi[c], G3->lo[c], G3->dview[c], n);
+    f[c] = G3->dview[c];
+  }
+  return MS_OK;
+}
+
+// Discrete energy of a 3D grid: W = h^3 [Z^-1 sum E.E + Z (sum H.H - h_tau sum H*.H)], H* the Step 2
+// increment that the current E gives (P1^{-1} of the H right-hand side), computed in FP64 with the
 // step's own filter, Pade and sweep kernels but not added to H.
 ms_status energy3d(ms_grid* g, double* W) {
   Grid3D* G3 = g->g3;
-  if (g->desc.precision != MS_FP64)
-    return fail3(MS_EUNSUPPORTED, "the energy of a 3D grid is computed on the FP64 path (copy the state into an FP64 grid)");
+  double* f[6];
+  MS3_TRY(diag_view3d(g, f));
   double** G = G3->s64;  // G[0..2]: filtered E
   double* R = G3->s64[3];
   const double* X = G3->s64[6];  // the last sweep's iterate
   const double s_eh = g->kappa2 / (g->Z * g->h);
   int nl = 0;
   for (int c = 0; c < 3; ++c) {
-    filter3d64(g, c, G3->f64[c], G[c]);
+    filter3d64(g, c, f[c], G[c]);
     const size_t n = G3->sh[c].size();
-    launch_dot(G3->f64[c], G3->f64[c], n, g->d_partial, reduce_blocks(n), g->d_result, 0, c > 0, g->stream);
+    launch_dot(f[c], f[c], n, g->d_partial, reduce_blocks(n), g->d_result, 0, c > 0, g->stream);
   }
   for (int hc = 0; hc < 3; ++hc) {
     const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
@@ -1281,9 +1319,9 @@ ms_status energy3d(ms_grid* g, double* W) {
     pade3d64(g, p2, p1, 3 + hc, G[p1], R, s_eh, 1);
     solve3d64(g, 3 + hc, R, nullptr, 0.0, &nl);
     const size_t n = G3->sh[3 + hc].size();
-    const double* H = G3->f64[3 + hc];
-    launch_dot(H, H, n, g->d_partial, reduce_blocks(n), g->d_result, 1, hc > 0, g->stream);
-    launch_dot(X, H, n, g->d_partial, reduce_blocks(n), g->d_result, 2, hc > 0, g->stream);
+    const double* Hc = f[3 + hc];
+    launch_dot(Hc, Hc, n, g->d_partial, reduce_blocks(n), g->d_result, 1, hc > 0, g->stream);
+    launch_dot(X, Hc, n, g->d_partial, reduce_blocks(n), g->d_result, 2, hc > 0, g->stream);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("3D energy: ") + cudaGetErrorString(e));
@@ -1294,12 +1332,12 @@ ms_status energy3d(ms_grid* g, double* W) {
   return MS_OK;
 }
 
-// Pade divergence of H on the N^3 cell centres of a 3D FP64 grid: div_h H = sum_a delta_a H_a, each
-// a node -> half-node derivative along its own axis; *norm = sqrt(h^3 sum div^2).
+// Pade divergence of H on the N^3 cell centres of a 3D grid (in FP64): div_h H = sum_a delta_a H_a,
+// each a node -> half-node derivative along its own axis; *norm = sqrt(h^3 sum div^2).
 ms_status divergence3d(ms_grid* g, double* norm) {
   Grid3D* G3 = g->g3;
-  if (g->desc.precision != MS_FP64)
-    return fail3(MS_EUNSUPPORTED, "the divergence of a 3D grid is computed on the FP64 path (copy the state into an FP64 grid)");
+  double* f[6];
+  MS3_TRY(diag_view3d(g, f));
   const int N = g->N;
   Shape3 sc;  // cell centres: N points on every axis, no walls
   for (int a = 0; a < 3; ++a) {
@@ -1310,12 +1348,12 @@ ms_status divergence3d(ms_grid* g, double* norm) {
   const PadeTable& t = g->pade[NODE_TO_HALF];
   const dim3 grd = grid3(sc, kBlk);
   const double sc_h = 1.0 / g->h;
-  k_pade3d64<0><<<grd, kBlk, 0, g->stream>>>(G3->f64[3], div, sc, G3->sh[3], t.d_w, t.rows, t.n_in, t.left, t.K,
-                                              t.B, t.all_explicit, 0, sc_h, 0);
-  k_pade3d64<1><<<grd, kBlk, 0, g->stream>>>(G3->f64[4], div, sc, G3->sh[4], t.d_w, t.rows, t.n_in, t.left, t.K,
-                                              t.B, t.all_explicit, 0, sc_h, 1);
-  k_pade3d64<2><<<grd, kBlk, 0, g->stream>>>(G3->f64[5], div, sc, G3->sh[5], t.d_w, t.rows, t.n_in, t.left, t.K,
-                                              t.B, t.all_explicit, 0, sc_h, 1);
+  k_pade3d64<0><<<grd, kBlk, 0, g->stream>>>(f[3], div, sc, G3->sh[3], t.d_w, t.rows, t.n_in, t.left, t.K, t.B,
+                                              t.all_explicit, 0, sc_h, 0);
+  k_pade3d64<1><<<grd, kBlk, 0, g->stream>>>(f[4], div, sc, G3->sh[4], t.d_w, t.rows, t.n_in, t.left, t.K, t.B,
+                                              t.all_explicit, 0, sc_h, 1);
+  k_pade3d64<2><<<grd, kBlk, 0, g->stream>>>(f[5], div, sc, G3->sh[5], t.d_w, t.rows, t.n_in, t.left, t.K, t.B,
+                                              t.all_explicit, 0, sc_h, 1);
   const size_t n = sc.size();
   launch_dot(div, div, n, g->d_partial, reduce_blocks(n), g->d_result, 0, 0, g->stream);
   cudaError_t e = cudaGetLastError();

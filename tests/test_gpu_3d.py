@@ -174,10 +174,18 @@ def test_fp64_reflect_energy_and_divergence_conserved():
         assert abs(g.divergence() - d0) <= 1e-10 * d0
 
 
-def test_fp32_3d_energy_is_unsupported():
-    with pkg.Grid(8, 0.4, precision=pkg.FP32_REFINED, dim=3) as g:
-        g.set_fields(*workloads.random_fields3(8, seed=3))
-        with pytest.raises(Exception, match="FP64"):
-            g.energy()
-        with pytest.raises(Exception, match="FP64"):
-            g.divergence()
+def test_fp32_energy_and_divergence_match_oracle_on_its_state():
+    """FP32_REFINED grids evaluate the diagnostics in FP64 on their float-float state: the same
+    values as the oracle on that state (read back exactly through ms_get_fields)."""
+    n, r = 9, 0.4
+    with pkg.Grid(n, r, precision=pkg.FP32_REFINED, dim=3) as g:
+        g.set_fields(*workloads.random_fields3(n, seed=3))
+        g.run(3)
+        o = oracle.Oracle3D(n, r)
+        for _ in range(2):  # twice: the FP64 tables and scratch are made on the first call
+            state = [np.ascontiguousarray(a) for a in g.get_fields()]
+            W, d = g.energy(), g.divergence()
+            assert abs(W - o.energy(state)) <= 1e-12 * abs(o.energy(state))
+            d_ref = o.divergence(state)[0]
+            assert abs(d - d_ref) <= 1e-12 * d_ref
+            g.step()
