@@ -507,7 +507,7 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
       }
     }
   } else {
-#pragma unroll 3
+#pragma unroll 4
   for (int ly = ly0; ly < ly1; ++ly) {
     const float* row = xcol + (ly + 1) * RSP;
     const float cm = row[-1], c0v = row[0], cp = row[1];
