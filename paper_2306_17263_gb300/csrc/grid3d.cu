@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
           const float* hp = hi + line + (mb + ca) * sa;
           const float* lp = lo + line + (mb + ca) * sa;
           float h0 = hp[0], l0 = lp[0];
-#pragma unroll 4
+#pragma unroll 8
           for (int j = ca; j < cb; ++j) {
             hp += sa;
             lp += sa;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, 
         const float* lq = lo + at0 + sq;
         float hm0 = hm[0], lm0 = lm[0], hq0 = hq[0], lq0 = lq[0];
         const float* c = dlt + (lane + 1) * X3P + 1;
-#pragma unroll 2
+#pragma unroll 4
         for (int j = ca; j < cb; ++j) {
           hm += sa;
           lm += sa;
