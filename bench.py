@@ -442,10 +442,6 @@ def run_ours(args, ws, rank, local):
     avg_ms = kms / cnt
     bytes_per_launch = kbytes / cnt
     hbm, hbm_src = measured_peaks()
-    if kind.endswith("64"):
-        # FP64 kernels are bound by the FP64 pipe: report achieved GB/s against HBM and note
-        # the ALU bound in the line's extras
-        pass
     achieved_gbs = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": achieved_gbs / hbm, "traffic": ncu_traffic(kind), "kernel": kind,
