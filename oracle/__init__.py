@@ -93,6 +93,11 @@ def lib() -> ctypes.CDLL:
             L.or2d_step_tracked.argtypes = [V, D, D, D, D]
             L.or2d_step_src.argtypes = [V, D, D, D, D, ctypes.c_int, ctypes.c_long]
             L.or2d_exact_driven.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D, D]
+            L.or2d_step_src_xy.argtypes = [V, D, D, D, D, ctypes.c_int, ctypes.c_long]
+            L.or2d_wall_ghosts.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           D, D, D, D]
+            L.or2d_ge_wall.argtypes = [V, D, ctypes.c_int, ctypes.c_double, D]
+            L.or2d_p1_ghost_shift.argtypes = [V, ctypes.c_int, D, D, D]
             PP = ctypes.POINTER(ctypes.c_void_p)
             L.or3d_sizeof.restype = ctypes.c_int
             L.or3d_setup.argtypes = [V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -266,6 +271,52 @@ class Oracle2D:
         lib().or2d_exact_driven(self.g, _p(s), ns, tE, tH, _p(ez), _p(hx), _p(hy))
         return ez, hx, hy
 
+    # -- sources with sine or cosine profiles, nonzero on the walls (Sec. 3.3, Method 2) --
+    @staticmethod
+    def _src_xy(src):
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.float64).reshape(-1, 6))
+        return a, a.shape[0]
+
+    def step_src_xy(self, ez, hx, hy, src, n):
+        """Step n with sources J_z = a X(m pi x) Y(n pi y) sin(w t), rows (m, n, a, w, px, py),
+        X = sin (px = 0) or cos (px = 1): the inhomogeneous ghosts of the H filter and the H solves,
+        and G_E on the walls from d_t J (PAPER closure)."""
+        s, ns = self._src_xy(src)
+        lib().or2d_step_src_xy(self.g, _p(ez), _p(hx), _p(hy), _p(s), ns, int(n))
+
+    def wall_ghosts(self, src, t0, t1, diff):
+        """Ghost data (g_x_lo, g_x_hi, g_y_lo, g_y_hi): H_x by column on y = 0, 1 and H_y by row on
+        x = 0, 1; the data of H at t1 (diff = 0) or of (H(t1) - H(t0)) / h_tau (diff = 1)."""
+        s, ns = self._src_xy(src)
+        out = [np.zeros(self.N + 1) for _ in range(4)]
+        lib().or2d_wall_ghosts(self.g, _p(s), ns, float(t0), float(t1), int(diff), *[_p(a) for a in out])
+        return out
+
+    def ge_wall(self, src, t):
+        """E_z-shaped array whose boundary nodes hold G_E = (h^2/12) Z d_t J_z at time t."""
+        s, ns = self._src_xy(src)
+        ge = self.zeros(F_EZ)
+        lib().or2d_ge_wall(self.g, _p(s), ns, float(t), _p(ge))
+        return ge
+
+    def p1_ghost_shift(self, f, glo, ghi):
+        """P1 (of H_x or H_y) applied to zero with the given ghost data: the affine part."""
+        c = self.zeros(f)
+        lib().or2d_p1_ghost_shift(self.g, int(f), _p(np.ascontiguousarray(glo, dtype=np.float64)),
+                                  _p(np.ascontiguousarray(ghi, dtype=np.float64)), _p(c))
+        return c
+
+    def exact_manufactured(self, m, n, A, w, tE, tH):
+        """The manufactured solution of `manufactured_sources` on this grid (E at tE, H at tH)."""
+        N, h = self.N, self.h
+        xn = np.arange(N + 1) * h
+        xh = (np.arange(N) + 0.5) * h
+        ez = manufactured_field(m, n, A, w, self.Z, F_EZ, xn[None, :], xn[:, None], tE)
+        hx = manufactured_field(m, n, A, w, self.Z, F_HX, xn[None, :], xh[:, None], tH)
+        hy = manufactured_field(m, n, A, w, self.Z, F_HY, xh[None, :], xn[:, None], tH)
+        return [np.ascontiguousarray(np.broadcast_to(a, self.shape(f)), dtype=np.float64)
+                for f, a in ((F_EZ, ez), (F_HX, hx), (F_HY, hy))]
+
     def nc_step(self, ez, hx, hy):
         """One step of the non-compact fourth-order comparator NC in place (Sec. 5.2, K4, a = 0)."""
         lib().or2d_nc_step(self.g, _p(ez), _p(hx), _p(hy))
@@ -342,6 +393,44 @@ class Oracle2D:
         g = self.zeros(F_EZ) if grad else None
         L = lib().or2d_misfit_grad(self.g, _p(ez0), _p(target), int(K), _p(g) if grad else None)
         return (L, g) if grad else L
+
+
+def manufactured_field(m, n, A, w, Z, comp, x, y, t):
+    """A closed-form PEC solution driven by a current that does not vanish on the walls:
+        E_z = A cos(w t) P,  P = sin^2(m pi x) sin^2(n pi y),
+        H   = (A sin(w t) / (Z w)) (-d_y P, d_x P)          (Faraday's law, H = 0 at t = 0),
+        J_z = (A sin(w t) / (Z w)) (Delta P + w^2 P)         (Ampere's law, d_t E = Z (curl H - J)).
+    E_z and H.n vanish on the walls; d_n H_t = -/+ J_z does not.  Evaluated at any (x, y), inside or
+    outside the square."""
+    pi = np.pi
+    sx, sy = np.sin(m * pi * x), np.sin(n * pi * y)
+    if comp == F_EZ:
+        return A * np.cos(w * t) * sx ** 2 * sy ** 2
+    c = A * np.sin(w * t) / (Z * w)
+    if comp == F_HX:
+        return -c * sx ** 2 * (n * pi * np.sin(2 * n * pi * y))
+    return c * (m * pi * np.sin(2 * m * pi * x)) * sy ** 2
+
+
+def manufactured_current(m, n, A, w, Z, x, y, t):
+    """J_z of `manufactured_field`, from its definition (Delta P written out term by term)."""
+    pi = np.pi
+    P = np.sin(m * pi * x) ** 2 * np.sin(n * pi * y) ** 2
+    lapP = (2 * (m * pi) ** 2 * np.cos(2 * m * pi * x) * np.sin(n * pi * y) ** 2
+            + 2 * (n * pi) ** 2 * np.sin(m * pi * x) ** 2 * np.cos(2 * n * pi * y))
+    return A * np.sin(w * t) / (Z * w) * (lapP + w * w * P)
+
+
+def manufactured_sources(m, n, A, w, Z):
+    """Rows (m, n, a, w, px, py) whose sum is J_z of `manufactured_field`: with
+    sin^2 = (1 - cos 2.)/2 the current is (A sin(w t) / (4 Z w)) times
+        w^2 + (4 m^2 pi^2 - w^2) cos(2 m pi x) + (4 n^2 pi^2 - w^2) cos(2 n pi y)
+          + (w^2 - 4 pi^2 (m^2 + n^2)) cos(2 m pi x) cos(2 n pi y)."""
+    pi2, c = np.pi ** 2, A / (4.0 * Z * w)
+    return [(0, 0, c * w * w, w, 1, 1),
+            (2 * m, 0, c * (4 * m * m * pi2 - w * w), w, 1, 1),
+            (0, 2 * n, c * (4 * n * n * pi2 - w * w), w, 1, 1),
+            (2 * m, 2 * n, c * (w * w - 4 * pi2 * (m * m + n * n)), w, 1, 1)]
 
 
 E_X, E_Y, E_Z, H_X, H_Y, H_Z = range(6)

@@ -1027,3 +1027,237 @@ void or2d_exact_driven(const or_grid2d* g, const double* src, int nsrc, double t
         hy[(size_t)j * N + i] += sh * pi * m * cos(pi * m * (i + 0.5) * h) * sin(pi * n * j * h);
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* Sources that do not vanish on the walls: inhomogeneous Neumann data (Sec. 3.3, Method 2).
+ * Source rows (m, n, a, w, px, py):
+ *   J_z = a X(m pi x) Y(n pi y) sin(w t),   X = sin if px = 0, cos if px = 1 (Y likewise by py),
+ * m, n >= 0 (a sine index >= 1).  The right-hand-side terms P(J) and curl d_t J are those of
+ * add_sources_e / add_sources_h with these profiles; every profile satisfies X'' = -(m pi)^2 X, so
+ * the filter factor is the same.  With J_z nonzero on a wall three boundary data change, each
+ * derived from Faraday's and Ampere's laws (d_t E = Z (curl H - J), d_t H = -curl E / Z) and the
+ * PEC conditions E_z = 0, H.n = 0 on the wall, the way Sec. 3.3 derives the Neumann data:
+ *   - on x = 0, 1 (H_y Neumann in x):  d_x H_y = J_z,   d_xxx H_y = d_tt J_z + d_xx J_z - d_yy J_z;
+ *     on y = 0, 1 (H_x Neumann in y):  d_y H_x = -J_z,  d_yyy H_x = -(d_tt J_z + d_yy J_z - d_xx J_z).
+ *     (Ampere's law on the wall gives the first derivative; differentiating it twice across the wall,
+ *     with div H = 0 and Delta E_z = d_tt E_z + Z d_t J_z = Z d_t J_z on the wall, the third.)
+ *     The ghost half a cell outside follows from the Taylor relation of Eq. "eq:gst2",
+ *     phi(h/2) - phi(-h/2) = h phi' + (h^3/24) phi''' + O(h^5) at the wall:
+ *       u(-1) = u(0) - g_lo,  u(n) = u(n-1) + g_hi,  g = h phi' + (h^3/24) phi''' on that wall.
+ *     The H filter of Step 1 takes the data of H at t^{n+1/2}; the H solves of Step 2 take the data
+ *     of their unknown H* = (H^{n+3/2} - H^{n+1/2}) / h_tau, i.e. the difference of the data at
+ *     t^{n+3/2} and t^{n+1/2} over h_tau.
+ *   - G_E on the boundary nodes is (h^2/12) Delta E_z = (h^2/12) Z d_t J_z at t^{n+1} (E_z = 0
+ *     there; with J = 0 this is the zero of Sec. 3.4).
+ * Ghost values at the Dirichlet end points of a wall (the corners) are not used: the second
+ * differences there are zero, as for every Dirichlet point.  The one-sided Pade rows of the PAPER
+ * closure need no ghost; the REFLECT rows assume even data at the walls and are not meant for
+ * these sources. */
+static double prof(int p, double k, double x) { return p ? cos(M_PI * k * x) : sin(M_PI * k * x); }
+static double dprof(int p, double k, double x) { return p ? -M_PI * k * sin(M_PI * k * x) : M_PI * k * cos(M_PI * k * x); }
+/* exact profile value on a wall: side 0 is x = 0, side 1 is x = 1 */
+static double prof_wall(int p, int k, int side) {
+  if (!p) return 0.0;
+  return (side && (k & 1)) ? -1.0 : 1.0;
+}
+/* profile at node i of n cells (exact at the two walls) */
+static double prof_node(int p, int k, int i, int n) {
+  if (i == 0) return prof_wall(p, k, 0);
+  if (i == n) return prof_wall(p, k, 1);
+  return prof(p, k, (double)i / n);
+}
+
+/* Second differences along one axis with ghost data on the Neumann ends of that axis
+ * (d2_axis with u(-1) = u(0) - glo[line], u(n) = u(n-1) + ghi[line]; line = the other index). */
+static void d2_axis_g(const or_grid2d* g, int f, int axis, const double* u, double* out, const double* glo,
+                      const double* ghi) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  double ih2 = 1.0 / (g->h * g->h);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) { out[p] = 0.0; continue; }
+      double um, up;
+      if (axis == 0) {
+        um = (i - 1 >= 0) ? u[p - 1] : u[p] - glo[j];
+        up = (i + 1 < nx) ? u[p + 1] : u[p] + ghi[j];
+      } else {
+        um = (j - 1 >= 0) ? u[p - nx] : u[p] - glo[i];
+        up = (j + 1 < ny) ? u[p + nx] : u[p] + ghi[i];
+      }
+      out[p] = (um - 2.0 * u[p] + up) * ih2;
+    }
+}
+
+/* Ghost data of H_x (indexed by column i, walls y = 0, 1) and H_y (indexed by row j, walls
+ * x = 0, 1).  diff = 0: the data of H at t1; diff = 1: of (H(t1) - H(t0)) / h_tau. */
+void or2d_wall_ghosts(const or_grid2d* g, const double* src, int nsrc, double t0, double t1, int diff, double* gx_lo,
+                      double* gx_hi, double* gy_lo, double* gy_hi) {
+  int N = g->N;
+  double h = g->h, pi2 = M_PI * M_PI;
+  for (int k = 0; k <= N; ++k) gx_lo[k] = gx_hi[k] = gy_lo[k] = gy_hi[k] = 0.0;
+  for (int q = 0; q < nsrc; ++q) {
+    const double* s = src + 6 * q;
+    int m = (int)s[0], n = (int)s[1], px = (int)s[4], py = (int)s[5];
+    double a = s[2], w = s[3];
+    double T = diff ? (sin(w * t1) - sin(w * t0)) / g->ht : sin(w * t1);
+    /* x walls, H_y: g = h J + (h^3/24)(d_tt + d_xx - d_yy) J = J (h + (h^3/24)(pi^2 n^2 - pi^2 m^2 - w^2)) */
+    double cx = h + h * h * h / 24.0 * (pi2 * n * n - pi2 * m * m - w * w);
+    /* y walls, H_x: g = -h J - (h^3/24)(d_tt + d_yy - d_xx) J = -J (h + (h^3/24)(pi^2 m^2 - pi^2 n^2 - w^2)) */
+    double cy = -(h + h * h * h / 24.0 * (pi2 * m * m - pi2 * n * n - w * w));
+    for (int j = 1; j < N; ++j) {
+      double Yj = prof_node(py, n, j, N);
+      gy_lo[j] += cx * a * prof_wall(px, m, 0) * Yj * T;
+      gy_hi[j] += cx * a * prof_wall(px, m, 1) * Yj * T;
+    }
+    for (int i = 1; i < N; ++i) {
+      double Xi = prof_node(px, m, i, N);
+      gx_lo[i] += cy * a * Xi * prof_wall(py, n, 0) * T;
+      gx_hi[i] += cy * a * Xi * prof_wall(py, n, 1) * T;
+    }
+  }
+}
+
+/* Right-hand-side filter of Eq. "eq:ell" for H_x or H_y with the ghost data on its Neumann axis. */
+static void filter_ghost(const or_grid2d* g, int f, const double* u, double* G, const double* glo, const double* ghi) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  int n = nx * ny;
+  double* t = (double*)malloc(sizeof(double) * n);
+  int neu_axis = (f == F_HX) ? 1 : 0;
+  d2_axis_g(g, f, neu_axis, u, G, glo, ghi);
+  d2_axis(g, f, 1 - neu_axis, u, t);
+  double h2_12 = g->h * g->h / 12.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) G[p] = 0.0;
+      else G[p] = g->beta * u[p] + h2_12 * (G[p] + t[p]);
+    }
+  free(t);
+}
+
+/* P1 of H_x or H_y applied to the zero field with the ghost data: the affine part of P1 with
+ * inhomogeneous ghosts, P1_g x = P1 x + P1_g 0.  The 9-point stencil with the ghost nodes,
+ * written as the Kronecker composition with the Neumann-axis difference first. */
+void or2d_p1_ghost_shift(const or_grid2d* g, int f, const double* glo, const double* ghi, double* c) {
+  int nx, ny, bx, by;
+  field_dims(g, f, &nx, &ny, &bx, &by);
+  int n = nx * ny;
+  double* z = (double*)calloc(n, sizeof(double));
+  double* dn = (double*)malloc(sizeof(double) * n);
+  double* dnd = (double*)malloc(sizeof(double) * n);
+  int neu_axis = (f == F_HX) ? 1 : 0;
+  d2_axis_g(g, f, neu_axis, z, dn, glo, ghi);
+  d2_axis(g, f, 1 - neu_axis, dn, dnd);
+  double h2_6 = g->h * g->h / 6.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t p = (size_t)j * nx + i;
+      if (!axis_interior(bx, i, nx) || !axis_interior(by, j, ny)) c[p] = 0.0;
+      else c[p] = -(dn[p] + h2_6 * dnd[p]);
+    }
+  free(z);
+  free(dn);
+  free(dnd);
+}
+
+/* G_E on the boundary nodes: (h^2/12) Z d_t J_z at time t (interior entries untouched). */
+void or2d_ge_wall(const or_grid2d* g, const double* src, int nsrc, double t, double* GE) {
+  int N = g->N;
+  double c = g->h * g->h / 12.0 * g->Z;
+  for (int j = 0; j <= N; ++j)
+    for (int i = 0; i <= N; ++i) {
+      if (i > 0 && i < N && j > 0 && j < N) continue;
+      double v = 0.0;
+      for (int q = 0; q < nsrc; ++q) {
+        const double* s = src + 6 * q;
+        int m = (int)s[0], n = (int)s[1], px = (int)s[4], py = (int)s[5];
+        v += s[2] * s[3] * cos(s[3] * t) * prof_node(px, m, i, N) * prof_node(py, n, j, N);
+      }
+      GE[(size_t)j * (N + 1) + i] = c * v;
+    }
+}
+
+/* P(J) (E side, t) and curl d_t J (H side, t) through the filter, for the profiled sources. */
+static void add_sources_e_xy(const or_grid2d* g, const double* src, int nsrc, double t, double* R) {
+  int N = g->N;
+  double h = g->h;
+  for (int q = 0; q < nsrc; ++q) {
+    const double* s = src + 6 * q;
+    int m = (int)s[0], n = (int)s[1], px = (int)s[4], py = (int)s[5];
+    double a = s[2], w = s[3];
+    double filt = g->beta - (h * h / 12.0) * M_PI * M_PI * ((double)m * m + (double)n * n);
+    double amp = -g->Z * (g->kappa2 - w * w) * filt * a * sin(w * t);
+    for (int j = 1; j < N; ++j)
+      for (int i = 1; i < N; ++i) R[(size_t)j * (N + 1) + i] += amp * prof(px, m, i * h) * prof(py, n, j * h);
+  }
+}
+
+static void add_sources_h_xy(const or_grid2d* g, const double* src, int nsrc, double t, double* Rx, double* Ry) {
+  int N = g->N;
+  double h = g->h;
+  for (int q = 0; q < nsrc; ++q) {
+    const double* s = src + 6 * q;
+    int m = (int)s[0], n = (int)s[1], px = (int)s[4], py = (int)s[5];
+    double a = s[2], w = s[3];
+    double filt = g->beta - (h * h / 12.0) * M_PI * M_PI * ((double)m * m + (double)n * n);
+    double c = filt * a * w * cos(w * t);
+    for (int j = 0; j < N; ++j) /* H_x at (x_i, y_{j+1/2}): d_y d_t J_z */
+      for (int i = 1; i < N; ++i) Rx[(size_t)j * (N + 1) + i] += c * prof(px, m, i * h) * dprof(py, n, (j + 0.5) * h);
+    for (int j = 1; j < N; ++j) /* H_y at (x_{i+1/2}, y_j): -d_x d_t J_z */
+      for (int i = 0; i < N; ++i) Ry[(size_t)j * N + i] -= c * dprof(px, m, (i + 0.5) * h) * prof(py, n, j * h);
+  }
+}
+
+/* One full step with profiled sources (PAPER closure): or2d_step_src with the ghost data above in
+ * the H filter of Step 1 and the H solves of Step 2, and G_E on the walls from d_t J. */
+void or2d_step_src_xy(or_grid2d* g, double* ez, double* hx, double* hy, const double* src, int nsrc, long n) {
+  int N = g->N;
+  int ne = or2d_field_size(g, F_EZ), nx_ = or2d_field_size(g, F_HX), ny_ = or2d_field_size(g, F_HY);
+  double* Gx = (double*)malloc(sizeof(double) * nx_);
+  double* Gy = (double*)malloc(sizeof(double) * ny_);
+  double* R = (double*)malloc(sizeof(double) * ne);
+  double* Es = (double*)malloc(sizeof(double) * ne);
+  double* GE = (double*)malloc(sizeof(double) * ne);
+  double* Rx = (double*)malloc(sizeof(double) * nx_);
+  double* Ry = (double*)malloc(sizeof(double) * ny_);
+  double* Hs = (double*)malloc(sizeof(double) * (nx_ > ny_ ? nx_ : ny_));
+  double* c = (double*)malloc(sizeof(double) * (nx_ > ny_ ? nx_ : ny_));
+  double* gd = (double*)malloc(sizeof(double) * 4 * (N + 1));
+  double *gxl = gd, *gxh = gd + (N + 1), *gyl = gd + 2 * (N + 1), *gyh = gd + 3 * (N + 1);
+  double th = (n + 0.5) * g->ht, t1 = (n + 1.0) * g->ht, t32 = (n + 1.5) * g->ht;
+  /* Step 1 */
+  or2d_wall_ghosts(g, src, nsrc, th, th, 0, gxl, gxh, gyl, gyh);
+  filter_ghost(g, F_HX, hx, Gx, gxl, gxh);
+  filter_ghost(g, F_HY, hy, Gy, gyl, gyh);
+  or2d_curl_h_to_e(g, Gx, Gy, R);
+  add_sources_e_xy(g, src, nsrc, th, R);
+  or2d_p1_solve_cg(g, F_EZ, R, Es);
+  for (int p = 0; p < ne; ++p) ez[p] += g->ht * Es[p];
+  /* Step 2 */
+  or2d_filter(g, F_EZ, ez, GE);
+  or2d_ge_wall(g, src, nsrc, t1, GE);
+  or2d_curl_e_to_h(g, GE, Rx, Ry);
+  add_sources_h_xy(g, src, nsrc, t1, Rx, Ry);
+  or2d_wall_ghosts(g, src, nsrc, th, t32, 1, gxl, gxh, gyl, gyh);
+  or2d_p1_ghost_shift(g, F_HX, gxl, gxh, c);
+  for (int p = 0; p < nx_; ++p) Rx[p] -= c[p];
+  or2d_p1_ghost_shift(g, F_HY, gyl, gyh, c);
+  for (int p = 0; p < ny_; ++p) Ry[p] -= c[p];
+  or2d_p1_solve_cg(g, F_HX, Rx, Hs);
+  for (int p = 0; p < nx_; ++p) hx[p] += g->ht * Hs[p];
+  or2d_p1_solve_cg(g, F_HY, Ry, Hs);
+  for (int p = 0; p < ny_; ++p) hy[p] += g->ht * Hs[p];
+  free(Gx);
+  free(Gy);
+  free(R);
+  free(Es);
+  free(GE);
+  free(Rx);
+  free(Ry);
+  free(Hs);
+  free(c);
+  free(gd);
+}
