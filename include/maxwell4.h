@@ -283,6 +283,29 @@ ms_status ms_init_driven(ms_grid* g, const ms_source* src, int nsrc);
 ms_status ms_error_vs_driven(ms_grid* g, const ms_source* src, int nsrc, double* l2_abs, double* l2_rel,
                              double* max_abs, double* sum_abs);
 
+/* Sources with sine or cosine profiles:
+ *   J_z = amp X(pi m x) Y(pi n y) sin(omega t),  X = sin (cos_x = 0, m >= 1) or cos (cos_x = 1, m >= 0),
+ * Y likewise with cos_y and n.  A cosine profile does not vanish on the walls, and the Neumann data of
+ * Sec. 3.3 become inhomogeneous; they are discretised by Method 2 of Sec. 3.3 (the Taylor ghost of
+ * Eq. "eq:gst2"), with the wall data from Ampere's law on the PEC walls:
+ *   on x = 0, 1:  d_x H_y = J_z,   d_xxx H_y = (d_tt + d_xx - d_yy) J_z;
+ *   on y = 0, 1:  d_y H_x = -J_z,  d_yyy H_x = -(d_tt + d_yy - d_xx) J_z;
+ * the H filter of Step 1 takes the ghosts of H^{n+1/2}, the H solves of Step 2 those of
+ * H* = (H^{n+3/2} - H^{n+1/2}) / h_tau, and G_E on the boundary nodes is (h^2/12) Z d_t J_z at t^{n+1}
+ * (Delta E_z = Z d_t J_z on a PEC wall).  The data must be compatible at the corners (J_z = 0 there,
+ * since H.n = 0 on both walls); ghost values at the corner points are not used.
+ * ms_set_sources_xy: replaces the grid's sources like ms_set_sources (rows with cos_x = cos_y = 0 are
+ *   exactly ms_set_sources rows).  Rows with a cosine profile need an FP64 grid with
+ *   MS_CLOSURE_PAPER (the REFLECT rows assume even data at the walls): MS_EUNSUPPORTED otherwise;
+ *   MS_EINVAL for an index below its minimum or a flag other than 0 / 1.  Initial data come from
+ *   ms_set_fields. */
+typedef struct {
+  int m, n;
+  int cos_x, cos_y;
+  double amp, omega;
+} ms_source_xy;
+ms_status ms_set_sources_xy(ms_grid* g, const ms_source_xy* src, int nsrc);
+
 /* ---------------------------------------------------------------------------------------
  * Initial data that is not a cavity mode, and the reverse (adjoint) pass.
  *

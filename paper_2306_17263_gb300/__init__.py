@@ -50,6 +50,11 @@ class _Source(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("amp", ctypes.c_double), ("omega", ctypes.c_double)]
 
 
+class _SourceXY(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("cos_x", ctypes.c_int), ("cos_y", ctypes.c_int),
+                ("amp", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
 class _Mode3(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("az", ctypes.c_double)]
@@ -107,6 +112,7 @@ def load() -> ctypes.CDLL:
             "ms_save": [V, ctypes.c_char_p],
             "ms_load": [V, ctypes.c_char_p],
             "ms_set_sources": [V, ctypes.POINTER(_Source), I],
+            "ms_set_sources_xy": [V, ctypes.POINTER(_SourceXY), I],
             "ms_init_driven": [V, ctypes.POINTER(_Source), I],
             "ms_error_vs_driven": [V, ctypes.POINTER(_Source), I, PD, PD, PD, PD],
             "ms_error_vs_exact3": [V, ctypes.POINTER(_Mode3), I, PD, PD, PD, PD],
@@ -157,6 +163,15 @@ def _sources(src):
     arr = (_Source * max(1, len(src)))()
     for k, (m, n, a, w) in enumerate(src):
         arr[k].m, arr[k].n, arr[k].amp, arr[k].omega = int(m), int(n), float(a), float(w)
+    return arr, len(src)
+
+
+def _sources_xy(src):
+    src = list(src)
+    arr = (_SourceXY * max(1, len(src)))()
+    for k, (m, n, a, w, px, py) in enumerate(src):
+        arr[k].m, arr[k].n, arr[k].cos_x, arr[k].cos_y = int(m), int(n), int(px), int(py)
+        arr[k].amp, arr[k].omega = float(a), float(w)
     return arr, len(src)
 
 
@@ -337,6 +352,13 @@ class Grid:
         """Rows (m, n, amp, omega); an empty list removes the sources."""
         arr, ns = _sources(src)
         _check(load().ms_set_sources(self._h, arr, ns))
+
+    def set_sources_xy(self, src):
+        """Rows (m, n, amp, omega, cos_x, cos_y): J_z = amp X(pi m x) Y(pi n y) sin(omega t) with X = sin
+        (cos_x = 0) or cos (cos_x = 1), Y likewise; cosine profiles need an FP64 grid with the PAPER
+        closure (maxwell4.h, ms_set_sources_xy)."""
+        arr, ns = _sources_xy(src)
+        _check(load().ms_set_sources_xy(self._h, arr, ns))
 
     def init_driven(self, src):
         """E^0, H^{1/2} = the exact particular solution driven by the sources."""

@@ -124,10 +124,20 @@ void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, doubl
   launch_filter64(ez, GE, g->sh[EZ], g->beta, g->stream);
   prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[EZ].size());
   *nl += 1;
+  if (with_sources && g->src_wall) {  // G_E on the boundary nodes from d_t J
+    launch_wall_ge64(g, GE);
+    prof_mark(g, KK_SRC, 8.0 * 4.0 * g->N);
+    *nl += 1;
+  }
   curl_eh64(g, GE, Rx, Ry, nl);
   if (with_sources && g->nsrc) {
     launch_src_h64(g, Rx, Ry, 1.0);
     prof_mark(g, KK_SRC, 8.0 * 2.0 * (double)g->sh[HX].size());
+    *nl += 1;
+  }
+  if (with_sources && g->src_wall) {  // the ghost part of P1 with the wall data of H*
+    launch_wall_hsolve64(g, Rx, Ry);
+    prof_mark(g, KK_SRC, 8.0 * 8.0 * g->N);
     *nl += 1;
   }
   p1_solve64(g, HX, Rx, hxs, hx_upd, g->ht, nl);
@@ -194,6 +204,11 @@ ms_status step64(ms_grid* g) {
   launch_filter64(hy, Gy, g->sh[HY], g->beta, g->stream);
   prof_mark(g, KK_FILTER64, 16.0 * (double)g->sh[HY].size());
   nl += 2;
+  if (g->src_wall) {  // the inhomogeneous ghosts of H^{n+1/2} in the filter
+    launch_wall_hfilter64(g, Gx, Gy);
+    prof_mark(g, KK_SRC, 8.0 * 8.0 * g->N);
+    nl += 1;
+  }
   curl_he64(g, Gx, Gy, R, &nl);
   if (g->nsrc) {
     launch_src_e64(g, R, 1.0);
@@ -846,17 +861,15 @@ ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double
   return MS_OK;
 }
 
-ms_status ms_set_sources(ms_grid* g, const ms_source* src, int nsrc) {
-  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
-  if (g->g3 || g->desc.scheme != MS_SCHEME_C4)
-    return fail(MS_EUNSUPPORTED, "sources are implemented for 2D grids of the compact scheme");
-  MS_TRY(check_sources(g, src, nsrc, false));
+// Replaces the grid's sources (validated by the caller).
+static ms_status set_sources_spec(ms_grid* g, const SrcSpec* src, int nsrc) {
   MS_CUDA(cudaStreamSynchronize(g->stream));
   cudaFree(g->d_src);
   cudaFree(g->d_srctab);
   g->d_src = nullptr;
   g->d_srctab = nullptr;
   g->nsrc = 0;
+  g->src_wall = 0;
   free_graph(&g->graph1);  // the captured steps do not contain the source launches
   free_graph(&g->graphk);
   g->launches_per_step = 0;
@@ -871,7 +884,41 @@ ms_status ms_set_sources(ms_grid* g, const ms_source* src, int nsrc) {
   MS_CUDA(cudaMemcpy(g->d_srctab, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice));
   g->nsrc = nsrc;
+  for (int q = 0; q < nsrc; ++q) g->src_wall |= (src[q].px | src[q].py);
   return MS_OK;
+}
+
+ms_status ms_set_sources(ms_grid* g, const ms_source* src, int nsrc) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3 || g->desc.scheme != MS_SCHEME_C4)
+    return fail(MS_EUNSUPPORTED, "sources are implemented for 2D grids of the compact scheme");
+  MS_TRY(check_sources(g, src, nsrc, false));
+  std::vector<SrcSpec> sp(nsrc);
+  for (int q = 0; q < nsrc; ++q) sp[q] = SrcSpec{src[q].m, src[q].n, 0, 0, src[q].amp, src[q].omega};
+  return set_sources_spec(g, sp.data(), nsrc);
+}
+
+ms_status ms_set_sources_xy(ms_grid* g, const ms_source_xy* src, int nsrc) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (g->g3 || g->desc.scheme != MS_SCHEME_C4)
+    return fail(MS_EUNSUPPORTED, "sources are implemented for 2D grids of the compact scheme");
+  if (nsrc < 0 || nsrc > 64 || (nsrc > 0 && !src)) return fail(MS_EINVAL, "invalid sources (0 <= nsrc <= 64)");
+  bool wall = false;
+  std::vector<SrcSpec> sp(nsrc);
+  for (int q = 0; q < nsrc; ++q) {
+    const ms_source_xy& r = src[q];
+    if ((r.cos_x != 0 && r.cos_x != 1) || (r.cos_y != 0 && r.cos_y != 1))
+      return fail(MS_EINVAL, "cos_x and cos_y must be 0 or 1");
+    if (r.m < (r.cos_x ? 0 : 1) || r.n < (r.cos_y ? 0 : 1))
+      return fail(MS_EINVAL, "source indices must be >= 1 (sine) or >= 0 (cosine)");
+    if (r.m > 1000000 || r.n > 1000000) return fail(MS_EINVAL, "source indices must be <= 1e6");
+    if (!std::isfinite(r.amp) || !std::isfinite(r.omega)) return fail(MS_EINVAL, "non-finite source");
+    wall |= (r.cos_x || r.cos_y);
+    sp[q] = SrcSpec{r.m, r.n, r.cos_x, r.cos_y, r.amp, r.omega};
+  }
+  if (wall && (g->desc.precision != MS_FP64 || g->desc.closure != MS_CLOSURE_PAPER))
+    return fail(MS_EUNSUPPORTED, "sources that do not vanish on the walls need an FP64 grid with the PAPER closure");
+  return set_sources_spec(g, sp.data(), nsrc);
 }
 
 ms_status ms_init_driven(ms_grid* g, const ms_source* src, int nsrc) {

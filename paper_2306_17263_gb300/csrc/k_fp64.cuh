@@ -39,13 +39,23 @@ void launch_de_update64(double* de, const double* es, const double* c, const dou
 void launch_lap_e64(const double* e, double* de, int N, double h, cudaStream_t st);
 // Current sources (k_src.cu): host tables and constants; launches that add P(J) to an E right-hand
 // side and curl d_t J to the H right-hand sides (scaled by `scale`), and the device step tick.
-int build_sources(ms_grid* g, const ms_source* src, int nsrc, std::vector<unsigned char>* dev_blob,
+// J_z = amp X(pi m x) Y(pi n y) sin(omega t), X = sin (px = 0) or cos (px = 1), Y likewise by py.
+struct SrcSpec {
+  int m, n, px, py;
+  double amp, omega;
+};
+int build_sources(ms_grid* g, const SrcSpec* src, int nsrc, std::vector<unsigned char>* dev_blob,
                   std::vector<double>* tabs);
 void launch_src_e64(ms_grid* g, double* R, double scale);
 void launch_src_h64(ms_grid* g, double* Rx, double* Ry, double scale);
 void launch_src_e32(ms_grid* g, float* R, double scale);
 void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale);
 void launch_tick(ms_grid* g);
+// Boundary data of sources that do not vanish on the walls (FP64 step): the H-filter ghosts of
+// Step 1, G_E on the boundary nodes, and the ghost part of P1 in the H right-hand sides of Step 2.
+void launch_wall_hfilter64(ms_grid* g, double* Gx, double* Gy);
+void launch_wall_ge64(ms_grid* g, double* GE);
+void launch_wall_hsolve64(ms_grid* g, double* Rx, double* Ry);
 // Non-compact fourth-order comparator NC (k_nc.cu)
 void launch_nc_e64(double* ez, const double* hx, const double* hy, int N, double c_e, cudaStream_t st);
 void launch_nc_h64(const double* ez, double* hx, double* hy, int N, double c_h, cudaStream_t st);

@@ -1,12 +1,23 @@
-// Current sources of the 2D TM_z problem (J = J_z z, div J = 0): a sum of driven sine modes
-//   J_z = a sin(m pi x) sin(n pi y) sin(w t),
-// which vanish on the walls together with every derivative the Neumann data of Sec. 3.3 use, so
-// the even ghosts stay exact.  The modified Helmholtz equations of Eq. "eq:mh" gain
+// Current sources of the 2D TM_z problem (J = J_z z, div J = 0): a sum of driven modes
+//   J_z = a X(m pi x) Y(n pi y) sin(w t),   X, Y = sin or cos,
+// The modified Helmholtz equations of Eq. "eq:mh" gain
 //   E:  P(J)^{n+1/2} = -Z (kappa^2 - w^2) J^{n+1/2},    H:  (curl d_t J)^{n+1} = (d_y d_t J_z, -d_x d_t J_z),
 // (from the Taylor expansion of Sec. 3.1 with Faraday's and Ampere's laws), each through the
 // right-hand-side filter of Eq. "eq:ell" with the exact Laplacian of the source, factor
 // f = beta - (h^2/12) pi^2 (m^2 + n^2).  The kernels add these terms to a right-hand side before
 // the solve; the step index is read from device memory so that captured graphs stay valid.
+//
+// Sine profiles vanish on the walls with every derivative the Neumann data of Sec. 3.3 use, so the
+// even ghosts stay exact.  A cosine profile does not, and three boundary data of the step change
+// (FP64 path; Method 2 of Sec. 3.3, the wall data from Ampere's law on the PEC walls):
+//   - the ghosts half a cell beyond a Neumann wall: u(-1) = u(0) - g_lo, u(n) = u(n-1) + g_hi with
+//     g = h d_n u + (h^3/24) d_nnn u on the wall, where on x = 0, 1 (H_y)
+//       d_x H_y = J_z,   d_xxx H_y = (d_tt + d_xx - d_yy) J_z,
+//     and on y = 0, 1 (H_x)  d_y H_x = -J_z,  d_yyy H_x = -(d_tt + d_yy - d_xx) J_z.
+//     In the H filter of Step 1 (data of H at t^{n+1/2}) the ghost adds -g_lo/12 or +g_hi/12 to G
+//     next to the wall; in the H solves of Step 2 (data of H* = (H^{n+3/2} - H^{n+1/2}) / h_tau)
+//     the right-hand side loses P1 applied to the ghosts alone, which is nonzero next to the wall;
+//   - G_E on the boundary nodes is (h^2/12) Delta E_z = (h^2/12) Z d_t J_z at t^{n+1}.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -16,12 +27,14 @@
 namespace ms {
 namespace {
 
-// Per source: ce = -Z (kappa^2 - w^2) f a,  ch = f a w,  kx = pi m,  ky = pi n,  w.
+// Per source: ce = -Z (kappa^2 - w^2) f a,  ch = f a w,  kx = pi m,  ky = pi n,  w, and for the
+// wall data: gy = a (h + (h^3/24)(pi^2 n^2 - pi^2 m^2 - w^2)) (ghosts of H_y on x = 0, 1),
+// gx = -a (h + (h^3/24)(pi^2 m^2 - pi^2 n^2 - w^2)) (ghosts of H_x on y = 0, 1), ge = (h^2/12) Z a w.
 struct SrcDev {
-  double ce, ch, kx, ky, w;
+  double ce, ch, kx, ky, w, gy, gx, ge;
 };
 
-// R (+)= scale * sum_q ce_q sin(w_q t) sx_q(i) sy_q(j) at the interior E_z nodes, t = (n + 1/2) h_tau.
+// R (+)= scale * sum_q ce_q sin(w_q t) X_q(i) Y_q(j) at the interior E_z nodes, t = (n + 1/2) h_tau.
 template <typename T>
 __global__ void k_src_e(T* __restrict__ R, int N, const SrcDev* __restrict__ s, int nsrc, const double* __restrict__ tab,
                         const long* __restrict__ d_step, double ht, double scale) {
@@ -29,7 +42,7 @@ __global__ void k_src_e(T* __restrict__ R, int N, const SrcDev* __restrict__ s, 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i < 1 || j < 1 || i >= N || j >= N) return;
   const double t = ((double)*d_step + 0.5) * ht;
-  const size_t per = 4 * (size_t)(N + 1);  // per-source table block: sx, sy, cxh, cyh
+  const size_t per = 4 * (size_t)(N + 1);  // per-source table block: X, Y at nodes, X', Y' at half-nodes
   double v = 0.0;
   for (int q = 0; q < nsrc; ++q) {
     const double* tq = tab + q * per;
@@ -38,7 +51,7 @@ __global__ void k_src_e(T* __restrict__ R, int N, const SrcDev* __restrict__ s, 
   R[(size_t)j * (N + 1) + i] += (T)(scale * v);
 }
 
-// R_x += scale sum ch_q cos(w_q t) ky_q sx_q(i) cyh_q(j);  R_y -= scale sum ch_q cos(w_q t) kx_q cxh_q(i) sy_q(j),
+// R_x += scale sum ch_q cos(w_q t) ky_q X_q(i) Y'_q(j)/ky_q;  R_y -= scale sum ch_q cos(w_q t) kx_q X'_q(i)/kx_q Y_q(j),
 // t = (n + 1) h_tau.
 template <typename T>
 __global__ void k_src_h(T* __restrict__ Rx, T* __restrict__ Ry, int N, const SrcDev* __restrict__ s, int nsrc,
@@ -68,39 +81,137 @@ __global__ void k_src_h(T* __restrict__ Rx, T* __restrict__ Ry, int N, const Src
 
 __global__ void k_tick(long* d_step) { *d_step += 1; }
 
+// Table layout per source (4 (N + 1) doubles): X at nodes i = 0..N, Y at nodes j = 0..N,
+// X'/(pi m) at half-nodes i = 0..N-1, Y'/(pi n) at half-nodes j = 0..N-1.
+__device__ __forceinline__ double wall_sum_hy(const SrcDev* s, int nsrc, const double* tab, int N, int side, int j,
+                                              double t0, double t1, double inv_dt) {
+  // ghost datum of H_y on wall x = side at row j: sum_q gy_q X_q(side) Y_q(j) T_q
+  if (j <= 0 || j >= N) return 0.0;
+  const size_t per = 4 * (size_t)(N + 1);
+  double v = 0.0;
+  for (int q = 0; q < nsrc; ++q) {
+    const double* tq = tab + q * per;
+    const double T = inv_dt > 0.0 ? (sin(s[q].w * t1) - sin(s[q].w * t0)) * inv_dt : sin(s[q].w * t1);
+    v += s[q].gy * T * tq[side ? N : 0] * tq[(N + 1) + j];
+  }
+  return v;
+}
+__device__ __forceinline__ double wall_sum_hx(const SrcDev* s, int nsrc, const double* tab, int N, int side, int i,
+                                              double t0, double t1, double inv_dt) {
+  // ghost datum of H_x on wall y = side at column i: sum_q gx_q X_q(i) Y_q(side) T_q
+  if (i <= 0 || i >= N) return 0.0;
+  const size_t per = 4 * (size_t)(N + 1);
+  double v = 0.0;
+  for (int q = 0; q < nsrc; ++q) {
+    const double* tq = tab + q * per;
+    const double T = inv_dt > 0.0 ? (sin(s[q].w * t1) - sin(s[q].w * t0)) * inv_dt : sin(s[q].w * t1);
+    v += s[q].gx * T * tq[i] * tq[(N + 1) + (side ? N : 0)];
+  }
+  return v;
+}
+
+// Step 1: the ghosts of H^{n+1/2} in the filter, G -= g_lo / 12 next to the low wall and
+// G += g_hi / 12 next to the high wall.  Thread k = 1..N-1 takes row k of G_y and column k of G_x.
+__global__ void k_wall_hfilter64(double* __restrict__ Gx, double* __restrict__ Gy, int N, const SrcDev* __restrict__ s,
+                                 int nsrc, const double* __restrict__ tab, const long* __restrict__ d_step, double ht) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < 1 || k >= N) return;
+  const double t = ((double)*d_step + 0.5) * ht;
+  Gy[(size_t)k * N] -= wall_sum_hy(s, nsrc, tab, N, 0, k, t, t, 0.0) * (1.0 / 12.0);
+  Gy[(size_t)k * N + N - 1] += wall_sum_hy(s, nsrc, tab, N, 1, k, t, t, 0.0) * (1.0 / 12.0);
+  Gx[k] -= wall_sum_hx(s, nsrc, tab, N, 0, k, t, t, 0.0) * (1.0 / 12.0);
+  Gx[(size_t)(N - 1) * (N + 1) + k] += wall_sum_hx(s, nsrc, tab, N, 1, k, t, t, 0.0) * (1.0 / 12.0);
+}
+
+// Step 2: G_E on the boundary nodes = sum_q ge_q cos(w_q t) X_q(i) Y_q(j), t = (n + 1) h_tau.
+// Thread k = 0..N takes nodes (k, 0) and (k, N), and for 0 < k < N also (0, k) and (N, k).
+__global__ void k_wall_ge64(double* __restrict__ GE, int N, const SrcDev* __restrict__ s, int nsrc,
+                            const double* __restrict__ tab, const long* __restrict__ d_step, double ht) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  const double t = ((double)*d_step + 1.0) * ht;
+  const size_t per = 4 * (size_t)(N + 1);
+  const int ni = (k > 0 && k < N) ? 4 : 2;
+  for (int e = 0; e < ni; ++e) {
+    const int i = e < 2 ? k : (e == 2 ? 0 : N);
+    const int j = e < 2 ? (e == 0 ? 0 : N) : k;
+    double v = 0.0;
+    for (int q = 0; q < nsrc; ++q) {
+      const double* tq = tab + q * per;
+      v += s[q].ge * cos(s[q].w * t) * tq[i] * tq[(N + 1) + j];
+    }
+    GE[(size_t)j * (N + 1) + i] = v;
+  }
+}
+
+// Step 2: the right-hand sides of the H solves lose P1 applied to the ghosts of H* alone (zero
+// field inside): next to a low wall with datum g (g = 0 at the Dirichlet end points),
+//   P1_g 0 = g / h^2 + (g_{-} - 2 g + g_{+}) / (6 h^2),   and the negative of it with g_hi next to a
+// high wall.  Thread k = 1..N-1 takes column k of R_x (rows 0 and N-1) and row k of R_y.
+__global__ void k_wall_hsolve64(double* __restrict__ Rx, double* __restrict__ Ry, int N, const SrcDev* __restrict__ s,
+                                int nsrc, const double* __restrict__ tab, const long* __restrict__ d_step, double ht,
+                                double ih2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < 1 || k >= N) return;
+  const double t0 = ((double)*d_step + 0.5) * ht, t1 = t0 + ht, idt = 1.0 / ht;
+  for (int side = 0; side < 2; ++side) {
+    const double sg = side ? -1.0 : 1.0;
+    {
+      const double gm = wall_sum_hx(s, nsrc, tab, N, side, k - 1, t0, t1, idt);
+      const double g0 = wall_sum_hx(s, nsrc, tab, N, side, k, t0, t1, idt);
+      const double gp = wall_sum_hx(s, nsrc, tab, N, side, k + 1, t0, t1, idt);
+      const double c = sg * ih2 * (g0 + (gm - 2.0 * g0 + gp) * (1.0 / 6.0));
+      Rx[(size_t)(side ? N - 1 : 0) * (N + 1) + k] -= c;
+    }
+    {
+      const double gm = wall_sum_hy(s, nsrc, tab, N, side, k - 1, t0, t1, idt);
+      const double g0 = wall_sum_hy(s, nsrc, tab, N, side, k, t0, t1, idt);
+      const double gp = wall_sum_hy(s, nsrc, tab, N, side, k + 1, t0, t1, idt);
+      const double c = sg * ih2 * (g0 + (gm - 2.0 * g0 + gp) * (1.0 / 6.0));
+      Ry[(size_t)k * N + (side ? N - 1 : 0)] -= c;
+    }
+  }
+}
+
 }  // namespace
 
-// Host tables: per source, sin(pi m i / N) (i = 0..N), sin(pi n j / N), cos(pi m (i + 1/2) / N)
-// (i = 0..N-1), cos(pi n (j + 1/2) / N), with the arguments reduced exactly in integers.
-int build_sources(ms_grid* g, const ms_source* src, int nsrc, std::vector<unsigned char>* dev_blob,
+// Host tables: per source, X(pi m i / N) (i = 0..N), Y(pi n j / N), X'/(pi m) at (i + 1/2) / N
+// (i = 0..N-1), Y'/(pi n) at (j + 1/2) / N, with the arguments reduced exactly in integers (so the
+// wall values are exact: sin 0, cos 0 = 1, cos(pi m) = (-1)^m).
+int build_sources(ms_grid* g, const SrcSpec* src, int nsrc, std::vector<unsigned char>* dev_blob,
                   std::vector<double>* tabs) {
   const int N = g->N;
   const double h = g->h, pi = M_PI;
   std::vector<SrcDev> sd(nsrc);
   tabs->assign((size_t)nsrc * 4 * (N + 1), 0.0);
-  auto sin_node = [&](int k, int i) {
+  auto at_node = [&](int p, int k, int i) {  // sin or cos of pi k i / N
+    const long q = ((long)k * i) % (2L * N);
+    if (p) return std::cos(pi * (double)q / N);
     if (i == 0 || i == N) return 0.0;
-    long q = ((long)k * i) % (2L * N);
     return std::sin(pi * (double)q / N);
   };
-  auto cos_half = [&](int k, int i) {
-    long q = ((long)k * (2L * i + 1)) % (4L * N);
-    return std::cos(pi * (double)q / (2.0 * N));
+  auto dunit_half = [&](int p, int k, int i) {  // d/dx of the profile at (i + 1/2) / N, over pi k
+    const long q = ((long)k * (2L * i + 1)) % (4L * N);
+    return p ? -std::sin(pi * (double)q / (2.0 * N)) : std::cos(pi * (double)q / (2.0 * N));
   };
   for (int q = 0; q < nsrc; ++q) {
     const int m = src[q].m, n = src[q].n;
     const double a = src[q].amp, w = src[q].omega;
+    const double pm2 = pi * pi * (double)m * m, pn2 = pi * pi * (double)n * n, h3 = h * h * h / 24.0;
     const double f = g->beta - (h * h / 12.0) * pi * pi * ((double)m * m + (double)n * n);
     sd[q].ce = -g->Z * (g->kappa2 - w * w) * f * a;
     sd[q].ch = f * a * w;
     sd[q].kx = pi * m;
     sd[q].ky = pi * n;
     sd[q].w = w;
+    sd[q].gy = a * (h + h3 * (pn2 - pm2 - w * w));
+    sd[q].gx = -a * (h + h3 * (pm2 - pn2 - w * w));
+    sd[q].ge = h * h / 12.0 * g->Z * a * w;
     double* tq = tabs->data() + (size_t)q * 4 * (N + 1);
-    for (int i = 0; i <= N; ++i) tq[i] = sin_node(m, i);
-    for (int j = 0; j <= N; ++j) tq[(N + 1) + j] = sin_node(n, j);
-    for (int i = 0; i < N; ++i) tq[2 * (N + 1) + i] = cos_half(m, i);
-    for (int j = 0; j < N; ++j) tq[3 * (N + 1) + j] = cos_half(n, j);
+    for (int i = 0; i <= N; ++i) tq[i] = at_node(src[q].px, m, i);
+    for (int j = 0; j <= N; ++j) tq[(N + 1) + j] = at_node(src[q].py, n, j);
+    for (int i = 0; i < N; ++i) tq[2 * (N + 1) + i] = dunit_half(src[q].px, m, i);
+    for (int j = 0; j < N; ++j) tq[3 * (N + 1) + j] = dunit_half(src[q].py, n, j);
   }
   dev_blob->resize(sd.size() * sizeof(SrcDev));
   std::memcpy(dev_blob->data(), sd.data(), dev_blob->size());
@@ -128,5 +239,18 @@ void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale) {
                                               g->ht, scale);
 }
 void launch_tick(ms_grid* g) { k_tick<<<1, 1, 0, g->stream>>>(g->d_step); }
+
+void launch_wall_hfilter64(ms_grid* g, double* Gx, double* Gy) {
+  k_wall_hfilter64<<<(g->N + 127) / 128, 128, 0, g->stream>>>(Gx, Gy, g->N, (const SrcDev*)g->d_src, g->nsrc,
+                                                              g->d_srctab, g->d_step, g->ht);
+}
+void launch_wall_ge64(ms_grid* g, double* GE) {
+  k_wall_ge64<<<(g->N + 1 + 127) / 128, 128, 0, g->stream>>>(GE, g->N, (const SrcDev*)g->d_src, g->nsrc, g->d_srctab,
+                                                              g->d_step, g->ht);
+}
+void launch_wall_hsolve64(ms_grid* g, double* Rx, double* Ry) {
+  k_wall_hsolve64<<<(g->N + 127) / 128, 128, 0, g->stream>>>(Rx, Ry, g->N, (const SrcDev*)g->d_src, g->nsrc,
+                                                             g->d_srctab, g->d_step, g->ht, 1.0 / (g->h * g->h));
+}
 
 }  // namespace ms

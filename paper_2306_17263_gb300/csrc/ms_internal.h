@@ -128,6 +128,7 @@ struct ms_grid {
 
   // current sources (k_src.cu): per-source constants, sine/cosine tables, device step index
   int nsrc = 0;
+  int src_wall = 0;  // some source has a cosine profile (nonzero on a wall)
   void* d_src = nullptr;
   double* d_srctab = nullptr;
   long* d_step = nullptr;

@@ -1,0 +1,122 @@
+"""Currents that do not vanish on the walls (Sec. 3.3, Method 2) on the GB300: FP64 parity with the
+oracle's step (ghost data of the H filter and the H solves, G_E on the walls), graph replay equal
+to single steps, fourth-order convergence to the manufactured solution through the C ABI, sine rows
+equal to the sine-mode entry point, and the argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2306_17263_gb300 as pkg  # noqa: E402
+
+A, W = 0.7, 3.0
+
+
+def _cat(fs):
+    return np.concatenate([np.ravel(a) for a in fs])
+
+
+def _rows(m, n, Z):
+    # the manufactured current plus a row that is nonzero on the walls y = 0, 1 only
+    return oracle.manufactured_sources(m, n, A, W, Z) + [(1, 0, 0.4, 4.5, 0, 1)]
+
+
+@pytest.mark.parametrize("n,steps,m,k", [(12, 3, 1, 1), (37, 20, 1, 2), (64, 9, 2, 1)])
+def test_fp64_wall_sources_match_oracle(n, steps, m, k):
+    r, Z = 0.5, 1.3
+    rows = _rows(m, k, Z)
+    init = workloads.random_fields(n, seed=1400 + n)
+    o = oracle.Oracle2D(n, r, Z=Z)
+    ref = [a.copy() for a in init]
+    for s in range(5, 5 + steps):
+        o.step_src_xy(*ref, rows, s)
+    with pkg.Grid(n, r, z=Z) as g:
+        g.set_sources_xy([(a, b, amp, w, px, py) for a, b, amp, w, px, py in rows])
+        g.set_fields(*init, step=5)
+        g.run(steps)
+        got = g.get_fields()
+    assert np.linalg.norm(_cat(got) - _cat(ref)) <= 1e-12 * np.linalg.norm(_cat(ref))
+
+
+def test_graph_replay_equals_single_steps():
+    n, steps, Z = 40, 23, 1.0
+    rows = _rows(1, 1, Z)
+    o = oracle.Oracle2D(n, 0.5, Z=Z)
+    init = o.exact_manufactured(1, 1, A, W, 0.0, 0.5 * o.ht)
+    outs = []
+    for mode in ("step", "run"):
+        with pkg.Grid(n, 0.5, z=Z) as g:
+            g.set_sources_xy(rows)
+            g.set_fields(*init, step=0)
+            if mode == "step":
+                for _ in range(steps):
+                    g.step()
+            else:
+                g.run(steps)
+            outs.append(g.get_fields())
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("m,k,Z", [(1, 1, 1.3), (1, 2, 1.0)])
+def test_fourth_order_convergence_to_the_manufactured_solution(m, k, Z):
+    T, errs = 0.5, []
+    rows = oracle.manufactured_sources(m, k, A, W, Z)
+    for n in (32, 64, 128):
+        o = oracle.Oracle2D(n, 0.5, Z=Z)
+        with pkg.Grid(n, 0.5, z=Z) as g:
+            g.set_sources_xy(rows)
+            g.set_fields(*o.exact_manufactured(m, k, A, W, 0.0, 0.5 * o.ht), step=0)
+            K = int(round(T / g.ht))
+            g.run(K)
+            got = g.get_fields()
+        ex = o.exact_manufactured(m, k, A, W, K * o.ht, (K + 0.5) * o.ht)
+        errs.append(np.linalg.norm(_cat(got) - _cat(ex)) / n)
+    rates = [math.log2(errs[j] / errs[j + 1]) for j in range(2)]
+    assert min(rates) > 3.7, (errs, rates)
+
+
+@pytest.mark.parametrize("prec", [pkg.FP64, pkg.FP32_REFINED])
+def test_sine_rows_equal_the_sine_mode_entry_point(prec):
+    src = [(2, 3, 1.0, 5.0), (1, 1, -0.5, 11.0)]
+    outs = []
+    for xy in (False, True):
+        with pkg.Grid(48, 0.5, z=1.3, precision=prec) as g:
+            if xy:
+                g.set_sources_xy([s + (0, 0) for s in src])
+            else:
+                g.set_sources(src)
+            g.init_driven(src)
+            g.run(11)
+            outs.append(g.get_fields())
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_argument_checks():
+    cos_row = [(2, 0, 1.0, 3.0, 1, 1)]
+    with pkg.Grid(16, 0.5, precision=pkg.FP32_REFINED) as g:
+        with pytest.raises(pkg.MaxwellError) as e:
+            g.set_sources_xy(cos_row)
+        assert e.value.status == -7
+    with pkg.Grid(16, 0.5, closure=pkg.CLOSURE_REFLECT) as g:
+        with pytest.raises(pkg.MaxwellError) as e:
+            g.set_sources_xy(cos_row)
+        assert e.value.status == -7
+    with pkg.Grid(16, 0.5) as g:
+        for bad in ([(0, 1, 1.0, 3.0, 0, 0)], [(1, 1, 1.0, 3.0, 2, 0)], [(-1, 1, 1.0, 3.0, 1, 0)],
+                    [(1, 1, float("nan"), 3.0, 1, 0)]):
+            with pytest.raises(pkg.MaxwellError) as e:
+                g.set_sources_xy(bad)
+            assert e.value.status == -1
+        g.set_sources_xy(cos_row)
+        g.set_sources_xy([])  # removes them
