@@ -287,6 +287,71 @@ def reverse_leg(pkg, torch):
             "memory": "no trajectory stored: the step is linear, the reverse pass needs only the final adjoint"}
 
 
+def _profiled_rate(pkg, torch, g, n, K, flush):
+    """Mean step time of K profiled steps (each kernel timed with CUDA events on the grid's stream,
+    launched one by one, L2 flushed between steps) and the share of the source kernels; then K steps
+    replayed from the captured graph (ms_run, as a user runs them), timed with CUDA events around the
+    replay (no flush inside it)."""
+    for _ in range(3):
+        g.step_profiled()
+    tot, src = 0.0, 0.0
+    for _ in range(K):
+        for kind, ms, _ in g.step_profiled():
+            tot += ms
+            if kind == "source":
+                src += ms
+        flush.zero_()
+    g.run(K)  # captures the graph
+    flush.zero_()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    g.run(K)
+    ev[1].record()
+    torch.cuda.synchronize()
+    graph_ms = ev[0].elapsed_time(ev[1]) / K
+    return {"steps": K, "ms_per_step": tot / K, "value": n * n / (tot / K * 1e-3), "unit": "cell-updates/s",
+            "source_kernel_share": src / tot, "graph_ms_per_step": graph_ms,
+            "graph_value": n * n / (graph_ms * 1e-3)}
+
+
+def variants_leg(pkg, torch, modes, r):
+    """The step variants: current sources (sine modes, both precisions, 2048^2), currents that do not
+    vanish on the walls (FP64, 1024^2, against the same FP64 step without sources) and the tracked-DE
+    step as printed in Sec. 3.4 (FP64, 1024^2)."""
+    import numpy as np
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    src = [(2, 3, 1.0, 5.0), (1, 1, -0.5, 11.0)]
+    out = {}
+    with pkg.Grid(2048, r, z=1.3, precision=pkg.FP32_REFINED, stream="torch") as g:
+        g.init_modes(modes)
+        out["plain_fp32_refined_2048"] = _profiled_rate(pkg, torch, g, 2048, 200, flush)
+    with pkg.Grid(2048, r, z=1.3, precision=pkg.FP32_REFINED, stream="torch") as g:
+        g.set_sources(src)
+        g.init_driven(src)
+        out["sources_fp32_refined_2048"] = _profiled_rate(pkg, torch, g, 2048, 200, flush)
+        out["sources_fp32_refined_2048"]["l2_rel_vs_driven"] = g.error_vs_driven(src)[1]
+    # a current that does not vanish on y = 0, 1 and is compatible at the corners:
+    # J_z = (1/(4w)) sin(w t) (w^2 + (4 pi^2 - w^2) cos 2 pi x + (4 pi^2 - w^2) cos 2 pi y
+    #                          + (w^2 - 8 pi^2) cos 2 pi x cos 2 pi y)
+    w, p2 = 3.0, math.pi ** 2
+    wall = [(0, 0, w / 4, w, 1, 1), (2, 0, (4 * p2 - w * w) / (4 * w), w, 1, 1),
+            (0, 2, (4 * p2 - w * w) / (4 * w), w, 1, 1), (2, 2, (w * w - 8 * p2) / (4 * w), w, 1, 1)]
+    for key, rows in (("plain_fp64_1024", None), ("wall_sources_fp64_1024", wall)):
+        with pkg.Grid(1024, r, precision=pkg.FP64, stream="torch") as g:
+            g.init_modes(modes)
+            if rows:
+                g.set_sources_xy(rows)
+            out[key] = _profiled_rate(pkg, torch, g, 1024, 50, flush)
+            out[key]["finite"] = bool(all(np.isfinite(a).all() for a in g.get_fields()))
+    with pkg.Grid(1024, r, precision=pkg.FP64, scheme=pkg.SCHEME_C4_DE, stream="torch") as g:
+        g.init_modes(modes)
+        out["tracked_de_fp64_1024"] = _profiled_rate(pkg, torch, g, 1024, 50, flush)
+        out["tracked_de_fp64_1024"]["l2_rel"] = g.error_vs_exact(modes)[1]
+    del flush
+    return out
+
+
 def leg_3d(pkg, torch, steps32=None, with_fp64=True):
     """3D six-component workload: 256^3 cells, r = 0.4, 500 steps, 2 seeded modes, FP32_REFINED
     (every step timed with CUDA events; the 6-component state, 0.8 GB, exceeds L2), plus 20 FP64
@@ -505,6 +570,7 @@ def run_ours(args, ws, rank, local):
         line["three_d"] = leg_3d(pkg, torch)
         line["error_vs_wavenumber"] = wavenumber_leg(pkg)
         line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, l2_abs, value)
+        line["variants"] = variants_leg(pkg, torch, modes, r)
         # CPU oracle on a bounded sample of the workload (rank 0, one core)
         v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
         line["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",

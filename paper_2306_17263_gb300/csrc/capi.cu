@@ -131,7 +131,7 @@ void h_increment64(ms_grid* g, const double* ez, double* hxs, double* hys, doubl
   }
   curl_eh64(g, GE, Rx, Ry, nl);
   if (with_sources && g->nsrc) {
-    launch_src_h64(g, Rx, Ry, 1.0);
+    launch_src_h64(g, Rx, Ry);
     prof_mark(g, KK_SRC, 8.0 * 2.0 * (double)g->sh[HX].size());
     *nl += 1;
   }
@@ -211,9 +211,11 @@ ms_status step64(ms_grid* g) {
   }
   curl_he64(g, Gx, Gy, R, &nl);
   if (g->nsrc) {
-    launch_src_e64(g, R, 1.0);
+    launch_src_time(g, 1.0, 1.0);
+    prof_mark(g, KK_SRC, 0.0);
+    launch_src_e64(g, R);
     prof_mark(g, KK_SRC, 16.0 * (double)g->sh[EZ].size());
-    nl += 1;
+    nl += 2;
   }
   // the solve's result lands in s64[5]; the last sweep also performs E += h_tau E*
   p1_solve64(g, EZ, R, g->s64[5], ez, g->ht, &nl);
@@ -580,6 +582,10 @@ ms_status ms_destroy(ms_grid* g) {
   cudaFree(g->de64);
   cudaFree(g->d_src);
   cudaFree(g->d_srctab);
+  cudaFree(g->d_srctab32);
+  cudaFree(g->d_srcfac);
+  cudaFree(g->d_walldata);
+  cudaFree(g->d_wresp);
   cudaFree(g->d_step);
   for (int k = 0; k < 6 && !g->shared64; ++k) cudaFree(g->s64[k]);
   for (int k = 0; k < 8; ++k) cudaFree(g->s32[k]);
@@ -866,8 +872,16 @@ static ms_status set_sources_spec(ms_grid* g, const SrcSpec* src, int nsrc) {
   MS_CUDA(cudaStreamSynchronize(g->stream));
   cudaFree(g->d_src);
   cudaFree(g->d_srctab);
+  cudaFree(g->d_srctab32);
+  cudaFree(g->d_srcfac);
+  cudaFree(g->d_walldata);
+  cudaFree(g->d_wresp);
   g->d_src = nullptr;
   g->d_srctab = nullptr;
+  g->d_srctab32 = nullptr;
+  g->d_srcfac = nullptr;
+  g->d_walldata = nullptr;
+  g->d_wresp = nullptr;
   g->nsrc = 0;
   g->src_wall = 0;
   free_graph(&g->graph1);  // the captured steps do not contain the source launches
@@ -879,12 +893,23 @@ static ms_status set_sources_spec(ms_grid* g, const SrcSpec* src, int nsrc) {
   build_sources(g, src, nsrc, &blob, &tabs);
   MS_TRY(dalloc((unsigned char**)&g->d_src, blob.size()));
   MS_TRY(dalloc(&g->d_srctab, tabs.size()));
+  MS_TRY(dalloc(&g->d_srctab32, tabs.size()));
+  MS_TRY(dalloc((unsigned char**)&g->d_srcfac, src_factor_bytes()));
   if (!g->d_step) MS_TRY(dalloc(&g->d_step, 1));
   MS_CUDA(cudaMemcpy(g->d_src, blob.data(), blob.size(), cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(g->d_srctab, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<float> tabs32(tabs.begin(), tabs.end());
+  MS_CUDA(cudaMemcpy(g->d_srctab32, tabs32.data(), tabs32.size() * sizeof(float), cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice));
   g->nsrc = nsrc;
   for (int q = 0; q < nsrc; ++q) g->src_wall |= (src[q].px | src[q].py);
+  if (g->src_wall && g->desc.precision == MS_FP32_REFINED) {  // wall terms of the FP32 source kernels
+    std::vector<float> wr;
+    wall_responses(g->N, &wr);
+    MS_TRY(dalloc(&g->d_walldata, wall_data_doubles(g->N)));
+    MS_TRY(dalloc(&g->d_wresp, wr.size()));
+    MS_CUDA(cudaMemcpy(g->d_wresp, wr.data(), wr.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   return MS_OK;
 }
 
@@ -916,8 +941,8 @@ ms_status ms_set_sources_xy(ms_grid* g, const ms_source_xy* src, int nsrc) {
     wall |= (r.cos_x || r.cos_y);
     sp[q] = SrcSpec{r.m, r.n, r.cos_x, r.cos_y, r.amp, r.omega};
   }
-  if (wall && (g->desc.precision != MS_FP64 || g->desc.closure != MS_CLOSURE_PAPER))
-    return fail(MS_EUNSUPPORTED, "sources that do not vanish on the walls need an FP64 grid with the PAPER closure");
+  if (wall && g->desc.closure != MS_CLOSURE_PAPER)
+    return fail(MS_EUNSUPPORTED, "sources that do not vanish on the walls need the PAPER closure");
   return set_sources_spec(g, sp.data(), nsrc);
 }
 

@@ -46,10 +46,19 @@ struct SrcSpec {
 };
 int build_sources(ms_grid* g, const SrcSpec* src, int nsrc, std::vector<unsigned char>* dev_blob,
                   std::vector<double>* tabs);
-void launch_src_e64(ms_grid* g, double* R, double scale);
-void launch_src_h64(ms_grid* g, double* Rx, double* Ry, double scale);
-void launch_src_e32(ms_grid* g, float* R, double scale);
-void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale);
+// The time factors of a step (first source launch of the step; FP32 factors in the units of the tile
+// solve, scale_e for E and scale_h for H), then the point kernels that read them.
+size_t src_factor_bytes();
+void launch_src_time(ms_grid* g, double scale_e, double scale_h);
+void launch_src_e64(ms_grid* g, double* R);
+void launch_src_h64(ms_grid* g, double* Rx, double* Ry);
+void launch_src_e32(ms_grid* g, float* R, double scale_e);
+void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale_h);
+// FP32 wall terms: the wall data of a step (launched after launch_src_time) and, on the host, the
+// Pade responses to the end values of a line.
+void launch_wall_data(ms_grid* g);
+size_t wall_data_doubles(int N);
+void wall_responses(int N, std::vector<float>* wr);
 void launch_tick(ms_grid* g);
 // Boundary data of sources that do not vanish on the walls (FP64 step): the H-filter ghosts of
 // Step 1, G_E on the boundary nodes, and the ghost part of P1 in the H right-hand sides of Step 2.

@@ -78,7 +78,15 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   prof_mark(g, KK_CURL32, 4.0 * (4.0 * nh + ne));            // H_x, H_y (hi, lo) in; b out
   // sources in the units of b: 6 h^2 P1 x = b with E += (12 Z / r) x, so b = (h^3 r^2 / (2 Z)) R
   const double hr2 = g->h * g->h * g->h * g->desc.r * g->desc.r;
-  if (g->nsrc) {
+  if (g->nsrc) {  // H += (12 / (r Z)) x, so b = (h^3 r^2 Z / 2) R on the H side
+    launch_src_time(g, hr2 / (2.0 * g->Z), hr2 * g->Z / 2.0);
+    prof_mark(g, KK_SRC, 0.0);
+    *nl += 1;
+    if (g->d_walldata) {
+      launch_wall_data(g);
+      prof_mark(g, KK_SRC, 8.0 * 12.0 * N1);
+      *nl += 1;
+    }
     launch_src_e32(g, bE, hr2 / (2.0 * g->Z));
     prof_mark(g, KK_SRC, 8.0 * ne);
     *nl += 1;
@@ -92,7 +100,7 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   float* by = g->s32[3];
   tiled_curl(g, 1, k.cb_hi, k.cb_lo, bx, by);
   prof_mark(g, KK_CURL32, 4.0 * (2.0 * ne + 2.0 * nh));      // E (hi, lo) in; b_x, b_y out
-  if (g->nsrc) {  // H += (12 / (r Z)) x, so b = (h^3 r^2 Z / 2) R
+  if (g->nsrc) {
     launch_src_h32(g, bx, by, hr2 * g->Z / 2.0);
     prof_mark(g, KK_SRC, 16.0 * nh);
     *nl += 1;

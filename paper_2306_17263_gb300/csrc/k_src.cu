@@ -34,48 +34,156 @@ struct SrcDev {
   double ce, ch, kx, ky, w, gy, gx, ge;
 };
 
-// R (+)= scale * sum_q ce_q sin(w_q t) X_q(i) Y_q(j) at the interior E_z nodes, t = (n + 1/2) h_tau.
+// The time factors are the same at every point: a one-block kernel at the start of each step
+// forms them (k_src_time), and the point kernels read them.  FP64: v = sum_q (ce_q sin(w_q t))
+// X_q(i) Y_q(j), the product taken in the order of the plain definition.  FP32 (right-hand sides of
+// the tile solve): the factors are scaled to the tile's units and rounded to float, and the sum is
+// taken in float from the float copy of the tables.
+constexpr int kMaxSrc = 64;
+struct SrcFac {
+  double e[kMaxSrc], hx[kMaxSrc], hy[kMaxSrc];
+  float e32[kMaxSrc], hx32[kMaxSrc], hy32[kMaxSrc];
+};
+
+// e_q = ce_q sin(w_q t_E), t_E = (n + 1/2) h_tau;  hx_q = ch_q cos(w_q t_H) ky_q, hy_q = ch_q cos(w_q t_H) kx_q,
+// t_H = (n + 1) h_tau; the float copies scaled by scale_e and scale_h.
+__global__ void k_src_time(const SrcDev* __restrict__ s, int nsrc, const long* __restrict__ d_step, double ht,
+                           double scale_e, double scale_h, SrcFac* __restrict__ fac) {
+  const int q = threadIdx.x;
+  if (q >= nsrc) return;
+  const double te = ((double)*d_step + 0.5) * ht, th = ((double)*d_step + 1.0) * ht;
+  const double fe = s[q].ce * sin(s[q].w * te);
+  const double c = s[q].ch * cos(s[q].w * th);
+  const double fx = c * s[q].ky, fy = c * s[q].kx;
+  fac->e[q] = fe;
+  fac->hx[q] = fx;
+  fac->hy[q] = fy;
+  fac->e32[q] = (float)(scale_e * fe);
+  fac->hx32[q] = (float)(scale_h * fx);
+  fac->hy32[q] = (float)(scale_h * fy);
+}
+
+// Wall data of one step (k_wall_data), 12 arrays of N + 1: the ghost data of H at t^{n+1/2}
+// (H_y on x = 0, 1 by row; H_x on y = 0, 1 by column), G_E on the walls at t^{n+1} (x = 0, x = 1 by
+// row; y = 0, y = 1 by column), and the ghost data of H* on the four walls.
+enum { WD_GY_LO, WD_GY_HI, WD_GX_LO, WD_GX_HI, WD_V_X0, WD_V_X1, WD_V_Y0, WD_V_Y1,
+       WD_SY_LO, WD_SY_HI, WD_SX_LO, WD_SX_HI, WD_COUNT };
+// Pade responses to one end value (float, zero beyond kWallReach outputs from that end):
+// half-node lines (N inputs, N - 1 outputs) to input 0 and to input N - 1, node lines (N + 1 inputs,
+// N outputs) to input 0 and to input N.
+constexpr int kWallReach = 64;
+struct WallView {
+  const double* wd;  // nullptr: no wall terms
+  const float* hn0;
+  const float* hn1;
+  const float* nh0;
+  const float* nh1;
+};
+__host__ __device__ inline WallView wall_view(const double* wd, const float* wr, int N) {
+  return WallView{wd, wr, wr + (N - 1), wr + 2 * (N - 1), wr + 2 * (N - 1) + N};
+}
+
+// R += sum_q e_q X_q(i) Y_q(j) at the interior E_z nodes.  FP32 with wall data: plus, in the units of
+// R scaled by cE / (kappa^2 Z / h), the Pade responses to the filter's ghost terms of Step 1,
+//   kappa^2 Z / h (W_{i-1,0} (-g^y_lo(j) / 12) + W_{i-1,N-1} g^y_hi(j) / 12
+//                  - W_{j-1,0} (-g^x_lo(i) / 12) - W_{j-1,N-1} g^x_hi(i) / 12)   (W = A^{-1} D1 per line).
 template <typename T>
-__global__ void k_src_e(T* __restrict__ R, int N, const SrcDev* __restrict__ s, int nsrc, const double* __restrict__ tab,
-                        const long* __restrict__ d_step, double ht, double scale) {
+__global__ void k_src_e(T* __restrict__ R, int N, int nsrc, const double* __restrict__ tab,
+                        const float* __restrict__ tab32, const SrcFac* __restrict__ fac, WallView wv, float cE) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i < 1 || j < 1 || i >= N || j >= N) return;
-  const double t = ((double)*d_step + 0.5) * ht;
   const size_t per = 4 * (size_t)(N + 1);  // per-source table block: X, Y at nodes, X', Y' at half-nodes
-  double v = 0.0;
-  for (int q = 0; q < nsrc; ++q) {
-    const double* tq = tab + q * per;
-    v += s[q].ce * sin(s[q].w * t) * tq[i] * tq[(N + 1) + j];
+  if constexpr (sizeof(T) == 8) {
+    double v = 0.0;
+    for (int q = 0; q < nsrc; ++q) {
+      const double* tq = tab + q * per;
+      v += fac->e[q] * tq[i] * tq[(N + 1) + j];
+    }
+    R[(size_t)j * (N + 1) + i] += v;
+  } else {
+    float v = 0.0f;
+    for (int q = 0; q < nsrc; ++q) {
+      const float* tq = tab32 + q * per;
+      v = fmaf(fac->e32[q] * tq[i], tq[(N + 1) + j], v);
+    }
+    const int M = N - 1;
+    if (wv.wd && (i - 1 < kWallReach || i - 1 >= M - kWallReach || j - 1 < kWallReach || j - 1 >= M - kWallReach)) {
+      const double* wd = wv.wd;
+      const size_t L = N + 1;
+      const float ax = wv.hn0[i - 1] * (float)(-wd[WD_GY_LO * L + j]) + wv.hn1[i - 1] * (float)wd[WD_GY_HI * L + j];
+      const float ay = wv.hn0[j - 1] * (float)(-wd[WD_GX_LO * L + i]) + wv.hn1[j - 1] * (float)wd[WD_GX_HI * L + i];
+      v = fmaf(cE * (1.0f / 12.0f), ax - ay, v);
+    }
+    R[(size_t)j * (N + 1) + i] += v;
   }
-  R[(size_t)j * (N + 1) + i] += (T)(scale * v);
 }
 
-// R_x += scale sum ch_q cos(w_q t) ky_q X_q(i) Y'_q(j)/ky_q;  R_y -= scale sum ch_q cos(w_q t) kx_q X'_q(i)/kx_q Y_q(j),
-// t = (n + 1) h_tau.
+// Ghost part of P1 next to a wall with data g (zero at the Dirichlet end points k = 0, N):
+// g_k / h^2 + (g_{k-1} - 2 g_k + g_{k+1}) / (6 h^2), in units of h^2.
+__device__ __forceinline__ double ghost_p1(const double* g, int k) {
+  return g[k] + (g[k - 1] - 2.0 * g[k] + g[k + 1]) * (1.0 / 6.0);
+}
+
+// R_x += sum_q hx_q X_q(i) Y'_q(j)/ky_q;  R_y -= sum_q hy_q X'_q(i)/kx_q Y_q(j).  FP32 with wall data:
+// plus the Pade responses to G_E on the walls, -cH (W_{j,0} v(i, 0) + W_{j,N} v(i, N)) on R_x and
+// +cH (W_{i,0} v(0, j) + W_{i,N} v(N, j)) on R_y (cH = scale kappa^2 / (Z h)), minus the ghost part of
+// P1 with the data of H* next to the walls (times sP = scale / h^2).
 template <typename T>
-__global__ void k_src_h(T* __restrict__ Rx, T* __restrict__ Ry, int N, const SrcDev* __restrict__ s, int nsrc,
-                        const double* __restrict__ tab, const long* __restrict__ d_step, double ht, double scale) {
+__global__ void k_src_h(T* __restrict__ Rx, T* __restrict__ Ry, int N, int nsrc, const double* __restrict__ tab,
+                        const float* __restrict__ tab32, const SrcFac* __restrict__ fac, WallView wv, float cH,
+                        double sP) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > N || j > N) return;
-  const double t = ((double)*d_step + 1.0) * ht;
   const size_t per = 4 * (size_t)(N + 1);
   if (j < N && i >= 1 && i < N) {
-    double v = 0.0;
-    for (int q = 0; q < nsrc; ++q) {
-      const double* tq = tab + q * per;
-      v += s[q].ch * cos(s[q].w * t) * s[q].ky * tq[i] * tq[3 * (N + 1) + j];
+    if constexpr (sizeof(T) == 8) {
+      double v = 0.0;
+      for (int q = 0; q < nsrc; ++q) {
+        const double* tq = tab + q * per;
+        v += fac->hx[q] * tq[i] * tq[3 * (N + 1) + j];
+      }
+      Rx[(size_t)j * (N + 1) + i] += v;
+    } else {
+      float v = 0.0f;
+      for (int q = 0; q < nsrc; ++q) {
+        const float* tq = tab32 + q * per;
+        v = fmaf(fac->hx32[q] * tq[i], tq[3 * (N + 1) + j], v);
+      }
+      if (wv.wd && (j < kWallReach || j >= N - kWallReach)) {
+        const double* wd = wv.wd;
+        const size_t L = N + 1;
+        v = fmaf(-cH, wv.nh0[j] * (float)wd[WD_V_Y0 * L + i] + wv.nh1[j] * (float)wd[WD_V_Y1 * L + i], v);
+        if (j == 0) v -= (float)(sP * ghost_p1(wd + WD_SX_LO * L, i));
+        if (j == N - 1) v += (float)(sP * ghost_p1(wd + WD_SX_HI * L, i));
+      }
+      Rx[(size_t)j * (N + 1) + i] += v;
     }
-    Rx[(size_t)j * (N + 1) + i] += (T)(scale * v);
   }
   if (i < N && j >= 1 && j < N) {
-    double v = 0.0;
-    for (int q = 0; q < nsrc; ++q) {
-      const double* tq = tab + q * per;
-      v += s[q].ch * cos(s[q].w * t) * s[q].kx * tq[2 * (N + 1) + i] * tq[(N + 1) + j];
+    if constexpr (sizeof(T) == 8) {
+      double v = 0.0;
+      for (int q = 0; q < nsrc; ++q) {
+        const double* tq = tab + q * per;
+        v += fac->hy[q] * tq[2 * (N + 1) + i] * tq[(N + 1) + j];
+      }
+      Ry[(size_t)j * N + i] -= v;
+    } else {
+      float v = 0.0f;
+      for (int q = 0; q < nsrc; ++q) {
+        const float* tq = tab32 + q * per;
+        v = fmaf(fac->hy32[q] * tq[2 * (N + 1) + i], tq[(N + 1) + j], v);
+      }
+      if (wv.wd && (i < kWallReach || i >= N - kWallReach)) {
+        const double* wd = wv.wd;
+        const size_t L = N + 1;
+        v = fmaf(-cH, wv.nh0[i] * (float)wd[WD_V_X0 * L + j] + wv.nh1[i] * (float)wd[WD_V_X1 * L + j], v);
+        if (i == 0) v += (float)(sP * ghost_p1(wd + WD_SY_LO * L, j));
+        if (i == N - 1) v -= (float)(sP * ghost_p1(wd + WD_SY_HI * L, j));
+      }
+      Ry[(size_t)j * N + i] -= v;
     }
-    Ry[(size_t)j * N + i] -= (T)(scale * v);
   }
 }
 
@@ -108,6 +216,36 @@ __device__ __forceinline__ double wall_sum_hx(const SrcDev* s, int nsrc, const d
     v += s[q].gx * T * tq[i] * tq[(N + 1) + (side ? N : 0)];
   }
   return v;
+}
+
+// The wall data of a step for the FP32 source kernels (layout WD_*); thread k = 0..N.
+__global__ void k_wall_data(double* __restrict__ wd, int N, const SrcDev* __restrict__ s, int nsrc,
+                            const double* __restrict__ tab, const long* __restrict__ d_step, double ht) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N) return;
+  const size_t L = N + 1, per = 4 * L;
+  const double th = ((double)*d_step + 0.5) * ht, t1 = th + 0.5 * ht, t32 = th + ht, idt = 1.0 / ht;
+  wd[WD_GY_LO * L + k] = wall_sum_hy(s, nsrc, tab, N, 0, k, th, th, 0.0);
+  wd[WD_GY_HI * L + k] = wall_sum_hy(s, nsrc, tab, N, 1, k, th, th, 0.0);
+  wd[WD_GX_LO * L + k] = wall_sum_hx(s, nsrc, tab, N, 0, k, th, th, 0.0);
+  wd[WD_GX_HI * L + k] = wall_sum_hx(s, nsrc, tab, N, 1, k, th, th, 0.0);
+  wd[WD_SY_LO * L + k] = wall_sum_hy(s, nsrc, tab, N, 0, k, th, t32, idt);
+  wd[WD_SY_HI * L + k] = wall_sum_hy(s, nsrc, tab, N, 1, k, th, t32, idt);
+  wd[WD_SX_LO * L + k] = wall_sum_hx(s, nsrc, tab, N, 0, k, th, t32, idt);
+  wd[WD_SX_HI * L + k] = wall_sum_hx(s, nsrc, tab, N, 1, k, th, t32, idt);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};  // G_E at (0, k), (N, k), (k, 0), (k, N)
+  for (int q = 0; q < nsrc; ++q) {
+    const double* tq = tab + q * per;
+    const double c = s[q].ge * cos(s[q].w * t1);
+    v[0] += c * tq[0] * tq[L + k];
+    v[1] += c * tq[N] * tq[L + k];
+    v[2] += c * tq[k] * tq[L];
+    v[3] += c * tq[k] * tq[L + N];
+  }
+  wd[WD_V_X0 * L + k] = v[0];
+  wd[WD_V_X1 * L + k] = v[1];
+  wd[WD_V_Y0 * L + k] = v[2];
+  wd[WD_V_Y1 * L + k] = v[3];
 }
 
 // Step 1: the ghosts of H^{n+1/2} in the filter, G -= g_lo / 12 next to the low wall and
@@ -218,25 +356,58 @@ int build_sources(ms_grid* g, const SrcSpec* src, int nsrc, std::vector<unsigned
   return (int)sizeof(SrcDev);
 }
 
-void launch_src_e64(ms_grid* g, double* R, double scale) {
-  dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
-  k_src_e<double><<<grd, blk, 0, g->stream>>>(R, g->N, (const SrcDev*)g->d_src, g->nsrc, g->d_srctab, g->d_step,
-                                               g->ht, scale);
+size_t src_factor_bytes() { return sizeof(SrcFac); }
+
+void launch_src_time(ms_grid* g, double scale_e, double scale_h) {
+  k_src_time<<<1, kMaxSrc, 0, g->stream>>>((const SrcDev*)g->d_src, g->nsrc, g->d_step, g->ht, scale_e, scale_h,
+                                           (SrcFac*)g->d_srcfac);
 }
-void launch_src_h64(ms_grid* g, double* Rx, double* Ry, double scale) {
+void launch_src_e64(ms_grid* g, double* R) {
   dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
-  k_src_h<double><<<grd, blk, 0, g->stream>>>(Rx, Ry, g->N, (const SrcDev*)g->d_src, g->nsrc, g->d_srctab, g->d_step,
-                                               g->ht, scale);
+  k_src_e<double><<<grd, blk, 0, g->stream>>>(R, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
+                                               (const SrcFac*)g->d_srcfac, WallView{}, 0.0f);
 }
-void launch_src_e32(ms_grid* g, float* R, double scale) {
+void launch_src_h64(ms_grid* g, double* Rx, double* Ry) {
   dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
-  k_src_e<float><<<grd, blk, 0, g->stream>>>(R, g->N, (const SrcDev*)g->d_src, g->nsrc, g->d_srctab, g->d_step, g->ht,
-                                              scale);
+  k_src_h<double><<<grd, blk, 0, g->stream>>>(Rx, Ry, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
+                                               (const SrcFac*)g->d_srcfac, WallView{}, 0.0f, 0.0);
 }
-void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale) {
+void launch_src_e32(ms_grid* g, float* R, double scale_e) {
   dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
-  k_src_h<float><<<grd, blk, 0, g->stream>>>(Rx, Ry, g->N, (const SrcDev*)g->d_src, g->nsrc, g->d_srctab, g->d_step,
-                                              g->ht, scale);
+  const WallView wv = g->d_walldata ? wall_view(g->d_walldata, g->d_wresp, g->N) : WallView{};
+  const float cE = (float)(scale_e * g->kappa2 * g->Z / g->h);
+  k_src_e<float><<<grd, blk, 0, g->stream>>>(R, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
+                                              (const SrcFac*)g->d_srcfac, wv, cE);
+}
+void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale_h) {
+  dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
+  const WallView wv = g->d_walldata ? wall_view(g->d_walldata, g->d_wresp, g->N) : WallView{};
+  const float cH = (float)(scale_h * g->kappa2 / (g->Z * g->h));
+  k_src_h<float><<<grd, blk, 0, g->stream>>>(Rx, Ry, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
+                                              (const SrcFac*)g->d_srcfac, wv, cH, scale_h / (g->h * g->h));
+}
+void launch_wall_data(ms_grid* g) {
+  k_wall_data<<<(g->N + 1 + 127) / 128, 128, 0, g->stream>>>(g->d_walldata, g->N, (const SrcDev*)g->d_src, g->nsrc,
+                                                             g->d_srctab, g->d_step, g->ht);
+}
+size_t wall_data_doubles(int N) { return (size_t)WD_COUNT * (N + 1); }
+
+// Pade responses for the FP32 wall terms (PAPER closure): rows of W = A^{-1} D1 within kWallReach of
+// either end, the entries of their first and last inputs.
+void wall_responses(int N, std::vector<float>* wr) {
+  wr->assign((size_t)2 * (N - 1) + 2 * N, 0.0f);
+  std::vector<double> row;
+  for (int kind = 0; kind < 2; ++kind) {
+    const int M = kind == HALF_TO_NODE ? N - 1 : N;
+    float* c0 = wr->data() + (kind == HALF_TO_NODE ? 0 : 2 * (N - 1));
+    float* c1 = c0 + M;
+    for (int i = 0; i < M; ++i) {
+      if (i >= kWallReach && i < M - kWallReach) continue;
+      pade_dense_row(M, MS_CLOSURE_PAPER, kind, i, &row);
+      c0[i] = (float)row[0];
+      c1[i] = (float)row[M];
+    }
+  }
 }
 void launch_tick(ms_grid* g) { k_tick<<<1, 1, 0, g->stream>>>(g->d_step); }
 

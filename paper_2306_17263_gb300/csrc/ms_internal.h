@@ -131,6 +131,10 @@ struct ms_grid {
   int src_wall = 0;  // some source has a cosine profile (nonzero on a wall)
   void* d_src = nullptr;
   double* d_srctab = nullptr;
+  float* d_srctab32 = nullptr;  // float copy of the tables (FP32_REFINED right-hand sides)
+  void* d_srcfac = nullptr;     // time factors of the current step (k_src_time)
+  double* d_walldata = nullptr;  // FP32 wall terms: wall data of the current step (k_wall_data)
+  float* d_wresp = nullptr;      // FP32 wall terms: Pade responses to the end values of a line
   long* d_step = nullptr;
 
   // 3D grids (desc.dim == 3): components, scratch and kernels live in grid3d.cu

@@ -1,7 +1,8 @@
 """Currents that do not vanish on the walls (Sec. 3.3, Method 2) on the GB300: FP64 parity with the
 oracle's step (ghost data of the H filter and the H solves, G_E on the walls), graph replay equal
-to single steps, fourth-order convergence to the manufactured solution through the C ABI, sine rows
-equal to the sine-mode entry point, and the argument checks."""
+to single steps, fourth-order convergence to the manufactured solution through the C ABI, the
+FP32_REFINED path within the discretisation error of the FP64 one, sine rows equal to the sine-mode
+entry point, and the argument checks."""
 import math
 
 import numpy as np
@@ -47,14 +48,15 @@ def test_fp64_wall_sources_match_oracle(n, steps, m, k):
     assert np.linalg.norm(_cat(got) - _cat(ref)) <= 1e-12 * np.linalg.norm(_cat(ref))
 
 
-def test_graph_replay_equals_single_steps():
+@pytest.mark.parametrize("prec", [pkg.FP64, pkg.FP32_REFINED])
+def test_graph_replay_equals_single_steps(prec):
     n, steps, Z = 40, 23, 1.0
     rows = _rows(1, 1, Z)
     o = oracle.Oracle2D(n, 0.5, Z=Z)
     init = o.exact_manufactured(1, 1, A, W, 0.0, 0.5 * o.ht)
     outs = []
     for mode in ("step", "run"):
-        with pkg.Grid(n, 0.5, z=Z) as g:
+        with pkg.Grid(n, 0.5, z=Z, precision=prec) as g:
             g.set_sources_xy(rows)
             g.set_fields(*init, step=0)
             if mode == "step":
@@ -68,21 +70,30 @@ def test_graph_replay_equals_single_steps():
 
 
 @pytest.mark.parametrize("m,k,Z", [(1, 1, 1.3), (1, 2, 1.0)])
-def test_fourth_order_convergence_to_the_manufactured_solution(m, k, Z):
-    T, errs = 0.5, []
+def test_convergence_and_fp32_within_discretisation_error(m, k, Z):
+    T, errs = 0.5, {pkg.FP64: [], pkg.FP32_REFINED: []}
     rows = oracle.manufactured_sources(m, k, A, W, Z)
     for n in (32, 64, 128):
         o = oracle.Oracle2D(n, 0.5, Z=Z)
-        with pkg.Grid(n, 0.5, z=Z) as g:
-            g.set_sources_xy(rows)
-            g.set_fields(*o.exact_manufactured(m, k, A, W, 0.0, 0.5 * o.ht), step=0)
-            K = int(round(T / g.ht))
-            g.run(K)
-            got = g.get_fields()
+        res = {}
+        for prec in (pkg.FP64, pkg.FP32_REFINED):
+            with pkg.Grid(n, 0.5, z=Z, precision=prec) as g:
+                g.set_sources_xy(rows)
+                g.set_fields(*o.exact_manufactured(m, k, A, W, 0.0, 0.5 * o.ht), step=0)
+                K = int(round(T / g.ht))
+                g.run(K)
+                res[prec] = g.get_fields()
         ex = o.exact_manufactured(m, k, A, W, K * o.ht, (K + 0.5) * o.ht)
-        errs.append(np.linalg.norm(_cat(got) - _cat(ex)) / n)
-    rates = [math.log2(errs[j] / errs[j + 1]) for j in range(2)]
-    assert min(rates) > 3.7, (errs, rates)
+        for prec in res:
+            errs[prec].append(np.linalg.norm(_cat(res[prec]) - _cat(ex)) / n)
+        e64, e32 = errs[pkg.FP64][-1], errs[pkg.FP32_REFINED][-1]
+        assert e32 <= 2 * e64, (n, e32, e64)
+        assert np.linalg.norm(_cat(res[pkg.FP32_REFINED]) - _cat(res[pkg.FP64])) / n <= e64
+    # the order is that of the scheme (FP64); FP32_REFINED is held to the discretisation error above,
+    # since it reaches its rounding floor near n = 128
+    e = errs[pkg.FP64]
+    rates = [math.log2(e[j] / e[j + 1]) for j in range(2)]
+    assert min(rates) > 3.7, (e, rates)
 
 
 @pytest.mark.parametrize("prec", [pkg.FP64, pkg.FP32_REFINED])
@@ -104,7 +115,7 @@ def test_sine_rows_equal_the_sine_mode_entry_point(prec):
 
 def test_argument_checks():
     cos_row = [(2, 0, 1.0, 3.0, 1, 1)]
-    with pkg.Grid(16, 0.5, precision=pkg.FP32_REFINED) as g:
+    with pkg.Grid(16, 0.5, closure=pkg.CLOSURE_REFLECT, precision=pkg.FP32_REFINED) as g:
         with pytest.raises(pkg.MaxwellError) as e:
             g.set_sources_xy(cos_row)
         assert e.value.status == -7
