@@ -295,10 +295,10 @@ ms_status ms_error_vs_driven(ms_grid* g, const ms_source* src, int nsrc, double*
  * (Delta E_z = Z d_t J_z on a PEC wall).  The data must be compatible at the corners (J_z = 0 there,
  * since H.n = 0 on both walls); ghost values at the corner points are not used.
  * ms_set_sources_xy: replaces the grid's sources like ms_set_sources (rows with cos_x = cos_y = 0 are
- *   exactly ms_set_sources rows).  Rows with a cosine profile need an FP64 grid with
- *   MS_CLOSURE_PAPER (the REFLECT rows assume even data at the walls): MS_EUNSUPPORTED otherwise;
- *   MS_EINVAL for an index below its minimum or a flag other than 0 / 1.  Initial data come from
- *   ms_set_fields. */
+ *   exactly ms_set_sources rows).  Rows with a cosine profile need MS_CLOSURE_PAPER (the REFLECT
+ *   rows assume even data at the walls): MS_EUNSUPPORTED otherwise; both precisions (FP32_REFINED
+ *   adds the wall terms to its right-hand sides as their Pade responses); MS_EINVAL for an index
+ *   below its minimum or a flag other than 0 / 1.  Initial data come from ms_set_fields. */
 typedef struct {
   int m, n;
   int cos_x, cos_y;

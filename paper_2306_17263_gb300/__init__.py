@@ -355,8 +355,8 @@ class Grid:
 
     def set_sources_xy(self, src):
         """Rows (m, n, amp, omega, cos_x, cos_y): J_z = amp X(pi m x) Y(pi n y) sin(omega t) with X = sin
-        (cos_x = 0) or cos (cos_x = 1), Y likewise; cosine profiles need an FP64 grid with the PAPER
-        closure (maxwell4.h, ms_set_sources_xy)."""
+        (cos_x = 0) or cos (cos_x = 1), Y likewise; cosine profiles need the PAPER closure
+        (maxwell4.h, ms_set_sources_xy)."""
         arr, ns = _sources_xy(src)
         _check(load().ms_set_sources_xy(self._h, arr, ns))
 

@@ -9,7 +9,7 @@
 //
 // Sine profiles vanish on the walls with every derivative the Neumann data of Sec. 3.3 use, so the
 // even ghosts stay exact.  A cosine profile does not, and three boundary data of the step change
-// (FP64 path; Method 2 of Sec. 3.3, the wall data from Ampere's law on the PEC walls):
+// (Method 2 of Sec. 3.3, the wall data from Ampere's law on the PEC walls):
 //   - the ghosts half a cell beyond a Neumann wall: u(-1) = u(0) - g_lo, u(n) = u(n-1) + g_hi with
 //     g = h d_n u + (h^3/24) d_nnn u on the wall, where on x = 0, 1 (H_y)
 //       d_x H_y = J_z,   d_xxx H_y = (d_tt + d_xx - d_yy) J_z,
@@ -18,6 +18,9 @@
 //     next to the wall; in the H solves of Step 2 (data of H* = (H^{n+3/2} - H^{n+1/2}) / h_tau)
 //     the right-hand side loses P1 applied to the ghosts alone, which is nonzero next to the wall;
 //   - G_E on the boundary nodes is (h^2/12) Delta E_z = (h^2/12) Z d_t J_z at t^{n+1}.
+// The FP64 step applies them with k_wall_hfilter64 / k_wall_ge64 / k_wall_hsolve64.  The FP32 tile
+// curl never forms G, so there the filter's ghost terms and G_E on the walls enter b as their Pade
+// responses (the curl is linear in G), added by the FP32 source kernels with the ghost part of P1.
 #include <cmath>
 #include <cstring>
 #include <vector>
