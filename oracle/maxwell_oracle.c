@@ -22,7 +22,10 @@
  *   - exact PEC cavity modes and the mean absolute error: Sec. 5.1, Eq. "eq:data";
  *   - Yee updating rules with the second-order stencil (c=1): Sec. 5.2;
  *   - the non-compact fourth-order comparator NC (stencil K4, a = 0, one-sided
- *     fourth-order differences at the line ends): Sec. 5.2, Eq. "eq:K4".
+ *     fourth-order differences at the line ends): Sec. 5.2, Eq. "eq:K4";
+ *   - current sources J_z: the source terms of the Taylor expansion of Sec. 3.1, and for
+ *     currents that do not vanish on the walls the Taylor ghosts of Method 2, Sec. 3.3,
+ *     Eq. "eq:gst2" (readings at or2d_wall_ghosts).
  *
  * Readings of points the paper leaves open:
  *   - the third rows of Step 1 / Step 2 are E_z and H_z (the printed E_y, H_y
@@ -33,7 +36,8 @@
  *   - closure PAPER uses the one-sided rows [26,-5,4,-1]/24 of Eq. "eq:lhs" at
  *     both ends of every Pade system; closure REFLECT replaces them by the rows
  *     that follow from the field's parity about the wall (see pade_row);
- *   - G_E = 0 on the PEC boundary nodes (E_z = 0 and Delta E_z = d_tt E_z = 0);
+ *   - G_E = 0 on the PEC boundary nodes (E_z = 0 and Delta E_z = d_tt E_z = 0), and
+ *     (h^2/12) Z d_t J_z there when a current does not vanish on the wall;
  *   - boundary values of the Dirichlet components are held at zero.
  *
  * Array layout (2D TM_z, N cells per side, h = 1/N): row-major [y][x].
