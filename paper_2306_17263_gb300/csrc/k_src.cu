@@ -399,6 +399,7 @@ size_t wall_data_doubles(int N) { return (size_t)WD_COUNT * (N + 1); }
 // either end, the entries of their first and last inputs.
 void wall_responses(int N, std::vector<float>* wr) {
   wr->assign((size_t)2 * (N - 1) + 2 * N, 0.0f);
+  if (N < 5) return;  // the end rows of the PAPER closure need 4 outputs per line (grids are larger)
   std::vector<double> row;
   for (int kind = 0; kind < 2; ++kind) {
     const int M = kind == HALF_TO_NODE ? N - 1 : N;
