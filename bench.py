@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
     p.add_argument("--only-3d", type=int, default=None, metavar="STEPS",
                    help="run only the 3D leg (FP32_REFINED, STEPS steps) and print its JSON (profiling)")
+    p.add_argument("--only-sources", type=int, default=None, metavar="STEPS",
+                   help="run only the FP32_REFINED 2048^2 step with two current sources (STEPS profiled "
+                        "steps and STEPS graph-replayed ones) and print its JSON (profiling)")
     return p.parse_args()
 
 
@@ -314,6 +317,19 @@ def _profiled_rate(pkg, torch, g, n, K, flush):
             "graph_value": n * n / (graph_ms * 1e-3)}
 
 
+SOURCES = [(2, 3, 1.0, 5.0), (1, 1, -0.5, 11.0)]  # (m, n, amplitude, omega) of J_z = a sin sin sin(w t)
+
+
+def sources_leg(pkg, torch, r, steps, flush):
+    """FP32_REFINED 2048^2 step with two sine-mode current sources, from their driven solution."""
+    with pkg.Grid(2048, r, z=1.3, precision=pkg.FP32_REFINED, stream="torch") as g:
+        g.set_sources(SOURCES)
+        g.init_driven(SOURCES)
+        res = _profiled_rate(pkg, torch, g, 2048, steps, flush)
+        res["l2_rel_vs_driven"] = g.error_vs_driven(SOURCES)[1]
+    return res
+
+
 def variants_leg(pkg, torch, modes, r):
     """The step variants: current sources (sine modes, both precisions, 2048^2), currents that do not
     vanish on the walls (FP64, 1024^2, against the same FP64 step without sources) and the tracked-DE
@@ -321,16 +337,11 @@ def variants_leg(pkg, torch, modes, r):
     import numpy as np
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    src = [(2, 3, 1.0, 5.0), (1, 1, -0.5, 11.0)]
     out = {}
     with pkg.Grid(2048, r, z=1.3, precision=pkg.FP32_REFINED, stream="torch") as g:
         g.init_modes(modes)
         out["plain_fp32_refined_2048"] = _profiled_rate(pkg, torch, g, 2048, 200, flush)
-    with pkg.Grid(2048, r, z=1.3, precision=pkg.FP32_REFINED, stream="torch") as g:
-        g.set_sources(src)
-        g.init_driven(src)
-        out["sources_fp32_refined_2048"] = _profiled_rate(pkg, torch, g, 2048, 200, flush)
-        out["sources_fp32_refined_2048"]["l2_rel_vs_driven"] = g.error_vs_driven(src)[1]
+    out["sources_fp32_refined_2048"] = sources_leg(pkg, torch, r, 200, flush)
     # a current that does not vanish on y = 0, 1 and is compatible at the corners:
     # J_z = (1/(4w)) sin(w t) (w^2 + (4 pi^2 - w^2) cos 2 pi x + (4 pi^2 - w^2) cos 2 pi y
     #                          + (w^2 - 8 pi^2) cos 2 pi x cos 2 pi y)
@@ -593,6 +604,15 @@ def main():
         torch.cuda.set_device(local)
         torch.cuda.set_stream(torch.cuda.Stream())
         print(json.dumps(leg_3d(pkg, torch, steps32=args.only_3d, with_fp64=False)), flush=True)
+        return 0
+    if args.only_sources is not None:
+        import torch
+
+        import paper_2306_17263_gb300 as pkg
+        torch.cuda.set_device(local)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        print(json.dumps(sources_leg(pkg, torch, workloads.config2()["r"], args.only_sources, flush)), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args, ws, rank)

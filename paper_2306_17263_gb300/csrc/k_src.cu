@@ -86,39 +86,65 @@ __host__ __device__ inline WallView wall_view(const double* wd, const float* wr,
   return WallView{wd, wr, wr + (N - 1), wr + 2 * (N - 1), wr + 2 * (N - 1) + N};
 }
 
+// Point kernels: a block is 32 columns by kSrcBy rows, and each thread takes kSrcRows rows kSrcBy
+// apart, all loads of a thread issued before its first update (one point per thread left the kernel
+// waiting on one memory round trip per wave).  Per point the arithmetic is that of the plain sum.
+constexpr int kSrcBy = 8;
+constexpr int kSrcRows = 8;
+
 // R += sum_q e_q X_q(i) Y_q(j) at the interior E_z nodes.  FP32 with wall data: plus, in the units of
 // R scaled by cE / (kappa^2 Z / h), the Pade responses to the filter's ghost terms of Step 1,
 //   kappa^2 Z / h (W_{i-1,0} (-g^y_lo(j) / 12) + W_{i-1,N-1} g^y_hi(j) / 12
 //                  - W_{j-1,0} (-g^x_lo(i) / 12) - W_{j-1,N-1} g^x_hi(i) / 12)   (W = A^{-1} D1 per line).
 template <typename T>
-__global__ void k_src_e(T* __restrict__ R, int N, int nsrc, const double* __restrict__ tab,
-                        const float* __restrict__ tab32, const SrcFac* __restrict__ fac, WallView wv, float cE) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i < 1 || j < 1 || i >= N || j >= N) return;
+__global__ void __launch_bounds__(32 * kSrcBy) k_src_e(T* __restrict__ R, int N, int nsrc, const double* __restrict__ tab,
+                                                       const float* __restrict__ tab32, const SrcFac* __restrict__ fac,
+                                                       WallView wv, float cE) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j0 = blockIdx.y * (kSrcBy * kSrcRows) + threadIdx.y;
+  if (i < 1 || i >= N) return;
   const size_t per = 4 * (size_t)(N + 1);  // per-source table block: X, Y at nodes, X', Y' at half-nodes
-  if constexpr (sizeof(T) == 8) {
-    double v = 0.0;
-    for (int q = 0; q < nsrc; ++q) {
+  T old[kSrcRows], v[kSrcRows];
+#pragma unroll
+  for (int r = 0; r < kSrcRows; ++r) {
+    const int j = j0 + r * kSrcBy;
+    old[r] = (j >= 1 && j < N) ? R[(size_t)j * (N + 1) + i] : (T)0;
+    v[r] = (T)0;
+  }
+  for (int q = 0; q < nsrc; ++q) {
+    if constexpr (sizeof(T) == 8) {
       const double* tq = tab + q * per;
-      v += fac->e[q] * tq[i] * tq[(N + 1) + j];
-    }
-    R[(size_t)j * (N + 1) + i] += v;
-  } else {
-    float v = 0.0f;
-    for (int q = 0; q < nsrc; ++q) {
+      const double fx = fac->e[q] * tq[i];
+#pragma unroll
+      for (int r = 0; r < kSrcRows; ++r) {
+        const int j = min(j0 + r * kSrcBy, N);
+        v[r] += fx * tq[(N + 1) + j];
+      }
+    } else {
       const float* tq = tab32 + q * per;
-      v = fmaf(fac->e32[q] * tq[i], tq[(N + 1) + j], v);
+      const float fx = fac->e32[q] * tq[i];
+#pragma unroll
+      for (int r = 0; r < kSrcRows; ++r) {
+        const int j = min(j0 + r * kSrcBy, N);
+        v[r] = fmaf(fx, tq[(N + 1) + j], v[r]);
+      }
     }
-    const int M = N - 1;
-    if (wv.wd && (i - 1 < kWallReach || i - 1 >= M - kWallReach || j - 1 < kWallReach || j - 1 >= M - kWallReach)) {
-      const double* wd = wv.wd;
-      const size_t L = N + 1;
-      const float ax = wv.hn0[i - 1] * (float)(-wd[WD_GY_LO * L + j]) + wv.hn1[i - 1] * (float)wd[WD_GY_HI * L + j];
-      const float ay = wv.hn0[j - 1] * (float)(-wd[WD_GX_LO * L + i]) + wv.hn1[j - 1] * (float)wd[WD_GX_HI * L + i];
-      v = fmaf(cE * (1.0f / 12.0f), ax - ay, v);
+  }
+#pragma unroll
+  for (int r = 0; r < kSrcRows; ++r) {
+    const int j = j0 + r * kSrcBy;
+    if (j < 1 || j >= N) continue;
+    if constexpr (sizeof(T) == 4) {
+      const int M = N - 1;
+      if (wv.wd && (i - 1 < kWallReach || i - 1 >= M - kWallReach || j - 1 < kWallReach || j - 1 >= M - kWallReach)) {
+        const double* wd = wv.wd;
+        const size_t L = N + 1;
+        const float ax = wv.hn0[i - 1] * (float)(-wd[WD_GY_LO * L + j]) + wv.hn1[i - 1] * (float)wd[WD_GY_HI * L + j];
+        const float ay = wv.hn0[j - 1] * (float)(-wd[WD_GX_LO * L + i]) + wv.hn1[j - 1] * (float)wd[WD_GX_HI * L + i];
+        v[r] = fmaf(cE * (1.0f / 12.0f), ax - ay, v[r]);
+      }
     }
-    R[(size_t)j * (N + 1) + i] += v;
+    R[(size_t)j * (N + 1) + i] = old[r] + v[r];
   }
 }
 
@@ -133,59 +159,72 @@ __device__ __forceinline__ double ghost_p1(const double* g, int k) {
 // +cH (W_{i,0} v(0, j) + W_{i,N} v(N, j)) on R_y (cH = scale kappa^2 / (Z h)), minus the ghost part of
 // P1 with the data of H* next to the walls (times sP = scale / h^2).
 template <typename T>
-__global__ void k_src_h(T* __restrict__ Rx, T* __restrict__ Ry, int N, int nsrc, const double* __restrict__ tab,
-                        const float* __restrict__ tab32, const SrcFac* __restrict__ fac, WallView wv, float cH,
-                        double sP) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > N || j > N) return;
+__global__ void __launch_bounds__(32 * kSrcBy) k_src_h(T* __restrict__ Rx, T* __restrict__ Ry, int N, int nsrc,
+                                                       const double* __restrict__ tab, const float* __restrict__ tab32,
+                                                       const SrcFac* __restrict__ fac, WallView wv, float cH, double sP) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j0 = blockIdx.y * (kSrcBy * kSrcRows) + threadIdx.y;
+  if (i > N) return;
   const size_t per = 4 * (size_t)(N + 1);
-  if (j < N && i >= 1 && i < N) {
+  const bool ix = i >= 1 && i < N;  // H_x column (interior in x)
+  const bool iy = i < N;            // H_y column
+  T ox[kSrcRows], oy[kSrcRows], vx[kSrcRows], vy[kSrcRows];
+#pragma unroll
+  for (int r = 0; r < kSrcRows; ++r) {
+    const int j = j0 + r * kSrcBy;
+    ox[r] = (ix && j < N) ? Rx[(size_t)j * (N + 1) + i] : (T)0;
+    oy[r] = (iy && j >= 1 && j < N) ? Ry[(size_t)j * N + i] : (T)0;
+    vx[r] = (T)0;
+    vy[r] = (T)0;
+  }
+  const int ic = min(i, N - 1);  // X' is tabulated at the N half-nodes
+  for (int q = 0; q < nsrc; ++q) {
     if constexpr (sizeof(T) == 8) {
-      double v = 0.0;
-      for (int q = 0; q < nsrc; ++q) {
-        const double* tq = tab + q * per;
-        v += fac->hx[q] * tq[i] * tq[3 * (N + 1) + j];
+      const double* tq = tab + q * per;
+      const double fx = fac->hx[q] * tq[i], fy = fac->hy[q] * tq[2 * (N + 1) + ic];
+#pragma unroll
+      for (int r = 0; r < kSrcRows; ++r) {
+        const int j = min(j0 + r * kSrcBy, N);
+        vx[r] += fx * tq[3 * (N + 1) + min(j, N - 1)];
+        vy[r] += fy * tq[(N + 1) + j];
       }
-      Rx[(size_t)j * (N + 1) + i] += v;
     } else {
-      float v = 0.0f;
-      for (int q = 0; q < nsrc; ++q) {
-        const float* tq = tab32 + q * per;
-        v = fmaf(fac->hx32[q] * tq[i], tq[3 * (N + 1) + j], v);
+      const float* tq = tab32 + q * per;
+      const float fx = fac->hx32[q] * tq[i], fy = fac->hy32[q] * tq[2 * (N + 1) + ic];
+#pragma unroll
+      for (int r = 0; r < kSrcRows; ++r) {
+        const int j = min(j0 + r * kSrcBy, N);
+        vx[r] = fmaf(fx, tq[3 * (N + 1) + min(j, N - 1)], vx[r]);
+        vy[r] = fmaf(fy, tq[(N + 1) + j], vy[r]);
       }
-      if (wv.wd && (j < kWallReach || j >= N - kWallReach)) {
-        const double* wd = wv.wd;
-        const size_t L = N + 1;
-        v = fmaf(-cH, wv.nh0[j] * (float)wd[WD_V_Y0 * L + i] + wv.nh1[j] * (float)wd[WD_V_Y1 * L + i], v);
-        if (j == 0) v -= (float)(sP * ghost_p1(wd + WD_SX_LO * L, i));
-        if (j == N - 1) v += (float)(sP * ghost_p1(wd + WD_SX_HI * L, i));
-      }
-      Rx[(size_t)j * (N + 1) + i] += v;
     }
   }
-  if (i < N && j >= 1 && j < N) {
-    if constexpr (sizeof(T) == 8) {
-      double v = 0.0;
-      for (int q = 0; q < nsrc; ++q) {
-        const double* tq = tab + q * per;
-        v += fac->hy[q] * tq[2 * (N + 1) + i] * tq[(N + 1) + j];
+#pragma unroll
+  for (int r = 0; r < kSrcRows; ++r) {
+    const int j = j0 + r * kSrcBy;
+    if (ix && j < N) {
+      if constexpr (sizeof(T) == 4) {
+        if (wv.wd && (j < kWallReach || j >= N - kWallReach)) {
+          const double* wd = wv.wd;
+          const size_t L = N + 1;
+          vx[r] = fmaf(-cH, wv.nh0[j] * (float)wd[WD_V_Y0 * L + i] + wv.nh1[j] * (float)wd[WD_V_Y1 * L + i], vx[r]);
+          if (j == 0) vx[r] -= (float)(sP * ghost_p1(wd + WD_SX_LO * L, i));
+          if (j == N - 1) vx[r] += (float)(sP * ghost_p1(wd + WD_SX_HI * L, i));
+        }
       }
-      Ry[(size_t)j * N + i] -= v;
-    } else {
-      float v = 0.0f;
-      for (int q = 0; q < nsrc; ++q) {
-        const float* tq = tab32 + q * per;
-        v = fmaf(fac->hy32[q] * tq[2 * (N + 1) + i], tq[(N + 1) + j], v);
+      Rx[(size_t)j * (N + 1) + i] = ox[r] + vx[r];
+    }
+    if (iy && j >= 1 && j < N) {
+      if constexpr (sizeof(T) == 4) {
+        if (wv.wd && (i < kWallReach || i >= N - kWallReach)) {
+          const double* wd = wv.wd;
+          const size_t L = N + 1;
+          vy[r] = fmaf(-cH, wv.nh0[i] * (float)wd[WD_V_X0 * L + j] + wv.nh1[i] * (float)wd[WD_V_X1 * L + j], vy[r]);
+          if (i == 0) vy[r] += (float)(sP * ghost_p1(wd + WD_SY_LO * L, j));
+          if (i == N - 1) vy[r] -= (float)(sP * ghost_p1(wd + WD_SY_HI * L, j));
+        }
       }
-      if (wv.wd && (i < kWallReach || i >= N - kWallReach)) {
-        const double* wd = wv.wd;
-        const size_t L = N + 1;
-        v = fmaf(-cH, wv.nh0[i] * (float)wd[WD_V_X0 * L + j] + wv.nh1[i] * (float)wd[WD_V_X1 * L + j], v);
-        if (i == 0) v += (float)(sP * ghost_p1(wd + WD_SY_LO * L, j));
-        if (i == N - 1) v -= (float)(sP * ghost_p1(wd + WD_SY_HI * L, j));
-      }
-      Ry[(size_t)j * N + i] -= v;
+      Ry[(size_t)j * N + i] = oy[r] - vy[r];
     }
   }
 }
@@ -365,25 +404,27 @@ void launch_src_time(ms_grid* g, double scale_e, double scale_h) {
   k_src_time<<<1, kMaxSrc, 0, g->stream>>>((const SrcDev*)g->d_src, g->nsrc, g->d_step, g->ht, scale_e, scale_h,
                                            (SrcFac*)g->d_srcfac);
 }
+static dim3 src_grid(int N) { return dim3((N + 1 + 31) / 32, (N + 1 + kSrcBy * kSrcRows - 1) / (kSrcBy * kSrcRows)); }
+
 void launch_src_e64(ms_grid* g, double* R) {
-  dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
+  dim3 blk(32, kSrcBy), grd = src_grid(g->N);
   k_src_e<double><<<grd, blk, 0, g->stream>>>(R, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
                                                (const SrcFac*)g->d_srcfac, WallView{}, 0.0f);
 }
 void launch_src_h64(ms_grid* g, double* Rx, double* Ry) {
-  dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
+  dim3 blk(32, kSrcBy), grd = src_grid(g->N);
   k_src_h<double><<<grd, blk, 0, g->stream>>>(Rx, Ry, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
                                                (const SrcFac*)g->d_srcfac, WallView{}, 0.0f, 0.0);
 }
 void launch_src_e32(ms_grid* g, float* R, double scale_e) {
-  dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
+  dim3 blk(32, kSrcBy), grd = src_grid(g->N);
   const WallView wv = g->d_walldata ? wall_view(g->d_walldata, g->d_wresp, g->N) : WallView{};
   const float cE = (float)(scale_e * g->kappa2 * g->Z / g->h);
   k_src_e<float><<<grd, blk, 0, g->stream>>>(R, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
                                               (const SrcFac*)g->d_srcfac, wv, cE);
 }
 void launch_src_h32(ms_grid* g, float* Rx, float* Ry, double scale_h) {
-  dim3 blk(32, 8), grd((g->N + 1 + 31) / 32, (g->N + 1 + 7) / 8);
+  dim3 blk(32, kSrcBy), grd = src_grid(g->N);
   const WallView wv = g->d_walldata ? wall_view(g->d_walldata, g->d_wresp, g->N) : WallView{};
   const float cH = (float)(scale_h * g->kappa2 / (g->Z * g->h));
   k_src_h<float><<<grd, blk, 0, g->stream>>>(Rx, Ry, g->N, g->nsrc, g->d_srctab, g->d_srctab32,
