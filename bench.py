@@ -205,6 +205,54 @@ def oracle_rate(n: int, steps: int, modes, time_budget: float = None):
     return n * n * done / dt, done, dt
 
 
+def _oracle_worker(job):
+    """One host process: the oracle on its own n x n copy of the workload for `steps` steps (or
+    until `budget` seconds have passed).  Returns (cell-updates, seconds)."""
+    n, steps, modes, budget = job
+    sys.path.insert(0, ROOT)
+    v, done, dt = oracle_rate(n, steps, modes, time_budget=budget)
+    return n * n * done, dt
+
+
+def host_info():
+    """Host core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if ln.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_all_cores(n: int, steps: int, modes, budget: float, procs: int):
+    """The oracle as it stands on every host core: `procs` independent processes (spawned, so none
+    inherits a CUDA context), each stepping its own copy of an n x n sample.  Returns
+    (cell-updates/s over all processes, cell-updates, wall seconds)."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [(64, 1, modes, None)] * procs)  # start-up outside the timing
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(n, steps, modes, budget)] * procs)
+        wall = time.perf_counter() - t0
+    cells = sum(c for c, _ in res)
+    return cells / wall, cells, wall
+
+
 def run_reference(args, ws, rank):
     """The reference arm: the FP64 CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -214,17 +262,23 @@ def run_reference(args, ws, rank):
     W = args.warmup
     # each step is one oracle step on an n_s x n_s sample of the workload; n_s keeps the run
     # within about two minutes (an oracle step costs ~0.45 us per cell on one core)
-    n_s = int(min(2048, max(64, math.sqrt(120.0 / (max(K, 1) * 0.45e-6)))))
+    # one oracle process per host core, each on its own n_s x n_s copy (the oracle is one thread);
+    # an oracle step costs ~0.45 us per cell on one core, more when every core shares the memory
+    ncores, model = host_info()
+    n_s = int(min(2048, max(64, math.sqrt(100.0 / (max(K + W, 1) * 0.9e-6)))))
     n_s -= n_s % 32
-    oracle_rate(n_s, W, cfg["modes"])
-    value, done, dt = oracle_rate(n_s, K, cfg["modes"])
+    if W:
+        oracle_all_cores(n_s, W, cfg["modes"], None, ncores)
+    value, cells, wall = oracle_all_cores(n_s, K, cfg["modes"], None, ncores)
     line = {
         "impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
-        "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / max(done, 1),
+        "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * wall / max(K, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_n": n_s, "precision": "fp64 (CPU oracle)"},
-        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{done} oracle steps on a {n_s}x{n_s} grid of the same workload"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": ncores, "cpu_model": model,
+                         "kind": "oracle",
+                         "sample": f"{ncores} oracle processes, one per host core, each {K} steps on its own "
+                                   f"{n_s}x{n_s} grid of the same workload"},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -422,6 +476,38 @@ def wavenumber_leg(pkg):
             "mae_c4": c4, "mae_nc": nc, "mae_yee": yee}
 
 
+def accuracy_leg(pkg, torch, cfg, closure):
+    """The whole 4000-step workload (T = 0.9765625) in FP32_REFINED and in FP64, each replayed from
+    its captured graph and timed with CUDA events: the L2 errors against the exact modes at T and
+    the distance between the two states (the mixed-path criterion: e32 <= 2 e64 and
+    |u32 - u64| <= e64; the FP64 path is the oracle's parity-pinned stand-in at this size)."""
+    import numpy as np
+
+    N, r, modes, K = cfg["n"], cfg["r"], cfg["modes"], cfg["steps"]
+    out, fields = {}, {}
+    for prec, key in ((pkg.FP32_REFINED, "fp32_refined"), (pkg.FP64, "fp64")):
+        with pkg.Grid(N, r, precision=prec, closure=closure, stream="torch") as g:
+            g.init_modes(modes)
+            g.run(17)  # captures the 16-step and 1-step graphs
+            g.init_modes(modes)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            g.run(K)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            l2_abs, l2_rel, max_abs, _ = g.error_vs_exact(modes)
+            fields[key] = g.get_fields()
+            out[key] = {"l2_abs": l2_abs, "l2_rel": l2_rel, "max_abs": max_abs, "ms_per_step": ms / K,
+                        "value": N * N * K / (ms * 1e-3), "unit": "cell-updates/s"}
+    diff = math.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(fields["fp32_refined"], fields["fp64"])) / N ** 2)
+    e32, e64 = out["fp32_refined"]["l2_abs"], out["fp64"]["l2_abs"]
+    out.update({"t": K * r / N, "steps": K, "l2_fp32_vs_fp64": diff, "mixed_criterion_holds": bool(e32 <= 2 * e64 and diff <= e64),
+                "timing": "graph replay of all 4000 steps, CUDA events, no L2 flush (state 100 MB in FP32_REFINED)"})
+    return out
+
+
 def yee_leg(pkg, torch, modes, r, c4_l2_abs, c4_value, T=4000 * 0.5 / 2048):
     """Plain second-order Yee (FP64) on the same modes and end time: its L2 error at three
     resolutions, the fitted order, and the resolution and time-to-solution it would need to
@@ -522,7 +608,19 @@ def run_ours(args, ws, rank, local):
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": achieved_gbs / hbm, "traffic": ncu_traffic(kind), "kernel": kind,
                 "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
-                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms}
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                "bytes": "state bytes the launch must move: 8 B per float-float (or FP64) point read or written"}
+    # whole step on the algorithmic bytes: every state component read and written once, 48 B per cell
+    step_bytes = 48.0 * N * N
+    step_gbs = step_bytes / (ms_step * 1e-3) / 1e9
+    step_roofline = {"achieved": step_gbs, "peak": hbm, "unit": "GB/s", "frac": step_gbs / hbm,
+                     "bytes_per_step": step_bytes, "bytes": "48 B per cell-update (3 components, hi+lo, read + write)"}
+    # bytes the four-launch FP32_REFINED step moves by design, right-hand-side planes b included
+    ne, nh = (N + 1.0) ** 2, N * (N + 1.0)
+    traffic_model = {"curl_step1": 16 * nh + 4 * ne, "solve_E": 4 * ne + 16 * ne, "curl_step2": 8 * ne + 8 * nh,
+                     "solve_H": 8 * nh + 32 * nh}
+    traffic_model["per_step"] = sum(traffic_model.values())
+    traffic_model["what"] = "bytes per launch if every array a launch reads or writes (state hi/lo and b) moves once"
     kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / total_ms, "GBps": v[2] / (v[1] * 1e-3) / 1e9}
                for k, v in sorted(per_kind.items(), key=lambda kv: -kv[1][1])}
 
@@ -535,6 +633,8 @@ def run_ours(args, ws, rank, local):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "gpu_launches": launches,
         "roofline": roofline,
+        "step_roofline": step_roofline,
+        "traffic_model": traffic_model if prec == pkg.FP32_REFINED else None,
         "kernels": kernels,
         "accuracy": {"t": K * r / N, "l2_abs": l2_abs, "l2_rel": l2_rel, "max_abs": max_abs},
         "clocks": clk,
@@ -552,6 +652,7 @@ def run_ours(args, ws, rank, local):
         ptr_in = pkg._ptrs([t.data_ptr() for t in host_in])
         ptr_out = pkg._ptrs([t.data_ptr() for t in host_out])
         pkg._check(L.ms_get_fields(g._h, ptr_in))
+        pkg._check(L.ms_run(g._h, 17))  # captures the step graphs outside the timed region
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pkg._check(L.ms_set_fields(g._h, ptr_in, 0))
@@ -561,31 +662,30 @@ def run_ours(args, ws, rank, local):
         nbytes = sum(t.numel() * 8 for t in host_in)
         line["e2e"] = {"value": N * N * K / e2e_s, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / K,
                        "d2h_bytes_per_step": nbytes / K, "seconds": e2e_s,
-                       "what": "ms_set_fields (host) + ms_run(K) (graph replay, no L2 flush) + ms_get_fields (host)"}
-        # FP64 GPU form on the same workload (a shorter run), for the mixed-vs-FP64 comparison
-        if prec == pkg.FP32_REFINED:
-            g64 = pkg.Grid(N, r, precision=pkg.FP64, closure=closure, stream="torch")
-            g64.init_modes(modes)
-            k64 = min(K, 100)
-            for _ in range(3):
-                g64.step_profiled()
-            t64 = 0.0
-            for _ in range(k64):
-                t64 += sum(ms for _, ms, _ in g64.step_profiled())
-                flush.zero_()
-            line["fp64_gpu"] = {"value": N * N / (t64 / k64 * 1e-3), "unit": "cell-updates/s", "steps": k64,
-                                "ms_per_step": t64 / k64}
-            g64.close()
+                       "what": "ms_set_fields (host) + ms_run(K) (graph replay, graphs captured beforehand, "
+                               "no L2 flush) + ms_get_fields (host)"}
+        # the whole workload in both precisions: errors at T, the mixed-path criterion, and the FP64
+        # GPU form's rate on the same workload
+        acc = accuracy_leg(pkg, torch, cfg, closure)
+        line["accuracy_at_T"] = acc
+        line["fp64_gpu"] = {"value": acc["fp64"]["value"], "unit": "cell-updates/s", "steps": cfg["steps"],
+                            "ms_per_step": acc["fp64"]["ms_per_step"], "timing": acc["timing"]}
         line["batched"] = batched_leg(pkg, torch)
         line["reverse_pass"] = reverse_leg(pkg, torch)
         line["three_d"] = leg_3d(pkg, torch)
         line["error_vs_wavenumber"] = wavenumber_leg(pkg)
-        line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, l2_abs, value)
+        line["yee_equal_error"] = yee_leg(pkg, torch, modes, r, acc["fp32_refined"]["l2_abs"], value)
         line["variants"] = variants_leg(pkg, torch, modes, r)
-        # CPU oracle on a bounded sample of the workload (rank 0, one core)
-        v, done, dt = oracle_rate(N, 1000, modes, time_budget=12.0)
-        line["cpu_baseline"] = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{done} oracle steps ({dt:.1f} s) on the full 2048x2048 grid"}
+        # CPU oracle on a bounded sample of the workload (rank 0): every host core, one oracle process
+        # per core on its own copy of the full 2048^2 grid, and one core alone
+        ncores, model = host_info()
+        v_all, cells_all, wall_all = oracle_all_cores(N, 1000, modes, 10.0, ncores)
+        v1, done, dt = oracle_rate(N, 1000, modes, time_budget=8.0)
+        line["cpu_baseline"] = {"value": v_all, "unit": "cell-updates/s", "cores": ncores, "cpu_model": model,
+                                "kind": "oracle",
+                                "sample": f"{ncores} oracle processes (one per core), each stepping its own full "
+                                          f"2048x2048 grid for ~10 s: {cells_all / N ** 2:.0f} steps in {wall_all:.1f} s",
+                                "one_core": {"value": v1, "sample": f"{done} oracle steps ({dt:.1f} s) on one core"}}
     g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -10,8 +10,11 @@
  *   H^{n+3/2} = H^{n+1/2} + h_tau H*
  * with kappa^2 = 24/h_tau^2 (Sec. 3.2), P1 = -(Delta_h + (h^2/6) Upsilon_h) + kappa^2(1 + 2/r^2)
  * (Definition "def:operatorsP"), curl_h the Pade compact curl of App. A.1 (Eq. "eq:lhs"),
- * Dirichlet / even-ghost Neumann boundaries of Table "tab:bc" and Corollary "cor:ghost_cor",
- * and J = rho = 0.
+ * Dirichlet / even-ghost Neumann boundaries of Table "tab:bc" and Corollary "cor:ghost_cor".
+ * J defaults to zero (rho = 0 throughout).  The source entry points (ms_set_sources,
+ * ms_set_sources_xy) add a current J_z: Step 1 then gains the filtered Z P(J) term of Eq. "eq:pj"
+ * on its right-hand side and Step 2 the filtered curl d_t J term (Sec. 3.1, 3.4), and currents
+ * that do not vanish on the walls bring the inhomogeneous ghosts of Sec. 3.3 (Method 2).
  *
  * Conventions for every entry point:
  *   - Status codes are returned, never thrown.  On failure a message is available from
@@ -249,6 +252,19 @@ const char* ms_kernel_kind_name(int kind);
 #define MS_STATIC_MAX_N 512
 #define MS_STATIC_SCRATCH_BYTES (2u * (MS_STATIC_MAX_N + 1u) * (MS_STATIC_MAX_N + 1u) * 8u)
 ms_status ms_p1_solve_static(int n, double r, int field, const double* b, double* x, void* stream);
+
+/* Richardson sweeps the GPU elliptic solves take to reduce the error of P1 x = b by the factor
+ * tol from x = 0, from the spectral bound of App. A.2: h^2 P1 has its spectrum in
+ * [c1 h^2, c1 h^2 + 16/3] (2D and 3D), c1 h^2 = (24/r^2)(1 + 2/r^2), so one sweep with the
+ * optimal relaxation contracts the error by (16/3) / (2 c1 h^2 + 16/3) (about 0.003 at r = 0.5).
+ *   dim: 2 or 3;  r: CFL number, 0 < r < the stability limit (MS_ECFL at or above it);
+ *   precision: ms_precision; it fixes the largest sweep count the solve kernels hold (FP64: 64;
+ *              FP32_REFINED: 6 in 2D, 8 in 3D);  tol: in (0, 1).
+ * *sweeps receives the count (0 on failure).  Returns MS_ENOTCONV, with a message, when tol needs
+ * more sweeps than the kernels hold, i.e. when the solve would stop short of tol.  Grid creation
+ * runs the same check with tol = 1e-17 (FP64) and 1e-10 (FP32_REFINED) and fails with the same
+ * status.  Needs no GPU. */
+ms_status ms_solver_sweeps(int dim, double r, int precision, double tol, int* sweeps);
 
 /* Number of kernel launches one ms_step issues (for launch accounting). */
 ms_status ms_launches_per_step(ms_grid* g, int* launches);

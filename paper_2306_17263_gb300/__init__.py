@@ -97,6 +97,7 @@ def load() -> ctypes.CDLL:
             "ms_apply_op": [V, I, PPD, PPD],
             "ms_launches_per_step": [V, ctypes.POINTER(I)],
             "ms_stability_limit": [I, PD],
+            "ms_solver_sweeps": [I, D, I, D, ctypes.POINTER(I)],
             "ms_create_batch": [ctypes.POINTER(_Desc), ctypes.POINTER(I), I, ctypes.POINTER(V)],
             "ms_batch_destroy": [V],
             "ms_batch_init_modes": [V, I, ctypes.POINTER(_Mode), I],
@@ -183,6 +184,14 @@ def stability_limit(dim: int = 2) -> float:
     """Largest stable CFL number of the scheme (from its Fourier symbol); needs no GPU."""
     v = ctypes.c_double()
     _check(load().ms_stability_limit(int(dim), ctypes.byref(v)))
+    return v.value
+
+
+def solver_sweeps(dim: int, r: float, precision: int, tol: float) -> int:
+    """Richardson sweeps of the GPU elliptic solve for error reduction `tol` (App. A.2 bound);
+    raises MaxwellError (MS_ENOTCONV) when the solve kernels cannot hold that many; needs no GPU."""
+    v = ctypes.c_int()
+    _check(load().ms_solver_sweeps(int(dim), float(r), int(precision), float(tol), ctypes.byref(v)))
     return v.value
 
 

@@ -50,16 +50,6 @@ ms_status dalloc(T** p, size_t n) {
   return MS_OK;
 }
 
-// Number of Richardson sweeps for P~ = h^2 P1 with spectrum in [c1h2, c1h2 + 16/3] (App. A.2)
-// to reduce the error below tol (x0 = 0, contraction (16/3) / (2 c1h2 + 16/3) per sweep).
-int richardson_sweeps(double c1h2, double tol) {
-  const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
-  int s = (int)std::ceil(std::log(tol) / std::log(rho));
-  if (s < 1) s = 1;
-  if (s > 64) s = 64;
-  return s;
-}
-
 double omega_of(double c1h2) { return 2.0 / (2.0 * c1h2 + 16.0 / 3.0); }
 
 // ---------------------------------------------------------------------------------------
@@ -441,6 +431,38 @@ ms_status ms_stability_limit(int dim, double* rmax) {
   return MS_OK;
 }
 
+// Largest Richardson sweep count the solve kernels of a precision hold.
+static int max_sweeps(int dim, int precision) {
+  if (precision == MS_FP64) return 64;
+  return dim == 2 ? kTiledMaxSweeps : kMaxSweeps3d32;
+}
+
+ms_status ms_solver_sweeps(int dim, double r, int precision, double tol, int* sweeps) {
+  if (!sweeps) return fail(MS_EINVAL, "sweeps is NULL");
+  *sweeps = 0;
+  if (dim != 2 && dim != 3) return fail(MS_EINVAL, "dim must be 2 or 3");
+  if (precision != MS_FP64 && precision != MS_FP32_REFINED) return fail(MS_EINVAL, "unknown precision");
+  if (!(r > 0.0) || !std::isfinite(r)) return fail(MS_EINVAL, "r must be positive");
+  if (!(tol > 0.0 && tol < 1.0)) return fail(MS_EINVAL, "tol must be in (0, 1)");
+  const double rmax = dim == 2 ? stability_limit_2d() : stability_limit_3d();
+  if (r >= rmax) return fail(MS_ECFL, "r is at or above the stability limit");
+  // Richardson on h^2 P1, spectrum in [c1 h^2, c1 h^2 + 16/3] (App. A.2) in 2D and 3D, from x = 0:
+  // contraction (16/3) / (2 c1 h^2 + 16/3) per sweep; h^2 c1 = (24 / r^2)(1 + 2 / r^2) for any h
+  const double c1h2 = (24.0 / (r * r)) * (1.0 + 2.0 / (r * r));
+  const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
+  const double s = std::ceil(std::log(tol) / std::log(rho));
+  const int cap = max_sweeps(dim, precision);
+  if (!(s <= cap)) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "reaching tol = %.3g needs %.0f Richardson sweeps; the %s solve holds at most %d", tol, s,
+             precision == MS_FP64 ? "FP64" : "FP32_REFINED", cap);
+    return fail(MS_ENOTCONV, buf);
+  }
+  *sweeps = s < 1 ? 1 : (int)s;
+  return MS_OK;
+}
+
 // shared64 != nullptr: the grid uses these six FP64 diagnostic planes (at least (n+1)^2 each,
 // owned by a batch) instead of allocating its own.
 static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64, ms_grid** out);
@@ -521,7 +543,10 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
         cudaMemcpy(t.d_wlo, wlo.data(), wlo.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
       return cleanup(fail(MS_ECUDA, "copy of Pade tables failed"));
   }
-  g->p1_sweeps = richardson_sweeps(g->c1 * g->h * g->h, 1e-17);
+  if (compact) {
+    ms_status sw = ms_solver_sweeps(2, d->r, MS_FP64, 1e-17, &g->p1_sweeps);
+    if (sw != MS_OK) return cleanup(sw);
+  }
   const size_t nmax = (size_t)(g->N + 1) * (g->N + 1);
   ms_status s = MS_OK;
   // FP64 scratch is used by the FP64 step and by the diagnostics of both precisions
@@ -901,15 +926,19 @@ static ms_status set_sources_spec(ms_grid* g, const SrcSpec* src, int nsrc) {
   std::vector<float> tabs32(tabs.begin(), tabs.end());
   MS_CUDA(cudaMemcpy(g->d_srctab32, tabs32.data(), tabs32.size() * sizeof(float), cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice));
-  g->nsrc = nsrc;
-  for (int q = 0; q < nsrc; ++q) g->src_wall |= (src[q].px | src[q].py);
-  if (g->src_wall && g->desc.precision == MS_FP32_REFINED) {  // wall terms of the FP32 source kernels
+  int wall = 0;
+  for (int q = 0; q < nsrc; ++q) wall |= (src[q].px | src[q].py);
+  if (wall && g->desc.precision == MS_FP32_REFINED) {  // wall terms of the FP32 source kernels
     std::vector<float> wr;
     wall_responses(g->N, &wr);
     MS_TRY(dalloc(&g->d_walldata, wall_data_doubles(g->N)));
     MS_TRY(dalloc(&g->d_wresp, wr.size()));
     MS_CUDA(cudaMemcpy(g->d_wresp, wr.data(), wr.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
+  // the step reads these two only once every buffer above is in place: a failure above leaves
+  // the grid without sources rather than with half of them
+  g->nsrc = nsrc;
+  g->src_wall = wall;
   return MS_OK;
 }
 
@@ -943,6 +972,9 @@ ms_status ms_set_sources_xy(ms_grid* g, const ms_source_xy* src, int nsrc) {
   }
   if (wall && g->desc.closure != MS_CLOSURE_PAPER)
     return fail(MS_EUNSUPPORTED, "sources that do not vanish on the walls need the PAPER closure");
+  if (wall && g->desc.precision == MS_FP32_REFINED && g->N < 5)
+    return fail(MS_EUNSUPPORTED, "FP32_REFINED sources that do not vanish on the walls need n >= 5 "
+                                 "(the PAPER end rows of a Pade line take four outputs)");
   return set_sources_spec(g, sp.data(), nsrc);
 }
 

@@ -120,23 +120,40 @@ ms_status ms_load(ms_grid* g, const char* path) {
     std::fclose(fp);
     return cfail(MS_ECUDA, "stream synchronisation failed");
   }
+  // the whole payload is read and checked on the host first: a truncated or inconsistent file
+  // leaves the grid's state untouched
+  std::vector<std::vector<double>> b64(nc);
+  std::vector<std::vector<float>> b32(2 * nc);
   for (int c = 0; c < nc && ok; ++c) {
     long long cnt = 0;
     ok = std::fread(&cnt, sizeof(long long), 1, fp) == 1 && cnt == (long long)n[c];
+    if (!ok) break;
     if (f64[c]) {
-      std::vector<double> buf(n[c]);
-      ok = ok && std::fread(buf.data(), sizeof(double), n[c], fp) == n[c];
-      ok = ok && cudaMemcpy(f64[c], buf.data(), n[c] * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+      b64[c].resize(n[c]);
+      ok = std::fread(b64[c].data(), sizeof(double), n[c], fp) == n[c];
     } else {
-      std::vector<float> buf(n[c]);
-      for (float* arr : {hi[c], lo[c]}) {
-        ok = ok && std::fread(buf.data(), sizeof(float), n[c], fp) == n[c];
-        ok = ok && cudaMemcpy(arr, buf.data(), n[c] * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+      for (int part = 0; part < 2 && ok; ++part) {
+        b32[2 * c + part].resize(n[c]);
+        ok = std::fread(b32[2 * c + part].data(), sizeof(float), n[c], fp) == n[c];
       }
     }
   }
+  if (ok) {  // nothing may follow the last component
+    char extra;
+    ok = std::fread(&extra, 1, 1, fp) == 0;
+  }
   std::fclose(fp);
   if (!ok) return cfail(MS_EINVAL, std::string("checkpoint ") + path + " is truncated or inconsistent");
+  for (int c = 0; c < nc; ++c) {
+    bool cp;
+    if (f64[c]) {
+      cp = cudaMemcpy(f64[c], b64[c].data(), n[c] * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+      cp = cudaMemcpy(hi[c], b32[2 * c].data(), n[c] * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(lo[c], b32[2 * c + 1].data(), n[c] * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!cp) return cfail(MS_ECUDA, "copying the checkpoint to the device failed");
+  }
   g->step = (long)h.step;
   if (g->d_step && cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice) != cudaSuccess)
     return cfail(MS_ECUDA, "restoring the device step index failed");

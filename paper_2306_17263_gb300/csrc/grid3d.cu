@@ -1122,8 +1122,6 @@ ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
     g->own_stream = true;
   }
   std::string err;
-  const double c1h2 = g->c1 * g->h * g->h;
-  const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
   ms_status s = MS_OK;
   if (d->precision == MS_FP64) {
     for (int kind = 0; kind < 2 && s == MS_OK; ++kind) {
@@ -1134,8 +1132,7 @@ ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
       if (s == MS_OK && cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         s = fail3(MS_ECUDA, "copy of Pade tables failed");
     }
-    int S = (int)std::ceil(std::log(1e-17) / std::log(rho));
-    g->p1_sweeps = S < 1 ? 1 : (S > 64 ? 64 : S);
+    if (s == MS_OK) s = ms_solver_sweeps(3, d->r, MS_FP64, 1e-17, &g->p1_sweeps);
     for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->f64[c], G3->sh[c].size());
     for (int k = 0; k < 7 && s == MS_OK; ++k) s = alloc3(&G3->s64[k], G3->nmax);
   } else {
@@ -1156,9 +1153,8 @@ ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
         s = fail3(MS_ECUDA, "copy of FP32 Pade tables failed");
     }
     if (s == MS_OK && upload_band_row() != 0) s = fail3(MS_ECUDA, "cannot upload the interior band row");
-    int S = (int)std::ceil(std::log(1e-10) / std::log(rho));
-    g->p1_sweeps32 = S < 1 ? 1 : S;
-    if (g->p1_sweeps32 > 8) s = fail3(MS_EUNSUPPORTED, "CFL number too close to the stability limit for the FP32 solve");
+    // Richardson sweeps to 1e-10 (below the FP32 rounding noise, which is not coherent)
+    if (s == MS_OK) s = ms_solver_sweeps(3, d->r, MS_FP32_REFINED, 1e-10, &g->p1_sweeps32);
     for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->hi[c], G3->sh[c].size());
     for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->lo[c], G3->sh[c].size());
     for (int k = 0; k < 4 && s == MS_OK; ++k) s = alloc3(&G3->s32[k], G3->nmax);
@@ -1279,12 +1275,7 @@ ms_status diag_view3d(ms_grid* g, double** f) {
     if (cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail3(MS_ECUDA, "copy of Pade tables failed");
   }
-  if (!g->p1_sweeps) {
-    const double c1h2 = g->c1 * g->h * g->h;
-    const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
-    const int S = (int)std::ceil(std::log(1e-17) / std::log(rho));
-    g->p1_sweeps = S < 1 ? 1 : (S > 64 ? 64 : S);
-  }
+  if (!g->p1_sweeps) MS3_TRY(ms_solver_sweeps(3, g->desc.r, MS_FP64, 1e-17, &g->p1_sweeps));
   for (int k = 0; k < 7; ++k)
     if (!G3->s64[k]) MS3_TRY(alloc3(&G3->s64[k], G3->nmax));
   for (int c = 0; c < 6; ++c) {

@@ -16,6 +16,8 @@ Shape3 field_shape3(int N, int c);
 
 struct Grid3D;
 
+constexpr int kMaxSweeps3d32 = 8;  // largest Richardson sweep count of the FP32 3D solve
+
 // 3D counterparts of the grid life cycle and state access, dispatched from capi.cu.
 ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out);
 void destroy_grid3d(ms_grid* g);

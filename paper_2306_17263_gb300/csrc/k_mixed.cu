@@ -75,7 +75,10 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   // Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y) on E_z, then the E solve
   float* bE = g->s32[4];
   tiled_curl(g, 0, k.cb_hi, k.cb_lo, bE, nullptr);
-  prof_mark(g, KK_CURL32, 4.0 * (4.0 * nh + ne));            // H_x, H_y (hi, lo) in; b out
+  // recorded bytes: the state each launch must touch (8 B per point per float-float read or
+  // write), the algorithmic bytes of a step being 48 B per cell (each component read and written
+  // once); the right-hand-side planes b are intermediates and are not counted
+  prof_mark(g, KK_CURL32, 8.0 * 2.0 * nh);                   // H_x, H_y (hi, lo) read
   // sources in the units of b: 6 h^2 P1 x = b with E += (12 Z / r) x, so b = (h^3 r^2 / (2 Z)) R
   const double hr2 = g->h * g->h * g->h * g->desc.r * g->desc.r;
   if (g->nsrc) {  // H += (12 / (r Z)) x, so b = (h^3 r^2 Z / 2) R on the H side
@@ -94,12 +97,12 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   const int fe[1] = {EZ};
   const float* be[1] = {bE};
   tiled_solve(g, 1, fe, be, k.S, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo);
-  prof_mark(g, KK_SOLVE32, 4.0 * (ne + 4.0 * ne));           // b in; E (hi, lo) read and written
+  prof_mark(g, KK_SOLVE32, 16.0 * ne);                       // E (hi, lo) read and written
   // Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x), then both H solves
   float* bx = g->s32[2];
   float* by = g->s32[3];
   tiled_curl(g, 1, k.cb_hi, k.cb_lo, bx, by);
-  prof_mark(g, KK_CURL32, 4.0 * (2.0 * ne + 2.0 * nh));      // E (hi, lo) in; b_x, b_y out
+  prof_mark(g, KK_CURL32, 8.0 * ne);                         // E (hi, lo) read
   if (g->nsrc) {
     launch_src_h32(g, bx, by, hr2 * g->Z / 2.0);
     prof_mark(g, KK_SRC, 16.0 * nh);
@@ -108,7 +111,7 @@ ms_status step_mixed(ms_grid* g, int* nl) {
   const int fh[2] = {HX, HY};
   const float* bh[2] = {bx, by};
   tiled_solve(g, 2, fh, bh, k.S, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo);
-  prof_mark(g, KK_SOLVE32, 4.0 * (2.0 * nh + 8.0 * nh));     // b_x, b_y in; H (hi, lo) read and written
+  prof_mark(g, KK_SOLVE32, 16.0 * 2.0 * nh);                 // H_x, H_y (hi, lo) read and written
   if (g->nsrc) {
     launch_tick(g);
     prof_mark(g, KK_SRC, 0.0);
@@ -150,13 +153,10 @@ ms_status mixed_setup(ms_grid* g) {
     }
   }
   // Richardson sweeps to 1e-10 (below the FP32 rounding noise, which is not coherent)
-  const double c1h2 = g->c1 * g->h * g->h;
-  const double rho = (16.0 / 3.0) / (2.0 * c1h2 + 16.0 / 3.0);
-  int s = (int)std::ceil(std::log(1e-10) / std::log(rho));
-  g->p1_sweeps32 = s < 1 ? 1 : s;
-  if (g->p1_sweeps32 > kTiledMaxSweeps) {
-    g_mixed_err = "CFL number too close to the stability limit for the FP32 tile solve";
-    return MS_EUNSUPPORTED;
+  const ms_status sw = ms_solver_sweeps(2, g->desc.r, MS_FP32_REFINED, 1e-10, &g->p1_sweeps32);
+  if (sw != MS_OK) {
+    g_mixed_err = "too many Richardson sweeps for the FP32 tile solve";
+    return sw;
   }
   if (tiled_configure() != 0) {
     g_mixed_err = "cannot configure shared memory of the tile kernels";

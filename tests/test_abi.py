@@ -85,3 +85,34 @@ def test_stability_limit_3d_matches_mode_recurrence():
                    for a in (N - 1, N - 3) for b in (N - 1, N - 3) for c in (N - 1, N - 3))
     assert amp(rmax * 0.999) < 1 + 1e-9
     assert amp(rmax * 1.003) > 1 + 1e-6
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("r", [0.2, 0.4, 0.5])
+def test_solver_sweeps_follow_the_contraction_bound(dim, r):
+    """App. A.2: h^2 P1 has its spectrum in [c1 h^2, c1 h^2 + 16/3], so Richardson contracts the
+    error by (16/3) / (2 c1 h^2 + 16/3) per sweep; the count is the smallest S with rho^S <= tol."""
+    c1h2 = (24 / r ** 2) * (1 + 2 / r ** 2)
+    rho = (16 / 3) / (2 * c1h2 + 16 / 3)
+    for prec, tol in ((pkg.FP64, 1e-17), (pkg.FP32_REFINED, 1e-10)):
+        s = pkg.solver_sweeps(dim, r, prec, tol)
+        assert rho ** s <= tol < rho ** (s - 1)
+
+
+def test_solver_sweeps_not_converged_and_invalid():
+    """MS_ENOTCONV when the tolerance needs more sweeps than the solve kernels hold; the other
+    failures are MS_ECFL (r at the stability limit) and MS_EINVAL."""
+    L = pkg.load()
+    v = ctypes.c_int(7)
+    assert L.ms_solver_sweeps(2, 0.5, pkg.FP32_REFINED, 1e-40, ctypes.byref(v)) == -6
+    assert v.value == 0 and "sweeps" in L.ms_last_error().decode()
+    assert L.ms_solver_sweeps(3, 0.4, pkg.FP32_REFINED, 1e-60, ctypes.byref(v)) == -6
+    assert L.ms_solver_sweeps(2, 0.5, pkg.FP64, 1e-300, ctypes.byref(v)) == -6
+    with pytest.raises(pkg.MaxwellError):
+        pkg.solver_sweeps(2, 0.5, pkg.FP32_REFINED, 1e-40)
+    assert L.ms_solver_sweeps(2, 0.69, pkg.FP64, 1e-10, ctypes.byref(v)) == -2
+    assert L.ms_solver_sweeps(3, 0.57, pkg.FP64, 1e-10, ctypes.byref(v)) == -2
+    for args in ((4, 0.5, 0, 1e-10), (2, 0.5, 3, 1e-10), (2, -0.5, 0, 1e-10), (2, 0.5, 0, 0.0),
+                 (2, 0.5, 0, 1.0), (2, float("nan"), 0, 1e-10)):
+        assert L.ms_solver_sweeps(*args, ctypes.byref(v)) == -1, args
+    assert L.ms_solver_sweeps(2, 0.5, 0, 1e-10, None) == -1

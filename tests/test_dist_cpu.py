@@ -62,19 +62,19 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
 
 
 def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
-    """Rank 0 prints one JSON line with the contract's keys; the oracle loop itself is replaced by
-    a stub here (its timing is what the line reports, not what this test checks)."""
+    """Rank 0 prints one JSON line with the contract's keys; the all-cores oracle run itself is
+    replaced by a stub here (its timing is what the line reports, not what this test checks)."""
     import json
 
     import bench
 
     calls = []
 
-    def fake_rate(n, steps, modes, time_budget=None):
-        calls.append((n, steps))
-        return 1.0e6, steps, 0.5
+    def fake_all(n, steps, modes, budget, procs):
+        calls.append((n, steps, procs))
+        return 1.0e6, n * n * steps * procs, 0.5
 
-    monkeypatch.setattr(bench, "oracle_rate", fake_rate)
+    monkeypatch.setattr(bench, "oracle_all_cores", fake_all)
 
     class A:
         steps, warmup, gpus = 4, 1, 1
@@ -88,7 +88,20 @@ def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] == 1.0e6 and d["steps"] == 4 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == os.cpu_count() and d["cpu_baseline"]["cpu_model"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
-    # one warm-up call, then the timed call, both on the same sample size
+    # one warm-up call, then the timed call, both on the same sample size and every core
     assert [c[1] for c in calls] == [1, 4] and calls[0][0] == calls[1][0]
+    assert all(c[2] == os.cpu_count() for c in calls)
+
+
+def test_oracle_on_every_core_counts_each_process():
+    """The all-cores oracle run: spawned processes each step their own copy of the sample; the
+    reported cell-updates are processes x n^2 x steps."""
+    import bench
+
+    modes = [(1, 2, 1.0)]
+    v, cells, wall = bench.oracle_all_cores(16, 3, modes, None, 2)
+    assert cells == 2 * 16 * 16 * 3
+    assert v > 0 and wall > 0

@@ -80,3 +80,28 @@ def test_mismatch_and_foreign_file_rejected(tmp_path):
     with pkg.Grid(32, 0.5) as g:
         with pytest.raises(pkg.MaxwellError):
             g.load_state(str(bad))
+
+
+@pytest.mark.parametrize("kw", CASES[:2])
+def test_truncated_checkpoint_leaves_the_state_unchanged(kw, tmp_path):
+    """A checkpoint cut short (or with bytes appended) is rejected with MS_EINVAL before any
+    component reaches the device: the grid keeps its fields and step count."""
+    path = str(tmp_path / "state.ckpt")
+    with pkg.Grid(**kw) as g:
+        _init(g)
+        g.run(3)
+        g.save(path)
+    data = open(path, "rb").read()
+    for bad in (data[: len(data) - 5], data[: len(data) // 2], data + b"\0"):
+        bad_path = str(tmp_path / "bad.ckpt")
+        open(bad_path, "wb").write(bad)
+        with pkg.Grid(**kw) as g:
+            g.set_fields(*workloads.random_fields(g.n, seed=11))
+            g.run(2)
+            before = g.get_fields()
+            with pytest.raises(pkg.MaxwellError) as e:
+                g.load_state(bad_path)
+            assert e.value.status == -1
+            assert g.step_count == 2
+            for a, b in zip(g.get_fields(), before):
+                assert np.array_equal(a, b)

@@ -131,3 +131,18 @@ def test_argument_checks():
             assert e.value.status == -1
         g.set_sources_xy(cos_row)
         g.set_sources_xy([])  # removes them
+
+
+def test_fp32_wall_sources_need_five_cells():
+    """FP32_REFINED grids take the wall terms as Pade responses to the line ends, which the PAPER
+    end rows give only for lines of at least four outputs: n = 4 is refused, not run without them."""
+    cos_row = [(2, 0, 1.0, 3.0, 1, 1)]
+    with pkg.Grid(4, 0.5, precision=pkg.FP32_REFINED) as g:
+        with pytest.raises(pkg.MaxwellError) as e:
+            g.set_sources_xy(cos_row)
+        assert e.value.status == -7
+        g.set_sources_xy([(1, 1, 1.0, 3.0, 0, 0)])  # sine rows need no wall terms
+    with pkg.Grid(5, 0.5, precision=pkg.FP32_REFINED) as g:
+        g.set_sources_xy(cos_row)
+    with pkg.Grid(4, 0.5) as g:  # FP64 applies the ghosts directly
+        g.set_sources_xy(cos_row)
