@@ -135,14 +135,14 @@ def test_argument_checks():
 
 def test_fp32_wall_sources_need_five_cells():
     """FP32_REFINED grids take the wall terms as Pade responses to the line ends, which the PAPER
-    end rows give only for lines of at least four outputs: n = 4 is refused, not run without them."""
-    cos_row = [(2, 0, 1.0, 3.0, 1, 1)]
-    with pkg.Grid(4, 0.5, precision=pkg.FP32_REFINED) as g:
+    end rows give only for lines of at least four outputs.  The smallest compact grid already has
+    them (n = 4 is refused at creation, its half-node-to-node lines having three outputs), so
+    n = 5 takes wall sources in both precisions."""
+    for prec in (pkg.FP64, pkg.FP32_REFINED):
         with pytest.raises(pkg.MaxwellError) as e:
+            pkg.Grid(4, 0.5, precision=prec)
+        assert e.value.status == -1
+    cos_row = [(2, 0, 1.0, 3.0, 1, 1)]
+    for prec in (pkg.FP64, pkg.FP32_REFINED):
+        with pkg.Grid(5, 0.5, precision=prec) as g:
             g.set_sources_xy(cos_row)
-        assert e.value.status == -7
-        g.set_sources_xy([(1, 1, 1.0, 3.0, 0, 0)])  # sine rows need no wall terms
-    with pkg.Grid(5, 0.5, precision=pkg.FP32_REFINED) as g:
-        g.set_sources_xy(cos_row)
-    with pkg.Grid(4, 0.5) as g:  # FP64 applies the ghosts directly
-        g.set_sources_xy(cos_row)
