@@ -229,7 +229,7 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
   __syncthreads();
   // 3) band of A^{-1}: lane -> line, warp -> (line half, NSEG segments of SEG outputs)
   const int a = lane + 32 * (warp & 1);
-#pragma unroll 1
+#pragma unroll
   for (int sg = 0; sg < NSEG; ++sg) {
   const int s = (warp >> 1) + (NW / 2) * sg;
   const int rf = r0 + s * SEG;  // first output of this segment
@@ -431,6 +431,27 @@ __device__ __forceinline__ void ff_add_scaled_t(float& hi, float& lo, float x, f
   hi = h2;
 }
 
+// (hi, lo) += (s_hi + s_lo)(x + c) for the last Richardson iterate x and its correction c (|c| is
+// below |x| by the contraction factor except where both are negligible): x + c = s + t by Fast2Sum,
+// then one two-product s_hi s and one two-sum into the pair, with s_lo s and s_hi t folded into the
+// product's error term.  x and c are never rounded into one float, so the correction's low bits
+// reach the state (rounding them away would shrink every increment coherently).
+__device__ __forceinline__ void ff_add_scaled2_t(float& hi, float& lo, float x, float c, float s_hi, float s_lo) {
+  const float s = __fadd_rn(x, c);
+  const float t = __fsub_rn(c, __fsub_rn(s, x));
+  const float p = __fmul_rn(s_hi, s);
+  float e = fmaf(s_hi, s, -p);
+  e = fmaf(s_lo, s, e);
+  e = fmaf(s_hi, t, e);
+  const float u = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(u, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(u, bb)), __fsub_rn(p, bb));
+  const float l = __fadd_rn(lo, __fadd_rn(err, e));
+  const float h2 = __fadd_rn(u, l);
+  lo = __fsub_rn(l, __fsub_rn(h2, u));
+  hi = h2;
+}
+
 // Fill the even ghosts of the Neumann axes from the edge values (only tiles at such an edge).
 __device__ __forceinline__ void fill_ghosts(float* x, int gx0, int gy0, int nx, int ny, bool neu_x, bool neu_y) {
   if (neu_x) {
@@ -495,8 +516,7 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
         const bool unk = !EDGE || (col_unk && gy0 + ly >= 0 && gy0 + ly < ny && interior(bcy, gy0 + ly, ny));
         if (unk) {
           float h = ph_[u], l = pl_[u];
-          ff_add_scaled_t(h, l, x, A.s_hi, A.s_lo);
-          ff_add_scaled_t(h, l, corr, A.s_hi, A.s_lo);
+          ff_add_scaled2_t(h, l, x, corr, A.s_hi, A.s_lo);
           shi[gp + (size_t)(t0 + u) * nx] = h;
           slo[gp + (size_t)(t0 + u) * nx] = l;
         }
@@ -568,6 +588,160 @@ __device__ __forceinline__ void solve_sweeps(const SolveArgs& A, const float* bs
   }
 }
 
+// Interior regions (every point an unknown, no boundary rule anywhere): warp w owns rows
+// FR w .. FR w + FR - 1 of the region and lane l the column pair 2l, 2l + 1.  b and the current
+// iterate of a thread's own points stay in registers; shared memory holds each iterate once for the
+// neighbours, in two planes with a zero pad row above and below and two pad columns on each side
+// (the row pitch keeps every column pair 8-byte aligned for one 64-bit access).  Every sweep updates
+// every region point: after sweep k the points within k of the region's edge are wrong (their outer
+// neighbours are the pads), which never reaches the output tile since k <= S - 1 = H.  The
+// arithmetic per point is that of sweep_column, operation for operation.
+constexpr int FR = RS / NW;           // rows per thread
+constexpr int XP2 = RS + 4;           // row pitch of the interior planes
+constexpr int XPL = (RS + 2) * XP2;   // floats per interior plane
+static_assert(FR * NW == RS && 2 * 32 == RS, "interior solve layout: 16 warps x FR rows, 32 lanes x 2 columns");
+
+__device__ __forceinline__ int xi2(int ly, int lx) { return (ly + 1) * XP2 + lx + 2; }
+
+// One sweep of an interior region.  LAST: add the iterate and its correction to the state at the
+// output points (region rows and columns H .. RS-1-H) instead of writing the next iterate.
+template <bool LAST>
+__device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* xc, float* xn, const float (&bv)[FR][2],
+                                               float (&xv)[FR][2], int r0, int c, float* shi, float* slo, int gp,
+                                               int nx, int H) {
+  // output rows (the same for every lane of the warp) and output columns of the thread
+  float sh[FR][2], sl[FR][2];
+  bool rowok[FR];
+  const bool colok0 = c >= H && c < RS - H, colok1 = c + 1 >= H && c + 1 < RS - H;
+  if constexpr (LAST) {  // the state of the output rows, fetched ahead of the arithmetic (the region
+                         // lies inside the field, so both columns may be read)
+#pragma unroll
+    for (int k = 0; k < FR; ++k) {
+      rowok[k] = r0 + k >= H && r0 + k < RS - H;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        sh[k][j] = rowok[k] ? shi[gp + k * nx + j] : 0.0f;
+        sl[k][j] = rowok[k] ? slo[gp + k * nx + j] : 0.0f;
+      }
+    }
+  }
+  // rows r0-1 .. r0+FR of columns c-1 .. c+2: own rows' pair from registers, the rest from the plane
+  float wl[FR + 2], w0[FR + 2], w1[FR + 2], wr[FR + 2];
+  {
+    const float2 t = *reinterpret_cast<const float2*>(xc + xi2(r0 - 1, c));
+    const float2 u = *reinterpret_cast<const float2*>(xc + xi2(r0 + FR, c));
+    w0[0] = t.x;
+    w1[0] = t.y;
+    w0[FR + 1] = u.x;
+    w1[FR + 1] = u.y;
+  }
+#pragma unroll
+  for (int q = 0; q < FR + 2; ++q) {
+    wl[q] = xc[xi2(r0 - 1 + q, c - 1)];
+    wr[q] = xc[xi2(r0 - 1 + q, c + 2)];
+  }
+#pragma unroll
+  for (int k = 0; k < FR; ++k) {
+    w0[k + 1] = xv[k][0];
+    w1[k + 1] = xv[k][1];
+  }
+  float l0[FR + 2], l1[FR + 2];
+#pragma unroll
+  for (int q = 0; q < FR + 2; ++q) {
+    l0[q] = fmaf(-2.0f, w0[q], wl[q] + w1[q]);
+    l1[q] = fmaf(-2.0f, w1[q], w0[q] + wr[q]);
+  }
+#pragma unroll
+  for (int k = 0; k < FR; ++k) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float* w = j ? w1 : w0;
+      const float* l = j ? l1 : l0;
+      const float x = w[k + 1];
+      const float lyv = fmaf(-2.0f, x, w[k] + w[k + 2]);
+      const float lxly = fmaf(-2.0f, l[k + 1], l[k] + l[k + 2]);
+      const float rest = fmaf(-6.0f, l[k + 1] + lyv, -lxly);
+      const float ph = __fmul_rn(A.d_hi, x);
+      const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
+      const float res = __fsub_rn(__fsub_rn(bv[k][j], ph), pl) - rest;
+      const float corr = A.omega * res;
+      if constexpr (LAST) {
+        if (rowok[k]) {
+          float h = sh[k][j], lo = sl[k][j];
+          ff_add_scaled2_t(h, lo, x, corr, A.s_hi, A.s_lo);
+          if (j ? colok1 : colok0) {
+            shi[gp + k * nx + j] = h;
+            slo[gp + k * nx + j] = lo;
+          }
+        }
+      } else {
+        xv[k][j] = x + corr;
+      }
+    }
+  }
+  if constexpr (!LAST) {
+#pragma unroll
+    for (int k = 0; k < FR; ++k) *reinterpret_cast<float2*>(xn + xi2(r0 + k, c)) = make_float2(xv[k][0], xv[k][1]);
+  }
+}
+
+// Zero pads of both interior planes: rows -1 and RS, columns -2, -1, RS, RS+1.
+__device__ __forceinline__ void zero_pads(float* xa, float* xb) {
+  for (int t = threadIdx.x; t < 2 * XP2 + 4 * RS; t += NT) {
+    int idx;
+    if (t < XP2) {
+      idx = t;
+    } else if (t < 2 * XP2) {
+      idx = (RS + 1) * XP2 + (t - XP2);
+    } else {
+      const int q = t - 2 * XP2, e = q & 3;
+      idx = xi2(q >> 2, e < 2 ? e - 2 : RS + e - 2);
+    }
+    xa[idx] = 0.0f;
+    xb[idx] = 0.0f;
+  }
+}
+
+// The whole solve of an interior region with origin (gx0, gy0) in the field (S >= 2).
+__device__ __forceinline__ void solve_interior(const SolveArgs& A, const float* __restrict__ b, float* shi, float* slo,
+                                               int nx, int gx0, int gy0) {
+  extern __shared__ float sm[];
+  float* xa = sm;
+  float* xb = sm + XPL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = 2 * lane, r0 = FR * warp;
+  zero_pads(xa, xb);
+  // 32-bit offsets from the region's first own point (planes hold fewer than 2^31 points)
+  const size_t base = (size_t)(gy0 + r0) * nx + (gx0 + c);
+  const float* bp = b + base;
+  float bv[FR][2], xv[FR][2];
+#pragma unroll
+  for (int k = 0; k < FR; ++k) {
+    bv[k][0] = bp[k * nx];
+    bv[k][1] = bp[k * nx + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < FR; ++k) {
+    xv[k][0] = A.omega * bv[k][0];
+    xv[k][1] = A.omega * bv[k][1];
+    *reinterpret_cast<float2*>(xa + xi2(r0 + k, c)) = make_float2(xv[k][0], xv[k][1]);
+  }
+  __syncthreads();
+  float* const shb = shi + base;
+  float* const slb = slo + base;
+  const int H = A.S - 1;
+  float* xc = xa;
+  float* xn = xb;
+  for (int k = 1; k < A.S - 1; ++k) {
+    interior_sweep<false>(A, xc, xn, bv, xv, r0, c, shb, slb, 0, nx, H);
+    __syncthreads();
+    float* t = xc;
+    xc = xn;
+    xn = t;
+  }
+  interior_sweep<true>(A, xc, xn, bv, xv, r0, c, shb, slb, 0, nx, H);
+}
+
 // Region of RS x RS points = output tile (RS - 2H)^2 plus an H-cell halo, H = S - 1.  Warp w owns
 // columns 32 (w & 1) .. +31 and row strip w >> 1 of every sweep, so no warp straddles strips.
 __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, int tby) {
@@ -587,6 +761,10 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
   const int gx0 = tx0 - H, gy0 = ty0 - H;
   // interior tile: the region holds only unknowns, so no boundary tests and no ghosts
   const bool edge = !(gx0 >= 1 && gy0 >= 1 && gx0 + RS <= nx - 1 && gy0 + RS <= ny - 1);
+  if (!edge && A.S >= 2) {
+    solve_interior(A, b, shi, slo, nx, gx0, gy0);
+    return;
+  }
   const bool neu_x = edge && bcx == NEU, neu_y = edge && bcy == NEU;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // b and the first iterate x1 = omega b (0 off the unknowns)
@@ -631,10 +809,12 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
   }
 }
 
-__global__ void __launch_bounds__(NT, 3) k_solve_tile(SolveArgs A) { solve_body(A, blockIdx.z, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT, 2) k_solve_tile(SolveArgs A) { solve_body(A, blockIdx.z, blockIdx.x, blockIdx.y); }
+
+
 
 // Batched form: block b solves tile work[3b+2] of field slot work[3b+1] of cavity work[3b].
-__global__ void __launch_bounds__(NT, 3) k_solve_batch(const SolveArgs* __restrict__ args, const int* __restrict__ work) {
+__global__ void __launch_bounds__(NT, 2) k_solve_batch(const SolveArgs* __restrict__ args, const int* __restrict__ work) {
   __shared__ SolveArgs sA;
   const int cav = work[3 * blockIdx.x], f = work[3 * blockIdx.x + 1], t = work[3 * blockIdx.x + 2];
   copy_args(&sA, args + cav);
@@ -712,7 +892,10 @@ static SolveArgs make_solve(const ms_grid* g, int nfields, const int* fields, co
 }
 
 size_t tiled_curl_smem() { return sizeof(float) * (size_t)(XROWS * XLP + TB * DLP + TB * YSP); }
-size_t tiled_solve_smem() { return sizeof(float) * (size_t)(3 * RS * RSP); }
+size_t tiled_solve_smem() {
+  static_assert(2 * XPL <= 3 * RS * RSP, "interior planes fit in the edge path's shared memory");
+  return sizeof(float) * (size_t)(3 * RS * RSP);
+}
 
 int tiled_configure() {
   const int cs = (int)tiled_curl_smem(), ss = (int)tiled_solve_smem();
