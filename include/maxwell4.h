@@ -266,6 +266,28 @@ ms_status ms_p1_solve_static(int n, double r, int field, const double* b, double
  * status.  Needs no GPU. */
 ms_status ms_solver_sweeps(int dim, double r, int precision, double tol, int* sweeps);
 
+/* P1 solver of a grid.  MS_SOLVER_RICHARDSON (every grid's default): Richardson sweeps of the 9- or
+ * 19-point operator, their count fixed by the spectral bound of App. A.2 (ms_solver_sweeps).
+ * MS_SOLVER_TRANSFORM_TC (3D FP32_REFINED grids only): the separable solve.  Every 1D operator of P1
+ * (Def. "def:operatorsP") is a Kronecker lift of D_2 (App. A.1), diagonalised per axis by the
+ * orthonormal sine transform (Dirichlet axes) or cosine transform (Neumann axes with even ghosts,
+ * Table "tab:bc"), so P1^{-1} is three transforms, a division by the eigenvalues and three inverse
+ * transforms.  Each transform is a dense GEMM on the tensor cores (bf16 operands split hi + lo, three
+ * products, FP32 accumulation in tensor memory), and the result is refined by Richardson sweeps
+ * with the exact residual until the App. A.2 bound reaches the Richardson path's tolerance.
+ *   ms_set_solver: MS_EINVAL for an unknown solver, MS_EUNSUPPORTED for the transform solver on
+ *     other grids, MS_ENOMEM / MS_ECUDA if its set-up (two padded working copies of a component,
+ *     transform matrices) fails.  The first selection allocates; a selection drops the captured
+ *     step graphs.  Synchronises the grid's stream.
+ *   ms_transform_solve3: x ~ (6 h^2 P1)^{-1} b for component comp (0..5) of a 3D FP32_REFINED grid by
+ *     the transforms alone, without refinement; b and x are distinct device FP32 arrays in the
+ *     component's full layout (wall points of x are set to zero).  Asynchronous on the grid's stream.
+ * A transform kernel whose bounded wait for its tensor-core work gives up records it; the next
+ * ms_sync of the grid returns MS_ETIMEOUT (and clears the record). */
+typedef enum { MS_SOLVER_RICHARDSON = 0, MS_SOLVER_TRANSFORM_TC = 1 } ms_solver;
+ms_status ms_set_solver(ms_grid* g, int solver);
+ms_status ms_transform_solve3(ms_grid* g, int comp, const float* b, float* x);
+
 /* Number of kernel launches one ms_step issues (for launch accounting). */
 ms_status ms_launches_per_step(ms_grid* g, int* launches);
 

@@ -22,6 +22,7 @@ __all__ = ["Grid", "Batch", "MaxwellError", "load", "lib_path", "FP64", "FP32_RE
 FP64, FP32_REFINED = 0, 1
 CLOSURE_PAPER, CLOSURE_REFLECT = 0, 1
 SCHEME_C4, SCHEME_YEE2, SCHEME_NC4, SCHEME_C4_DE = 0, 1, 2, 3
+SOLVER_RICHARDSON, SOLVER_TRANSFORM_TC = 0, 1
 OPS = {
     "filter_ez": 0, "filter_hx": 1, "filter_hy": 2, "curl_he": 3, "curl_eh": 4,
     "p1_ez": 5, "p1_hx": 6, "p1_hy": 7, "p1solve_ez": 8, "p1solve_hx": 9, "p1solve_hy": 10,
@@ -98,6 +99,8 @@ def load() -> ctypes.CDLL:
             "ms_launches_per_step": [V, ctypes.POINTER(I)],
             "ms_stability_limit": [I, PD],
             "ms_solver_sweeps": [I, D, I, D, ctypes.POINTER(I)],
+            "ms_set_solver": [V, I],
+            "ms_transform_solve3": [V, I, V, V],
             "ms_create_batch": [ctypes.POINTER(_Desc), ctypes.POINTER(I), I, ctypes.POINTER(V)],
             "ms_batch_destroy": [V],
             "ms_batch_init_modes": [V, I, ctypes.POINTER(_Mode), I],
@@ -333,6 +336,16 @@ class Grid:
         fn = load().ms_error_vs_exact3 if self.dim == 3 else load().ms_error_vs_exact
         _check(fn(self._h, arr, nm, *[ctypes.byref(v) for v in out]))
         return tuple(v.value for v in out)
+
+    def set_solver(self, solver: int):
+        """Select the P1 solver (SOLVER_RICHARDSON, or SOLVER_TRANSFORM_TC on 3D FP32_REFINED grids)."""
+        _check(load().ms_set_solver(self._h, int(solver)))
+
+    def transform_solve(self, comp: int, b, x):
+        """x ~ (6 h^2 P1)^{-1} b by the tensor-core transforms alone (device float32 tensors in the
+        component's layout), asynchronous on the grid's stream."""
+        _check(load().ms_transform_solve3(self._h, int(comp), ctypes.c_void_p(b.data_ptr()),
+                                           ctypes.c_void_p(x.data_ptr())))
 
     def step_profiled(self, cap: int = 512):
         """One step with an event after every launch: list of (kernel kind, ms, algorithmic bytes)."""

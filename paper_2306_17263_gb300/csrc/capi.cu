@@ -413,7 +413,7 @@ void prof_mark(ms_grid* g, int kind, double bytes) {
 const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64", "curl32", "solve32",
                                         "filter3d64", "pade3d64", "sweep3d64", "dfilt3d32", "band3d32",
-                                        "sweep3d32", "nc64", "source", "term3d32"};
+                                        "sweep3d32", "nc64", "source", "term3d32", "tsgemm", "tspack"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }
 
@@ -737,7 +737,30 @@ ms_status ms_run(ms_grid* g, long nsteps) {
 ms_status ms_sync(ms_grid* g) {
   if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
   MS_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->g3) return transform_status3d(g);
   return MS_OK;
+}
+
+ms_status ms_set_solver(ms_grid* g, int solver) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (solver != MS_SOLVER_RICHARDSON && solver != MS_SOLVER_TRANSFORM_TC) return fail(MS_EINVAL, "unknown solver");
+  if (solver == MS_SOLVER_TRANSFORM_TC && (!g->g3 || g->desc.precision != MS_FP32_REFINED))
+    return fail(MS_EUNSUPPORTED, "the transform solver is implemented for 3D FP32_REFINED grids");
+  if (!g->g3) return MS_OK;
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  MS_TRY(set_solver3d(g, solver));
+  free_graph(&g->graph1);  // captured steps hold the previous solver's launches
+  free_graph(&g->graphk);
+  g->launches_per_step = 0;
+  return MS_OK;
+}
+
+ms_status ms_transform_solve3(ms_grid* g, int comp, const float* b, float* x) {
+  if (!valid_grid(g) || !b || !x) return fail(MS_EINVAL, "invalid argument");
+  if (!g->g3 || g->desc.precision != MS_FP32_REFINED)
+    return fail(MS_EUNSUPPORTED, "the transform solver is implemented for 3D FP32_REFINED grids");
+  if (comp < 0 || comp > 5) return fail(MS_EINVAL, "comp must be in [0, 5]");
+  return transform_solve3d(g, comp, b, x);
 }
 
 ms_status ms_get_step(ms_grid* g, long* step) {

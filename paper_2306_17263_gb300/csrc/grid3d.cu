@@ -23,6 +23,7 @@
 #include "grid3d.cuh"
 #include "k_fp64.cuh"
 #include "k_tiled.cuh"
+#include "k_transform.cuh"
 
 namespace ms {
 
@@ -45,6 +46,9 @@ struct Grid3D {
   float* s32[4] = {};   // FP32: differences, R, sweep ping-pong [2]
   double* dview[6] = {};  // FP32_REFINED grids: FP64 copy of the state for the diagnostics
   size_t nmax = 0;      // points of the largest component
+  int solver = MS_SOLVER_RICHARDSON;  // FP32_REFINED: P1 solve by Richardson sweeps or by transforms
+  TransformSolver* ts = nullptr;       // made when the transform solver is first selected
+  int ts_sweeps = 0;                   // refinement sweeps after a transform solve
 };
 
 namespace {
@@ -881,8 +885,36 @@ int term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, flo
   return 2;
 }
 
+// Transform solve (tensor cores) of component c followed by ts_sweeps Richardson sweeps with the
+// exact residual, the last of which updates the state.
+void solve3d32_ts(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_hi, float s_lo, int* nl) {
+  Grid3D* G3 = g->g3;
+  const Shape3& s = G3->sh[c];
+  const float* b = G3->s32[1];
+  float* buf[2] = {G3->s32[2], G3->s32[3]};
+  *nl += ts_solve(*G3->ts, s, b, buf[0], 6.0f * (float)(g->c1 * g->h * g->h), g->stream, g);
+  const dim3 grd = sweep_grid3(s), blk(SWX, SWY, 1);
+  const int R = G3->ts_sweeps;
+  for (int k = 0; k < R; ++k) {
+    const float* xin = buf[k & 1];
+    float* xo = buf[(k + 1) & 1];
+    if (k == R - 1)
+      k_sweep3d32<false, true><<<grd, blk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, G3->hi[c], G3->lo[c],
+                                                           s_hi, s_lo);
+    else
+      k_sweep3d32<false, false><<<grd, blk, 0, g->stream>>>(b, xin, xo, s, d_hi, d_lo, omega, G3->hi[c], G3->lo[c],
+                                                            s_hi, s_lo);
+    prof_mark(g, KK_SWEEP3D32, 4.0 * (double)s.size() * (2.0 + (k == R - 1 ? 4.0 : 1.0)));
+  }
+  *nl += R;
+}
+
 void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_hi, float s_lo, int S, int* nl) {
   Grid3D* G3 = g->g3;
+  if (G3->solver == MS_SOLVER_TRANSFORM_TC) {
+    solve3d32_ts(g, c, d_hi, d_lo, omega, s_hi, s_lo, nl);
+    return;
+  }
   const Shape3& s = G3->sh[c];
   const float* b = G3->s32[1];
   float* buf[2] = {G3->s32[2], G3->s32[3]};
@@ -1183,9 +1215,69 @@ ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
   return MS_OK;
 }
 
+// Accuracy of one transform solve relative to the solution (bf16 three-product split: about 16
+// correct bits per pass over six passes, measured at up to 2e-5 on random data), which fixes the
+// refinement sweeps: ts_accuracy * rho^R <= 1e-10, the target of the Richardson solve.
+constexpr double kTsAccuracy = 5e-5;
+
+ms_status set_solver3d(ms_grid* g, int solver) {
+  Grid3D* G3 = g->g3;
+  if (solver == MS_SOLVER_RICHARDSON) {
+    G3->solver = solver;
+    return MS_OK;
+  }
+  if (!G3->ts) {
+    G3->ts = new TransformSolver();
+    std::string err;
+    const int rc = ts_setup(g->N, G3->ts, &err);
+    if (rc != 0) {
+      ts_free(G3->ts);
+      delete G3->ts;
+      G3->ts = nullptr;
+      return fail3(rc == -2 ? MS_ENOMEM : MS_ECUDA, err);
+    }
+  }
+  int R = 0;
+  MS3_TRY(ms_solver_sweeps(3, g->desc.r, MS_FP32_REFINED, 1e-10 / kTsAccuracy, &R));
+  G3->ts_sweeps = R;
+  G3->solver = solver;
+  return MS_OK;
+}
+
+ms_status transform_solve3d(ms_grid* g, int c, const float* b, float* x) {
+  Grid3D* G3 = g->g3;
+  if (!G3->ts) {  // set the solver up without selecting it
+    const int keep = G3->solver;
+    MS3_TRY(set_solver3d(g, MS_SOLVER_TRANSFORM_TC));
+    G3->solver = keep;
+  }
+  ts_solve(*G3->ts, G3->sh[c], b, x, 6.0f * (float)(g->c1 * g->h * g->h), g->stream, g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail3(MS_ECUDA, std::string("transform solve: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+ms_status transform_status3d(ms_grid* g) {
+  Grid3D* G3 = g->g3;
+  if (!G3 || !G3->ts) return MS_OK;
+  int flag = 0;
+  if (cudaMemcpy(&flag, G3->ts->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail3(MS_ECUDA, "reading the transform solver's status failed");
+  if (flag) {
+    cudaMemset(G3->ts->d_err, 0, sizeof(int));
+    return fail3(MS_ETIMEOUT, "a transform GEMM gave up waiting for its tensor-core MMAs; its output is invalid");
+  }
+  return MS_OK;
+}
+
 void destroy_grid3d(ms_grid* g) {
   Grid3D* G3 = g->g3;
   if (!G3) return;
+  if (G3->ts) {
+    ts_free(G3->ts);
+    delete G3->ts;
+    G3->ts = nullptr;
+  }
   for (int c = 0; c < 6; ++c) {
     cudaFree(G3->f64[c]);
     cudaFree(G3->hi[c]);

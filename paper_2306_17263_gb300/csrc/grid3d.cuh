@@ -30,6 +30,13 @@ double stability_limit_3d();
 // the norm of the Pade divergence of H on the cell centres.
 ms_status energy3d(ms_grid* g, double* W);
 ms_status divergence3d(ms_grid* g, double* norm);
+// P1 solver of a 3D FP32_REFINED grid (MS_SOLVER_*); the transform solver's set-up happens on its
+// first selection.  transform_solve3d: x ~ (6 h^2 P1)^{-1} b for component c by the transforms alone
+// (device FP32 arrays in the component's layout).  transform_status3d: MS_ETIMEOUT if a transform
+// kernel gave up a bounded wait since the last check.
+ms_status set_solver3d(ms_grid* g, int solver);
+ms_status transform_solve3d(ms_grid* g, int c, const float* b, float* x);
+ms_status transform_status3d(ms_grid* g);
 // Device arrays of the state of a 3D grid: component c has n[c] points in f64[c] (MS_FP64) or in
 // hi[c] + lo[c] (MS_FP32_REFINED; the other pointers are NULL).  Returns the component count (6).
 int state_arrays3d(ms_grid* g, double** f64, float** hi, float** lo, size_t* n);
