@@ -146,12 +146,21 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def bf16_peak():
+    """Dense bf16 tensor peak of the pod (burst), TFLOP/s; the recipe's fallback if unmeasured."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 # source files that define each kernel kind reported by ms_step_profiled
 KIND_SOURCES = {
     "curl32": ["k_tiled.cu", "k_tiled.cuh"], "solve32": ["k_tiled.cu", "k_tiled.cuh"],
     "filter64": ["k_fp64.cu", "k_fp64.cuh"], "pade64": ["k_fp64.cu", "k_fp64.cuh"],
     "dfilt3d32": ["grid3d.cu", "grid3d.cuh"], "band3d32": ["grid3d.cu", "grid3d.cuh"],
-    "term3d32": ["grid3d.cu", "grid3d.cuh"],
+    "term3d32": ["grid3d.cu", "grid3d.cuh"], "tsgemm": ["k_transform.cu", "k_transform.cuh"],
     "sweep3d32": ["grid3d.cu", "grid3d.cuh"],
     "p1sweep64": ["k_fp64.cu", "k_fp64.cuh"], "yee64": ["k_fp64.cu", "k_fp64.cuh"],
 }
@@ -425,9 +434,13 @@ def leg_3d(pkg, torch, steps32=None, with_fp64=True):
     n, r, modes, K = c["n"], c["r"], c["modes"], c["steps"]
     out = {"workload": "3D PEC cube 256^3 cells, modes (2,3,1) + one seeded mode (indices in [1,16]), r=0.4",
            "unit": "cell-updates/s", "l2": "state 0.8 GB > L2; no flush"}
-    legs = [(pkg.FP32_REFINED, steps32 or K, "fp32_refined")] + ([(pkg.FP64, 20, "fp64")] if with_fp64 else [])
-    for prec, steps, key in legs:
+    legs = [(pkg.FP32_REFINED, steps32 or K, "fp32_refined", pkg.SOLVER_RICHARDSON),
+            (pkg.FP32_REFINED, min(steps32 or K, 50), "fp32_refined_transform_tc", pkg.SOLVER_TRANSFORM_TC)]
+    legs += [(pkg.FP64, 20, "fp64", pkg.SOLVER_RICHARDSON)] if with_fp64 else []
+    for prec, steps, key, solver in legs:
         g = pkg.Grid(n, r, precision=prec, dim=3, stream="torch")
+        if solver != pkg.SOLVER_RICHARDSON:
+            g.set_solver(solver)
         g.init_modes(modes)
         for _ in range(3):
             g.step_profiled()
@@ -444,7 +457,18 @@ def leg_3d(pkg, torch, steps32=None, with_fp64=True):
         kinds = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / total, "GBps": v[2] / (v[1] * 1e-3) / 1e9}
                  for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])}
         out[key] = {"steps": steps, "ms_per_step": total / steps, "value": n ** 3 * steps / (total * 1e-3),
-                    "l2_abs": l2_abs, "l2_rel": l2_rel, "launches_per_step": g.launches_per_step, "kernels": kinds}
+                    "l2_abs": l2_abs, "l2_rel": l2_rel, "launches_per_step": g.launches_per_step, "kernels": kinds,
+                    "step_roofline": {"bytes_per_step": 96.0 * n ** 3,
+                                      "achieved_GBps": 96.0 * n ** 3 / (total / steps * 1e-3) / 1e9,
+                                      "bytes": "96 B per cell-update (6 components, hi+lo, read + write)"}}
+        if "tsgemm" in per:
+            P = -(-n // 128) * 128
+            cnt, ms_tot = per["tsgemm"][0], per["tsgemm"][1]
+            flops = 6.0 * P ** 4  # three bf16 products of a P x P transform over P^3 points
+            tflops = flops / (ms_tot / cnt * 1e-3) / 1e12
+            out[key]["tensor"] = {"kernel": "tsgemm", "flop_per_launch": flops, "avg_launch_ms": ms_tot / cnt,
+                                  "achieved_tflops": tflops, "peak_tflops": bf16_peak(), "frac": tflops / bf16_peak(),
+                                  "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
         g.close()
     return out
 

@@ -37,7 +37,8 @@ constexpr int LBO = 128;                  // bytes between core matrices adjacen
 constexpr int SBO = (KC / 8) * 128;       // bytes between core matrices adjacent in M / N
 constexpr int TILE_BYTES = TM * KC * 2;   // one bf16 operand piece of a stage (TN == TM)
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A hi, A lo, B hi, B lo
-constexpr int GT = 256;                   // threads per CTA
+constexpr int GT = 512;                   // threads per CTA
+constexpr int ITEMS = (TN * KC / 8) / GT; // B items (8 consecutive k of one column) per thread and chunk
 constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;  // two stages, plus alignment slack
 constexpr int kWaitTries = 1 << 20;       // bound of every mbarrier wait
 static_assert(TN == TM, "operand pieces share one size");
@@ -74,6 +75,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
   }
   return done != 0;
+}
+
+// 16-byte asynchronous copy global -> shared (completion by cp.async.wait_all).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
 // Eight FP32 values to their bf16 hi parts and the bf16 rounding of the remainders.
@@ -132,51 +138,67 @@ __global__ void __launch_bounds__(GT, 1) k_ts_gemm(TsPass p) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
+  // B item q of a chunk: column j and k group kg, placed so that eight consecutive threads write
+  // one contiguous 128-byte run of a core-matrix column
+  auto item = [&](int q, int& j, int& kg) {
+    if (p.sk == 1) {
+      j = (q >> 6) * 8 + (q & 7);
+      kg = (q >> 3) & 7;
+    } else {
+      j = q & (TN - 1);
+      kg = q / TN;
+    }
+  };
+  // global loads of the B items of chunk c into registers
+  auto load_b = [&](int c, float (&v)[ITEMS][8]) {
+    const int k0 = c * KC;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      int j, kg;
+      item(tid + GT * i, j, kg);
+      if (p.sk == 1) {  // k contiguous: two 16-byte loads
+        const float4* src = reinterpret_cast<const float4*>(inb + (long long)j * p.sn0 + k0 + kg * 8);
+        const float4 a = src[0], b = src[1];
+        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
+        v[i][4] = b.x; v[i][5] = b.y; v[i][6] = b.z; v[i][7] = b.w;
+      } else {  // columns contiguous: a warp reads 32 consecutive columns of each k
+        const float* src = inb + (long long)(k0 + kg * 8) * p.sk + j;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[i][e] = src[(long long)e * p.sk];
+      }
+    }
+  };
   bool ok = true;
   int committed = 0;  // chunks whose MMAs were issued and committed
+  float vb[ITEMS][8];
+  load_b(0, vb);
   for (int c = 0; c < p.nkc; ++c) {
     const int s = c & 1;
     unsigned char* const st = sm + s * STAGE_BYTES;
     if (c >= 2) ok = mbar_wait(&mbar[s], ((c - 2) >> 1) & 1);  // the MMAs that last read this stage
     ok = __syncthreads_and(ok);  // one decision for the whole block
     if (!ok) break;
-    // A: the transform matrix block, already in the operand layout
+    // A: the transform matrix block, already in the operand layout, copied asynchronously
     const uint4* qh = p.qhi + (size_t)(mt * p.nkc + c) * (TILE_BYTES / 16);
     const uint4* ql = p.qlo + (size_t)(mt * p.nkc + c) * (TILE_BYTES / 16);
-    uint4* const sah = reinterpret_cast<uint4*>(st);
-    uint4* const sal = reinterpret_cast<uint4*>(st + TILE_BYTES);
 #pragma unroll
     for (int i = tid; i < TILE_BYTES / 16; i += GT) {
-      sah[i] = qh[i];
-      sal[i] = ql[i];
+      cp_async16(st + 16 * i, qh + i);
+      cp_async16(st + TILE_BYTES + 16 * i, ql + i);
     }
-    // B: 8 consecutive k of one data column per item, split into bf16 hi / lo core-matrix rows
-    const int k0 = c * KC;
+    // B of this chunk (in registers) split into bf16 hi / lo core-matrix rows
 #pragma unroll
-    for (int i = 0; i < (TN * KC / 8) / GT; ++i) {
-      const int q = tid + GT * i;
+    for (int i = 0; i < ITEMS; ++i) {
       int j, kg;
-      float v[8];
-      if (p.sk == 1) {  // k contiguous: eight lanes take eight columns of one k group
-        j = (q >> 6) * 8 + (q & 7);
-        kg = (q >> 3) & 7;
-        const float4* src = reinterpret_cast<const float4*>(inb + (long long)j * p.sn0 + k0 + kg * 8);
-        const float4 a = src[0], b = src[1];
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-      } else {  // columns contiguous: a warp reads 32 consecutive columns of each k
-        j = q & (TN - 1);
-        kg = q / TN;
-        const float* src = inb + (long long)(k0 + kg * 8) * p.sk + j;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = src[(long long)e * p.sk];
-      }
+      item(tid + GT * i, j, kg);
       uint4 hi, lo;
-      split8(v, hi, lo);
+      split8(vb[i], hi, lo);
       const int off = cm_off(j, kg * 8);
       *reinterpret_cast<uint4*>(st + 2 * TILE_BYTES + off) = hi;
       *reinterpret_cast<uint4*>(st + 3 * TILE_BYTES + off) = lo;
     }
+    if (c + 1 < p.nkc) load_b(c + 1, vb);  // in flight during the MMAs of this chunk
+    asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -208,9 +230,9 @@ __global__ void __launch_bounds__(GT, 1) k_ts_gemm(TsPass p) {
     if (tid == 0) atomicExch(p.err, 1);
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // warp w: tensor-memory lanes (rows) 32 (w % 4) .., columns 64 (w / 4) .. + 63
+    // warp w: tensor-memory lanes (rows) 32 (w % 4) .., columns 32 (w / 4) .. + 31
     const int m = mt * TM + 32 * (warp & 3) + lane;
-    const int jb = 64 * (warp >> 2);
+    const int jb = 32 * (warp >> 2);
     float* const outb = p.out + (long long)m * p.sk + n1 * p.sn1 + n0b * p.sn0;
     float mum = 0.0f, mu1 = 0.0f;
     if (p.mu_m) {
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(GT, 1) k_ts_gemm(TsPass p) {
       mu1 = p.mu_1[n1];
     }
 #pragma unroll
-    for (int cc = 0; cc < 64; cc += 16) {
+    for (int cc = 0; cc < 32; cc += 16) {
       uint32_t r[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
