@@ -404,6 +404,36 @@ ms_status ms_batch_error_vs_exact(ms_batch* b, int cavity, const ms_mode* modes,
 /* count: cavities; cells: sum of n[b]^2 (Yee cells advanced per step); launches: kernels per step. */
 ms_status ms_batch_info(ms_batch* b, int* count, long long* cells, int* launches);
 
+/* Launch plan of a batch: plan[0] = work-list order (0: cavity by cavity, tiles row by row; 1: the
+ * boundary-ring tiles of every cavity first, since they take the general and slower paths; 2:
+ * largest cavities first), plan[1] = steps per captured graph in ms_batch_run (1..256), plan[2] = 1
+ * for persistent launches (as many blocks as are resident at once, each striding over the work
+ * list), 0 for one block per work item.  Every plan runs exactly the same arithmetic per cavity;
+ * only the order and the launch shape change.  The default is {0, 16, 0}.  ms_batch_set_plan drops
+ * the captured graphs (MS_EINVAL for an invalid plan).
+ *
+ * ms_batch_autotune: chooses the plan by measurement.  Candidates: orders 0..2 x 8 or 32 steps per
+ * graph x persistent or not; each is captured and timed with CUDA events over about trial_steps
+ * steps (1..4096), and the fastest per step is applied.  The trials step the batch's current state,
+ * so the call must come before any cavity's fields are set (the state is then zero and stays zero;
+ * MS_EINVAL otherwise); step counters are not advanced.  The choice is cached under a key of the
+ * cavity sizes, r, Z, closure and the device (SM count and name): in memory for the process, and
+ * appended to the file named by the environment variable MS_AUTOTUNE_CACHE if it is set, so a later
+ * process with the same key reuses it without trials.  plan (3 ints, may be NULL) receives the
+ * applied plan, *from_cache (may be NULL) whether it came from the cache.  Synchronous.
+ *
+ * The cache itself (host only, no GPU needed): keys of 1..512 characters from [A-Za-z0-9:;._-=,];
+ * ms_autotune_cache_get sets *found and, if found, plan (memory first, then the cache file, whose
+ * last line for a key wins); ms_autotune_cache_put stores a valid plan in memory and appends it to
+ * the file (MS_EINVAL if the file cannot be written); ms_autotune_cache_clear empties the memory
+ * copy (the file stays). */
+ms_status ms_batch_set_plan(ms_batch* b, const int* plan);
+ms_status ms_batch_get_plan(ms_batch* b, int* plan);
+ms_status ms_batch_autotune(ms_batch* b, int trial_steps, int* plan, int* from_cache);
+ms_status ms_autotune_cache_get(const char* key, int* plan, int* found);
+ms_status ms_autotune_cache_put(const char* key, const int* plan);
+ms_status ms_autotune_cache_clear(void);
+
 /* Checkpoint / resume (the paper has none).  ms_save writes the grid's state (the fields in their
  * working representation: FP64 arrays, or the exact FP32 hi and lo arrays of MS_FP32_REFINED, plus
  * the tracked Delta E_z of MS_SCHEME_C4_DE), its step counter and its descriptor to `path`;

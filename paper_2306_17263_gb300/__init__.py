@@ -100,6 +100,12 @@ def load() -> ctypes.CDLL:
             "ms_stability_limit": [I, PD],
             "ms_solver_sweeps": [I, D, I, D, ctypes.POINTER(I)],
             "ms_set_solver": [V, I],
+            "ms_batch_set_plan": [V, ctypes.POINTER(I)],
+            "ms_batch_get_plan": [V, ctypes.POINTER(I)],
+            "ms_batch_autotune": [V, I, ctypes.POINTER(I), ctypes.POINTER(I)],
+            "ms_autotune_cache_get": [ctypes.c_char_p, ctypes.POINTER(I), ctypes.POINTER(I)],
+            "ms_autotune_cache_put": [ctypes.c_char_p, ctypes.POINTER(I)],
+            "ms_autotune_cache_clear": [],
             "ms_transform_solve3": [V, I, V, V],
             "ms_create_batch": [ctypes.POINTER(_Desc), ctypes.POINTER(I), I, ctypes.POINTER(V)],
             "ms_batch_destroy": [V],
@@ -181,6 +187,24 @@ def _sources_xy(src):
 
 def _ptrs(ptrs):
     return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+
+
+def autotune_cache_get(key: str):
+    """Cached launch plan of `key` (memory, then the MS_AUTOTUNE_CACHE file), or None; no GPU."""
+    p = (ctypes.c_int * 3)()
+    found = ctypes.c_int()
+    _check(load().ms_autotune_cache_get(key.encode(), p, ctypes.byref(found)))
+    return tuple(p) if found.value else None
+
+
+def autotune_cache_put(key: str, plan):
+    """Store a launch plan in the cache (and append it to the MS_AUTOTUNE_CACHE file); no GPU."""
+    _check(load().ms_autotune_cache_put(key.encode(), (ctypes.c_int * 3)(*[int(v) for v in plan])))
+
+
+def autotune_cache_clear():
+    """Forget the in-memory cache (the file stays); no GPU."""
+    _check(load().ms_autotune_cache_clear())
 
 
 def stability_limit(dim: int = 2) -> float:
@@ -511,6 +535,23 @@ class Batch:
 
     def sync(self):
         _check(load().ms_batch_sync(self._h))
+
+    def set_plan(self, order: int, chunk: int, persistent: int):
+        """Launch plan: work-list order (0, 1, 2), steps per captured graph, persistent launches."""
+        _check(load().ms_batch_set_plan(self._h, (ctypes.c_int * 3)(int(order), int(chunk), int(persistent))))
+
+    def plan(self):
+        p = (ctypes.c_int * 3)()
+        _check(load().ms_batch_get_plan(self._h, p))
+        return tuple(p)
+
+    def autotune(self, trial_steps: int = 16):
+        """Choose the launch plan by timing the candidates (before any fields are set); returns
+        (plan, from_cache)."""
+        p = (ctypes.c_int * 3)()
+        hit = ctypes.c_int()
+        _check(load().ms_batch_autotune(self._h, int(trial_steps), p, ctypes.byref(hit)))
+        return tuple(p), bool(hit.value)
 
     def error_vs_exact(self, cavity: int, modes):
         arr, nm = _modes(modes)

@@ -1,8 +1,13 @@
 // C ABI of include/maxwell4.h: grid life cycle, the time step (Sec. 3.4 Step 1 / Step 2),
 // graph-captured time loop, diagnostics and operator-level entry points.
+#include <array>
+#include <cctype>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1093,6 +1098,8 @@ struct ms_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   long long cells = 0;
+  int plan[3] = {0, 16, 0};  // work-list order, steps per captured graph, persistent launches
+  bool touched = false;      // some cavity's fields were set (the state may be nonzero)
 };
 
 namespace {
@@ -1107,8 +1114,77 @@ ms_status batch_cavity(ms_batch* b, int cavity, ms_grid** g) {
 }
 
 ms_status batch_step_launch(ms_batch* b) {
-  tiled_batch_step(b->tb, b->stream);
+  tiled_batch_step(b->tb, b->stream, b->plan[2]);
   return check_launch("batch step");
+}
+
+// Apply a plan: rebuild the work lists when the order changes, drop the captured graphs.
+ms_status batch_apply_plan(ms_batch* b, const int* plan) {
+  if (plan[0] != b->plan[0]) {
+    MS_CUDA(cudaStreamSynchronize(b->stream));
+    tiled_batch_free(&b->tb);
+    std::string err;
+    if (tiled_batch_build(b->cav.data(), (int)b->cav.size(), plan[0], &b->tb, &err) != 0) return fail(MS_ENOMEM, err);
+  }
+  free_graph(&b->graph1);
+  free_graph(&b->graphk);
+  for (int k = 0; k < 3; ++k) b->plan[k] = plan[k];
+  return MS_OK;
+}
+
+bool valid_plan(const int* plan) {
+  return plan && plan[0] >= 0 && plan[0] <= 2 && plan[1] >= 1 && plan[1] <= 256 && (plan[2] == 0 || plan[2] == 1);
+}
+
+// ---- autotune cache: key -> plan, in memory and (if MS_AUTOTUNE_CACHE names a file) on disk ----
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 3>> g_tune;
+
+bool valid_key(const char* key) {
+  if (!key || !*key || std::strlen(key) > 512) return false;
+  for (const char* c = key; *c; ++c)
+    if (!(std::isalnum((unsigned char)*c) || std::strchr(":;._-=,", *c))) return false;
+  return true;
+}
+
+bool tune_file_lookup(const std::string& key, std::array<int, 3>* plan) {
+  const char* path = std::getenv("MS_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return false;
+  char k[600];
+  int a, b, c;
+  bool found = false;
+  while (std::fscanf(fp, "%599s %d %d %d", k, &a, &b, &c) == 4) {
+    const int p[3] = {a, b, c};
+    if (key == k && valid_plan(p)) {  // the last entry of a key wins
+      *plan = {a, b, c};
+      found = true;
+    }
+  }
+  std::fclose(fp);
+  return found;
+}
+
+// Key of a batch: the cavity sizes (FNV-1a hash and count), r, Z, closure, and the device's SM count
+// and name, so a cached plan is reused only for the same work on the same kind of GPU.
+std::string batch_key(const ms_batch* b) {
+  unsigned long long h = 1469598103934665603ull;
+  for (const ms_grid* g : b->cav) {
+    h ^= (unsigned long long)g->N;
+    h *= 1099511628211ull;
+  }
+  int dev = 0, sms = 0;
+  cudaDeviceProp prop{};
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name;
+  for (const char* c = prop.name; *c; ++c) name += std::isalnum((unsigned char)*c) ? *c : '_';
+  char buf[400];
+  snprintf(buf, sizeof buf, "batch:%016llx:%zu;r=%.17g;z=%.17g;c=%d;sm=%d;%s", h, b->cav.size(), b->desc.r,
+           b->desc.z_imp, b->desc.closure, sms, name.c_str());
+  return buf;
 }
 
 ms_status batch_capture(ms_batch* b, Graph* gr, int steps) {
@@ -1194,7 +1270,7 @@ ms_status ms_create_batch(const ms_grid_desc* d, const int* n, int count, ms_bat
     b->cells += (long long)n[c] * n[c];
   }
   std::string err;
-  if (tiled_batch_build(b->cav.data(), count, &b->tb, &err) != 0) return cleanup(fail(MS_ENOMEM, err));
+  if (tiled_batch_build(b->cav.data(), count, b->plan[0], &b->tb, &err) != 0) return cleanup(fail(MS_ENOMEM, err));
   *out = b;
   return MS_OK;
 }
@@ -1202,13 +1278,125 @@ ms_status ms_create_batch(const ms_grid_desc* d, const int* n, int count, ms_bat
 ms_status ms_batch_init_modes(ms_batch* b, int cavity, const ms_mode* modes, int nmodes) {
   ms_grid* g;
   MS_TRY(batch_cavity(b, cavity, &g));
+  b->touched = true;
   return ms_init_modes(g, modes, nmodes);
 }
 
 ms_status ms_batch_set_fields(ms_batch* b, int cavity, const double* const* comps, long step) {
   ms_grid* g;
   MS_TRY(batch_cavity(b, cavity, &g));
+  b->touched = true;
   return ms_set_fields(g, comps, step);
+}
+
+ms_status ms_batch_set_plan(ms_batch* b, const int* plan) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  if (!valid_plan(plan)) return fail(MS_EINVAL, "plan must be {order 0..2, chunk 1..256, persistent 0|1}");
+  return batch_apply_plan(b, plan);
+}
+
+ms_status ms_batch_get_plan(ms_batch* b, int* plan) {
+  if (!valid_batch(b) || !plan) return fail(MS_EINVAL, "invalid argument");
+  for (int k = 0; k < 3; ++k) plan[k] = b->plan[k];
+  return MS_OK;
+}
+
+ms_status ms_autotune_cache_get(const char* key, int* plan, int* found) {
+  if (!valid_key(key) || !plan || !found) return fail(MS_EINVAL, "invalid key or output");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  *found = 0;
+  auto it = g_tune.find(key);
+  std::array<int, 3> p{};
+  if (it != g_tune.end()) {
+    p = it->second;
+  } else if (tune_file_lookup(key, &p)) {
+    g_tune[key] = p;
+  } else {
+    return MS_OK;
+  }
+  for (int k = 0; k < 3; ++k) plan[k] = p[k];
+  *found = 1;
+  return MS_OK;
+}
+
+ms_status ms_autotune_cache_put(const char* key, const int* plan) {
+  if (!valid_key(key)) return fail(MS_EINVAL, "invalid key");
+  if (!valid_plan(plan)) return fail(MS_EINVAL, "invalid plan");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {plan[0], plan[1], plan[2]};
+  const char* path = std::getenv("MS_AUTOTUNE_CACHE");
+  if (path && *path) {
+    FILE* fp = std::fopen(path, "a");
+    if (!fp) return fail(MS_EINVAL, std::string("cannot append to the autotune cache ") + path);
+    const bool ok = std::fprintf(fp, "%s %d %d %d\n", key, plan[0], plan[1], plan[2]) > 0;
+    if (std::fclose(fp) != 0 || !ok) return fail(MS_EINVAL, std::string("writing the autotune cache failed: ") + path);
+  }
+  return MS_OK;
+}
+
+ms_status ms_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return MS_OK;
+}
+
+ms_status ms_batch_autotune(ms_batch* b, int trial_steps, int* plan, int* from_cache) {
+  if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
+  if (trial_steps < 1 || trial_steps > 4096) return fail(MS_EINVAL, "trial_steps must be in [1, 4096]");
+  if (b->touched)
+    return fail(MS_EINVAL, "autotune before setting any cavity's fields: its trial steps run on the zero state");
+  const std::string key = batch_key(b);
+  int cached[3], found = 0;
+  MS_TRY(ms_autotune_cache_get(key.c_str(), cached, &found));
+  if (from_cache) *from_cache = found;
+  if (found) {
+    MS_TRY(batch_apply_plan(b, cached));
+    if (plan)
+      for (int k = 0; k < 3; ++k) plan[k] = b->plan[k];
+    return MS_OK;
+  }
+  // trials: every candidate captured as its own graph and timed with CUDA events over whole graph
+  // launches; the state is zero and stays zero, and the cavities' step counters are not advanced
+  cudaEvent_t e0, e1;
+  MS_CUDA(cudaEventCreate(&e0));
+  MS_CUDA(cudaEventCreate(&e1));
+  int best[3] = {0, 16, 0};
+  float best_ms = 1e30f;
+  ms_status st = MS_OK;
+  for (int order = 0; order <= 2 && st == MS_OK; ++order)
+    for (int chunk : {8, 32})
+      for (int pers = 0; pers <= 1 && st == MS_OK; ++pers) {
+        const int cand[3] = {order, chunk, pers};
+        st = batch_apply_plan(b, cand);
+        if (st == MS_OK) st = batch_capture(b, &b->graphk, chunk);
+        if (st != MS_OK) break;
+        const int reps = trial_steps > chunk ? (trial_steps + chunk - 1) / chunk : 1;
+        if (cudaGraphLaunch(b->graphk.exec, b->stream) != cudaSuccess ||  // warm-up
+            cudaEventRecord(e0, b->stream) != cudaSuccess) {
+          st = fail(MS_ECUDA, "autotune trial launch failed");
+          break;
+        }
+        for (int r = 0; r < reps && st == MS_OK; ++r)
+          if (cudaGraphLaunch(b->graphk.exec, b->stream) != cudaSuccess) st = fail(MS_ECUDA, "autotune trial launch failed");
+        float ms = 0.0f;
+        if (st == MS_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          st = fail(MS_ECUDA, "autotune timing failed");
+        if (st != MS_OK) break;
+        const float per_step = ms / (float)(reps * chunk);
+        if (per_step < best_ms) {
+          best_ms = per_step;
+          for (int k = 0; k < 3; ++k) best[k] = cand[k];
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MS_OK) return st;
+  MS_TRY(batch_apply_plan(b, best));
+  MS_TRY(ms_autotune_cache_put(key.c_str(), best));
+  if (plan)
+    for (int k = 0; k < 3; ++k) plan[k] = best[k];
+  return MS_OK;
 }
 
 ms_status ms_batch_get_fields(ms_batch* b, int cavity, double* const* comps) {
@@ -1234,7 +1422,7 @@ ms_status ms_batch_step(ms_batch* b) {
 ms_status ms_batch_run(ms_batch* b, long nsteps) {
   if (!valid_batch(b)) return fail(MS_EINVAL, "invalid batch");
   if (nsteps < 0) return fail(MS_EINVAL, "nsteps must be >= 0");
-  const int chunk = 16;
+  const int chunk = b->plan[1];
   if (nsteps >= chunk) MS_TRY(batch_capture(b, &b->graphk, chunk));
   if (nsteps % chunk) MS_TRY(batch_capture(b, &b->graph1, 1));
   long left = nsteps;

@@ -27,6 +27,7 @@
 // strides and 32-bit offsets, tiles away from the walls take block-uniform paths without any
 // boundary test, and the interior band of A^{-1} (the same Toeplitz row for every grid,
 // 24 (-rho) rho^|d| / (1 - rho^2), rho = -11 + sqrt(120)) is read from constant memory.
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -392,14 +393,19 @@ __device__ __forceinline__ void copy_args(T* dst, const T* src) {
   __syncthreads();
 }
 
-// Batched form: block b processes tile work[2b+1] of cavity work[2b].
+// Batched form: item w is tile work[2w+1] of cavity work[2w]; block b takes items b, b + gridDim.x,
+// ... (one item per block when the grid covers the list, persistent blocks when it does not).
 template <int STEP>
-__global__ void __launch_bounds__(NT, 3) k_curl_batch(const CurlArgs* __restrict__ args, const int* __restrict__ work) {
+__global__ void __launch_bounds__(NT, 3) k_curl_batch(const CurlArgs* __restrict__ args, const int* __restrict__ work,
+                                                      int nwork) {
   __shared__ CurlArgs sA;
-  const int cav = work[2 * blockIdx.x], t = work[2 * blockIdx.x + 1];
-  copy_args(&sA, args + cav);
-  const int nt = sA.ntiles;
-  curl_body<STEP>(sA, (t % nt) * TB, (t / nt) * TB);
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int cav = work[2 * w], t = work[2 * w + 1];
+    copy_args(&sA, args + cav);
+    const int nt = sA.ntiles;
+    curl_body<STEP>(sA, (t % nt) * TB, (t / nt) * TB);
+    __syncthreads();  // sA and the tile buffers are rewritten by the next item
+  }
 }
 
 }  // namespace
@@ -813,19 +819,26 @@ __global__ void __launch_bounds__(NT, 2) k_solve_tile(SolveArgs A) { solve_body(
 
 
 
-// Batched form: block b solves tile work[3b+2] of field slot work[3b+1] of cavity work[3b].
-__global__ void __launch_bounds__(NT, 2) k_solve_batch(const SolveArgs* __restrict__ args, const int* __restrict__ work) {
+// Batched form: item w solves tile work[3w+2] of field slot work[3w+1] of cavity work[3w]; blocks
+// stride over the items as in k_curl_batch.
+__global__ void __launch_bounds__(NT, 2) k_solve_batch(const SolveArgs* __restrict__ args, const int* __restrict__ work,
+                                                       int nwork) {
   __shared__ SolveArgs sA;
-  const int cav = work[3 * blockIdx.x], f = work[3 * blockIdx.x + 1], t = work[3 * blockIdx.x + 2];
-  copy_args(&sA, args + cav);
-  const int nt = sA.ntiles;
-  solve_body(sA, f, t % nt, t / nt);
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int cav = work[3 * w], f = work[3 * w + 1], t = work[3 * w + 2];
+    copy_args(&sA, args + cav);
+    const int nt = sA.ntiles;
+    solve_body(sA, f, t % nt, t / nt);
+    __syncthreads();
+  }
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
 // Host side
+
+static int g_curl_resident = 0, g_solve_resident = 0;  // resident blocks per batch kernel (tiled_configure)
 
 static PhaseArgs phase(const ms_grid* g, int src, int axis, int kind, float cb_hi, float cb_lo) {
   const Shape& s = g->sh[src];
@@ -906,6 +919,14 @@ int tiled_configure() {
       cudaFuncSetAttribute(k_solve_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, ss) != cudaSuccess ||
       cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, ss) != cudaSuccess)
     return -1;
+  // blocks of the batch kernels resident on the device at once (persistent launches)
+  int dev = 0, sms = 0, pc = 0, ps = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_curl_batch<0>, NT, cs) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_solve_batch, NT, ss) != cudaSuccess)
+    return -1;
+  g_curl_resident = sms * pc;
+  g_solve_resident = sms * ps;
   // interior Toeplitz row of A^{-1}: 24 (-rho) rho^|d| / (1 - rho^2) (rho < 0), split hi + lo
   const long double rho = -11.0L + std::sqrt(120.0L);
   float w[2 * KB + 2], wl[3];
@@ -938,10 +959,14 @@ void tiled_solve(ms_grid* g, int nfields, const int* fields, const float* const*
 // ---------------------------------------------------------------------------------------
 // Batched launches: one work list of (cavity, tile) entries covers every cavity.
 
-int tiled_batch_build(ms_grid* const* cav, int count, TiledBatch* tb, std::string* err) {
+int tiled_batch_build(ms_grid* const* cav, int count, int order, TiledBatch* tb, std::string* err) {
   std::vector<CurlArgs> curl(2 * (size_t)count);
   std::vector<SolveArgs> solve(2 * (size_t)count);
-  std::vector<int> wc, we, wh;
+  // cavities in list order, or largest first (order 2)
+  std::vector<int> seq(count);
+  for (int c = 0; c < count; ++c) seq[c] = c;
+  if (order == 2)
+    std::stable_sort(seq.begin(), seq.end(), [&](int a, int b) { return cav[a]->N > cav[b]->N; });
   for (int c = 0; c < count; ++c) {
     ms_grid* g = cav[c];
     const MixedConsts k = mixed_consts(g);
@@ -956,17 +981,31 @@ int tiled_batch_build(ms_grid* const* cav, int count, TiledBatch* tb, std::strin
     const float* bh[2] = {bx, by};
     solve[c] = make_solve(g, 1, fe, be, k.S, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo);
     solve[count + c] = make_solve(g, 2, fh, bh, k.S, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo);
-    const int ntc = curl[c].ntiles, nts = solve[c].ntiles;
-    for (int t = 0; t < ntc * ntc; ++t) {
-      wc.push_back(c);
-      wc.push_back(t);
-    }
-    for (int t = 0; t < nts * nts; ++t) {
-      we.insert(we.end(), {c, 0, t});
-      wh.insert(wh.end(), {c, 0, t});
-      wh.insert(wh.end(), {c, 1, t});
-    }
   }
+  // work lists; order 1 puts the tiles of every cavity's boundary ring (the general, slower paths)
+  // ahead of all interior tiles
+  std::vector<int> wc, we, wh;
+  for (int pass = 0; pass < (order == 1 ? 2 : 1); ++pass)
+    for (int c : seq) {
+      const int ntc = curl[c].ntiles, nts = solve[c].ntiles;
+      auto take = [&](int t, int nt) {
+        if (order != 1) return true;
+        const int tx = t % nt, ty = t / nt;
+        const bool ring = tx == 0 || ty == 0 || tx == nt - 1 || ty == nt - 1;
+        return ring == (pass == 0);
+      };
+      for (int t = 0; t < ntc * ntc; ++t) {
+        if (!take(t, ntc)) continue;
+        wc.push_back(c);
+        wc.push_back(t);
+      }
+      for (int t = 0; t < nts * nts; ++t) {
+        if (!take(t, nts)) continue;
+        we.insert(we.end(), {c, 0, t});
+        wh.insert(wh.end(), {c, 0, t});
+        wh.insert(wh.end(), {c, 1, t});
+      }
+    }
   tb->n_curl = (int)(wc.size() / 2);
   tb->n_solveE = (int)(we.size() / 3);
   tb->n_solveH = (int)(wh.size() / 3);
@@ -992,12 +1031,16 @@ int tiled_batch_build(ms_grid* const* cav, int count, TiledBatch* tb, std::strin
   return 0;
 }
 
-void tiled_batch_step(const TiledBatch& tb, cudaStream_t st) {
+void tiled_batch_step(const TiledBatch& tb, cudaStream_t st, int persistent) {
   const size_t cs = tiled_curl_smem(), ss = tiled_solve_smem();
-  k_curl_batch<0><<<tb.n_curl, NT, cs, st>>>(tb.d_curl, tb.d_work + tb.off_curl);
-  k_solve_batch<<<tb.n_solveE, NT, ss, st>>>(tb.d_solve, tb.d_work + tb.off_solveE);
-  k_curl_batch<1><<<tb.n_curl, NT, cs, st>>>(tb.d_curl + tb.count, tb.d_work + tb.off_curl);
-  k_solve_batch<<<tb.n_solveH, NT, ss, st>>>(tb.d_solve + tb.count, tb.d_work + tb.off_solveH);
+  auto blocks = [&](int n, int resident) { return (persistent && resident > 0 && resident < n) ? resident : n; };
+  k_curl_batch<0><<<blocks(tb.n_curl, g_curl_resident), NT, cs, st>>>(tb.d_curl, tb.d_work + tb.off_curl, tb.n_curl);
+  k_solve_batch<<<blocks(tb.n_solveE, g_solve_resident), NT, ss, st>>>(tb.d_solve, tb.d_work + tb.off_solveE,
+                                                                      tb.n_solveE);
+  k_curl_batch<1><<<blocks(tb.n_curl, g_curl_resident), NT, cs, st>>>(tb.d_curl + tb.count, tb.d_work + tb.off_curl,
+                                                                     tb.n_curl);
+  k_solve_batch<<<blocks(tb.n_solveH, g_solve_resident), NT, ss, st>>>(tb.d_solve + tb.count,
+                                                                      tb.d_work + tb.off_solveH, tb.n_solveH);
 }
 
 void tiled_batch_free(TiledBatch* tb) {

@@ -38,8 +38,11 @@ struct TiledBatch {
   int count = 0, n_curl = 0, n_solveE = 0, n_solveH = 0;
   size_t off_curl = 0, off_solveE = 0, off_solveH = 0;
 };
-int tiled_batch_build(ms_grid* const* cav, int count, TiledBatch* tb, std::string* err);
-void tiled_batch_step(const TiledBatch& tb, cudaStream_t st);
+// order: 0 cavity by cavity (row-major tiles), 1 the boundary-ring tiles of every cavity first,
+// 2 largest cavities first.  persistent: launch only as many blocks as are resident at once, each
+// striding over the work list.
+int tiled_batch_build(ms_grid* const* cav, int count, int order, TiledBatch* tb, std::string* err);
+void tiled_batch_step(const TiledBatch& tb, cudaStream_t st, int persistent);
 void tiled_batch_free(TiledBatch* tb);
 
 }  // namespace ms

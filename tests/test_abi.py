@@ -116,3 +116,28 @@ def test_solver_sweeps_not_converged_and_invalid():
                  (2, 0.5, 0, 1.0), (2, float("nan"), 0, 1e-10)):
         assert L.ms_solver_sweeps(*args, ctypes.byref(v)) == -1, args
     assert L.ms_solver_sweeps(2, 0.5, 0, 1e-10, None) == -1
+
+
+def test_autotune_cache_memory_and_file(tmp_path, monkeypatch):
+    """The batch autotuner's plan cache: a stored plan is found again in memory, survives the loss of
+    the memory copy through the MS_AUTOTUNE_CACHE file (last line of a key wins), and keys and plans
+    are validated; no GPU involved."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("MS_AUTOTUNE_CACHE", str(path))
+    pkg.autotune_cache_clear()
+    assert pkg.autotune_cache_get("batch:abc;r=0.5") is None
+    pkg.autotune_cache_put("batch:abc;r=0.5", (1, 32, 0))
+    assert pkg.autotune_cache_get("batch:abc;r=0.5") == (1, 32, 0)
+    pkg.autotune_cache_put("batch:abc;r=0.5", (2, 8, 1))
+    assert path.read_text().splitlines() == ["batch:abc;r=0.5 1 32 0", "batch:abc;r=0.5 2 8 1"]
+    pkg.autotune_cache_clear()
+    assert pkg.autotune_cache_get("batch:abc;r=0.5") == (2, 8, 1)  # from the file
+    assert pkg.autotune_cache_get("batch:other") is None
+    monkeypatch.delenv("MS_AUTOTUNE_CACHE")
+    pkg.autotune_cache_clear()
+    assert pkg.autotune_cache_get("batch:abc;r=0.5") is None  # memory only now
+    for key, plan in (("bad key", (0, 16, 0)), ("", (0, 16, 0)), ("k", (3, 16, 0)), ("k", (0, 0, 0)),
+                      ("k", (0, 300, 0)), ("k", (0, 16, 2))):
+        with pytest.raises(pkg.MaxwellError) as e:
+            pkg.autotune_cache_put(key, plan)
+        assert e.value.status == -1

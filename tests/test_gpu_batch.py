@@ -87,3 +87,44 @@ def test_config4_batch_sampled_cavities():
         # modes up to index 30 on 64 cells have about 4 points per wavelength, where the scheme's
         # own error reaches ~10% within 20 steps: only a sanity bound; parity is the bit check
         assert np.isfinite(errs[k][0]) and errs[k][1] < 0.5
+
+
+@pytest.mark.parametrize("plan", [(1, 8, 0), (2, 32, 1), (0, 4, 1)])
+def test_launch_plans_are_bit_identical(plan):
+    """Every launch plan (work-list order, steps per graph, persistent blocks) runs the same
+    arithmetic per cavity: fields equal the default plan's bit for bit."""
+    sizes = [64, 96, 160, 33, 64]
+    r, steps = 0.5, 21
+    inits = [workloads.random_fields(n, seed=2000 + k) for k, n in enumerate(sizes)]
+    out = []
+    for p in ((0, 16, 0), plan):
+        with pkg.Batch(sizes, r) as b:
+            b.set_plan(*p)
+            assert b.plan() == p
+            for k, init in enumerate(inits):
+                b.set_fields(k, *init)
+            b.run(steps)
+            out.append([b.get_fields(k) for k in range(len(sizes))])
+    for fa, fb in zip(*out):
+        for a, c in zip(fa, fb):
+            assert np.array_equal(a, c)
+
+
+def test_autotune_cache_and_preconditions(tmp_path, monkeypatch):
+    monkeypatch.setenv("MS_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    pkg.autotune_cache_clear()
+    sizes = [96, 64, 128]
+    with pkg.Batch(sizes, 0.5) as b:
+        plan, hit = b.autotune(4)
+        assert not hit and b.plan() == plan
+        assert plan[0] in (0, 1, 2) and plan[1] in (8, 32) and plan[2] in (0, 1)
+    pkg.autotune_cache_clear()  # the second batch finds the plan in the file
+    with pkg.Batch(sizes, 0.5) as b:
+        plan2, hit2 = b.autotune(4)
+        assert hit2 and plan2 == plan
+        b.init_modes(0, [(1, 2, 1.0)])
+        with pytest.raises(pkg.MaxwellError) as e:  # the state is no longer zero
+            b.autotune(4)
+        assert e.value.status == -1
+        with pytest.raises(pkg.MaxwellError):
+            b.set_plan(3, 16, 0)
