@@ -121,6 +121,8 @@ def lib() -> ctypes.CDLL:
             L.or3d_cg_iters_total.restype = ctypes.c_long
             L.or3d_cg_solves.argtypes = [V]
             L.or3d_cg_solves.restype = ctypes.c_long
+            L.or3d_step_src.argtypes = [V, PP, D, ctypes.c_int, ctypes.c_long]
+            L.or3d_exact_driven.argtypes = [V, D, ctypes.c_int, ctypes.c_double, ctypes.c_double, PP]
             _lib = L
     return _lib
 
@@ -558,3 +560,21 @@ class Oracle3D:
     def cg_stats(self):
         L = lib()
         return L.or3d_cg_iters_total(self.g), L.or3d_cg_solves(self.g)
+
+    @staticmethod
+    def _src3(src):
+        s = np.ascontiguousarray(np.asarray(src, dtype=np.float64).reshape(-1, 7))
+        return s, s.shape[0]
+
+    def step_src(self, f, src, n):
+        """Step n in place with current sources, rows (m, n, p, a_x, a_y, a_z, w): divergence-free
+        driven modes J = (a_x cos sin sin, a_y sin cos sin, a_z sin sin cos) sin(w t)."""
+        s, ns = self._src3(src)
+        lib().or3d_step_src(self.g, _pp(f), _p(s), ns, int(n))
+
+    def exact_driven(self, src, tE, tH):
+        """The exact driven solution of those sources (E at tE, H at tH)."""
+        s, ns = self._src3(src)
+        f = self.fields()
+        lib().or3d_exact_driven(self.g, _p(s), ns, tE, tH, _pp(f))
+        return f

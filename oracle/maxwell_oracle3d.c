@@ -16,7 +16,8 @@
  *   - P1 = -(Delta_h + (h^2/6) Upsilon_h) + kappa^2 (1 + 2/r^2): Def. "def:operatorsP";
  *   - curl_h = [[0, -d_z, d_y], [d_z, 0, -d_x], [-d_y, d_x, 0]] with the Pade
  *     derivatives of App. A.1: Sec. 3.4;
- *   - Step 1 / Step 2 with J = rho = 0: Sec. 3.4 (third rows read as E_z, H_z);
+ *   - Step 1 / Step 2 with J = rho = 0: Sec. 3.4 (third rows read as E_z, H_z), and with
+ *     divergence-free current sources (or3d_step_src, end of this file);
  *   - conjugate-gradient solves: Sec. 3.2.
  * The exact cavity mode used for checks is not in the paper (it treats 2D only in its
  * experiments): E = A (cos ax sin by sin cz, sin ax cos by sin cz, sin ax sin by cos cz)
@@ -455,3 +456,118 @@ double or3d_divergence(const or_grid3d* g, const double* const* f, double* div_o
 
 long or3d_cg_iters_total(const or_grid3d* g) { return g->cg_iters_total; }
 long or3d_cg_solves(const or_grid3d* g) { return g->cg_solves; }
+
+/* ------------------------------------------------------------------ */
+/* Current sources on 3D grids: divergence-free driven modes shaped like a cavity mode's E,
+ *   J = (a_x cos ax sin by sin cz, a_y sin ax cos by sin cz, a_z sin ax sin by cos cz) sin(w t),
+ *   (a, b, c) = pi (m, n, p),  (a_x, a_y, a_z) . (m, n, p) = 0,
+ * rows (m, n, p, a_x, a_y, a_z, w).  div J = 0, so rho = 0 and the normal data of E stay
+ * homogeneous (d_n E_n = rho = 0); the tangential components of J vanish on every wall with all
+ * the derivatives the Neumann data of H involve (Sec. 3.3), so the even ghosts of Cor.
+ * "cor:ghost_cor" stay exact.  The source terms are those of the 2D oracle's add_sources_e /
+ * add_sources_h written for the vector current (Sec. 3.1: the Taylor expansion with Faraday's and
+ * Ampere's laws):
+ *   E:  P(J) = Z (-kappa^2 J + grad div J - d_tt J) = -Z (kappa^2 - w^2) J     at t^{n+1/2},
+ *   H:  + curl d_t J = w cos(w t) (a_z b - a_y c, a_x c - a_z a, a_y a - a_x b) (H-mode shapes)  at t^{n+1},
+ * each through the right-hand-side filter of Eq. "eq:ell" with the exact Laplacian of the source
+ * (factor beta - (h^2/12)(a^2 + b^2 + c^2)).  A source with p = 0 is J = a_z sin ax sin by z^, the
+ * 2D TM_z source extended in z (likewise m = 0, n = 0 in the other orientations). */
+
+/* R[q] += amp[q] * shape of component (side == 0 ? q : 3 + q) with the wavenumbers k3. */
+static void add_shaped3(const or_grid3d* g, int side, const double* k3, const double* amp, double* const* R) {
+  const double h = g->h;
+  for (int q = 0; q < 3; ++q) {
+    const int c = side == 0 ? q : 3 + q;
+    int d[3];
+    or3d_dims(g, c, d);
+    for (int k = 0; k < d[2]; ++k)
+      for (int j = 0; j < d[1]; ++j)
+        for (int i = 0; i < d[0]; ++i) {
+          if (!unknown3(g, c, d, i, j, k)) continue;
+          int idx[3] = {i, j, k};
+          double v = amp[q];
+          for (int ax = 0; ax < 3; ++ax) {
+            if (or3d_bc(c, ax) == BC_DIR3) v *= sin(k3[ax] * idx[ax] * h);
+            else v *= cos(k3[ax] * (idx[ax] + 0.5) * h);
+          }
+          R[q][((size_t)k * d[1] + j) * d[0] + i] += v;
+        }
+  }
+}
+
+static void add_sources3(const or_grid3d* g, const double* src, int nsrc, double t, int side, double* const* R) {
+  for (int q = 0; q < nsrc; ++q) {
+    const double* s = src + 7 * q;
+    const double k3[3] = {M_PI * s[0], M_PI * s[1], M_PI * s[2]};
+    const double ax = s[3], ay = s[4], az = s[5], w = s[6];
+    const double filt = g->beta - (g->h * g->h / 12.0) * (k3[0] * k3[0] + k3[1] * k3[1] + k3[2] * k3[2]);
+    double amp[3];
+    if (side == 0) {
+      const double f = -g->Z * (g->kappa2 - w * w) * filt * sin(w * t);
+      amp[0] = f * ax;
+      amp[1] = f * ay;
+      amp[2] = f * az;
+    } else {
+      const double f = filt * w * cos(w * t);
+      amp[0] = f * (az * k3[1] - ay * k3[2]);
+      amp[1] = f * (ax * k3[2] - az * k3[0]);
+      amp[2] = f * (ay * k3[0] - ax * k3[1]);
+    }
+    add_shaped3(g, side, k3, amp, R);
+  }
+}
+
+/* One full step with sources: or3d_step with P(J)^{n+1/2} added to the E right-hand sides and
+ * curl d_t J^{n+1} to the H right-hand sides; n is the index of the step (E^n -> E^{n+1}). */
+void or3d_step_src(or_grid3d* g, double* const* f, const double* src, int nsrc, long n) {
+  double* G[3];
+  double* R[3];
+  double* X[3];
+  for (int q = 0; q < 3; ++q) {
+    long m = or3d_field_size(g, 3 + q) > or3d_field_size(g, q) ? or3d_field_size(g, 3 + q) : or3d_field_size(g, q);
+    G[q] = (double*)malloc(sizeof(double) * m);
+    R[q] = (double*)malloc(sizeof(double) * m);
+    X[q] = (double*)malloc(sizeof(double) * m);
+  }
+  for (int q = 0; q < 3; ++q) or3d_filter(g, 3 + q, f[3 + q], G[q]);
+  or3d_curl_h_to_e(g, (const double* const*)G, R);
+  add_sources3(g, src, nsrc, (n + 0.5) * g->ht, 0, R);
+  for (int q = 0; q < 3; ++q) {
+    or3d_p1_solve_cg(g, q, R[q], X[q]);
+    long m = or3d_field_size(g, q);
+    for (long p = 0; p < m; ++p) f[q][p] += g->ht * X[q][p];
+  }
+  for (int q = 0; q < 3; ++q) or3d_filter(g, q, f[q], G[q]);
+  or3d_curl_e_to_h(g, (const double* const*)G, R);
+  add_sources3(g, src, nsrc, (n + 1.0) * g->ht, 1, R);
+  for (int q = 0; q < 3; ++q) {
+    or3d_p1_solve_cg(g, 3 + q, R[q], X[q]);
+    long m = or3d_field_size(g, 3 + q);
+    for (long p = 0; p < m; ++p) f[3 + q][p] += g->ht * X[q][p];
+  }
+  for (int q = 0; q < 3; ++q) {
+    free(G[q]);
+    free(R[q]);
+    free(X[q]);
+  }
+}
+
+/* Exact driven solution for these sources (particular solution, w^2 != a^2 + b^2 + c^2), from
+ * d_tt E = Delta E - Z d_t J (div E = 0) and Faraday's law:
+ *   E = A cos(w t) (a_x, a_y, a_z) (E-mode shapes),  A = Z w / (w^2 - (a^2 + b^2 + c^2)),
+ *   H = -(A sin(w t) / (Z w)) (a_z b - a_y c, a_x c - a_z a, a_y a - a_x b) (H-mode shapes),
+ * at times tE, tH; wall points zero. */
+void or3d_exact_driven(const or_grid3d* g, const double* src, int nsrc, double tE, double tH, double* const* f) {
+  for (int c = 0; c < 6; ++c) memset(f[c], 0, sizeof(double) * or3d_field_size(g, c));
+  for (int q = 0; q < nsrc; ++q) {
+    const double* s = src + 7 * q;
+    const double k3[3] = {M_PI * s[0], M_PI * s[1], M_PI * s[2]};
+    const double ax = s[3], ay = s[4], az = s[5], w = s[6];
+    const double A = g->Z * w / (w * w - (k3[0] * k3[0] + k3[1] * k3[1] + k3[2] * k3[2]));
+    const double ce = A * cos(w * tE), sh = -A * sin(w * tH) / (g->Z * w);
+    const double ae[3] = {ce * ax, ce * ay, ce * az};
+    const double ah[3] = {sh * (az * k3[1] - ay * k3[2]), sh * (ax * k3[2] - az * k3[0]), sh * (ay * k3[0] - ax * k3[1])};
+    add_shaped3(g, 0, k3, ae, f);
+    add_shaped3(g, 1, k3, ah, f + 3);
+  }
+}
