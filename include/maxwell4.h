@@ -148,6 +148,29 @@ ms_status ms_init_modes3(ms_grid* g, const ms_mode3* modes, int nmodes);
 ms_status ms_error_vs_exact3(ms_grid* g, const ms_mode3* modes, int nmodes, double* l2_abs, double* l2_rel,
                              double* max_abs, double* sum_abs);
 
+/* Current sources on 3D grids (both precisions): divergence-free driven modes shaped like a
+ * cavity mode's E,
+ *   J = (ax cos(pi m x) sin(pi n y) sin(pi p z), ay sin cos sin, az sin sin cos) sin(omega t),
+ * with (ax, ay, az) . (m, n, p) = 0 (so div J = 0 and rho stays 0), m, n, p >= 0 with at least two
+ * of them >= 1.  Their tangential components vanish on every wall with all the derivatives the
+ * Neumann data of Sec. 3.3 involve, and d_n E_n = rho = 0, so the even ghosts of Cor.
+ * "cor:ghost_cor" stay exact.  Step 1 gains the filtered P(J) = Z(-kappa^2 J + grad div J - d_tt J)
+ * at t^{n+1/2} and Step 2 the filtered curl d_t J at t^{n+1} (Sec. 3.1, 3.4, the filter of
+ * Eq. "eq:ell" with the exact Laplacian of the source).  A source with p = 0 is the 2D TM_z source
+ * a_z sin sin extended along z.  ms_set_sources3 replaces the grid's sources (nsrc = 0 removes
+ * them; at most 64) and drops the captured step graphs; the step index that times them is the
+ * grid's step counter.  ms_init_driven3 sets E^0, H^{1/2} to the exact driven solution of the
+ * sources (the particular solution E = A cos(omega t) (ax, ay, az) (E-mode shapes),
+ * A = Z omega / (omega^2 - pi^2 (m^2 + n^2 + p^2)), H from Faraday's law; MS_EINVAL at resonance)
+ * and the step counter to 0.  MS_EINVAL for invalid rows, MS_EUNSUPPORTED on 2D grids. */
+typedef struct {
+  int m, n, p;
+  double ax, ay, az;
+  double omega;
+} ms_source3;
+ms_status ms_set_sources3(ms_grid* g, const ms_source3* src, int nsrc);
+ms_status ms_init_driven3(ms_grid* g, const ms_source3* src, int nsrc);
+
 /* Copy host FP64 fields (layout above) to the device state and set the step counter to
  * `step` (E at step h_tau, H at (step + 1/2) h_tau).  Dirichlet boundary entries are ignored
  * and stored as zero. */

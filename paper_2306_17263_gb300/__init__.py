@@ -56,6 +56,11 @@ class _SourceXY(ctypes.Structure):
                 ("amp", ctypes.c_double), ("omega", ctypes.c_double)]
 
 
+class _Source3(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("ax", ctypes.c_double),
+                ("ay", ctypes.c_double), ("az", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
 class _Mode3(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("az", ctypes.c_double)]
@@ -100,6 +105,8 @@ def load() -> ctypes.CDLL:
             "ms_stability_limit": [I, PD],
             "ms_solver_sweeps": [I, D, I, D, ctypes.POINTER(I)],
             "ms_set_solver": [V, I],
+            "ms_set_sources3": [V, ctypes.POINTER(_Source3), I],
+            "ms_init_driven3": [V, ctypes.POINTER(_Source3), I],
             "ms_batch_set_plan": [V, ctypes.POINTER(I)],
             "ms_batch_get_plan": [V, ctypes.POINTER(I)],
             "ms_batch_autotune": [V, I, ctypes.POINTER(I), ctypes.POINTER(I)],
@@ -183,6 +190,15 @@ def _sources_xy(src):
         arr[k].m, arr[k].n, arr[k].cos_x, arr[k].cos_y = int(m), int(n), int(px), int(py)
         arr[k].amp, arr[k].omega = float(a), float(w)
     return arr, len(src)
+
+
+def _sources3(src):
+    """Rows (m, n, p, a_x, a_y, a_z, omega) as a ctypes array."""
+    rows = list(src)
+    arr = (_Source3 * max(len(rows), 1))()
+    for k, r in enumerate(rows):
+        arr[k] = _Source3(int(r[0]), int(r[1]), int(r[2]), float(r[3]), float(r[4]), float(r[5]), float(r[6]))
+    return arr, len(rows)
 
 
 def _ptrs(ptrs):
@@ -360,6 +376,16 @@ class Grid:
         fn = load().ms_error_vs_exact3 if self.dim == 3 else load().ms_error_vs_exact
         _check(fn(self._h, arr, nm, *[ctypes.byref(v) for v in out]))
         return tuple(v.value for v in out)
+
+    def set_sources3(self, src):
+        """3D current sources: divergence-free driven modes, rows (m, n, p, a_x, a_y, a_z, omega)."""
+        arr, n = _sources3(src)
+        _check(load().ms_set_sources3(self._h, arr, n))
+
+    def init_driven3(self, src):
+        """E^0, H^{1/2} = the exact driven solution of 3D sources (step counter 0)."""
+        arr, n = _sources3(src)
+        _check(load().ms_init_driven3(self._h, arr, n))
 
     def set_solver(self, solver: int):
         """Select the P1 solver (SOLVER_RICHARDSON, or SOLVER_TRANSFORM_TC on 3D FP32_REFINED grids)."""

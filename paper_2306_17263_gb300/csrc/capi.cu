@@ -14,6 +14,7 @@
 #include "grid3d.cuh"
 #include "k_fp64.cuh"
 #include "k_mixed.cuh"
+#include "k_src3.cuh"
 #include "k_tiled.cuh"
 
 using namespace ms;
@@ -655,7 +656,7 @@ ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step
   if (g->g3) {
     MS_TRY(set_fields3d(g, comps, 0));
     g->step = step;
-    return MS_OK;
+    return sync_step(g);
   }
   for (int f = 0; f < 3; ++f)
     if (!comps[f]) return fail(MS_EINVAL, "NULL component");
@@ -685,7 +686,7 @@ ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
   if (g->g3) {
     MS_TRY(set_fields3d(g, comps, 1));
     g->step = step;
-    return MS_OK;
+    return sync_step(g);
   }
   double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
   for (int f = 0; f < 3; ++f) {
@@ -970,10 +971,23 @@ static ms_status set_sources_spec(ms_grid* g, const SrcSpec* src, int nsrc) {
   return MS_OK;
 }
 
+ms_status ms_set_sources3(ms_grid* g, const ms_source3* src, int nsrc) {
+  if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
+  if (!g->g3) return fail(MS_EUNSUPPORTED, "ms_set_sources3 needs a 3D grid (2D grids: ms_set_sources)");
+  MS_TRY(check_sources3(src, nsrc, false));
+  MS_CUDA(cudaStreamSynchronize(g->stream));
+  free_graph(&g->graph1);  // the captured steps do not contain the source launches
+  free_graph(&g->graphk);
+  g->launches_per_step = 0;
+  if (nsrc > 0 && !g->d_step) MS_TRY(dalloc(&g->d_step, 1));
+  MS_TRY(sync_step(g));
+  return src3_set(g, src, nsrc);
+}
+
 ms_status ms_set_sources(ms_grid* g, const ms_source* src, int nsrc) {
   if (!valid_grid(g)) return fail(MS_EINVAL, "invalid grid");
   if (g->g3 || g->desc.scheme != MS_SCHEME_C4)
-    return fail(MS_EUNSUPPORTED, "sources are implemented for 2D grids of the compact scheme");
+    return fail(MS_EUNSUPPORTED, "ms_set_sources takes 2D grids of the compact scheme (3D grids: ms_set_sources3)");
   MS_TRY(check_sources(g, src, nsrc, false));
   std::vector<SrcSpec> sp(nsrc);
   for (int q = 0; q < nsrc; ++q) sp[q] = SrcSpec{src[q].m, src[q].n, 0, 0, src[q].amp, src[q].omega};

@@ -23,6 +23,7 @@
 #include "grid3d.cuh"
 #include "k_fp64.cuh"
 #include "k_tiled.cuh"
+#include "k_src3.cuh"
 #include "k_transform.cuh"
 
 namespace ms {
@@ -801,6 +802,11 @@ ms_status step3d64(ms_grid* g) {
   double** G = G3->s64;  // G[0..2]
   double* R = G3->s64[3];
   const double s_he = g->kappa2 * g->Z / g->h, s_eh = g->kappa2 / (g->Z * g->h);
+  if (g->src3) {  // time factors of this step's source terms
+    src3_time(g);
+    prof_mark(g, KK_SRC, 0.0);
+    nl += 1;
+  }
   // Step 1: R_e = kappa^2 Z (d_{e+1} G_{e+2} - d_{e+2} G_{e+1}) on E_e, P1 E* = R, E += h_tau E*
   for (int c = 0; c < 3; ++c) filter3d64(g, 3 + c, G3->f64[3 + c], G[c]);
   nl += 3;
@@ -809,6 +815,11 @@ ms_status step3d64(ms_grid* g) {
     pade3d64(g, p1, 3 + p2, e, G[p2], R, s_he, 0);
     pade3d64(g, p2, 3 + p1, e, G[p1], R, -s_he, 1);
     nl += 2;
+    if (g->src3) {
+      src3_add(g, e, R);
+      prof_mark(g, KK_SRC, 16.0 * (double)G3->sh[e].size());
+      nl += 1;
+    }
     solve3d64(g, e, R, G3->f64[e], g->ht, &nl);
   }
   // Step 2: R_h = -(kappa^2/Z)(d_{h+1} G_{E,h+2} - d_{h+2} G_{E,h+1}) on H_h
@@ -819,7 +830,17 @@ ms_status step3d64(ms_grid* g) {
     pade3d64(g, p1, p2, 3 + hc, G[p2], R, -s_eh, 0);
     pade3d64(g, p2, p1, 3 + hc, G[p1], R, s_eh, 1);
     nl += 2;
+    if (g->src3) {
+      src3_add(g, 3 + hc, R);
+      prof_mark(g, KK_SRC, 16.0 * (double)G3->sh[3 + hc].size());
+      nl += 1;
+    }
     solve3d64(g, 3 + hc, R, G3->f64[3 + hc], g->ht, &nl);
+  }
+  if (g->src3) {  // the device step index advances with the step
+    launch_tick(g);
+    prof_mark(g, KK_SRC, 0.0);
+    nl += 1;
   }
   g->launches_per_step = nl;
   cudaError_t e = cudaGetLastError();
@@ -946,17 +967,36 @@ void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_h
 ms_status step3d32(ms_grid* g) {
   const MixedConsts k = mixed_consts(g);
   int nl = 0;
+  Grid3D* G3 = g->g3;
+  if (g->src3) {
+    src3_time(g);
+    prof_mark(g, KK_SRC, 0.0);
+    nl += 1;
+  }
+  auto add_src = [&](int c) {  // source term in the units of b, before the solve of component c
+    if (!g->src3) return;
+    src3_add(g, c, G3->s32[1]);
+    prof_mark(g, KK_SRC, 8.0 * (double)G3->sh[c].size());
+    nl += 1;
+  };
   for (int e = 0; e < 3; ++e) {
     const int p1 = (e + 1) % 3, p2 = (e + 2) % 3;
     nl += term3d32(g, p1, 3 + p2, e, k.cb_hi, k.cb_lo, 1.0f, 0);
     nl += term3d32(g, p2, 3 + p1, e, k.cb_hi, k.cb_lo, -1.0f, 1);
+    add_src(e);
     solve3d32(g, e, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo, k.S, &nl);
   }
   for (int hc = 0; hc < 3; ++hc) {
     const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
     nl += term3d32(g, p1, p2, 3 + hc, k.cb_hi, k.cb_lo, -1.0f, 0);
     nl += term3d32(g, p2, p1, 3 + hc, k.cb_hi, k.cb_lo, 1.0f, 1);
+    add_src(3 + hc);
     solve3d32(g, 3 + hc, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo, k.S, &nl);
+  }
+  if (g->src3) {
+    launch_tick(g);
+    prof_mark(g, KK_SRC, 0.0);
+    nl += 1;
   }
   g->launches_per_step = nl;
   cudaError_t e = cudaGetLastError();
@@ -1100,6 +1140,58 @@ ms_status check_modes3(const ms_mode3* modes, int nm) {
 }
 
 }  // namespace
+
+// Rows of 3D sources: indices >= 0 with at least two >= 1, (ax, ay, az) . (m, n, p) = 0, finite
+// values; off resonance (omega^2 != pi^2 |k|^2) when a driven solution is asked for.
+ms_status check_sources3(const ms_source3* src, int nsrc, bool need_off_resonance) {
+  if (nsrc < 0 || nsrc > 64 || (nsrc > 0 && !src)) return fail3(MS_EINVAL, "invalid sources (0 <= nsrc <= 64)");
+  for (int q = 0; q < nsrc; ++q) {
+    const ms_source3& s = src[q];
+    if (s.m < 0 || s.n < 0 || s.p < 0 || s.m > 1000000 || s.n > 1000000 || s.p > 1000000)
+      return fail3(MS_EINVAL, "source indices must be in [0, 1e6]");
+    if ((s.m > 0) + (s.n > 0) + (s.p > 0) < 2) return fail3(MS_EINVAL, "a source needs at least two nonzero indices");
+    if (!std::isfinite(s.ax) || !std::isfinite(s.ay) || !std::isfinite(s.az) || !std::isfinite(s.omega))
+      return fail3(MS_EINVAL, "non-finite source");
+    const double dot = s.ax * s.m + s.ay * s.n + s.az * s.p;
+    const double scale = std::fabs(s.ax * s.m) + std::fabs(s.ay * s.n) + std::fabs(s.az * s.p);
+    if (std::fabs(dot) > 1e-12 * (scale > 0 ? scale : 1.0))
+      return fail3(MS_EINVAL, "source polarisation must satisfy (ax, ay, az) . (m, n, p) = 0 (div J = 0)");
+    if (need_off_resonance) {
+      const double k2 = M_PI * M_PI * ((double)s.m * s.m + (double)s.n * s.n + (double)s.p * s.p);
+      if (std::fabs(s.omega * s.omega - k2) <= 1e-12 * (k2 > 1 ? k2 : 1.0) || s.omega == 0.0)
+        return fail3(MS_EINVAL, "driven solution needs 0 < omega^2 != pi^2 (m^2 + n^2 + p^2)");
+    }
+  }
+  return MS_OK;
+}
+
+ms_status mode_field3_tables(ms_grid* g, int c, const std::vector<double>& tq, const std::vector<double>& coef,
+                             double* out) {
+  const Shape3& s = g->g3->sh[c];
+  const int nm = (int)coef.size(), per = s.n[0] + s.n[1] + s.n[2];
+  const size_t oy = (size_t)nm * s.n[0], oz = oy + (size_t)nm * s.n[1], oc = oz + (size_t)nm * s.n[2];
+  std::vector<double> host(oc + nm, 0.0);
+  for (int q = 0; q < nm; ++q) {
+    for (int i = 0; i < s.n[0]; ++i) host[(size_t)q * s.n[0] + i] = tq[(size_t)q * per + i];
+    for (int j = 0; j < s.n[1]; ++j) host[oy + (size_t)q * s.n[1] + j] = tq[(size_t)q * per + s.n[0] + j];
+    for (int k = 0; k < s.n[2]; ++k) host[oz + (size_t)q * s.n[2] + k] = tq[(size_t)q * per + s.n[0] + s.n[1] + k];
+    host[oc + q] = coef[q];
+  }
+  if (host.size() > g->modetab_cap) {
+    cudaFree(g->d_modetab);
+    g->d_modetab = nullptr;
+    g->modetab_cap = 0;
+    MS3_TRY(alloc3(&g->d_modetab, host.size()));
+    g->modetab_cap = host.size();
+  }
+  MS3_CUDA(cudaMemcpyAsync(g->d_modetab, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  k_mode_field3<<<grid3(s, kBlk), kBlk, 0, g->stream>>>(out, s, g->d_modetab, g->d_modetab + oy, g->d_modetab + oz,
+                                                         g->d_modetab + oc, nm);
+  MS3_CUDA(cudaGetLastError());
+  MS3_CUDA(cudaStreamSynchronize(g->stream));  // the host table is released on return
+  return MS_OK;
+}
+
 
 double stability_limit_3d() {
   static double cached = 0.0;
@@ -1273,6 +1365,7 @@ ms_status transform_status3d(ms_grid* g) {
 void destroy_grid3d(ms_grid* g) {
   Grid3D* G3 = g->g3;
   if (!G3) return;
+  src3_free(g);
   if (G3->ts) {
     ts_free(G3->ts);
     delete G3->ts;
@@ -1463,6 +1556,21 @@ ms_status ms_init_modes3(ms_grid* g, const ms_mode3* modes, int nmodes) {
     MS3_TRY(store3(g, c, tmp));
   }
   g->step = 0;
+  if (g->d_step) MS3_CUDA(cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice));
+  MS3_CUDA(cudaStreamSynchronize(g->stream));
+  return MS_OK;
+}
+
+ms_status ms_init_driven3(ms_grid* g, const ms_source3* src, int nsrc) {
+  if (!g || !g->g3) return fail3(MS_EUNSUPPORTED, "ms_init_driven3 needs a 3D grid");
+  MS3_TRY(check_sources3(src, nsrc, true));
+  double* tmp = g->g3->s64[1];
+  for (int c = 0; c < 6; ++c) {
+    MS3_TRY(exact_driven3(g, src, nsrc, 0.0, 0.5 * g->ht, c, tmp));
+    MS3_TRY(store3(g, c, tmp));
+  }
+  g->step = 0;
+  if (g->d_step) MS3_CUDA(cudaMemcpy(g->d_step, &g->step, sizeof(long), cudaMemcpyHostToDevice));
   MS3_CUDA(cudaStreamSynchronize(g->stream));
   return MS_OK;
 }

@@ -1,6 +1,8 @@
 // Three-dimensional grids (six components) behind the same C ABI (grid3d.cu).
 #pragma once
 
+#include <vector>
+
 #include "ms_internal.h"
 
 namespace ms {
@@ -37,6 +39,11 @@ ms_status divergence3d(ms_grid* g, double* norm);
 ms_status set_solver3d(ms_grid* g, int solver);
 ms_status transform_solve3d(ms_grid* g, int c, const float* b, float* x);
 ms_status transform_status3d(ms_grid* g);
+// out = sum_q coef[q] X_q(i) Y_q(j) Z_q(k) on the unknowns of component c (zero elsewhere), the
+// tables given per term as [x values | y values | z values]; synchronous.
+ms_status check_sources3(const ms_source3* src, int nsrc, bool need_off_resonance);
+ms_status mode_field3_tables(ms_grid* g, int c, const std::vector<double>& tq, const std::vector<double>& coef,
+                             double* out);
 // Device arrays of the state of a 3D grid: component c has n[c] points in f64[c] (MS_FP64) or in
 // hi[c] + lo[c] (MS_FP32_REFINED; the other pointers are NULL).  Returns the component count (6).
 int state_arrays3d(ms_grid* g, double** f64, float** hi, float** lo, size_t* n);

@@ -79,6 +79,7 @@ struct Prof {
 struct ms_grid;
 namespace ms {
 struct Grid3D;  // six-component state of a 3D grid (grid3d.cu)
+struct Src3;    // current sources of a 3D grid (k_src3.cu)
 // Record an event after a launch of the given kind when the grid is being profiled.
 void prof_mark(ms_grid* g, int kind, double bytes = 0.0);
 // Set the message returned by ms_last_error on this thread.
@@ -139,5 +140,6 @@ struct ms_grid {
 
   // 3D grids (desc.dim == 3): components, scratch and kernels live in grid3d.cu
   ms::Grid3D* g3 = nullptr;
+  ms::Src3* src3 = nullptr;  // 3D current sources (k_src3.cu), or none
   ms::Prof prof;
 };
