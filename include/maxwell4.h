@@ -406,6 +406,16 @@ ms_status ms_adjoint_steps(ms_grid* g, long nsteps, double* const* lam);
 ms_status ms_adjoint_steps_device(ms_grid* g, long nsteps, double* const* lam);
 ms_status ms_taylor_init_T(ms_grid* g, const double* l_hx, const double* l_hy, double* dEz0);
 
+/* Arithmetic of the reverse pass: MS_FP64 (every grid), or MS_FP32_REFINED (FP32_REFINED grids,
+ * their default).  The FP32 reverse pass keeps the adjoint state as float-float pairs and is the
+ * transpose of the FP32_REFINED forward operator (its truncated Pade tables): the adjoint solve
+ * u = P1^{-1} l returns its last Richardson iterate and correction as a pair, the transposed band
+ * W^T u is accumulated in float-float, and only the difference D^T W^T u (the transposed Pade
+ * derivative) is rounded to FP32, so a smooth adjoint field loses no accuracy to cancellation.
+ * ms_adjoint_run / _steps convert at the FP64 interface; the Taylor transpose stays FP64.
+ * MS_EINVAL for an unknown precision, MS_EUNSUPPORTED for FP32 on an FP64 grid. */
+ms_status ms_set_adjoint_precision(ms_grid* g, int precision);
+
 /* ---------------------------------------------------------------------------------------
  * Batches: many independent 2D cavities of uneven sizes advanced together.  Each cavity is the
  * problem of ms_create_grid with n = n[b] cells per side; all share the rest of the descriptor

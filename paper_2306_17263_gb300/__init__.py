@@ -105,6 +105,7 @@ def load() -> ctypes.CDLL:
             "ms_stability_limit": [I, PD],
             "ms_solver_sweeps": [I, D, I, D, ctypes.POINTER(I)],
             "ms_set_solver": [V, I],
+            "ms_set_adjoint_precision": [V, I],
             "ms_set_sources3": [V, ctypes.POINTER(_Source3), I],
             "ms_init_driven3": [V, ctypes.POINTER(_Source3), I],
             "ms_batch_set_plan": [V, ctypes.POINTER(I)],
@@ -386,6 +387,10 @@ class Grid:
         """E^0, H^{1/2} = the exact driven solution of 3D sources (step counter 0)."""
         arr, n = _sources3(src)
         _check(load().ms_init_driven3(self._h, arr, n))
+
+    def set_adjoint_precision(self, precision: int):
+        """Arithmetic of the reverse pass (FP64, or FP32_REFINED on FP32_REFINED grids, their default)."""
+        _check(load().ms_set_adjoint_precision(self._h, int(precision)))
 
     def set_solver(self, solver: int):
         """Select the P1 solver (SOLVER_RICHARDSON, or SOLVER_TRANSFORM_TC on 3D FP32_REFINED grids)."""

@@ -13,6 +13,7 @@
 #include <string>
 
 #include "k_fp64.cuh"
+#include "k_mixed.cuh"
 
 namespace ms {
 
@@ -208,6 +209,24 @@ ms_status taylor_init_dev(ms_grid* g, const double* ez0) {
   return ms_set_fields_device(g, comps, 0);
 }
 
+// The reverse pass in FP32 (adjoint32.cu) on FP32_REFINED grids unless FP64 was selected.
+bool use32(const ms_grid* g) {
+  const int prec = g->adj_precision < 0 ? g->desc.precision : g->adj_precision;
+  return prec == MS_FP32_REFINED;
+}
+
+// (M^T)^nsteps on adj[0..2] in the selected arithmetic (FP32: through the float-float state).
+ms_status adjoint_steps_any(ms_grid* g, long nsteps) {
+  if (!use32(g)) return adjoint_steps(g, nsteps);
+  MS_ATRY(adjoint32_setup(g));
+  const double* in[3] = {g->adj[0], g->adj[1], g->adj[2]};
+  adjoint32_load(g, in);
+  MS_ATRY(adjoint32_steps(g, nsteps));
+  double* out[3] = {g->adj[0], g->adj[1], g->adj[2]};
+  adjoint32_store(g, out);
+  return check("FP32 adjoint steps");
+}
+
 // adj[0..2] = (l_E, 0, 0) from a device array, then (M^T)^nsteps, then out = l_E + T_H^T l_H.
 ms_status adjoint_run_dev(ms_grid* g, long nsteps, const double* lEz, double* out) {
   if (nsteps < 0) return afail(MS_EINVAL, "nsteps must be >= 0");
@@ -215,7 +234,7 @@ ms_status adjoint_run_dev(ms_grid* g, long nsteps, const double* lEz, double* ou
   launch_zero_dirichlet64(g->adj[0], g->sh[EZ], g->stream);
   MS_ACUDA(cudaMemsetAsync(g->adj[1], 0, g->sh[HX].size() * sizeof(double), g->stream));
   MS_ACUDA(cudaMemsetAsync(g->adj[2], 0, g->sh[HY].size() * sizeof(double), g->stream));
-  MS_ATRY(adjoint_steps(g, nsteps));
+  MS_ATRY(adjoint_steps_any(g, nsteps));
   MS_ATRY(copy_in(g, out, g->adj[0], g->sh[EZ].size(), cudaMemcpyDeviceToDevice));
   taylor_h64_T(g, g->adj[1], g->adj[2], out, 1);
   return check("adjoint run");
@@ -224,6 +243,7 @@ ms_status adjoint_run_dev(ms_grid* g, long nsteps, const double* lEz, double* ou
 }  // namespace
 
 void adjoint_teardown(ms_grid* g) {
+  adjoint32_teardown(g);
   free_graph(&g->adj_graph1);
   free_graph(&g->adj_graphk);
   for (int k = 0; k < 2; ++k) {
@@ -284,7 +304,7 @@ ms_status ms_adjoint_steps_device(ms_grid* g, long nsteps, double* const* lam) {
     MS_ATRY(copy_in(g, g->adj[f], lam[f], g->sh[f].size(), cudaMemcpyDeviceToDevice));
     launch_zero_dirichlet64(g->adj[f], g->sh[f], g->stream);
   }
-  MS_ATRY(adjoint_steps(g, nsteps));
+  MS_ATRY(adjoint_steps_any(g, nsteps));
   for (int f = 0; f < 3; ++f) MS_ATRY(copy_in(g, lam[f], g->adj[f], g->sh[f].size(), cudaMemcpyDeviceToDevice));
   return check("adjoint steps");
 }
@@ -297,11 +317,20 @@ ms_status ms_adjoint_steps(ms_grid* g, long nsteps, double* const* lam) {
     MS_ATRY(copy_in(g, g->adj[f], lam[f], g->sh[f].size(), cudaMemcpyHostToDevice));
     launch_zero_dirichlet64(g->adj[f], g->sh[f], g->stream);
   }
-  MS_ATRY(adjoint_steps(g, nsteps));
+  MS_ATRY(adjoint_steps_any(g, nsteps));
   for (int f = 0; f < 3; ++f)
     MS_ACUDA(cudaMemcpyAsync(lam[f], g->adj[f], g->sh[f].size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
   MS_ACUDA(cudaStreamSynchronize(g->stream));
   return check("adjoint steps");
+}
+
+ms_status ms_set_adjoint_precision(ms_grid* g, int precision) {
+  if (!valid(g)) return afail(MS_EINVAL, "invalid grid");
+  if (precision != MS_FP64 && precision != MS_FP32_REFINED) return afail(MS_EINVAL, "unknown precision");
+  if (precision == MS_FP32_REFINED && g->desc.precision != MS_FP32_REFINED)
+    return afail(MS_EUNSUPPORTED, "the FP32 reverse pass needs an FP32_REFINED grid (its FP32 tables)");
+  g->adj_precision = precision;
+  return MS_OK;
 }
 
 ms_status ms_taylor_init_T(ms_grid* g, const double* l_hx, const double* l_hy, double* dEz0) {

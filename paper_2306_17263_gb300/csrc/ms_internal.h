@@ -80,6 +80,7 @@ struct ms_grid;
 namespace ms {
 struct Grid3D;  // six-component state of a 3D grid (grid3d.cu)
 struct Src3;    // current sources of a 3D grid (k_src3.cu)
+struct Adj32;   // FP32 reverse pass of an FP32_REFINED grid (adjoint32.cu)
 // Record an event after a launch of the given kind when the grid is being profiled.
 void prof_mark(ms_grid* g, int kind, double bytes = 0.0);
 // Set the message returned by ms_last_error on this thread.
@@ -126,6 +127,8 @@ struct ms_grid {
   ms::PadeTable padeT[2];
   double* adj[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   ms::Graph adj_graph1, adj_graphk;
+  int adj_precision = -1;     // arithmetic of the reverse pass (MS_FP64 / MS_FP32_REFINED); -1: the grid's
+  ms::Adj32* adj32 = nullptr;  // FP32 reverse pass state (adjoint32.cu)
 
   // current sources (k_src.cu): per-source constants, sine/cosine tables, device step index
   int nsrc = 0;
