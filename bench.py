@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the e2e, FP64 and CPU legs")
     p.add_argument("--only-3d", type=int, default=None, metavar="STEPS",
                    help="run only the 3D leg (FP32_REFINED, STEPS steps) and print its JSON (profiling)")
+    p.add_argument("--only-reverse", type=int, default=None, metavar="STEPS",
+                   help="run only the gradient workload (1024^2, STEPS forward and reverse steps) and print its "
+                        "JSON (profiling)")
     p.add_argument("--only-sources", type=int, default=None, metavar="STEPS",
                    help="run only the FP32_REFINED 2048^2 step with two current sources (STEPS profiled "
                         "steps and STEPS graph-replayed ones) and print its JSON (profiling)")
@@ -331,38 +334,48 @@ def batched_leg(pkg, torch, steps: int = 64):
             "l2_rel_last_cavity": err[1]}
 
 
-def reverse_leg(pkg, torch):
+def reverse_leg(pkg, torch, steps=None):
     """Gradient workload: 1024^2 cells, 2000 steps, Taylor-initialised random field; the FP32_REFINED
-    forward run and the FP64 reverse pass (ms_adjoint_run_device), each timed with CUDA events."""
+    forward run, the FP32 reverse pass (float-float adjoint state, the grid's default) and the FP64
+    reverse pass on the same grid, each timed with CUDA events, and the two gradients compared."""
     c = workloads.config5()
-    n, K = c["n"], c["steps"]
+    n, K = c["n"], steps or c["steps"]
     g = pkg.Grid(n, c["r"], precision=pkg.FP32_REFINED, stream="torch")
     ez0 = torch.tensor(workloads.sine_series_field(n, c["ell"], c["ez0_seed"]), device="cuda")
     lam = torch.zeros_like(ez0)
-    out = torch.empty_like(ez0)
+    out32, out64 = torch.empty_like(ez0), torch.empty_like(ez0)
     lam[1:-1, 1:-1] = torch.tensor(workloads.sine_series_field(n, c["ell"], c["direction_seeds"][0]),
                                    device="cuda")[1:-1, 1:-1]
     g.taylor_init_device(ez0)
     g.run(16)
-    g.adjoint_run_device(16, lam, out)  # builds the graphs and the transposed tables
+    g.adjoint_run_device(16, lam, out32)  # builds the graphs of the FP32 reverse pass
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     ev[0].record()
     g.taylor_init_device(ez0)
     g.run(K)
     ev[1].record()
     ev[2].record()
-    g.adjoint_run_device(K, lam, out)
+    g.adjoint_run_device(K, lam, out32)
     ev[3].record()
+    g.set_adjoint_precision(pkg.FP64)
+    g.adjoint_run_device(16, lam, out64)  # builds the FP64 graphs and tables
     torch.cuda.synchronize()
-    fwd_ms, rev_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    ev[4].record()
+    g.adjoint_run_device(K, lam, out64)
+    ev[5].record()
+    torch.cuda.synchronize()
+    fwd_ms, rev_ms, rev64_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3]), ev[4].elapsed_time(ev[5])
     g.close()
-    ok = bool(torch.isfinite(out).all().item())
+    ok = bool(torch.isfinite(out32).all().item())
+    rel = float(torch.linalg.norm(out32 - out64) / torch.linalg.norm(out64))
     return {"workload": "1024x1024 cells, 2000 steps, Gaussian random field E_z^0 (correlation length 0.05), "
-                        "H^(1/2) by Taylor series", "forward_precision": "fp32_refined", "reverse_precision": "fp64",
-            "forward_ms": fwd_ms, "reverse_ms": rev_ms,
+                        "H^(1/2) by Taylor series", "forward_precision": "fp32_refined",
+            "reverse_precision": "fp32 (float-float adjoint state)",
+            "forward_ms": fwd_ms, "reverse_ms": rev_ms, "reverse_fp64_ms": rev64_ms,
             "forward_value": n * n * K / (fwd_ms * 1e-3), "reverse_value": n * n * K / (rev_ms * 1e-3),
-            "unit": "cell-updates/s", "finite": ok,
+            "reverse_fp64_value": n * n * K / (rev64_ms * 1e-3), "unit": "cell-updates/s", "finite": ok,
+            "gradient_rel_diff_fp32_vs_fp64_reverse": rel,
             "memory": "no trajectory stored: the step is linear, the reverse pass needs only the final adjoint"}
 
 
@@ -741,6 +754,14 @@ def main():
         torch.cuda.set_device(local)
         torch.cuda.set_stream(torch.cuda.Stream())
         print(json.dumps(leg_3d(pkg, torch, steps32=args.only_3d, with_fp64=False)), flush=True)
+        return 0
+    if args.only_reverse is not None:
+        import torch
+
+        import paper_2306_17263_gb300 as pkg
+        torch.cuda.set_device(local)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        print(json.dumps(reverse_leg(pkg, torch, steps=args.only_reverse)), flush=True)
         return 0
     if args.only_sources is not None:
         import torch
