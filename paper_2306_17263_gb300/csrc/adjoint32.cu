@@ -38,7 +38,6 @@ struct Adj32 {
   float* uc[2] = {};  // ... and its correction
   float* vh[2] = {};  // W^T u, float-float, in the target field's layout
   float* vl[2] = {};
-  float* y[2] = {};   // Y^T u before the filter (FP32)
   float* sw[2] = {};  // sweep iterates
   Graph g1, gk;
 };
@@ -115,86 +114,178 @@ struct BandT {
   int M, K, B, all_explicit;
 };
 
-__global__ void k_bandT32(BandT p) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = p.line_lo + blockIdx.y * blockDim.y + threadIdx.y;
-  if (m > p.M || l >= p.line_hi) return;
-  const size_t vo = (size_t)m * p.va + (size_t)l * p.vc;
-  if (m == p.M) {
-    p.vh[vo] = 0.0f;
-    p.vl[vo] = 0.0f;
-    return;
-  }
-  float sh = 0.0f, sl = 0.0f;
-  const int r0 = max(0, m - p.K - 1), r1 = min(p.M - 1, m + p.K);
-  for (int r = r0; r <= r1; ++r) {
-    const int t = m - r + p.K;  // tap of input m in row r
-    const float* wh = pade_row_ptr(p.whi, r, p.M, p.K, p.B, p.all_explicit);
-    const float* wl = pade_row_ptr(p.wlo, r, p.M, p.K, p.B, p.all_explicit);
-    const size_t uo = (size_t)(r + p.uoff) * p.ua + (size_t)l * p.uc_;
-    const float a = p.ux[uo], c = p.uc[uo], w = wh[t];
-    const float prod = __fmul_rn(w, a);
-    float e = fmaf(w, a, -prod);
-    e = fmaf(w, c, e);
-    e = fmaf(wl[t], a, e);
-    const float s = __fadd_rn(sh, prod);
-    const float bb = __fsub_rn(s, sh);
-    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
-    sh = s;
-    sl = __fadd_rn(sl, __fadd_rn(err, e));
-  }
-  const float h2 = __fadd_rn(sh, sl);
-  p.vh[vo] = h2;
-  p.vl[vo] = __fsub_rn(sl, __fsub_rn(h2, sh));
+// One term of the float-float sum: (sh, sl) += (w + wl)(a + c), exact product of the hi parts.
+__device__ __forceinline__ void ff_fma_acc(float& sh, float& sl, float w, float wl, float a, float c) {
+  const float prod = __fmul_rn(w, a);
+  float e = fmaf(w, a, -prod);
+  e = fmaf(w, c, e);
+  e = fmaf(wl, a, e);
+  const float s = __fadd_rn(sh, prod);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
-// y = sx (v^x_{i-1} - v^x_i) + sy (v^y_{j-1} - v^y_j) at the unknowns of a field (v_{-1} = 0),
-// differences of float-float values; 0 elsewhere.  sx, sy in {-1, 0, 1}.
-__global__ void k_combineT32(const float* __restrict__ vxh, const float* __restrict__ vxl, const float* __restrict__ vyh,
-                             const float* __restrict__ vyl, float* __restrict__ y, int nx, int ny, int bcx, int bcy,
-                             float sx, float sy) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nx || j >= ny) return;
-  const size_t p = (size_t)j * nx + i;
-  if (!interior(bcx, i, nx) || !interior(bcy, j, ny)) {
-    y[p] = 0.0f;
-    return;
+// Tiles of the transposed band: AXIS 0 (lines are rows): 8 lines x 128 outputs per block, a warp
+// per line and four outputs per lane 32 apart; AXIS 1 (lines are columns): 32 lines x 32 outputs,
+// lanes across the lines.  The inputs a tile reads (its outputs widened by the band's reach, zero
+// past the line) are staged once in shared memory with coalesced loads; outputs whose window lies
+// in the interior rows of the table read the one interior row.
+constexpr int BT_THREADS = 256;
+constexpr int BT_KMAX = kTiledKMax;
+template <int AXIS>
+struct BandTile {
+  static constexpr int LINES = AXIS == 0 ? 8 : 32;
+  static constexpr int OUTS = AXIS == 0 ? 128 : 32;
+  static constexpr int WIN = OUTS + 2 * BT_KMAX + 2;  // staged inputs per line
+};
+
+template <int AXIS>
+__global__ void __launch_bounds__(BT_THREADS) k_bandT32(BandT p) {
+  using T = BandTile<AXIS>;
+  __shared__ float sx[T::LINES][T::WIN + 1];
+  __shared__ float sc[T::LINES][T::WIN + 1];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.x * T::OUTS;               // first output of the tile
+  const int l0 = p.line_lo + blockIdx.y * T::LINES;  // first line of the tile
+  const int base = m0 - p.K - 1;                     // input index of slot 0
+  const int win = T::OUTS + 2 * p.K + 2;
+  // stage u on [base, base + win) of every line of the tile
+  if (AXIS == 0) {
+    for (int e = tid; e < T::LINES * win; e += BT_THREADS) {
+      const int ll = e / win, q = e - ll * win, r = base + q, l = l0 + ll;
+      float a = 0.0f, c = 0.0f;
+      if (r >= 0 && r < p.M && l < p.line_hi) {
+        const size_t uo = (size_t)(r + p.uoff) * p.ua + (size_t)l * p.uc_;
+        a = p.ux[uo];
+        c = p.uc[uo];
+      }
+      sx[ll][q] = a;
+      sc[ll][q] = c;
+    }
+  } else {
+    for (int e = tid; e < T::LINES * win; e += BT_THREADS) {
+      const int q = e / T::LINES, ll = e - q * T::LINES, r = base + q, l = l0 + ll;
+      float a = 0.0f, c = 0.0f;
+      if (r >= 0 && r < p.M && l < p.line_hi) {
+        const size_t uo = (size_t)(r + p.uoff) * p.ua + (size_t)l * p.uc_;
+        a = p.ux[uo];
+        c = p.uc[uo];
+      }
+      sx[ll][q] = a;
+      sc[ll][q] = c;
+    }
   }
-  float v = 0.0f;
-  if (sx != 0.0f) {
-    const float h0 = i > 0 ? vxh[p - 1] : 0.0f, l0 = i > 0 ? vxl[p - 1] : 0.0f;
-    v = sx * (__fsub_rn(h0, vxh[p]) + __fsub_rn(l0, vxl[p]));
+  // the interior row of the table (taps d = m - r = -K .. K+1 at index d + K)
+  __shared__ float wh_s[2 * BT_KMAX + 2], wl_s[2 * BT_KMAX + 2];
+  const int rs = 2 * p.K + 2;
+  if (!p.all_explicit && tid < rs) {
+    wh_s[tid] = p.whi[(size_t)(2 * p.B) * rs + tid];
+    wl_s[tid] = p.wlo[(size_t)(2 * p.B) * rs + tid];
   }
-  if (sy != 0.0f) {
-    const float h0 = j > 0 ? vyh[p - nx] : 0.0f, l0 = j > 0 ? vyl[p - nx] : 0.0f;
-    v = fmaf(sy, __fsub_rn(h0, vyh[p]) + __fsub_rn(l0, vyl[p]), v);
+  __syncthreads();
+  constexpr int PER = T::OUTS * T::LINES / BT_THREADS;  // outputs per thread
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    int ll, mo;
+    if (AXIS == 0) {
+      ll = tid >> 5;
+      mo = (tid & 31) + 32 * k;
+    } else {
+      ll = tid & 31;
+      mo = (tid >> 5) + 8 * k;
+    }
+    const int m = m0 + mo, l = l0 + ll;
+    if (m > p.M || l >= p.line_hi) continue;
+    const size_t vo = (size_t)m * p.va + (size_t)l * p.vc;
+    if (m == p.M) {
+      p.vh[vo] = 0.0f;
+      p.vl[vo] = 0.0f;
+      continue;
+    }
+    float sh = 0.0f, sl = 0.0f;
+    const int r0 = max(0, m - p.K - 1), r1 = min(p.M - 1, m + p.K);
+    if (!p.all_explicit && r0 >= p.B && r1 < p.M - p.B) {
+      // interior row: taps |m - r| >= 3 are below 1.2e-4 of the centre tap (|rho|^3), so their sum
+      // (below 2e-4 of |v|) is accumulated in plain FP32 (error ~1e-11 |v|, including the dropped
+      // lo parts); the five central taps go through the float-float sum
+      const float* ax = &sx[ll][m - base];  // ax[-d] = u_{m-d}
+      const float* ac = &sc[ll][m - base];
+      float small = 0.0f;
+#pragma unroll
+      for (int d = BT_KMAX + 1; d >= -BT_KMAX; --d) {  // farthest taps first
+        if (d >= -2 && d <= 2) continue;
+        if (d > p.K + 1 || d < -p.K) continue;
+        small = fmaf(wh_s[d + p.K], ax[-d], small);
+      }
+#pragma unroll
+      for (int d = 2; d >= -2; --d) ff_fma_acc(sh, sl, wh_s[d + p.K], wl_s[d + p.K], ax[-d], ac[-d]);
+      sl = __fadd_rn(sl, small);
+    } else {
+      for (int r = r0; r <= r1; ++r) {
+        const int t = m - r + p.K;  // tap of input m in row r
+        const float* wh = pade_row_ptr(p.whi, r, p.M, p.K, p.B, p.all_explicit);
+        const float* wl = pade_row_ptr(p.wlo, r, p.M, p.K, p.B, p.all_explicit);
+        ff_fma_acc(sh, sl, wh[t], wl[t], sx[ll][r - base], sc[ll][r - base]);
+      }
+    }
+    const float h2 = __fadd_rn(sh, sl);
+    p.vh[vo] = h2;
+    p.vl[vo] = __fsub_rn(sl, __fsub_rn(h2, sh));
   }
-  y[p] = v;
 }
 
-// (l_hi, l_lo) += (s_hi + s_lo) (12 beta y + L y) at the unknowns (L the 5-point h^2 Delta_h with
-// Dirichlet zeros and even Neumann ghosts), with error-free transformations.
-__global__ void k_filter_accT32(const float* __restrict__ y, float* __restrict__ lh, float* __restrict__ ll, int nx,
-                                int ny, int bcx, int bcy, float cb_hi, float cb_lo, float s_hi, float s_lo) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nx || j >= ny) return;
-  if (!interior(bcx, i, nx) || !interior(bcy, j, ny)) return;
-  const size_t p = (size_t)j * nx + i;
-  const int im = clampi(i - 1, nx), ip = clampi(i + 1, nx), jm = clampi(j - 1, ny), jp = clampi(j + 1, ny);
-  const float c = y[p];
-  const float lap = fmaf(-4.0f, c, (y[(size_t)j * nx + im] + y[(size_t)j * nx + ip]) +
-                                       (y[(size_t)jm * nx + i] + y[(size_t)jp * nx + i]));
+// l (hi, lo) += (s_hi + s_lo)(12 beta y + L y) at the unknowns of a field, with
+//   y = sx (v^x_{i-1} - v^x_i) + sy (v^y_{j-1} - v^y_j)  (v_{-1} = 0; sx, sy in {-1, 0, 1}),
+// the differences taken of float-float values; L the 5-point h^2 Delta_h with Dirichlet zeros and
+// even Neumann ghosts.  A 32 x 8 tile of y with a one-point halo is formed in shared memory (0 off
+// the unknowns), then filtered and added to l with error-free transformations.
+constexpr int FT_X = 32, FT_Y = 8;
+__global__ void __launch_bounds__(FT_X * FT_Y) k_combine_filterT32(const float* __restrict__ vxh, const float* __restrict__ vxl,
+                                                                   const float* __restrict__ vyh, const float* __restrict__ vyl,
+                                                                   float* __restrict__ lh, float* __restrict__ ll, int nx,
+                                                                   int ny, int bcx, int bcy, float sx, float sy, float cb_hi,
+                                                                   float cb_lo, float s_hi, float s_lo) {
+  __shared__ float ys[FT_Y + 2][FT_X + 2];
+  const int i0 = blockIdx.x * FT_X - 1, j0 = blockIdx.y * FT_Y - 1;
+  for (int e = threadIdx.y * FT_X + threadIdx.x; e < (FT_X + 2) * (FT_Y + 2); e += FT_X * FT_Y) {
+    const int a = e / (FT_X + 2), b = e - a * (FT_X + 2);
+    // ghost positions take the clamped point (even ghosts of a Neumann axis; a Dirichlet axis has
+    // its stored zero wall there, whose y is 0 below)
+    const int i = clampi(i0 + b, nx), j = clampi(j0 + a, ny);
+    float v = 0.0f;
+    if (interior(bcx, i, nx) && interior(bcy, j, ny)) {
+      const size_t p = (size_t)j * nx + i;
+      if (sx != 0.0f) {
+        const float h0 = i > 0 ? vxh[p - 1] : 0.0f, l0 = i > 0 ? vxl[p - 1] : 0.0f;
+        v = sx * (__fsub_rn(h0, vxh[p]) + __fsub_rn(l0, vxl[p]));
+      }
+      if (sy != 0.0f) {
+        const float h0 = j > 0 ? vyh[p - nx] : 0.0f, l0 = j > 0 ? vyl[p - nx] : 0.0f;
+        v = fmaf(sy, __fsub_rn(h0, vyh[p]) + __fsub_rn(l0, vyl[p]), v);
+      }
+    }
+    ys[a][b] = v;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * FT_X + threadIdx.x, j = blockIdx.y * FT_Y + threadIdx.y;
+  if (i >= nx || j >= ny || !interior(bcx, i, nx) || !interior(bcy, j, ny)) return;
+  const int a = threadIdx.y + 1, b = threadIdx.x + 1;
+  const float c = ys[a][b];
+  const float lap = fmaf(-4.0f, c, (ys[a][b - 1] + ys[a][b + 1]) + (ys[a - 1][b] + ys[a + 1][b]));
   const float f = fmaf(cb_hi, c, fmaf(cb_lo, c, lap));
+  const size_t p = (size_t)j * nx + i;
   float h = lh[p], l = ll[p];
   const float prod = __fmul_rn(s_hi, f);
   float e = fmaf(s_hi, f, -prod);
   e = fmaf(s_lo, f, e);
-  const float s = __fadd_rn(h, prod);
-  const float bb = __fsub_rn(s, h);
-  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(prod, bb));
+  const float s2 = __fadd_rn(h, prod);
+  const float bb = __fsub_rn(s2, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s2, bb)), __fsub_rn(prod, bb));
   const float l2 = __fadd_rn(l, __fadd_rn(err, e));
-  const float h2 = __fadd_rn(s, l2);
-  ll[p] = __fsub_rn(l2, __fsub_rn(h2, s));
+  const float h2 = __fadd_rn(s2, l2);
+  ll[p] = __fsub_rn(l2, __fsub_rn(h2, s2));
   lh[p] = h2;
 }
 
@@ -263,24 +354,28 @@ void bandT32(ms_grid* g, int axis, int kind, int us, int fu, int ft, int uoff, i
   p.K = t.K;
   p.B = t.B;
   p.all_explicit = t.all_explicit;
-  const dim3 blk(64, 4, 1);
-  const dim3 grd((t.M + 1 + blk.x - 1) / blk.x, (p.line_hi - p.line_lo + blk.y - 1) / blk.y);
-  k_bandT32<<<grd, blk, 0, g->stream>>>(p);
+  const int nl = p.line_hi - p.line_lo;
+  if (axis == 0) {
+    using T = BandTile<0>;
+    k_bandT32<0><<<dim3((t.M + 1 + T::OUTS - 1) / T::OUTS, (nl + T::LINES - 1) / T::LINES), BT_THREADS, 0,
+                   g->stream>>>(p);
+  } else {
+    using T = BandTile<1>;
+    k_bandT32<1><<<dim3((t.M + 1 + T::OUTS - 1) / T::OUTS, (nl + T::LINES - 1) / T::LINES), BT_THREADS, 0,
+                   g->stream>>>(p);
+  }
 }
 
-void combineT32(ms_grid* g, int ft, int vx, float sx, int vy, float sy, int yslot) {
-  Adj32* A = g->adj32;
-  const Shape& s = g->sh[ft];
-  k_combineT32<<<grid2(s.nx, s.ny), kBlk2, 0, g->stream>>>(
-      vx >= 0 ? A->vh[vx] : nullptr, vx >= 0 ? A->vl[vx] : nullptr, vy >= 0 ? A->vh[vy] : nullptr,
-      vy >= 0 ? A->vl[vy] : nullptr, A->y[yslot], s.nx, s.ny, s.bcx, s.bcy, sx, sy);
-}
-
-void filter_accT32(ms_grid* g, int f, int yslot, const MixedConsts& k, float s_hi, float s_lo) {
+// l_f += s F~ (sx Y^T along x + sy Y^T along y) from the v pairs vx, vy (slots, -1: none).
+void combine_filterT32(ms_grid* g, int f, int vx, float sx, int vy, float sy, const MixedConsts& k, float s_hi,
+                       float s_lo) {
   Adj32* A = g->adj32;
   const Shape& s = g->sh[f];
-  k_filter_accT32<<<grid2(s.nx, s.ny), kBlk2, 0, g->stream>>>(A->y[yslot], A->lh[f], A->ll[f], s.nx, s.ny, s.bcx,
-                                                               s.bcy, k.cb_hi, k.cb_lo, s_hi, s_lo);
+  const dim3 blk(FT_X, FT_Y, 1), grd((s.nx + FT_X - 1) / FT_X, (s.ny + FT_Y - 1) / FT_Y);
+  k_combine_filterT32<<<grd, blk, 0, g->stream>>>(
+      vx >= 0 ? A->vh[vx] : nullptr, vx >= 0 ? A->vl[vx] : nullptr, vy >= 0 ? A->vh[vy] : nullptr,
+      vy >= 0 ? A->vl[vy] : nullptr, A->lh[f], A->ll[f], s.nx, s.ny, s.bcx, s.bcy, sx, sy, k.cb_hi, k.cb_lo, s_hi,
+      s_lo);
 }
 
 // One transposed step on the float-float adjoint state.
@@ -291,17 +386,14 @@ void adjoint_step32(ms_grid* g) {
   solveT32(g, HY, 1, k);
   bandT32(g, 1, NODE_TO_HALF, 0, HX, EZ, 0, 0);  // columns of H_x -> columns of E
   bandT32(g, 0, NODE_TO_HALF, 1, HY, EZ, 0, 1);  // rows of H_y -> rows of E
-  combineT32(g, EZ, 1, 1.0f, 0, -1.0f, 0);
-  filter_accT32(g, EZ, 0, k, k.sH_hi, k.sH_lo);
+  combine_filterT32(g, EZ, 1, 1.0f, 0, -1.0f, k, k.sH_hi, k.sH_lo);
   // S1^T: u_E = P~^{-1} l_E; y_Hy = Y_x^T u_E, y_Hx = -Y_y^T u_E (half-to-node bands, output r at
   // node r + 1); l_H += sE F~ y_H
   solveT32(g, EZ, 0, k);
   bandT32(g, 0, HALF_TO_NODE, 0, EZ, HY, 1, 1);  // rows of E -> rows of H_y
   bandT32(g, 1, HALF_TO_NODE, 0, EZ, HX, 1, 0);  // columns of E -> columns of H_x
-  combineT32(g, HY, 1, 1.0f, -1, 0.0f, 1);
-  combineT32(g, HX, -1, 0.0f, 0, -1.0f, 0);
-  filter_accT32(g, HY, 1, k, k.sE_hi, k.sE_lo);
-  filter_accT32(g, HX, 0, k, k.sE_hi, k.sE_lo);
+  combine_filterT32(g, HY, 1, 1.0f, -1, 0.0f, k, k.sE_hi, k.sE_lo);
+  combine_filterT32(g, HX, -1, 0.0f, 0, -1.0f, k, k.sE_hi, k.sE_lo);
 }
 
 ms_status capture32(ms_grid* g, Graph* gr, int steps) {
@@ -330,8 +422,7 @@ ms_status adjoint32_setup(ms_grid* g) {
   g->adj32 = A;
   const size_t n = (size_t)(g->N + 1) * (g->N + 1);
   float** planes[] = {&A->lh[0], &A->lh[1], &A->lh[2], &A->ll[0], &A->ll[1], &A->ll[2], &A->ux[0], &A->ux[1],
-                      &A->uc[0], &A->uc[1], &A->vh[0], &A->vh[1], &A->vl[0], &A->vl[1], &A->y[0],  &A->y[1],
-                      &A->sw[0], &A->sw[1]};
+                      &A->uc[0], &A->uc[1], &A->vh[0], &A->vh[1], &A->vl[0], &A->vl[1], &A->sw[0], &A->sw[1]};
   for (float** p : planes) {
     if (cudaMalloc((void**)p, n * sizeof(float) + 256) != cudaSuccess) {
       adjoint32_teardown(g);
@@ -351,7 +442,7 @@ void adjoint32_teardown(ms_grid* g) {
   free_graph32(&A->g1);
   free_graph32(&A->gk);
   float* all[] = {A->lh[0], A->lh[1], A->lh[2], A->ll[0], A->ll[1], A->ll[2], A->ux[0], A->ux[1], A->uc[0],
-                  A->uc[1], A->vh[0], A->vh[1], A->vl[0], A->vl[1], A->y[0],  A->y[1],  A->sw[0], A->sw[1]};
+                  A->uc[1], A->vh[0], A->vh[1], A->vl[0], A->vl[1], A->sw[0], A->sw[1]};
   for (float* p : all) cudaFree(p);
   delete A;
   g->adj32 = nullptr;
