@@ -162,7 +162,7 @@ def bf16_peak():
 KIND_SOURCES = {
     "curl32": ["k_tiled.cu", "k_tiled.cuh"], "solve32": ["k_tiled.cu", "k_tiled.cuh"],
     "filter64": ["k_fp64.cu", "k_fp64.cuh"], "pade64": ["k_fp64.cu", "k_fp64.cuh"],
-    "dfilt3d32": ["grid3d.cu", "grid3d.cuh"], "band3d32": ["grid3d.cu", "grid3d.cuh"],
+    "filt3d32": ["grid3d.cu", "grid3d.cuh"], "band3d32": ["grid3d.cu", "grid3d.cuh"],
     "term3d32": ["grid3d.cu", "grid3d.cuh"], "tsgemm": ["k_transform.cu", "k_transform.cuh"],
     "sweep3d32": ["grid3d.cu", "grid3d.cuh"],
     "p1sweep64": ["k_fp64.cu", "k_fp64.cuh"], "yee64": ["k_fp64.cu", "k_fp64.cuh"],

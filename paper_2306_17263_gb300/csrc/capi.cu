@@ -418,7 +418,7 @@ void prof_mark(ms_grid* g, int kind, double bytes) {
 
 const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64", "curl32", "solve32",
-                                        "filter3d64", "pade3d64", "sweep3d64", "dfilt3d32", "band3d32",
+                                        "filter3d64", "pade3d64", "sweep3d64", "filt3d32", "band3d32",
                                         "sweep3d32", "nc64", "source", "term3d32", "tsgemm", "tspack"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }

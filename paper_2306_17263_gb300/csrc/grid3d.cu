@@ -8,13 +8,13 @@
 //
 // MS_FP64: one operator per launch in FP64 (filter, Pade band along one axis, Richardson sweep).
 // MS_FP32_REFINED: the arithmetic of the 2D FP32 path (k_mixed.cu) carried to 3D: float-float
-// state; per Pade term one tile kernel (k_term3d32) forms the float-float first differences of
-// the source state along the line, filters them (d = 12 beta delta + L delta, the filter
-// commuting with the difference under the ghost rules) and applies the A^{-1} band (farthest
-// taps first), accumulating the right-hand side (a difference-filter kernel and a band kernel
-// take over for tables wider than the tile holds); the solve (k_sweep3d32) is the Richardson
-// iteration on 6 h^2 P1 with the exact two-product residual and the split last correction,
-// each sweep one launch that marches tiles along z.
+// state; each half-step first filters its three source components once into float-float
+// G = 12 beta u + L u (k_ffilt3d32), then per Pade term one tile kernel (k_term3d32) forms the
+// first differences of G along the line (the filter commutes with the difference under the ghost
+// rules) and applies the A^{-1} band (farthest taps first), accumulating the right-hand side (a
+// difference kernel and a band kernel take over for tables wider than the tile holds); the solve
+// (k_sweep3d32) is the Richardson iteration on 6 h^2 P1 with the exact two-product residual and
+// the split last correction, each sweep one launch that marches tiles along z.
 #include <cmath>
 #include <cstdio>
 #include <string>
@@ -45,6 +45,8 @@ struct Grid3D {
   float* lo[6] = {};
   double* s64[7] = {};  // FP64: G[3], R, sweep ping-pong [2], solve output; FP32 grids use [0], [1]
   float* s32[4] = {};   // FP32: differences, R, sweep ping-pong [2]
+  float* gh[3] = {};    // FP32: filtered components G~ (hi, lo) of one half-step, slot c % 3
+  float* gl[3] = {};
   double* dview[6] = {};  // FP32_REFINED grids: FP64 copy of the state for the diagnostics
   size_t nmax = 0;      // points of the largest component
   int solver = MS_SOLVER_RICHARDSON;  // FP32_REFINED: P1 solve by Richardson sweeps or by transforms
@@ -216,41 +218,102 @@ constexpr int KB3 = 7;
 __constant__ float c_w3[2 * KB3 + 2];
 __constant__ float c_wl3[3];
 
-// Filtered first differences along AXIS of a float-float source, written at the points of the
-// destination component (output o = m + out_off for difference m = 0 .. M-1):
-//   delta_m = (hi_{m+1} - hi_m) + (lo_{m+1} - lo_m),  d = 12 beta delta + L delta,
-// L the 7-point stencil with these ghost rules: along the line, zero differences beyond the ends
-// for a source that is Neumann along it (even ghosts of u) and even differences for a source
-// that is Dirichlet along it; across the line, the source's own rule (wall zeros / even ghosts).
-// Indices are 32-bit (n <= 512: at most 513^3 points per component).
+// Float-float filter of one component, Eq. "eq:ell" in the units of the FP32 step:
+//   G = 12 beta u + L u,  L = h^2 Delta_h (7 points),
+// with even ghosts on Neumann axes and the stored wall zeros on Dirichlet axes; G = 0 at wall
+// points.  12 beta u is an exact two-product of the hi parts plus the cross terms; L u, a sum of
+// first differences each taken of the float-float values (so FP32 holds it to its own relative
+// accuracy), joins the low word, and two-sum renormalises the pair.  The Pade terms below then
+// difference G: D1 G = (12 beta + L') D1 u, the filter commuting with the difference under the
+// ghost rules (zero differences beyond the ends of a Neumann line, even ones on a Dirichlet line).
+// A thread takes one (x, y) column of a 32 x 8 tile and marches FZ3 planes along z, its z
+// neighbours in registers; the ten loads of the next plane (own point one plane further, x and y
+// neighbours) are issued before the current plane is computed.
+constexpr int FZ3 = 8;
+__global__ void __launch_bounds__(256) k_ffilt3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 s,
+                                                   float* __restrict__ gh, float* __restrict__ gl, float cb_hi,
+                                                   float cb_lo) {
+  const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n0 || j >= n1) return;
+  const int k0 = blockIdx.z * FZ3, k1 = min(k0 + FZ3, n2);
+  const int sz = n0 * n1;
+  const bool unk_xy = interior(s.bc[0], i, n0) && interior(s.bc[1], j, n1);
+  const int nb[4] = {clampi(i - 1, n0) - i, clampi(i + 1, n0) - i, (clampi(j - 1, n1) - j) * n0,
+                     (clampi(j + 1, n1) - j) * n0};
+  int p = k0 * sz + j * n0 + i;
+  const int pm = p + (clampi(k0 - 1, n2) - k0) * sz;
+  float hm = hi[pm], lm = lo[pm], hc = hi[p], lc = lo[p];
+  float nh[4], nl[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    nh[t] = hi[p + nb[t]];
+    nl[t] = lo[p + nb[t]];
+  }
+  int pp = p + (clampi(k0 + 1, n2) - k0) * sz;
+  float hp = hi[pp], lp = lo[pp];
+  for (int k = k0; k < k1; ++k, p += sz) {
+    // loads of plane k + 1 (its neighbours) and k + 2 (own point), if this column continues
+    const bool more = k + 1 < k1;
+    float nh2[4], nl2[4], hp2 = 0.0f, lp2 = 0.0f;
+    if (more) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        nh2[t] = hi[p + sz + nb[t]];
+        nl2[t] = lo[p + sz + nb[t]];
+      }
+      const int p2 = p + sz + (clampi(k + 2, n2) - (k + 1)) * sz;
+      hp2 = hi[p2];
+      lp2 = lo[p2];
+    }
+    float g_hi = 0.0f, g_lo = 0.0f;
+    if (unk_xy && interior(s.bc[2], k, n2)) {
+      auto dv = [&](float a, float b) { return (a - hc) + (b - lc); };
+      const float lap = ((dv(nh[0], nl[0]) + dv(nh[1], nl[1])) + (dv(nh[2], nl[2]) + dv(nh[3], nl[3]))) +
+                        (dv(hm, lm) + dv(hp, lp));
+      const float pr = __fmul_rn(cb_hi, hc);
+      float e = fmaf(cb_hi, hc, -pr);
+      e = fmaf(cb_hi, lc, e);
+      e = fmaf(cb_lo, hc, e);
+      const float t = __fadd_rn(e, lap);
+      g_hi = __fadd_rn(pr, t);
+      const float bb = __fsub_rn(g_hi, pr);
+      g_lo = __fadd_rn(__fsub_rn(pr, __fsub_rn(g_hi, bb)), __fsub_rn(t, bb));
+    }
+    gh[p] = g_hi;
+    gl[p] = g_lo;
+    hm = hc;
+    lm = lc;
+    hc = hp;
+    lc = lp;
+    hp = hp2;
+    lp = lp2;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      nh[t] = nh2[t];
+      nl[t] = nl2[t];
+    }
+  }
+}
+
+// First differences of G along AXIS at the destination points (fallback for Pade tables wider
+// than the term tile holds): d = (gh_{m+1} - gh_m) + (gl_{m+1} - gl_m) at o = m + out_off, 0 at
+// the other points.  Indices are 32-bit (n <= 512: at most 513^3 points per component).
 template <int AXIS>
-__global__ void k_dfilt3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 ss, float* __restrict__ d,
-                            Shape3 sd, int out_off, int M, int ghost_even, float cb_hi, float cb_lo) {
+__global__ void k_diff3d32(const float* __restrict__ gh, const float* __restrict__ gl, Shape3 ss, float* __restrict__ d,
+                           Shape3 sd, int out_off, int M) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
   if (x >= sd.n[0] || y >= sd.n[1]) return;
   const int pd = (z * sd.n[1] + y) * sd.n[0] + x;
   const int m = (AXIS == 0 ? x : (AXIS == 1 ? y : z)) - out_off;
-  if (!unk3(sd, x, y, z) || m < 0 || m >= M) {
+  if (m < 0 || m >= M) {
     d[pd] = 0.0f;
     return;
   }
   const int st[3] = {1, ss.n[0], ss.n[0] * ss.n[1]};
-  const int sa = st[AXIS];
   const int cx = AXIS == 0 ? m : x, cy = AXIS == 1 ? m : y, cz = AXIS == 2 ? m : z;
-  const int ps = (cz * ss.n[1] + cy) * ss.n[0] + cx;  // source index of difference m
-  auto delta = [&](int q) { return (hi[q + sa] - hi[q]) + (lo[q + sa] - lo[q]); };
-  const float v = delta(ps);
-  const float a1 = m > 0 ? delta(ps - sa) : (ghost_even ? v : 0.0f);
-  const float a2 = m < M - 1 ? delta(ps + sa) : (ghost_even ? v : 0.0f);
-  // the two other axes in increasing order, neighbours clamped (even ghosts on Neumann axes)
-  constexpr int P1 = AXIS == 0 ? 1 : 0, P2 = AXIS == 2 ? 1 : 2;
-  const int u1 = P1 == 0 ? x : y, u2 = P2 == 1 ? y : z;
-  const int m1 = u1 > 0 ? -st[P1] : 0, p1 = u1 < ss.n[P1] - 1 ? st[P1] : 0;
-  const int m2 = u2 > 0 ? -st[P2] : 0, p2 = u2 < ss.n[P2] - 1 ? st[P2] : 0;
-  const float b1 = delta(ps + m1), b2 = delta(ps + p1);
-  const float c1 = delta(ps + m2), c2 = delta(ps + p2);
-  const float lap = (((a1 - v) + (a2 - v)) + ((b1 - v) + (b2 - v))) + ((c1 - v) + (c2 - v));
-  d[pd] = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
+  const int ps = (cz * ss.n[1] + cy) * ss.n[0] + cx;
+  d[pd] = (gh[ps + st[AXIS]] - gh[ps]) + (gl[ps + st[AXIS]] - gl[ps]);
 }
 
 // y = A^{-1} d along AXIS, then R (+)= sign * y at the unknowns of the destination component.
@@ -303,302 +366,212 @@ __global__ void k_band3d32(const float* __restrict__ d, float* __restrict__ R, S
   R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
 }
 
-// One Pade term fused: the filtered differences of the difference-filter kernel above and the
-// A^{-1} band of the band kernel, on a tile of T3O destination points along AXIS times NPL lines
-// along the in-tile transverse axis P, at one coordinate of the other transverse axis Q.  The
-// differences of the centre Q plane go to shared memory with a one-line halo in P and K3H + 1
-// points along the line; the Q neighbours of the filter come from global memory; the band reads
-// shared memory.  Every destination point of the tile is written (walls included).  The filter
-// sums its neighbours in the order of k_dfilt3d32 (along, then P, then Q), so d is the same.
-constexpr int T3O = 64;          // destination points along the line per tile
-constexpr int K3H = 13;          // band reach held in shared memory (table half-width <= 12)
-constexpr int D3L = T3O + 2 * K3H;       // filtered differences per line
-constexpr int D3P = D3L | 1;
-constexpr int X3L = D3L + 2;             // raw differences per line
-constexpr int X3P = X3L | 1;
+constexpr int T3O = 64;             // band rows per tile
+constexpr int K3H = 13;             // reach held in shared memory (table half-width <= 12)
+constexpr int D3L = T3O + 2 * K3H;  // differences per line
 
+// Interior row of the band at row r, d[t] = delta_{r - KB3 + t} (t = 0 .. 2 KB3 + 1), taps summed
+// farthest first, the lo parts of the three central taps before the central hi tap.
+__device__ __forceinline__ float band_fast3(const float* d) {
+  float acc = c_w3[2 * KB3 + 1] * d[2 * KB3 + 1];
+#pragma unroll
+  for (int dist = KB3; dist >= 1; --dist) {
+    acc = fmaf(c_w3[KB3 + dist], d[KB3 + dist], acc);
+    acc = fmaf(c_w3[KB3 - dist], d[KB3 - dist], acc);
+  }
+  acc = fmaf(c_wl3[0], d[KB3 - 1], acc);
+  acc = fmaf(c_wl3[2], d[KB3 + 1], acc);
+  acc = fmaf(c_wl3[1], d[KB3], acc);
+  return fmaf(c_w3[KB3], d[KB3], acc);
+}
+
+// Explicit table row r (hi + lo), dc[t] = delta_{r + t}, taps farthest first as in the interior
+// row, hi and lo products summed apart.  The loop is unrolled to the largest half-width the tile
+// holds, the taps beyond K predicated off; taps outside the line read the zeros stored there.
+__device__ __forceinline__ float band_gen3(const float* dc, int r, int M, const float* __restrict__ whi,
+                                           const float* __restrict__ wlo, int K, int B, int all_explicit) {
+  const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit) + K;  // wh[d]: tap of delta_{r + d}
+  const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit) + K;
+  float acc = 0.0f, lo2 = 0.0f;
+#pragma unroll
+  for (int dist = K3H; dist >= 1; --dist) {
+    if (dist <= K + 1) {
+      const float d = dc[dist];
+      acc = fmaf(__ldg(wh + dist), d, acc);
+      lo2 = fmaf(__ldg(wl + dist), d, lo2);
+    }
+    if (dist <= K) {
+      const float d = dc[-dist];
+      acc = fmaf(__ldg(wh - dist), d, acc);
+      lo2 = fmaf(__ldg(wl - dist), d, lo2);
+    }
+  }
+  lo2 = fmaf(__ldg(wl), dc[0], lo2);
+  return fmaf(__ldg(wh), dc[0], acc + lo2);
+}
+
+// One Pade term y = A^{-1} D1 G along AXIS, R (+)= sign y, on a tile of T3O band rows r0 ..
+// r0 + T3O - 1 of 32 lines along the transverse axis P (y for x lines, x otherwise), at one
+// coordinate q of the other transverse axis Q.  The first differences of G over the rows' reach
+// (K3H on each side) go to shared memory, a row per line; a thread then takes eight consecutive
+// rows of one line (lanes across the lines, so every lane of a warp is at the same rows and the
+// end rows of the table take their path together) through a register window.  x lines are read
+// and written along x by whole warps, the results passing through shared memory; y and z lines
+// are read and written with the lanes across x.  Rows away from the line ends take the interior
+// row from constant memory; the end rows take the explicit FP32 hi + lo table rows.  Wall lines
+// need no test: G is 0 on them, so y is 0 there.  Without accumulation the first and last tiles of
+// a line also write the wall points beyond the band rows (0).
 template <int AXIS>
 struct TermGeo {
-  static constexpr int P = AXIS == 0 ? 1 : 0;          // in-tile transverse axis
-  static constexpr int Q = AXIS == 2 ? 1 : 2;          // the other transverse axis
-  static constexpr int NPL = AXIS == 0 ? 8 : 32;       // lines per tile
+  static constexpr int P = AXIS == 0 ? 1 : 0;  // in-tile transverse axis
+  static constexpr int Q = AXIS == 2 ? 1 : 2;  // the other transverse axis
 };
+constexpr int DP3 = D3L | 1;  // odd row pitch: lanes across the rows are conflict-free
 
 template <int AXIS>
-__global__ void __launch_bounds__(256) k_term3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 ss,
-                                                  float* __restrict__ R, Shape3 sd, int out_off, int M, int ghost_even,
-                                                  float cb_hi, float cb_lo, const float* __restrict__ whi,
-                                                  const float* __restrict__ wlo, int K, int B, int all_explicit,
-                                                  float sign, int accumulate) {
-  using G = TermGeo<AXIS>;
-  constexpr int P = G::P, Q = G::Q, NPL = G::NPL;
-  __shared__ float dlt[(NPL + 2) * X3P];
-  __shared__ float dd[NPL * D3P];
-  // tile coordinates: along (destination) o0, lines p0 .. p0+NPL-1, transverse q
-  int o0, p0, q;
-  if (AXIS == 0) { o0 = blockIdx.x * T3O; p0 = blockIdx.y * NPL; q = blockIdx.z; }
-  else if (AXIS == 1) { p0 = blockIdx.x * NPL; o0 = blockIdx.y * T3O; q = blockIdx.z; }
-  else { p0 = blockIdx.x * NPL; q = blockIdx.y; o0 = blockIdx.z * T3O; }
-  const int r0 = o0 - out_off;  // difference / band index of the first destination point
+__global__ void __launch_bounds__(256, 4) k_term3d32(const float* __restrict__ gh, const float* __restrict__ gl, Shape3 ss,
+                                                     float* __restrict__ R, Shape3 sd, int out_off, int M,
+                                                     const float* __restrict__ whi, const float* __restrict__ wlo, int K,
+                                                     int B, int all_explicit, float sign, int accumulate) {
+  constexpr int P = TermGeo<AXIS>::P, Q = TermGeo<AXIS>::Q;
+  __shared__ float dd[32 * DP3];
+  int tr, p0, q;
+  if (AXIS == 0) { tr = blockIdx.x; p0 = blockIdx.y * 32; q = blockIdx.z; }
+  else if (AXIS == 1) { p0 = blockIdx.x * 32; tr = blockIdx.y; q = blockIdx.z; }
+  else { p0 = blockIdx.x * 32; q = blockIdx.y; tr = blockIdx.z; }
+  const int r0 = tr * T3O;  // first band row of the tile
   const int st[3] = {1, ss.n[0], ss.n[0] * ss.n[1]};
   const int sdt[3] = {1, sd.n[0], sd.n[0] * sd.n[1]};
-  const int nA = sd.n[AXIS], nP = sd.n[P], nQ = sd.n[Q];
-  const bool q_wall = sd.bc[Q] == DIR && (q == 0 || q == nQ - 1);
-  // source index of difference m on source line (p, q): along index m, transverse p, q
-  auto src_index = [&](int m, int p, int qq) { return m * st[AXIS] + p * st[P] + qq * st[Q]; };
-  auto delta_at = [&](int idx) { return (hi[idx + st[AXIS]] - hi[idx]) + (lo[idx + st[AXIS]] - lo[idx]); };
-  auto p_line = [&](int p) -> int {  // source line for transverse P index p (-1: zero line)
-    if (p >= 0 && p < nP) return p;
-    if (ss.bc[P] == NEU) return p < 0 ? 0 : nP - 1;
-    return -1;
-  };
-  // Tiles whose transverse lines and neighbours are all in range (the along-line ends are handled
-  // per element): warp-structured loops with one base address per row.
-  const bool inner = !q_wall && p0 - 1 >= 0 && p0 + NPL + 1 <= nP && q >= 1 && q + 1 <= nQ - 1;
+  const int nA = sd.n[AXIS], nP = sd.n[P];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW3 = 8;
-  if (inner) {
-    const int sa = st[AXIS], sq = st[Q];
-    // difference at along index m on the line whose difference-0 index is `line`: ghost rules of
-    // k_dfilt3d32 at the ends
-    auto delta_m = [&](int line, int m) -> float {
-      if (m < 0 || m >= M) {
-        if (!ghost_even || m < -1 || m > M) return 0.0f;
-        m = m < 0 ? 0 : M - 1;
-      }
-      return delta_at(line + m * sa);
-    };
-    if (AXIS == 0) {
-      for (int pl = warp; pl < NPL + 2; pl += NW3) {
-        const int line = src_index(0, p0 - 1 + pl, q);
+  const bool last_tile = r0 + T3O >= M;
+  const int mb = r0 - K3H;  // m of difference column 0
+  auto fast = [&](int r) { return !all_explicit && r >= B && r < M - B && r >= KB3 && r + KB3 + 1 < M; };
+  // x lines: warp w reads and writes lines 4 w .. 4 w + 3 of the tile along x
+  float racc[8];  // R at this thread's outputs when accumulating, fetched first
+  if (AXIS == 0) {
 #pragma unroll
-        for (int cc = 0; cc < (X3L + 31) / 32; ++cc) {
-          const int j = lane + 32 * cc;
-          if (32 * cc + 32 <= X3L || j < X3L) dlt[pl * X3P + j] = delta_m(line, r0 - K3H - 1 + j);
-        }
-      }
-      __syncthreads();
-      const int pl = warp;
-      const int line = src_index(0, p0 + pl, q);
-      const float* cbase = dlt + (pl + 1) * X3P + 1;
+    for (int i = 0; i < 4; ++i) {
+      const int p = p0 + 4 * warp + i, ld = p * sdt[P] + q * sdt[Q];
 #pragma unroll
-      for (int cc = 0; cc < (D3L + 31) / 32; ++cc) {
-        const int j = lane + 32 * cc;
-        if (32 * cc + 32 <= D3L || j < D3L) {
-          const int m = r0 - K3H + j;
-          float out = 0.0f;
-          if (m >= 0 && m < M) {
-            const float* c = cbase + j;
-            const float v = c[0];
-            const int at = line + m * sa;
-            const float lap = (((c[-1] - v) + (c[1] - v)) + ((c[-X3P] - v) + (c[X3P] - v))) +
-                              ((delta_at(at - sq) - v) + (delta_at(at + sq) - v));
-            out = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
-          }
-          dd[pl * D3P + j] = out;
-        }
+      for (int c = 0; c < 2; ++c) {
+        const int r = r0 + lane + 32 * c;
+        racc[2 * i + c] = (accumulate && p < nP && r < M) ? R[ld + r + out_off] : 0.0f;
       }
-    } else {
-      // lanes across the lines, warp w along a contiguous run of the line: each source row is read
-      // once per run and its hi / lo kept for the next difference; the along-line ends (ghosts)
-      // are split off, so the sliding loops carry no range tests
-      const int mb = r0 - K3H - 1;  // m of raw column 0
-      {
-        constexpr int RJ = (X3L + NW3 - 1) / NW3;
-        const int ja = warp * RJ, jb = min(ja + RJ, X3L);
-        const int ca = max(ja, min(jb, -mb)), cb = max(ca, min(jb, M - mb));
-        const int line = src_index(0, p0 - 1, q) + lane;
-        float* row = dlt + lane * X3P;
-        for (int j = ja; j < ca; ++j) row[j] = delta_m(line, mb + j);
-        if (ca < cb) {
-          const float* hp = hi + line + (mb + ca) * sa;
-          const float* lp = lo + line + (mb + ca) * sa;
-          float h0 = hp[0], l0 = lp[0];
-#pragma unroll 8
-          for (int j = ca; j < cb; ++j) {
-            hp += sa;
-            lp += sa;
-            const float h1 = *hp, l1 = *lp;
-            row[j] = (h1 - h0) + (l1 - l0);
-            h0 = h1;
-            l0 = l1;
-          }
-        }
-        for (int j = cb; j < jb; ++j) row[j] = delta_m(line, mb + j);
-      }
-      for (int idx = threadIdx.x; idx < 2 * X3L; idx += blockDim.x) {  // the last two lines
-        const int e = idx >= X3L, j = idx - e * X3L;
-        dlt[(32 + e) * X3P + j] = delta_m(src_index(0, p0 + 31 + e, q), mb + j);
-      }
-      __syncthreads();
-      const int mf = r0 - K3H;  // m of filtered column 0
-      constexpr int RD = (D3L + NW3 - 1) / NW3;
-      const int ja = warp * RD, jb = min(ja + RD, D3L);
-      const int ca = max(ja, min(jb, -mf)), cb = max(ca, min(jb, M - mf));
-      float* out = dd + lane * D3P;
-      for (int j = ja; j < ca; ++j) out[j] = 0.0f;
-      if (ca < cb) {
-        // Q neighbours (lines q - 1 and q + 1) slide along the line the same way
-        const int at0 = src_index(0, p0, q) + lane + (mf + ca) * sa;
-        const float* hm = hi + at0 - sq;
-        const float* lm = lo + at0 - sq;
-        const float* hq = hi + at0 + sq;
-        const float* lq = lo + at0 + sq;
-        float hm0 = hm[0], lm0 = lm[0], hq0 = hq[0], lq0 = lq[0];
-        const float* c = dlt + (lane + 1) * X3P + 1;
-#pragma unroll 4
-        for (int j = ca; j < cb; ++j) {
-          hm += sa;
-          lm += sa;
-          hq += sa;
-          lq += sa;
-          const float hm1 = *hm, lm1 = *lm, hq1 = *hq, lq1 = *lq;
-          const float c1 = (hm1 - hm0) + (lm1 - lm0);
-          const float c2 = (hq1 - hq0) + (lq1 - lq0);
-          const float v = c[j];
-          const float lap = (((c[j - 1] - v) + (c[j + 1] - v)) + ((c[j - X3P] - v) + (c[j + X3P] - v))) +
-                            ((c1 - v) + (c2 - v));
-          out[j] = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
-          hm0 = hm1;
-          lm0 = lm1;
-          hq0 = hq1;
-          lq0 = lq1;
-        }
-      }
-      for (int j = cb; j < jb; ++j) out[j] = 0.0f;
     }
-    __syncthreads();
-  } else if (!q_wall) {
-    // 1) raw differences of the centre plane: lines p0-1 .. p0+NPL, m = r0 - K3H - 1 + j
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < (NPL + 2) * X3L; idx += blockDim.x) {
-      int pl, j;
-      if (AXIS == 0) { pl = idx / X3L; j = idx - pl * X3L; }
-      else { j = idx / (NPL + 2); pl = idx - j * (NPL + 2); }
-      int m = r0 - K3H - 1 + j;
-      const int pp = p_line(p0 - 1 + pl);
-      float v = 0.0f;
-      if (pp >= 0) {
-        bool zero = false;
-        if (m < 0 || m >= M) {
-          if (!ghost_even || m < -1 || m > M) zero = true;
-          else m = m < 0 ? 0 : M - 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ll = 4 * warp + i, p = p0 + ll;
+      if (p >= nP) break;
+      const int line = p * st[P] + q * st[Q];
+      const int ns = ss.n[0];
+      float h[4], l[4];  // G at source points mb + lane + 32 c (chunk 3: none, only its lane 0 is read)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int sidx = mb + lane + 32 * c;
+        const bool ok = sidx >= 0 && sidx < ns;
+        h[c] = ok ? gh[line + sidx] : 0.0f;
+        l[c] = ok ? gl[line + sidx] : 0.0f;
+      }
+      h[3] = l[3] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float h1 = __shfl_down_sync(0xffffffffu, h[c], 1), l1 = __shfl_down_sync(0xffffffffu, l[c], 1);
+        const float hn = __shfl_sync(0xffffffffu, h[c + 1], 0), ln = __shfl_sync(0xffffffffu, l[c + 1], 0);
+        if (lane == 31) {
+          h1 = hn;
+          l1 = ln;
         }
-        if (!zero) v = delta_at(src_index(m, pp, q));
+        const int j = lane + 32 * c, m = mb + j;
+        if (j < D3L) dd[ll * DP3 + j] = (m >= 0 && m < M) ? (h1 - h[c]) + (l1 - l[c]) : 0.0f;
       }
-      dlt[pl * X3P + j] = v;
     }
-    __syncthreads();
-    // 2) filtered differences d = 12 beta delta + L delta on lines p0 .. p0+NPL-1
-    const int qm = q > 0 ? q - 1 : (ss.bc[Q] == NEU ? 0 : -1);
-    const int qp = q < nQ - 1 ? q + 1 : (ss.bc[Q] == NEU ? nQ - 1 : -1);
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < NPL * D3L; idx += blockDim.x) {
-      int pl, j;
-      if (AXIS == 0) { pl = idx / D3L; j = idx - pl * D3L; }
-      else { j = idx / NPL; pl = idx - j * NPL; }
-      const int m = r0 - K3H + j;
-      const int p = p0 + pl;
-      float out = 0.0f;
-      const bool p_unk = p < nP && interior(sd.bc[P], p, nP);
-      if (p_unk && m >= 0 && m < M) {
-        const float* c = dlt + (pl + 1) * X3P + j + 1;
-        const float v = c[0];
-        const float a1 = c[-1], a2 = c[1];
-        const float b1 = c[-X3P], b2 = c[X3P];
-        const float c1 = qm >= 0 ? delta_at(src_index(m, p, qm)) : 0.0f;
-        const float c2 = qp >= 0 ? delta_at(src_index(m, p, qp)) : 0.0f;
-        const float lap = (((a1 - v) + (a2 - v)) + ((b1 - v) + (b2 - v))) + ((c1 - v) + (c2 - v));
-        out = fmaf(cb_hi, v, fmaf(cb_lo, v, lap));
-      }
-      dd[pl * D3P + j] = out;
-    }
-    __syncthreads();
   }
-  // 3) band y = A^{-1} d and R (+)= sign y at every destination point of the tile
-  auto band_row = [&](const float* dc, int r) -> float {  // dc[t] = d_{r + t}
-    if (!all_explicit && r >= B && r < M - B && r >= KB3 && r + KB3 + 1 < M) {
-      float acc = c_w3[2 * KB3 + 1] * dc[KB3 + 1];
+  const int p = p0 + lane;  // the line of this thread in the band phase
+  const bool live = p < nP;
+  const int ob = 8 * warp, rb = r0 + ob;
+  const int sA = sdt[AXIS];
+  const int ld = p * sdt[P] + q * sdt[Q];
+  if (AXIS != 0) {
 #pragma unroll
-      for (int dist = KB3; dist >= 1; --dist) {
-        acc = fmaf(c_w3[KB3 + dist], dc[dist], acc);
-        acc = fmaf(c_w3[KB3 - dist], dc[-dist], acc);
-      }
-      acc = fmaf(c_wl3[0], dc[-1], acc);
-      acc = fmaf(c_wl3[2], dc[1], acc);
-      acc = fmaf(c_wl3[1], dc[0], acc);
-      return fmaf(c_w3[KB3], dc[0], acc);
-    }
-    const float* wh = pade_row_ptr(whi, r, M, K, B, all_explicit);
-    const float* wl = pade_row_ptr(wlo, r, M, K, B, all_explicit);
-    float acc = 0.0f, lo2 = 0.0f;
-    for (int dist = K + 1; dist >= 1; --dist) {
-      for (int side = 1; side >= -1; side -= 2) {
-        const int mm = r + side * dist, t = mm - r + K;
-        if (t < 0 || t > 2 * K + 1 || mm < 0 || mm >= M) continue;
-        const float dm = dc[mm - r];
-        acc = fmaf(__ldg(wh + t), dm, acc);
-        lo2 = fmaf(__ldg(wl + t), dm, lo2);
-      }
-    }
-    lo2 = fmaf(__ldg(wl + K), dc[0], lo2);
-    return fmaf(__ldg(wh + K), dc[0], acc + lo2);
-  };
-  if (inner) {  // every transverse line of the tile is an unknown line
-    if (AXIS == 0) {
-      const int pl = warp;
-      const int pd0 = (p0 + pl) * sdt[1] + q * sdt[2];
+    for (int u = 0; u < 8; ++u) racc[u] = (accumulate && live && rb + u < M) ? R[ld + (rb + u + out_off) * sA] : 0.0f;
+    // differences j in [w RJ, (w + 1) RJ) of the lane's line, all loads issued first
+    constexpr int RJ = (D3L + 7) / 8;
+    const int sa = st[AXIS];
+    const int ja = warp * RJ;
+    const float* gph = gh + p * st[P] + q * st[Q];
+    const float* gpl = gl + p * st[P] + q * st[Q];
+    float hv[RJ + 1], lv[RJ + 1];
 #pragma unroll
-      for (int cc = 0; cc < T3O / 32; ++cc) {
-        const int od = o0 + lane + 32 * cc;
-        if (od >= nA) continue;
-        const int r = od - out_off, pd = pd0 + od;
-        if (!interior(sd.bc[AXIS], od, nA) || r < 0 || r >= M) {
-          if (!accumulate) R[pd] = 0.0f;
-          continue;
-        }
-        const float y = band_row(dd + pl * D3P + (r - r0 + K3H), r);
-        R[pd] = accumulate ? R[pd] + sign * y : sign * y;
-      }
+    for (int i = 0; i <= RJ; ++i) {
+      const int sidx = mb + ja + i;  // source point
+      const bool ok = live && sidx >= 0 && sidx <= M;
+      hv[i] = ok ? gph[sidx * sa] : 0.0f;
+      lv[i] = ok ? gpl[sidx * sa] : 0.0f;
+    }
+    float* row = dd + lane * DP3;
+#pragma unroll
+    for (int i = 0; i < RJ; ++i) {
+      const int j = ja + i, m = mb + j;
+      if (j < D3L) row[j] = (m >= 0 && m < M) ? (hv[i + 1] - hv[i]) + (lv[i + 1] - lv[i]) : 0.0f;
+    }
+  }
+  __syncthreads();
+  float y[8];
+  if (live) {
+    const float* row = dd + lane * DP3;
+    if (rb + 7 < M && fast(rb) && fast(rb + 7)) {
+      float v[23];
+#pragma unroll
+      for (int i = 0; i < 23; ++i) v[i] = row[ob + K3H - KB3 + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) y[u] = band_fast3(v + u);
     } else {
-      for (int o = warp; o < T3O; o += NW3) {
-        const int od = o0 + o;
-        if (od >= nA) break;
-        int coord[3];
-        coord[AXIS] = od;
-        coord[P] = p0 + lane;
-        coord[Q] = q;
-        const int pd = coord[0] * sdt[0] + coord[1] * sdt[1] + coord[2] * sdt[2];
-        const int r = od - out_off;
-        if (!interior(sd.bc[AXIS], od, nA) || r < 0 || r >= M) {
-          if (!accumulate) R[pd] = 0.0f;
-          continue;
-        }
-        const float y = band_row(dd + lane * D3P + (r - r0 + K3H), r);
-        R[pd] = accumulate ? R[pd] + sign * y : sign * y;
+#pragma unroll 1
+      for (int u = 0; u < 8; ++u) {
+        const int rr = rb + u;
+        const float* dc = row + rr - r0 + K3H;
+        y[u] = rr >= M ? 0.0f : (fast(rr) ? band_fast3(dc - KB3) : band_gen3(dc, rr, M, whi, wlo, K, B, all_explicit));
       }
+    }
+  }
+  if (AXIS != 0) {
+    if (!live) return;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (rb + u < M) R[ld + (rb + u + out_off) * sA] = accumulate ? racc[u] + sign * y[u] : sign * y[u];
+    if (!accumulate && warp == 0) {
+      if (tr == 0)
+        for (int od = 0; od < out_off; ++od) R[ld + od * sA] = 0.0f;
+      if (last_tile)
+        for (int od = M + out_off; od < nA; ++od) R[ld + od * sA] = 0.0f;
     }
     return;
   }
-  for (int idx = threadIdx.x; idx < NPL * T3O; idx += blockDim.x) {
-    int pl, o;
-    if (AXIS == 0) { pl = idx / T3O; o = idx - pl * T3O; }
-    else { o = idx / NPL; pl = idx - o * NPL; }
-    const int od = o0 + o, p = p0 + pl;
-    if (od >= nA || p >= nP) continue;
-    int coord[3];
-    coord[AXIS] = od;
-    coord[P] = p;
-    coord[Q] = q;
-    const int pd = coord[0] * sdt[0] + coord[1] * sdt[1] + coord[2] * sdt[2];
-    const int r = od - out_off;
-    const bool unk = !q_wall && interior(sd.bc[AXIS], od, nA) && interior(sd.bc[P], p, nP) && r >= 0 && r < M;
-    if (!unk) {
-      if (!accumulate) R[pd] = 0.0f;
-      continue;
+  // x lines: y through shared memory (row = line, column = band row), written along x
+  __syncthreads();
+  if (live) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) dd[lane * DP3 + ob + u] = y[u];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ll = 4 * warp + i, pl = p0 + ll;
+    if (pl >= nP) break;
+    const int ldl = pl * sdt[P] + q * sdt[Q];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int o = lane + 32 * c, r = r0 + o;
+      if (r < M) {
+        const float yv = dd[ll * DP3 + o];
+        R[ldl + r + out_off] = accumulate ? racc[2 * i + c] + sign * yv : sign * yv;
+      }
     }
-    const float acc = band_row(dd + pl * D3P + (r - r0 + K3H), r);
-    R[pd] = accumulate ? R[pd] + sign * acc : sign * acc;
+    if (!accumulate) {
+      if (tr == 0 && lane < out_off) R[ldl + lane] = 0.0f;
+      if (last_tile && M + out_off + lane < nA) R[ldl + M + out_off + lane] = 0.0f;
+    }
   }
 }
 
@@ -848,50 +821,56 @@ ms_status step3d64(ms_grid* g) {
   return MS_OK;
 }
 
-// FP32_REFINED: one Pade term y = A^{-1} D1 G~ of source component cs along axis, added with
-// `sign` into R on component cd.
-// Returns the number of launches issued.
-int term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, float sign, int accumulate) {
+// FP32_REFINED: G (hi, lo) = 12 beta u + L u of component c into the filter buffers of slot c % 3.
+void filter3d32(ms_grid* g, int c, float cb_hi, float cb_lo) {
+  Grid3D* G3 = g->g3;
+  const Shape3& s = G3->sh[c];
+  const dim3 grd((s.n[0] + 31) / 32, (s.n[1] + 7) / 8, (s.n[2] + FZ3 - 1) / FZ3), blk(32, 8, 1);
+  k_ffilt3d32<<<grd, blk, 0, g->stream>>>(G3->hi[c], G3->lo[c], s, G3->gh[c % 3], G3->gl[c % 3], cb_hi, cb_lo);
+  // state hi + lo in, G hi + lo out
+  prof_mark(g, KK_FILT3D32, 16.0 * (double)s.size());
+}
+
+// FP32_REFINED: one Pade term y = A^{-1} D1 G of source component cs (G made by filter3d32) along
+// axis, added with `sign` into R on component cd.  Returns the number of launches issued.
+int term3d32(ms_grid* g, int axis, int cs, int cd, float sign, int accumulate) {
   Grid3D* G3 = g->g3;
   const Shape3& ss = G3->sh[cs];
   const Shape3& sd = G3->sh[cd];
   const int kind = (ss.bc[axis] == NEU) ? HALF_TO_NODE : NODE_TO_HALF;
   const PadeTable& t = g->pade32[kind];
   const int off = (kind == HALF_TO_NODE) ? 1 : 0;
-  const int ghost_even = (ss.bc[axis] == DIR);
+  const float* gh = G3->gh[cs % 3];
+  const float* gl = G3->gl[cs % 3];
+  float* R = G3->s32[1];
   if (t.K + 1 <= K3H) {
-    // fused difference-filter and band in one tiled kernel
-    const int nA = sd.n[axis];
-    const int ta = (nA + T3O - 1) / T3O;
-    float* R = G3->s32[1];
+    // differences and band in one tiled kernel
+    const int nt = (t.M + T3O - 1) / T3O;
     if (axis == 0) {
-      dim3 grd(ta, (sd.n[1] + 7) / 8, sd.n[2]);
-      k_term3d32<0><<<grd, 256, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, R, sd, off, t.M, ghost_even, cb_hi, cb_lo,
-                                                 t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
+      const dim3 grd(nt, (sd.n[1] + 31) / 32, sd.n[2]);
+      k_term3d32<0><<<grd, 256, 0, g->stream>>>(gh, gl, ss, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit,
+                                                 sign, accumulate);
     } else if (axis == 1) {
-      dim3 grd((sd.n[0] + 31) / 32, ta, sd.n[2]);
-      k_term3d32<1><<<grd, 256, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, R, sd, off, t.M, ghost_even, cb_hi, cb_lo,
-                                                 t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
+      const dim3 grd((sd.n[0] + 31) / 32, nt, sd.n[2]);
+      k_term3d32<1><<<grd, 256, 0, g->stream>>>(gh, gl, ss, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit,
+                                                 sign, accumulate);
     } else {
-      dim3 grd((sd.n[0] + 31) / 32, sd.n[1], ta);
-      k_term3d32<2><<<grd, 256, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, R, sd, off, t.M, ghost_even, cb_hi, cb_lo,
-                                                 t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign, accumulate);
+      const dim3 grd((sd.n[0] + 31) / 32, sd.n[1], nt);
+      k_term3d32<2><<<grd, 256, 0, g->stream>>>(gh, gl, ss, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit,
+                                                 sign, accumulate);
     }
-    // state hi + lo in, R out (read too when accumulating)
+    // G hi + lo in, R out (read too when accumulating)
     prof_mark(g, KK_TERM3D32, 4.0 * (2.0 * (double)ss.size() + (accumulate ? 2.0 : 1.0) * (double)sd.size()));
     return 1;
   }
   float* d = G3->s32[0];
-  float* R = G3->s32[1];
   const dim3 grd = grid3(sd, kBlk);
   if (axis == 0)
-    k_dfilt3d32<0><<<grd, kBlk, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, d, sd, off, t.M, ghost_even, cb_hi, cb_lo);
+    k_diff3d32<0><<<grd, kBlk, 0, g->stream>>>(gh, gl, ss, d, sd, off, t.M);
   else if (axis == 1)
-    k_dfilt3d32<1><<<grd, kBlk, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, d, sd, off, t.M, ghost_even, cb_hi, cb_lo);
+    k_diff3d32<1><<<grd, kBlk, 0, g->stream>>>(gh, gl, ss, d, sd, off, t.M);
   else
-    k_dfilt3d32<2><<<grd, kBlk, 0, g->stream>>>(G3->hi[cs], G3->lo[cs], ss, d, sd, off, t.M, ghost_even, cb_hi, cb_lo);
-  // state hi + lo in, d out
-  prof_mark(g, KK_DFILT3D32, 4.0 * (2.0 * (double)ss.size() + (double)sd.size()));
+    k_diff3d32<2><<<grd, kBlk, 0, g->stream>>>(gh, gl, ss, d, sd, off, t.M);
   if (axis == 0)
     k_band3d32<0><<<grd, kBlk, 0, g->stream>>>(d, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign,
                                                 accumulate);
@@ -901,8 +880,9 @@ int term3d32(ms_grid* g, int axis, int cs, int cd, float cb_hi, float cb_lo, flo
   else
     k_band3d32<2><<<grd, kBlk, 0, g->stream>>>(d, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit, sign,
                                                 accumulate);
-  // d in, R out (read too when accumulating)
-  prof_mark(g, KK_BAND3D32, 4.0 * (double)sd.size() * (accumulate ? 3.0 : 2.0));
+  // G hi + lo in, d out; d in, R out (read too when accumulating)
+  prof_mark(g, KK_BAND3D32,
+            4.0 * (2.0 * (double)ss.size() + (double)sd.size()) + 4.0 * (double)sd.size() * (accumulate ? 3.0 : 2.0));
   return 2;
 }
 
@@ -979,17 +959,23 @@ ms_status step3d32(ms_grid* g) {
     prof_mark(g, KK_SRC, 8.0 * (double)G3->sh[c].size());
     nl += 1;
   };
+  // Step 1: G~ of H_x, H_y, H_z, then per E component its two Pade terms and its solve
+  for (int c = 3; c < 6; ++c) filter3d32(g, c, k.cb_hi, k.cb_lo);
+  nl += 3;
   for (int e = 0; e < 3; ++e) {
     const int p1 = (e + 1) % 3, p2 = (e + 2) % 3;
-    nl += term3d32(g, p1, 3 + p2, e, k.cb_hi, k.cb_lo, 1.0f, 0);
-    nl += term3d32(g, p2, 3 + p1, e, k.cb_hi, k.cb_lo, -1.0f, 1);
+    nl += term3d32(g, p1, 3 + p2, e, 1.0f, 0);
+    nl += term3d32(g, p2, 3 + p1, e, -1.0f, 1);
     add_src(e);
     solve3d32(g, e, k.d_hi, k.d_lo, k.omega, k.sE_hi, k.sE_lo, k.S, &nl);
   }
+  // Step 2: G~ of the updated E components, then per H component
+  for (int c = 0; c < 3; ++c) filter3d32(g, c, k.cb_hi, k.cb_lo);
+  nl += 3;
   for (int hc = 0; hc < 3; ++hc) {
     const int p1 = (hc + 1) % 3, p2 = (hc + 2) % 3;
-    nl += term3d32(g, p1, p2, 3 + hc, k.cb_hi, k.cb_lo, -1.0f, 0);
-    nl += term3d32(g, p2, p1, 3 + hc, k.cb_hi, k.cb_lo, 1.0f, 1);
+    nl += term3d32(g, p1, p2, 3 + hc, -1.0f, 0);
+    nl += term3d32(g, p2, p1, 3 + hc, 1.0f, 1);
     add_src(3 + hc);
     solve3d32(g, 3 + hc, k.d_hi, k.d_lo, k.omega, k.sH_hi, k.sH_lo, k.S, &nl);
   }
@@ -1282,6 +1268,8 @@ ms_status create_grid3d(const ms_grid_desc* d, ms_grid** out) {
     for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->hi[c], G3->sh[c].size());
     for (int c = 0; c < 6 && s == MS_OK; ++c) s = alloc3(&G3->lo[c], G3->sh[c].size());
     for (int k = 0; k < 4 && s == MS_OK; ++k) s = alloc3(&G3->s32[k], G3->nmax);
+    for (int k = 0; k < 3 && s == MS_OK; ++k) s = alloc3(&G3->gh[k], G3->nmax);
+    for (int k = 0; k < 3 && s == MS_OK; ++k) s = alloc3(&G3->gl[k], G3->nmax);
     for (int k = 0; k < 2 && s == MS_OK; ++k) s = alloc3(&G3->s64[k], G3->nmax);
   }
   if (s == MS_OK) s = alloc3(&g->d_result, 8);
@@ -1379,6 +1367,10 @@ void destroy_grid3d(ms_grid* g) {
   }
   for (int k = 0; k < 7; ++k) cudaFree(G3->s64[k]);
   for (int k = 0; k < 4; ++k) cudaFree(G3->s32[k]);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(G3->gh[k]);
+    cudaFree(G3->gl[k]);
+  }
   for (int k = 0; k < 2; ++k) {
     cudaFree(g->pade32[k].d_whi);
     cudaFree(g->pade32[k].d_wlo);

@@ -59,7 +59,7 @@ struct Graph {
 // Kernel kinds reported by ms_step_profiled.
 enum KernelKind {
   KK_FILTER64 = 0, KK_PADE64 = 1, KK_P1SWEEP64 = 2, KK_YEE64 = 3, KK_CURL32 = 4, KK_SOLVE32 = 5,
-  KK_FILTER3D64 = 6, KK_PADE3D64 = 7, KK_SWEEP3D64 = 8, KK_DFILT3D32 = 9, KK_BAND3D32 = 10, KK_SWEEP3D32 = 11,
+  KK_FILTER3D64 = 6, KK_PADE3D64 = 7, KK_SWEEP3D64 = 8, KK_FILT3D32 = 9, KK_BAND3D32 = 10, KK_SWEEP3D32 = 11,
   KK_NC64 = 12, KK_SRC = 13, KK_TERM3D32 = 14, KK_TSGEMM = 15, KK_TSPACK = 16,
   KK_COUNT
 };
