@@ -218,6 +218,29 @@ constexpr int KB3 = 7;
 __constant__ float c_w3[2 * KB3 + 2];
 __constant__ float c_wl3[3];
 
+// Paired FP32 arithmetic (two correctly rounded operations per instruction, sm_100 and later):
+// bitwise the same as the scalar operations on each half.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// ff_add_scaled3 on two independent pairs at once.
+__device__ __forceinline__ void ff_add_scaled3_2(float2& hi, float2& lo, float2 x, float2 s_hi, float2 s_lo) {
+  const float2 p = mul2(s_hi, x);
+  float2 e = fma2(s_hi, x, neg2(p));
+  e = fma2(s_lo, x, e);
+  const float2 s = add2(hi, p);
+  const float2 bb = sub2(s, hi);
+  const float2 err = add2(sub2(hi, sub2(s, bb)), sub2(p, bb));
+  const float2 l = add2(lo, add2(err, e));
+  const float2 h2 = add2(s, l);
+  lo = sub2(l, sub2(h2, s));
+  hi = h2;
+}
+
 // Float-float filter of one component, Eq. "eq:ell" in the units of the FP32 step:
 //   G = 12 beta u + L u,  L = h^2 Delta_h (7 points),
 // with even ghosts on Neumann axes and the stored wall zeros on Dirichlet axes; G = 0 at wall
@@ -226,73 +249,95 @@ __constant__ float c_wl3[3];
 // accuracy), joins the low word, and two-sum renormalises the pair.  The Pade terms below then
 // difference G: D1 G = (12 beta + L') D1 u, the filter commuting with the difference under the
 // ghost rules (zero differences beyond the ends of a Neumann line, even ones on a Dirichlet line).
-// A thread takes one (x, y) column of a 32 x 8 tile and marches FZ3 planes along z, its z
-// neighbours in registers; the ten loads of the next plane (own point one plane further, x and y
-// neighbours) are issued before the current plane is computed.
-constexpr int FZ3 = 8;
-__global__ void __launch_bounds__(256) k_ffilt3d32(const float* __restrict__ hi, const float* __restrict__ lo, Shape3 s,
-                                                   float* __restrict__ gh, float* __restrict__ gl, float cb_hi,
-                                                   float cb_lo) {
+// The layout is that of the sweep below: a block of 32 x 8 threads takes a 32 x 16 tile, a thread
+// rows j and j + 8 of one column as a pair (paired FP32 instructions), marching FZ3 planes along
+// z with the planes z-1, z, z+1 (hi and lo, one-point halo in x and y, clamped) in a ring in
+// shared memory; the next plane is fetched into registers while the current one is computed.
+constexpr int FZ3 = 16;
+constexpr int FTX = 32, FTT = 8, FTY = 2 * FTT;
+constexpr int FXP = FTX + 2, FRP = FTT + 2, FN = FRP * FXP;
+static_assert(FN <= 2 * FTX * FTT, "two staged pairs per thread");
+__global__ void __launch_bounds__(FTX * FTT, 6) k_ffilt3d32(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                            Shape3 s, float* __restrict__ gh, float* __restrict__ gl,
+                                                            float cb_hi, float cb_lo) {
+  __shared__ float2 hs[3][FRP][FXP];
+  __shared__ float2 ls[3][FRP][FXP];
   const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-  if (i >= n0 || j >= n1) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * FTX + tx, j = blockIdx.y * FTY + ty;  // rows j and j + FTT
   const int k0 = blockIdx.z * FZ3, k1 = min(k0 + FZ3, n2);
+  const bool in0 = i < n0 && j < n1, in1 = i < n0 && j + FTT < n1;
+  const bool ux = i < n0 && interior(s.bc[0], i, n0);
+  const bool unk0 = in0 && ux && interior(s.bc[1], j, n1), unk1 = in1 && ux && interior(s.bc[1], j + FTT, n1);
   const int sz = n0 * n1;
-  const bool unk_xy = interior(s.bc[0], i, n0) && interior(s.bc[1], j, n1);
-  const int nb[4] = {clampi(i - 1, n0) - i, clampi(i + 1, n0) - i, (clampi(j - 1, n1) - j) * n0,
-                     (clampi(j + 1, n1) - j) * n0};
+  const int t1 = ty * FTX + tx, t2 = t1 + FTX * FTT;
+  const bool has2 = t2 < FN;
+  auto pair_off = [&](int e, int half) {
+    const int row = e / FXP, col = e - row * FXP;
+    return clampi(blockIdx.y * FTY + row - 1 + half * FTT, n1) * n0 + clampi(blockIdx.x * FTX + col - 1, n0);
+  };
+  const int o1a = pair_off(t1, 0), o1b = pair_off(t1, 1);
+  const int o2a = pair_off(has2 ? t2 : t1, 0), o2b = pair_off(has2 ? t2 : t1, 1);
+  float2 ha, la, hb, lb;
+  auto fetch = [&](int kk) {
+    const int q = clampi(kk, n2) * sz;
+    ha = make_float2(hi[q + o1a], hi[q + o1b]);
+    la = make_float2(lo[q + o1a], lo[q + o1b]);
+    if (has2) {
+      hb = make_float2(hi[q + o2a], hi[q + o2b]);
+      lb = make_float2(lo[q + o2a], lo[q + o2b]);
+    }
+  };
+  auto stage = [&](int slot) {
+    (&hs[slot][0][0])[t1] = ha;
+    (&ls[slot][0][0])[t1] = la;
+    if (has2) {
+      (&hs[slot][0][0])[t2] = hb;
+      (&ls[slot][0][0])[t2] = lb;
+    }
+  };
+  fetch(k0 - 1);
+  stage(0);
+  fetch(k0);
+  stage(1);
+  fetch(k0 + 1);
+  int zm = 0, z0 = 1, zp = 2;
   int p = k0 * sz + j * n0 + i;
-  const int pm = p + (clampi(k0 - 1, n2) - k0) * sz;
-  float hm = hi[pm], lm = lo[pm], hc = hi[p], lc = lo[p];
-  float nh[4], nl[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    nh[t] = hi[p + nb[t]];
-    nl[t] = lo[p + nb[t]];
-  }
-  int pp = p + (clampi(k0 + 1, n2) - k0) * sz;
-  float hp = hi[pp], lp = lo[pp];
+  const int dj = FTT * n0;
+  const int c0 = tx + 1, r0 = ty + 1;
+  const float2 cbh = bc2(cb_hi), cbl = bc2(cb_lo);
   for (int k = k0; k < k1; ++k, p += sz) {
-    // loads of plane k + 1 (its neighbours) and k + 2 (own point), if this column continues
-    const bool more = k + 1 < k1;
-    float nh2[4], nl2[4], hp2 = 0.0f, lp2 = 0.0f;
-    if (more) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        nh2[t] = hi[p + sz + nb[t]];
-        nl2[t] = lo[p + sz + nb[t]];
-      }
-      const int p2 = p + sz + (clampi(k + 2, n2) - (k + 1)) * sz;
-      hp2 = hi[p2];
-      lp2 = lo[p2];
+    stage(zp);
+    __syncthreads();
+    if (k + 1 < k1) fetch(k + 2);
+    const float2 hc = hs[z0][r0][c0], lc = ls[z0][r0][c0];
+    auto dv = [&](int pl, int rr, int cc) { return add2(sub2(hs[pl][rr][cc], hc), sub2(ls[pl][rr][cc], lc)); };
+    const float2 lap = add2(add2(add2(dv(z0, r0, c0 - 1), dv(z0, r0, c0 + 1)), add2(dv(z0, r0 - 1, c0), dv(z0, r0 + 1, c0))),
+                            add2(dv(zm, r0, c0), dv(zp, r0, c0)));
+    const float2 pr = mul2(cbh, hc);
+    float2 e = fma2(cbh, hc, neg2(pr));
+    e = fma2(cbh, lc, e);
+    e = fma2(cbl, hc, e);
+    const float2 t = add2(e, lap);
+    const float2 g_hi = add2(pr, t);
+    const float2 bb = sub2(g_hi, pr);
+    const float2 g_lo = add2(sub2(pr, sub2(g_hi, bb)), sub2(t, bb));
+    const bool uz = interior(s.bc[2], k, n2);
+    if (in0) {
+      const bool u = unk0 && uz;
+      gh[p] = u ? g_hi.x : 0.0f;
+      gl[p] = u ? g_lo.x : 0.0f;
     }
-    float g_hi = 0.0f, g_lo = 0.0f;
-    if (unk_xy && interior(s.bc[2], k, n2)) {
-      auto dv = [&](float a, float b) { return (a - hc) + (b - lc); };
-      const float lap = ((dv(nh[0], nl[0]) + dv(nh[1], nl[1])) + (dv(nh[2], nl[2]) + dv(nh[3], nl[3]))) +
-                        (dv(hm, lm) + dv(hp, lp));
-      const float pr = __fmul_rn(cb_hi, hc);
-      float e = fmaf(cb_hi, hc, -pr);
-      e = fmaf(cb_hi, lc, e);
-      e = fmaf(cb_lo, hc, e);
-      const float t = __fadd_rn(e, lap);
-      g_hi = __fadd_rn(pr, t);
-      const float bb = __fsub_rn(g_hi, pr);
-      g_lo = __fadd_rn(__fsub_rn(pr, __fsub_rn(g_hi, bb)), __fsub_rn(t, bb));
+    if (in1) {
+      const bool u = unk1 && uz;
+      gh[p + dj] = u ? g_hi.y : 0.0f;
+      gl[p + dj] = u ? g_lo.y : 0.0f;
     }
-    gh[p] = g_hi;
-    gl[p] = g_lo;
-    hm = hc;
-    lm = lc;
-    hc = hp;
-    lc = lp;
-    hp = hp2;
-    lp = lp2;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      nh[t] = nh2[t];
-      nl[t] = nl2[t];
-    }
+    __syncthreads();  // the slot of plane k - 1 is staged again as plane k + 2
+    const int t0 = zm;
+    zm = z0;
+    z0 = zp;
+    zp = t0;
   }
 }
 
@@ -429,7 +474,7 @@ struct TermGeo {
 constexpr int DP3 = D3L | 1;  // odd row pitch: lanes across the rows are conflict-free
 
 template <int AXIS>
-__global__ void __launch_bounds__(256, 4) k_term3d32(const float* __restrict__ gh, const float* __restrict__ gl, Shape3 ss,
+__global__ void __launch_bounds__(256, AXIS == 0 ? 4 : 5) k_term3d32(const float* __restrict__ gh, const float* __restrict__ gl, Shape3 ss,
                                                      float* __restrict__ R, Shape3 sd, int out_off, int M,
                                                      const float* __restrict__ whi, const float* __restrict__ wlo, int K,
                                                      int B, int all_explicit, float sign, int accumulate) {
@@ -459,31 +504,38 @@ __global__ void __launch_bounds__(256, 4) k_term3d32(const float* __restrict__ g
         racc[2 * i + c] = (accumulate && p < nP && r < M) ? R[ld + r + out_off] : 0.0f;
       }
     }
+    // G at source points mb + lane + 32 c of the warp's four lines, every load issued first
+    // (lines past the grid read the last line, unused)
+    const int ns = ss.n[0];
+    const bool inner = mb >= 0 && mb + 96 <= ns;  // block-uniform: no tests along the line
+    float h[4][3], l[4][3];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int ll = 4 * warp + i, p = p0 + ll;
-      if (p >= nP) break;
-      const int line = p * st[P] + q * st[Q];
-      const int ns = ss.n[0];
-      float h[4], l[4];  // G at source points mb + lane + 32 c (chunk 3: none, only its lane 0 is read)
+      const int pl = min(p0 + 4 * warp + i, nP - 1);
+      const float* hr = gh + pl * st[P] + q * st[Q] + mb + lane;
+      const float* lr = gl + pl * st[P] + q * st[Q] + mb + lane;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int sidx = mb + lane + 32 * c;
-        const bool ok = sidx >= 0 && sidx < ns;
-        h[c] = ok ? gh[line + sidx] : 0.0f;
-        l[c] = ok ? gl[line + sidx] : 0.0f;
+        const bool ok = inner || (sidx >= 0 && sidx < ns);
+        h[i][c] = ok ? hr[32 * c] : 0.0f;
+        l[i][c] = ok ? lr[32 * c] : 0.0f;
       }
-      h[3] = l[3] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ll = 4 * warp + i;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        float h1 = __shfl_down_sync(0xffffffffu, h[c], 1), l1 = __shfl_down_sync(0xffffffffu, l[c], 1);
-        const float hn = __shfl_sync(0xffffffffu, h[c + 1], 0), ln = __shfl_sync(0xffffffffu, l[c + 1], 0);
+        float h1 = __shfl_down_sync(0xffffffffu, h[i][c], 1), l1 = __shfl_down_sync(0xffffffffu, l[i][c], 1);
+        const float hn = __shfl_sync(0xffffffffu, c < 2 ? h[i][c < 2 ? c + 1 : 0] : 0.0f, 0);
+        const float ln = __shfl_sync(0xffffffffu, c < 2 ? l[i][c < 2 ? c + 1 : 0] : 0.0f, 0);
         if (lane == 31) {
           h1 = hn;
           l1 = ln;
         }
         const int j = lane + 32 * c, m = mb + j;
-        if (j < D3L) dd[ll * DP3 + j] = (m >= 0 && m < M) ? (h1 - h[c]) + (l1 - l[c]) : 0.0f;
+        if (j < D3L) dd[ll * DP3 + j] = (m >= 0 && m < M) ? (h1 - h[i][c]) + (l1 - l[i][c]) : 0.0f;
       }
     }
   }
@@ -499,21 +551,36 @@ __global__ void __launch_bounds__(256, 4) k_term3d32(const float* __restrict__ g
     constexpr int RJ = (D3L + 7) / 8;
     const int sa = st[AXIS];
     const int ja = warp * RJ;
-    const float* gph = gh + p * st[P] + q * st[Q];
-    const float* gpl = gl + p * st[P] + q * st[Q];
+    const int pc = live ? p : nP - 1;  // lanes past the tile's lines read the last line, unused
+    const float* gph = gh + pc * st[P] + q * st[Q];
+    const float* gpl = gl + pc * st[P] + q * st[Q];
     float hv[RJ + 1], lv[RJ + 1];
-#pragma unroll
-    for (int i = 0; i <= RJ; ++i) {
-      const int sidx = mb + ja + i;  // source point
-      const bool ok = live && sidx >= 0 && sidx <= M;
-      hv[i] = ok ? gph[sidx * sa] : 0.0f;
-      lv[i] = ok ? gpl[sidx * sa] : 0.0f;
-    }
     float* row = dd + lane * DP3;
+    if (mb + ja >= 0 && mb + ja + RJ < M) {
+      // the warp's run lies inside the line: no tests (warp-uniform)
+      const float* hr = gph + (mb + ja) * sa;
+      const float* lr = gpl + (mb + ja) * sa;
 #pragma unroll
-    for (int i = 0; i < RJ; ++i) {
-      const int j = ja + i, m = mb + j;
-      if (j < D3L) row[j] = (m >= 0 && m < M) ? (hv[i + 1] - hv[i]) + (lv[i + 1] - lv[i]) : 0.0f;
+      for (int i = 0; i <= RJ; ++i) {
+        hv[i] = hr[i * sa];
+        lv[i] = lr[i * sa];
+      }
+#pragma unroll
+      for (int i = 0; i < RJ; ++i)
+        if (ja + i < D3L) row[ja + i] = (hv[i + 1] - hv[i]) + (lv[i + 1] - lv[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i <= RJ; ++i) {
+        const int sidx = mb + ja + i;  // source point
+        const bool ok = sidx >= 0 && sidx <= M;
+        hv[i] = ok ? gph[sidx * sa] : 0.0f;
+        lv[i] = ok ? gpl[sidx * sa] : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < RJ; ++i) {
+        const int j = ja + i, m = mb + j;
+        if (j < D3L) row[j] = (m >= 0 && m < M) ? (hv[i + 1] - hv[i]) + (lv[i + 1] - lv[i]) : 0.0f;
+      }
     }
   }
   __syncthreads();
@@ -527,7 +594,7 @@ __global__ void __launch_bounds__(256, 4) k_term3d32(const float* __restrict__ g
 #pragma unroll
       for (int u = 0; u < 8; ++u) y[u] = band_fast3(v + u);
     } else {
-#pragma unroll 1
+#pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int rr = rb + u;
         const float* dc = row + rr - r0 + K3H;
@@ -579,112 +646,146 @@ __global__ void __launch_bounds__(256, 4) k_term3d32(const float* __restrict__ g
 // - (LxLy + LyLz + LzLx), d = 6 c1 h^2 as hi + lo), x_{k+1} = x_k + omega (b - 6 h^2 P1 x_k) from
 // x_1 = omega b.  FIRST: the sweep from x_1, read as omega b.  LAST: the state (hi, lo) += s x +
 // s corr (two separate error-free additions) instead of writing x.
-// A block takes a tile of SWX x SWY points and marches SWZ planes along z.  The iterate on planes
-// z-1, z, z+1 over the tile with a one-point halo in x and y sits in a ring in shared memory; the
-// next plane is fetched into registers, and the per-point operands (b, the state) of the next
-// plane too, while the current one is computed.  Halo indices are clamped: the even ghosts of a
-// Neumann axis; on a Dirichlet axis the clamped values are seen only by wall points, which are not
-// updated.
-constexpr int SWX = 32, SWY = 8, SWZ = 16;
-constexpr int SWXP = SWX + 2, SWYP = SWY + 2;
+// A block of SWX x SWT threads takes a tile of SWX x SWY points and marches SWZ planes along z;
+// a thread takes rows j and j + SWT of one column, and every operation acts on that pair at once
+// (paired FP32 instructions).  The iterate on planes z-1, z, z+1 over the tile with a one-point
+// halo in x and y sits in a ring in shared memory as pairs: pair row pr holds tile rows pr - 1 and
+// pr - 1 + SWT, so a shift in x or y is the same shift of both halves.  The next plane is
+// fetched into registers, and the per-point operands (b, the state) of the next plane too, while
+// the current one is computed.  Tiles cover the unknowns only: halo points past a Neumann end
+// are its even ghosts (clamped), walls of a Dirichlet axis are taken as zeros without a load, so
+// no sweep reads or writes a wall point.
+constexpr int SWX = 32, SWT = 8, SWY = 2 * SWT, SWZ = 16;
+constexpr int SWXP = SWX + 2, SWRP = SWT + 2;  // pair rows of a staged plane
+constexpr int SWN = SWRP * SWXP;               // staged pairs per plane
+static_assert(SWN <= 2 * SWX * SWT, "two staged pairs per thread");
 
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(256, 8) k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin,
-                                                      float* __restrict__ xout, Shape3 s, float d_hi, float d_lo,
-                                                      float omega, float* __restrict__ shi, float* __restrict__ slo,
-                                                      float s_hi, float s_lo) {
-  __shared__ float xs[3][SWYP][SWXP];
+__global__ void __launch_bounds__(SWX * SWT, LAST ? 4 : 5) k_sweep3d32(const float* __restrict__ b, const float* __restrict__ xin,
+                                                            float* __restrict__ xout, Shape3 s, float d_hi, float d_lo,
+                                                            float omega, float* __restrict__ shi,
+                                                            float* __restrict__ slo, float s_hi, float s_lo) {
+  __shared__ float2 xs[3][SWRP][SWXP];
   const int n0 = s.n[0], n1 = s.n[1], n2 = s.n[2];
+  // tiles cover the unknowns only: index u along an axis is point u + lo (lo = 1 on a Dirichlet
+  // axis, whose walls are read as the zeros they hold, without a load)
+  const int lo0 = s.bc[0] == DIR, lo1 = s.bc[1] == DIR, lo2 = s.bc[2] == DIR;
+  const int nu0 = n0 - 2 * lo0, nu1 = n1 - 2 * lo1, nu2 = n2 - 2 * lo2;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * SWX + tx, j = blockIdx.y * SWY + ty;
-  const int k0 = blockIdx.z * SWZ, k1 = min(k0 + SWZ, n2);
-  const bool inside = i < n0 && j < n1;
-  const bool unk_xy = inside && interior(s.bc[0], i, n0) && interior(s.bc[1], j, n1);
-  const int bcz = s.bc[2];
+  const int iu = blockIdx.x * SWX + tx, ju = blockIdx.y * SWY + ty;  // rows ju and ju + SWT
+  const int k0 = blockIdx.z * SWZ, k1 = min(k0 + SWZ, nu2);
+  const bool in0 = iu < nu0 && ju < nu1, in1 = iu < nu0 && ju + SWT < nu1;
   const int sz = n0 * n1;
   const float* X0 = FIRST ? b : xin;
-  // plane loader: thread t stages elements t and t + 256 (< SWYP * SWXP) of the tile with halo,
-  // at global offsets fixed for the whole march
-  const int t1 = ty * SWX + tx, t2 = t1 + SWX * SWY;
-  const bool has2 = t2 < SWYP * SWXP;
-  auto plane_off = [&](int e) {
+  // position q along an axis of n points: false where the value is a wall zero, else the point
+  // (even ghosts of a Neumann axis clamped)
+  auto place = [](int q, int n, int dir, int* at) {
+    if (dir) {
+      *at = q;
+      return q > 0 && q < n - 1;
+    }
+    *at = clampi(q, n);
+    return true;
+  };
+  // plane loader: thread t stages pairs t and t + 256 (< SWN), at offsets fixed for the march
+  const int t1 = ty * SWX + tx, t2 = t1 + SWX * SWT;
+  const bool has2 = t2 < SWN;
+  auto pair_off = [&](int e, int half, bool* live) {
     const int row = e / SWXP, col = e - row * SWXP;
-    return clampi(blockIdx.y * SWY + row - 1, n1) * n0 + clampi(blockIdx.x * SWX + col - 1, n0);
+    int y, x;
+    const bool ly = place(lo1 + blockIdx.y * SWY + row - 1 + half * SWT, n1, lo1, &y);
+    const bool lx = place(lo0 + blockIdx.x * SWX + col - 1, n0, lo0, &x);
+    *live = ly && lx;
+    return *live ? y * n0 + x : 0;
   };
-  const int o1 = plane_off(t1), o2 = plane_off(has2 ? t2 : t1);
-  float ra = 0.0f, rb = 0.0f;
-  auto fetch = [&](int kk) {
-    const float* P = X0 + clampi(kk, n2) * sz;
-    ra = P[o1];
-    if (has2) rb = P[o2];
+  bool v1a, v1b, v2a, v2b;
+  const int o1a = pair_off(t1, 0, &v1a), o1b = pair_off(t1, 1, &v1b);
+  const int o2a = pair_off(has2 ? t2 : t1, 0, &v2a), o2b = pair_off(has2 ? t2 : t1, 1, &v2b);
+  float2 ra = make_float2(0.0f, 0.0f), rb = make_float2(0.0f, 0.0f);
+  auto fetch = [&](int ku) {  // plane of unknown index ku (-1 .. nu2)
+    int z;
+    const bool lz = place(lo2 + ku, n2, lo2, &z);
+    const float* P = X0 + (lz ? z : 0) * sz;
+    ra = make_float2(lz && v1a ? P[o1a] : 0.0f, lz && v1b ? P[o1b] : 0.0f);
+    if (has2) rb = make_float2(lz && v2a ? P[o2a] : 0.0f, lz && v2b ? P[o2b] : 0.0f);
   };
-  auto stage = [&](float(*pl)[SWXP]) {
-    float* f = &pl[0][0];
-    f[t1] = FIRST ? omega * ra : ra;
-    if (has2) f[t2] = FIRST ? omega * rb : rb;
+  const float2 om2 = bc2(omega);
+  auto stage = [&](float2(*pl)[SWXP]) {
+    float2* f = &pl[0][0];
+    f[t1] = FIRST ? mul2(om2, ra) : ra;
+    if (has2) f[t2] = FIRST ? mul2(om2, rb) : rb;
   };
   // per-point operands of the next plane
-  float bq = 0.0f, hq = 0.0f, lq = 0.0f;
+  float2 bq = make_float2(0.0f, 0.0f), hq = bq, lq = bq;
+  const int dj = SWT * n0;
   auto fetch_pt = [&](int p) {
-    bq = b[p];
-    if (LAST) {
-      hq = shi[p];
-      lq = slo[p];
+    if (in0) {
+      bq.x = b[p];
+      if (LAST) {
+        hq.x = shi[p];
+        lq.x = slo[p];
+      }
+    }
+    if (in1) {
+      bq.y = b[p + dj];
+      if (LAST) {
+        hq.y = shi[p + dj];
+        lq.y = slo[p + dj];
+      }
     }
   };
-  float(*Zm)[SWXP] = xs[0];
-  float(*Z0)[SWXP] = xs[1];
-  float(*Zp)[SWXP] = xs[2];
+  float2(*Zm)[SWXP] = xs[0];
+  float2(*Z0)[SWXP] = xs[1];
+  float2(*Zp)[SWXP] = xs[2];
   fetch(k0 - 1);
   stage(Zm);
   fetch(k0);
   stage(Z0);
   fetch(k0 + 1);
-  int p = k0 * sz + j * n0 + i;
-  if (inside) fetch_pt(p);
-  const int c0 = tx + 1, r0 = ty + 1;
+  int p = (lo2 + k0) * sz + (lo1 + ju) * n0 + lo0 + iu;
+  fetch_pt(p);
+  const int c0 = tx + 1, r0 = ty + 1;  // halo coordinates in the pair layout
+  const float2 m2 = bc2(-2.0f), m6 = bc2(-6.0f), dh2 = bc2(d_hi), dl2 = bc2(d_lo), sh2 = bc2(s_hi), sl2 = bc2(s_lo);
   for (int k = k0; k < k1; ++k, p += sz) {
     stage(Zp);
     __syncthreads();
     if (k + 1 < k1) fetch(k + 2);
-    const float bc = bq, hc = hq, lc = lq;
-    if (inside && k + 1 < k1) fetch_pt(p + sz);
-    if (inside) {
-      if (!(unk_xy && interior(bcz, k, n2))) {
-        if (!LAST) xout[p] = 0.0f;
-      } else {
-        // second differences as a + b - 2 v: the residual's dominant term d x is an exact
-        // two-product, so the rounding of these sums is far below an ulp of the residual
-        auto LX = [&](const float(*Pl)[SWXP], int rr) {
-          return fmaf(-2.0f, Pl[rr][c0], Pl[rr][c0 - 1] + Pl[rr][c0 + 1]);
-        };
-        auto LY = [&](const float(*Pl)[SWXP]) {
-          return fmaf(-2.0f, Pl[r0][c0], Pl[r0 - 1][c0] + Pl[r0 + 1][c0]);
-        };
-        const float x = Z0[r0][c0];
-        const float lx = LX(Z0, r0), ly = LY(Z0);
-        const float lz = fmaf(-2.0f, x, Zm[r0][c0] + Zp[r0][c0]);
-        const float lxly = fmaf(-2.0f, lx, LX(Z0, r0 - 1) + LX(Z0, r0 + 1));
-        const float lxlz = fmaf(-2.0f, lx, LX(Zm, r0) + LX(Zp, r0));
-        const float lylz = fmaf(-2.0f, ly, LY(Zm) + LY(Zp));
-        const float rest = fmaf(-6.0f, (lx + ly) + lz, -((lxly + lylz) + lxlz));
-        const float ph = __fmul_rn(d_hi, x);
-        const float pl = fmaf(d_lo, x, fmaf(d_hi, x, -ph));
-        const float res = __fsub_rn(__fsub_rn(bc, ph), pl) - rest;
-        const float corr = omega * res;
-        if (LAST) {
-          float h = hc, l = lc;
-          ff_add_scaled3(h, l, x, s_hi, s_lo);
-          ff_add_scaled3(h, l, corr, s_hi, s_lo);
-          shi[p] = h;
-          slo[p] = l;
-        } else {
-          xout[p] = x + corr;
-        }
+    const float2 bc = bq, hc = hq, lc = lq;
+    if (k + 1 < k1) fetch_pt(p + sz);
+    // second differences as a + b - 2 v: the residual's dominant term d x is an exact
+    // two-product, so the rounding of these sums is far below an ulp of the residual
+    auto LX = [&](const float2(*Pl)[SWXP], int rr) { return fma2(m2, Pl[rr][c0], add2(Pl[rr][c0 - 1], Pl[rr][c0 + 1])); };
+    auto LY = [&](const float2(*Pl)[SWXP]) { return fma2(m2, Pl[r0][c0], add2(Pl[r0 - 1][c0], Pl[r0 + 1][c0])); };
+    const float2 x = Z0[r0][c0];
+    const float2 lx = LX(Z0, r0), ly = LY(Z0);
+    const float2 lz = fma2(m2, x, add2(Zm[r0][c0], Zp[r0][c0]));
+    const float2 lxly = fma2(m2, lx, add2(LX(Z0, r0 - 1), LX(Z0, r0 + 1)));
+    const float2 lxlz = fma2(m2, lx, add2(LX(Zm, r0), LX(Zp, r0)));
+    const float2 lylz = fma2(m2, ly, add2(LY(Zm), LY(Zp)));
+    const float2 rest = fma2(m6, add2(add2(lx, ly), lz), neg2(add2(add2(lxly, lylz), lxlz)));
+    const float2 ph = mul2(dh2, x);
+    const float2 pl = fma2(dl2, x, fma2(dh2, x, neg2(ph)));
+    const float2 res = sub2(sub2(sub2(bc, ph), pl), rest);
+    if (LAST) {
+      const float2 corr = mul2(om2, res);
+      float2 h = hc, l = lc;
+      ff_add_scaled3_2(h, l, x, sh2, sl2);
+      ff_add_scaled3_2(h, l, corr, sh2, sl2);
+      if (in0) {
+        shi[p] = h.x;
+        slo[p] = l.x;
       }
+      if (in1) {
+        shi[p + dj] = h.y;
+        slo[p + dj] = l.y;
+      }
+    } else {
+      const float2 xn = fma2(om2, res, x);
+      if (in0) xout[p] = xn.x;
+      if (in1) xout[p + dj] = xn.y;
     }
     __syncthreads();  // the slot of plane k - 1 is staged again as plane k + 2
-    float(*t)[SWXP] = Zm;
+    float2(*t)[SWXP] = Zm;
     Zm = Z0;
     Z0 = Zp;
     Zp = t;
@@ -703,8 +804,9 @@ __global__ void k_single3d32(const float* __restrict__ b, Shape3 s, float omega,
   slo[p] = l;
 }
 
-dim3 sweep_grid3(const Shape3& s) {
-  return dim3((s.n[0] + SWX - 1) / SWX, (s.n[1] + SWY - 1) / SWY, (s.n[2] + SWZ - 1) / SWZ);
+dim3 sweep_grid3(const Shape3& s) {  // tiles over the unknowns
+  const int nu0 = s.n[0] - 2 * (s.bc[0] == DIR), nu1 = s.n[1] - 2 * (s.bc[1] == DIR), nu2 = s.n[2] - 2 * (s.bc[2] == DIR);
+  return dim3((nu0 + SWX - 1) / SWX, (nu1 + SWY - 1) / SWY, (nu2 + SWZ - 1) / SWZ);
 }
 
 __global__ void k_split3(const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
@@ -825,7 +927,7 @@ ms_status step3d64(ms_grid* g) {
 void filter3d32(ms_grid* g, int c, float cb_hi, float cb_lo) {
   Grid3D* G3 = g->g3;
   const Shape3& s = G3->sh[c];
-  const dim3 grd((s.n[0] + 31) / 32, (s.n[1] + 7) / 8, (s.n[2] + FZ3 - 1) / FZ3), blk(32, 8, 1);
+  const dim3 grd((s.n[0] + FTX - 1) / FTX, (s.n[1] + FTY - 1) / FTY, (s.n[2] + FZ3 - 1) / FZ3), blk(FTX, FTT, 1);
   k_ffilt3d32<<<grd, blk, 0, g->stream>>>(G3->hi[c], G3->lo[c], s, G3->gh[c % 3], G3->gl[c % 3], cb_hi, cb_lo);
   // state hi + lo in, G hi + lo out
   prof_mark(g, KK_FILT3D32, 16.0 * (double)s.size());
@@ -894,7 +996,7 @@ void solve3d32_ts(ms_grid* g, int c, float d_hi, float d_lo, float omega, float 
   const float* b = G3->s32[1];
   float* buf[2] = {G3->s32[2], G3->s32[3]};
   *nl += ts_solve(*G3->ts, s, b, buf[0], 6.0f * (float)(g->c1 * g->h * g->h), g->stream, g);
-  const dim3 grd = sweep_grid3(s), blk(SWX, SWY, 1);
+  const dim3 grd = sweep_grid3(s), blk(SWX, SWT, 1);
   const int R = G3->ts_sweeps;
   for (int k = 0; k < R; ++k) {
     const float* xin = buf[k & 1];
@@ -925,7 +1027,7 @@ void solve3d32(ms_grid* g, int c, float d_hi, float d_lo, float omega, float s_h
   for (int k = 0; k < L; ++k) {
     const bool last = (k == L - 1);
     float* xo = buf[k & 1];
-    const dim3 grd = sweep_grid3(s), blk(SWX, SWY, 1);
+    const dim3 grd = sweep_grid3(s), blk(SWX, SWT, 1);
     float* hi = G3->hi[c];
     float* lo = G3->lo[c];
     if (S == 1)
