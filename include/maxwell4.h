@@ -480,6 +480,15 @@ ms_status ms_load(ms_grid* g, const char* path);
 /* Message of the last failed call on this thread ("" if none). */
 const char* ms_last_error(void);
 
+/* Test hooks for the failure paths (host side; no device work).  ms_debug_fail_alloc(n) makes the
+ * n-th device allocation the library makes from now on fail as an out-of-memory device would
+ * (nothing is allocated; the call reports MS_ENOMEM, or the status of the operation that needed
+ * the memory), then disarms itself; n = 0 disarms, n < 0 is MS_EINVAL.  ms_debug_live_allocs
+ * returns the number of device allocations the library holds, so a test can check that a failed
+ * creation released everything.  Process-wide, not thread-safe against concurrent creations. */
+ms_status ms_debug_fail_alloc(int n);
+long ms_debug_live_allocs(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -150,6 +150,10 @@ def load() -> ctypes.CDLL:
         L.ms_kernel_kind_name.restype = ctypes.c_char_p
         L.ms_last_error.argtypes = []
         L.ms_last_error.restype = ctypes.c_char_p
+        L.ms_debug_fail_alloc.argtypes = [I]
+        L.ms_debug_fail_alloc.restype = I
+        L.ms_debug_live_allocs.argtypes = []
+        L.ms_debug_live_allocs.restype = ctypes.c_long
         _lib = L
         return L
 
@@ -237,6 +241,17 @@ def solver_sweeps(dim: int, r: float, precision: int, tol: float) -> int:
     v = ctypes.c_int()
     _check(load().ms_solver_sweeps(int(dim), float(r), int(precision), float(tol), ctypes.byref(v)))
     return v.value
+
+
+def debug_fail_alloc(n: int) -> None:
+    """Test hook: the n-th device allocation of the library from now on fails as out of memory
+    (host-side injection, nothing is allocated); 0 disarms."""
+    _check(load().ms_debug_fail_alloc(int(n)))
+
+
+def debug_live_allocs() -> int:
+    """Device allocations the library holds now (leak checks in tests)."""
+    return int(load().ms_debug_live_allocs())
 
 
 class Grid:

@@ -75,23 +75,41 @@ ms_status check(const char* what) {
 ms_status adjoint_setup(ms_grid* g) {
   if (g->adj[0]) return MS_OK;
   if (g->shared64) return afail(MS_EUNSUPPORTED, "the reverse pass is not available on batch cavities");
+  // on any failure everything allocated here is released, so the next call starts afresh
+  auto release = [&]() {
+    for (int kind = 0; kind < 2; ++kind) {
+      dev_free(g->padeT[kind].d_w);
+      g->padeT[kind].d_w = nullptr;
+    }
+    for (int k = 0; k < 6; ++k) {
+      dev_free(g->adj[k]);
+      g->adj[k] = nullptr;
+    }
+  };
   for (int kind = 0; kind < 2; ++kind) {
     PadeTable& t = g->padeT[kind];
     build_pade_table_T(g->pade[kind], &t);
-    MS_ACUDA(cudaMalloc((void**)&t.d_w, t.w.size() * sizeof(double)));
-    MS_ACUDA(cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    const cudaError_t e = dev_malloc((void**)&t.d_w, t.w.size() * sizeof(double));
+    if (e != cudaSuccess) {
+      release();
+      return afail(MS_ENOMEM, std::string("cudaMalloc of the transposed Pade tables: ") + cudaGetErrorString(e));
+    }
+    if (cudaMemcpy(t.d_w, t.w.data(), t.w.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+      release();
+      return afail(MS_ECUDA, "copy of the transposed Pade tables failed");
+    }
   }
   const size_t nmax = (size_t)(g->N + 1) * (g->N + 1);
   for (int k = 0; k < 6; ++k) {
-    cudaError_t e = cudaMalloc((void**)&g->adj[k], nmax * sizeof(double) + 256);
+    const cudaError_t e = dev_malloc((void**)&g->adj[k], nmax * sizeof(double) + 256);
     if (e != cudaSuccess) {
-      for (int q = 0; q <= k; ++q) {
-        cudaFree(g->adj[q]);
-        g->adj[q] = nullptr;
-      }
+      release();
       return afail(MS_ENOMEM, std::string("cudaMalloc of adjoint planes: ") + cudaGetErrorString(e));
     }
-    MS_ACUDA(cudaMemsetAsync(g->adj[k], 0, nmax * sizeof(double), g->stream));
+    if (cudaMemsetAsync(g->adj[k], 0, nmax * sizeof(double), g->stream) != cudaSuccess) {
+      release();
+      return afail(MS_ECUDA, "clearing the adjoint planes failed");
+    }
   }
   return MS_OK;
 }
@@ -247,11 +265,11 @@ void adjoint_teardown(ms_grid* g) {
   free_graph(&g->adj_graph1);
   free_graph(&g->adj_graphk);
   for (int k = 0; k < 2; ++k) {
-    cudaFree(g->padeT[k].d_w);
+    dev_free(g->padeT[k].d_w);
     g->padeT[k].d_w = nullptr;
   }
   for (int k = 0; k < 6; ++k) {
-    cudaFree(g->adj[k]);
+    dev_free(g->adj[k]);
     g->adj[k] = nullptr;
   }
 }

@@ -424,7 +424,7 @@ ms_status adjoint32_setup(ms_grid* g) {
   float** planes[] = {&A->lh[0], &A->lh[1], &A->lh[2], &A->ll[0], &A->ll[1], &A->ll[2], &A->ux[0], &A->ux[1],
                       &A->uc[0], &A->uc[1], &A->vh[0], &A->vh[1], &A->vl[0], &A->vl[1], &A->sw[0], &A->sw[1]};
   for (float** p : planes) {
-    if (cudaMalloc((void**)p, n * sizeof(float) + 256) != cudaSuccess) {
+    if (dev_malloc((void**)p, n * sizeof(float) + 256) != cudaSuccess) {
       adjoint32_teardown(g);
       return a32fail(MS_ENOMEM, "cudaMalloc of the FP32 adjoint planes failed");
     }
@@ -443,7 +443,7 @@ void adjoint32_teardown(ms_grid* g) {
   free_graph32(&A->gk);
   float* all[] = {A->lh[0], A->lh[1], A->lh[2], A->ll[0], A->ll[1], A->ll[2], A->ux[0], A->ux[1], A->uc[0],
                   A->uc[1], A->vh[0], A->vh[1], A->vl[0], A->vl[1], A->sw[0], A->sw[1]};
-  for (float* p : all) cudaFree(p);
+  for (float* p : all) dev_free(p);
   delete A;
   g->adj32 = nullptr;
 }

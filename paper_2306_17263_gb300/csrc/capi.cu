@@ -2,6 +2,7 @@
 // graph-captured time loop, diagnostics and operator-level entry points.
 #include <array>
 #include <cctype>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -48,7 +49,7 @@ ms_status check_launch(const char* what) {
 
 template <typename T>
 ms_status dalloc(T** p, size_t n) {
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 256);
+  cudaError_t e = dev_malloc((void**)p, n * sizeof(T) + 256);
   if (e != cudaSuccess) {
     *p = nullptr;
     return fail(MS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -267,7 +268,7 @@ void free_graph(Graph* gr) {
 ms_status ensure_partial(ms_grid* g, size_t n) {
   int b = reduce_blocks(n);
   if (b <= g->partial_cap) return MS_OK;
-  if (g->d_partial) cudaFree(g->d_partial);
+  if (g->d_partial) dev_free(g->d_partial);
   MS_TRY(dalloc(&g->d_partial, (size_t)b * 4));
   g->partial_cap = b;
   return MS_OK;
@@ -317,7 +318,7 @@ ms_status exact_fields64(ms_grid* g, const ms_mode* modes, int nm, double tE, do
     host[offs[HY][2] + m] = A * std::sin(w * tH) / (w * g->Z) * pi * kx;
   }
   if (host.size() > g->modetab_cap) {
-    if (g->d_modetab) cudaFree(g->d_modetab);
+    if (g->d_modetab) dev_free(g->d_modetab);
     g->d_modetab = nullptr;
     g->modetab_cap = 0;
     MS_TRY(dalloc(&g->d_modetab, host.size()));
@@ -425,10 +426,46 @@ const char* kernel_kind_name(int k) {
 
 }  // namespace ms
 
+namespace {
+std::atomic<int> g_fail_alloc{0};    // the allocation that fails, counted from 1; 0: none armed
+std::atomic<long> g_live_allocs{0};  // device allocations held by the library
+}  // namespace
+
+namespace ms {
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int n = g_fail_alloc.load();
+  while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) {  // the armed allocation: fail as an out-of-memory device would, allocating nothing
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  else *p = nullptr;
+  return e;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  if (cudaFree(p) == cudaSuccess) g_live_allocs.fetch_sub(1);
+}
+
+}  // namespace ms
+
 // =======================================================================================
 extern "C" {
 
 const char* ms_last_error(void) { return g_last_error.c_str(); }
+
+ms_status ms_debug_fail_alloc(int n) {
+  if (n < 0) return fail(MS_EINVAL, "n must be >= 0");
+  g_fail_alloc.store(n);
+  return MS_OK;
+}
+
+long ms_debug_live_allocs(void) { return g_live_allocs.load(); }
 
 ms_status ms_stability_limit(int dim, double* rmax) {
   if (!rmax) return fail(MS_EINVAL, "rmax is NULL");
@@ -601,29 +638,29 @@ ms_status ms_destroy(ms_grid* g) {
   destroy_grid3d(g);
   for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
   for (int k = 0; k < 2; ++k) {
-    cudaFree(g->pade[k].d_w);
-    cudaFree(g->pade[k].d_whi);
-    cudaFree(g->pade[k].d_wlo);
+    dev_free(g->pade[k].d_w);
+    dev_free(g->pade[k].d_whi);
+    dev_free(g->pade[k].d_wlo);
   }
   for (int f = 0; f < 3; ++f) {
-    cudaFree(g->f64[f]);
-    cudaFree(g->hi[f]);
-    cudaFree(g->lo[f]);
+    dev_free(g->f64[f]);
+    dev_free(g->hi[f]);
+    dev_free(g->lo[f]);
   }
-  cudaFree(g->de64);
-  cudaFree(g->d_src);
-  cudaFree(g->d_srctab);
-  cudaFree(g->d_srctab32);
-  cudaFree(g->d_srcfac);
-  cudaFree(g->d_walldata);
-  cudaFree(g->d_wresp);
-  cudaFree(g->d_step);
-  for (int k = 0; k < 6 && !g->shared64; ++k) cudaFree(g->s64[k]);
-  for (int k = 0; k < 8; ++k) cudaFree(g->s32[k]);
+  dev_free(g->de64);
+  dev_free(g->d_src);
+  dev_free(g->d_srctab);
+  dev_free(g->d_srctab32);
+  dev_free(g->d_srcfac);
+  dev_free(g->d_walldata);
+  dev_free(g->d_wresp);
+  dev_free(g->d_step);
+  for (int k = 0; k < 6 && !g->shared64; ++k) dev_free(g->s64[k]);
+  for (int k = 0; k < 8; ++k) dev_free(g->s32[k]);
   mixed_teardown(g);
-  cudaFree(g->d_partial);
-  cudaFree(g->d_result);
-  cudaFree(g->d_modetab);
+  dev_free(g->d_partial);
+  dev_free(g->d_result);
+  dev_free(g->d_modetab);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;
   return MS_OK;
@@ -833,7 +870,7 @@ ms_status ms_energy(ms_grid* g, double* W) {
   }
   auto release = [&](ms_status s) {
     cudaStreamSynchronize(g->stream);
-    for (double* p : extra) cudaFree(p);
+    for (double* p : extra) dev_free(p);
     return s;
   };
   ms_status s = state64(g, tmp, view);
@@ -924,12 +961,12 @@ ms_status ms_error_vs_exact(ms_grid* g, const ms_mode* modes, int nmodes, double
 // Replaces the grid's sources (validated by the caller).
 static ms_status set_sources_spec(ms_grid* g, const SrcSpec* src, int nsrc) {
   MS_CUDA(cudaStreamSynchronize(g->stream));
-  cudaFree(g->d_src);
-  cudaFree(g->d_srctab);
-  cudaFree(g->d_srctab32);
-  cudaFree(g->d_srcfac);
-  cudaFree(g->d_walldata);
-  cudaFree(g->d_wresp);
+  dev_free(g->d_src);
+  dev_free(g->d_srctab);
+  dev_free(g->d_srctab32);
+  dev_free(g->d_srcfac);
+  dev_free(g->d_walldata);
+  dev_free(g->d_wresp);
   g->d_src = nullptr;
   g->d_srctab = nullptr;
   g->d_srctab32 = nullptr;
@@ -1234,7 +1271,7 @@ ms_status ms_batch_destroy(ms_batch* b) {
   free_graph(&b->graphk);
   tiled_batch_free(&b->tb);
   for (ms_grid* g : b->cav) ms_destroy(g);
-  for (int k = 0; k < 6; ++k) cudaFree(b->s64[k]);
+  for (int k = 0; k < 6; ++k) dev_free(b->s64[k]);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return MS_OK;

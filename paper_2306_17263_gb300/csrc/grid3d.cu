@@ -1133,7 +1133,7 @@ int upload_band_row() {
 
 template <typename T>
 ms_status alloc3(T** p, size_t n) {
-  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 256);
+  cudaError_t e = dev_malloc((void**)p, n * sizeof(T) + 256);
   if (e != cudaSuccess) {
     *p = nullptr;
     return fail3(MS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -1200,7 +1200,7 @@ ms_status exact3(ms_grid* g, const ms_mode3* modes, int nm, double tE, double tH
     host[oc + q] = amp[c];
   }
   if (host.size() > g->modetab_cap) {
-    cudaFree(g->d_modetab);
+    dev_free(g->d_modetab);
     g->d_modetab = nullptr;
     g->modetab_cap = 0;
     MS3_TRY(alloc3(&g->d_modetab, host.size()));
@@ -1266,7 +1266,7 @@ ms_status mode_field3_tables(ms_grid* g, int c, const std::vector<double>& tq, c
     host[oc + q] = coef[q];
   }
   if (host.size() > g->modetab_cap) {
-    cudaFree(g->d_modetab);
+    dev_free(g->d_modetab);
     g->d_modetab = nullptr;
     g->modetab_cap = 0;
     MS3_TRY(alloc3(&g->d_modetab, host.size()));
@@ -1462,20 +1462,20 @@ void destroy_grid3d(ms_grid* g) {
     G3->ts = nullptr;
   }
   for (int c = 0; c < 6; ++c) {
-    cudaFree(G3->f64[c]);
-    cudaFree(G3->hi[c]);
-    cudaFree(G3->lo[c]);
-    cudaFree(G3->dview[c]);
+    dev_free(G3->f64[c]);
+    dev_free(G3->hi[c]);
+    dev_free(G3->lo[c]);
+    dev_free(G3->dview[c]);
   }
-  for (int k = 0; k < 7; ++k) cudaFree(G3->s64[k]);
-  for (int k = 0; k < 4; ++k) cudaFree(G3->s32[k]);
+  for (int k = 0; k < 7; ++k) dev_free(G3->s64[k]);
+  for (int k = 0; k < 4; ++k) dev_free(G3->s32[k]);
   for (int k = 0; k < 3; ++k) {
-    cudaFree(G3->gh[k]);
-    cudaFree(G3->gl[k]);
+    dev_free(G3->gh[k]);
+    dev_free(G3->gl[k]);
   }
   for (int k = 0; k < 2; ++k) {
-    cudaFree(g->pade32[k].d_whi);
-    cudaFree(g->pade32[k].d_wlo);
+    dev_free(g->pade32[k].d_whi);
+    dev_free(g->pade32[k].d_wlo);
     g->pade32[k].d_whi = g->pade32[k].d_wlo = nullptr;
   }
   delete G3;

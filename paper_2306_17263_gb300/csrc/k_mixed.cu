@@ -141,8 +141,8 @@ ms_status mixed_setup(ms_grid* g) {
       whi[k] = s.hi;
       wlo[k] = s.lo;
     }
-    if (cudaMalloc(&t.d_whi, whi.size() * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&t.d_wlo, wlo.size() * sizeof(float)) != cudaSuccess) {
+    if (dev_malloc(&t.d_whi, whi.size() * sizeof(float)) != cudaSuccess ||
+        dev_malloc(&t.d_wlo, wlo.size() * sizeof(float)) != cudaSuccess) {
       g_mixed_err = "cudaMalloc of FP32 Pade tables failed";
       return MS_ENOMEM;
     }
@@ -165,7 +165,7 @@ ms_status mixed_setup(ms_grid* g) {
   // right-hand-side planes of the tile kernels: s32[4] (E_z), s32[2] (H_x), s32[3] (H_y)
   const size_t nmax = (size_t)(g->N + 1) * (g->N + 1);
   for (int k = 2; k < 5; ++k) {
-    if (cudaMalloc(&g->s32[k], nmax * sizeof(float) + 256) != cudaSuccess) {
+    if (dev_malloc(&g->s32[k], nmax * sizeof(float) + 256) != cudaSuccess) {
       g_mixed_err = "cudaMalloc of FP32 scratch failed";
       return MS_ENOMEM;
     }
@@ -176,8 +176,8 @@ ms_status mixed_setup(ms_grid* g) {
 
 void mixed_teardown(ms_grid* g) {
   for (int k = 0; k < 2; ++k) {
-    cudaFree(g->pade32[k].d_whi);
-    cudaFree(g->pade32[k].d_wlo);
+    dev_free(g->pade32[k].d_whi);
+    dev_free(g->pade32[k].d_wlo);
     g->pade32[k].d_whi = g->pade32[k].d_wlo = nullptr;
   }
 }

@@ -89,12 +89,12 @@ void shapes3(const ms_grid* g, const ms_source3* src, int nsrc, int c, std::vect
 void src3_free(ms_grid* g) {
   Src3* S = g->src3;
   if (!S) return;
-  cudaFree(S->tab);
-  cudaFree(S->tab32);
-  cudaFree(S->coef);
-  cudaFree(S->omega);
-  cudaFree(S->fac);
-  cudaFree(S->fac32);
+  dev_free(S->tab);
+  dev_free(S->tab32);
+  dev_free(S->coef);
+  dev_free(S->omega);
+  dev_free(S->fac);
+  dev_free(S->fac32);
   delete S;
   g->src3 = nullptr;
 }
@@ -126,7 +126,7 @@ ms_status src3_set(ms_grid* g, const ms_source3* src, int nsrc) {
   std::vector<float> tab32(tab.begin(), tab.end());
   Src3* D = new Src3(S);
   g->src3 = D;
-  auto alloc = [](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+  auto alloc = [](void** p, size_t bytes) { return dev_malloc(p, bytes) == cudaSuccess; };
   bool ok = alloc((void**)&D->tab, tab.size() * sizeof(double)) && alloc((void**)&D->tab32, tab32.size() * sizeof(float)) &&
             alloc((void**)&D->coef, coef.size() * sizeof(double)) && alloc((void**)&D->omega, omega.size() * sizeof(double)) &&
             alloc((void**)&D->fac, coef.size() * sizeof(double)) && alloc((void**)&D->fac32, coef.size() * sizeof(float));

@@ -1015,9 +1015,9 @@ int tiled_batch_build(ms_grid* const* cav, int count, int order, TiledBatch* tb,
   std::vector<int> work(wc);
   work.insert(work.end(), we.begin(), we.end());
   work.insert(work.end(), wh.begin(), wh.end());
-  if (cudaMalloc(&tb->d_curl, curl.size() * sizeof(CurlArgs)) != cudaSuccess ||
-      cudaMalloc(&tb->d_solve, solve.size() * sizeof(SolveArgs)) != cudaSuccess ||
-      cudaMalloc(&tb->d_work, work.size() * sizeof(int)) != cudaSuccess) {
+  if (dev_malloc(&tb->d_curl, curl.size() * sizeof(CurlArgs)) != cudaSuccess ||
+      dev_malloc(&tb->d_solve, solve.size() * sizeof(SolveArgs)) != cudaSuccess ||
+      dev_malloc(&tb->d_work, work.size() * sizeof(int)) != cudaSuccess) {
     *err = "cudaMalloc of the batch work lists failed";
     return -1;
   }
@@ -1044,9 +1044,9 @@ void tiled_batch_step(const TiledBatch& tb, cudaStream_t st, int persistent) {
 }
 
 void tiled_batch_free(TiledBatch* tb) {
-  cudaFree(tb->d_curl);
-  cudaFree(tb->d_solve);
-  cudaFree(tb->d_work);
+  dev_free(tb->d_curl);
+  dev_free(tb->d_solve);
+  dev_free(tb->d_work);
   *tb = TiledBatch{};
 }
 

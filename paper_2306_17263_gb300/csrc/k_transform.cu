@@ -354,11 +354,11 @@ int ts_setup(int N, TransformSolver* ts, std::string* err) {
     return -1;
   }
   for (int k = 0; k < 2; ++k)
-    if (cudaMalloc(&ts->w[k], n3 * sizeof(float)) != cudaSuccess) {
+    if (dev_malloc(&ts->w[k], n3 * sizeof(float)) != cudaSuccess) {
       *err = "cudaMalloc of the transform working arrays failed";
       return -2;
     }
-  if (cudaMalloc(&ts->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ts->d_err, 0, sizeof(int)) != cudaSuccess) {
+  if (dev_malloc(&ts->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ts->d_err, 0, sizeof(int)) != cudaSuccess) {
     *err = "cudaMalloc of the transform error flag failed";
     return -2;
   }
@@ -366,7 +366,7 @@ int ts_setup(int N, TransformSolver* ts, std::string* err) {
     std::vector<double> Q, mu;
     transform_matrix(N, P, bc, &Q, &mu);
     std::vector<float> muf(mu.begin(), mu.end());
-    if (cudaMalloc(&ts->mu[bc], P * sizeof(float)) != cudaSuccess ||
+    if (dev_malloc(&ts->mu[bc], P * sizeof(float)) != cudaSuccess ||
         cudaMemcpy(ts->mu[bc], muf.data(), P * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
       *err = "transform eigenvalue tables failed";
       return -2;
@@ -376,7 +376,7 @@ int ts_setup(int N, TransformSolver* ts, std::string* err) {
       operand_blocks(Q, P, dir == 1, &hi, &lo);
       for (int part = 0; part < 2; ++part) {
         const std::vector<uint16_t>& v = part ? lo : hi;
-        if (cudaMalloc(&ts->q[bc][dir][part], v.size() * 2) != cudaSuccess ||
+        if (dev_malloc(&ts->q[bc][dir][part], v.size() * 2) != cudaSuccess ||
             cudaMemcpy(ts->q[bc][dir][part], v.data(), v.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
           *err = "transform matrices failed";
           return -2;
@@ -388,12 +388,12 @@ int ts_setup(int N, TransformSolver* ts, std::string* err) {
 }
 
 void ts_free(TransformSolver* ts) {
-  for (float* p : ts->w) cudaFree(p);
+  for (float* p : ts->w) dev_free(p);
   for (auto& a : ts->q)
     for (auto& b : a)
-      for (uint4* p : b) cudaFree(p);
-  for (float* p : ts->mu) cudaFree(p);
-  cudaFree(ts->d_err);
+      for (uint4* p : b) dev_free(p);
+  for (float* p : ts->mu) dev_free(p);
+  dev_free(ts->d_err);
   *ts = TransformSolver{};
 }
 

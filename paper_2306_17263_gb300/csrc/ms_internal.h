@@ -85,6 +85,14 @@ struct Adj32;   // FP32 reverse pass of an FP32_REFINED grid (adjoint32.cu)
 void prof_mark(ms_grid* g, int kind, double bytes = 0.0);
 // Set the message returned by ms_last_error on this thread.
 void set_last_error(const char* msg);
+// Every device allocation and release of the library goes through these two (capi.cu), so a test
+// can make the n-th allocation fail on the host (ms_debug_fail_alloc) and count what is held.
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
 }  // namespace ms
 
 struct ms_grid {

@@ -141,3 +141,22 @@ def test_autotune_cache_memory_and_file(tmp_path, monkeypatch):
         with pytest.raises(pkg.MaxwellError) as e:
             pkg.autotune_cache_put(key, plan)
         assert e.value.status == -1
+
+
+def test_alloc_failure_hook_host_side():
+    """The allocation-failure hook arms, disarms and rejects a negative count without a GPU, and
+    descriptor validation runs before any allocation (an armed failure is not consumed)."""
+    assert pkg.debug_live_allocs() == 0
+    with pytest.raises(pkg.MaxwellError) as e:
+        pkg.debug_fail_alloc(-1)
+    assert e.value.status == -1
+    L = pkg.load()
+    pkg.debug_fail_alloc(1)
+    try:
+        h = ctypes.c_void_p()
+        d = _desc(dim=1)
+        assert L.ms_create_grid(ctypes.byref(d), ctypes.byref(h)) == -1
+        assert not h.value
+        assert pkg.debug_live_allocs() == 0
+    finally:
+        pkg.debug_fail_alloc(0)
