@@ -448,6 +448,10 @@ def variants_leg(pkg, torch, modes, r):
         g.init_modes(modes)
         out["tracked_de_fp64_1024"] = _profiled_rate(pkg, torch, g, 1024, 50, flush)
         out["tracked_de_fp64_1024"]["l2_rel"] = g.error_vs_exact(modes)[1]
+    with pkg.Grid(2048, r, z=1.3, precision=pkg.FP32_REFINED, scheme=pkg.SCHEME_C4_DE, stream="torch") as g:
+        g.init_modes(modes)
+        out["tracked_de_fp32_refined_2048"] = _profiled_rate(pkg, torch, g, 2048, 200, flush)
+        out["tracked_de_fp32_refined_2048"]["l2_rel"] = g.error_vs_exact(modes)[1]
     del flush
     return out
 

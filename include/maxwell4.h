@@ -78,7 +78,9 @@ typedef enum { MS_CLOSURE_PAPER = 0, MS_CLOSURE_REFLECT = 1 } ms_closure;
  * MS_SCHEME_C4_DE is the compact scheme in the form Step 1 / Step 2 print it: Delta E_z is
  * carried as state DE, advanced after Step 1 by Eq. "eq:mhe" (DE += kappa^2 (E^{n+1} - E^n)
  * - Z (24/h_tau) curl_h H^{n+1/2}), and Step 2 filters E with it (Eq. "eq:helm2") instead of
- * with Delta_h E.  FP64, 2D.  DE starts as the exact Delta E of the modes (ms_init_modes) or as
+ * with Delta_h E.  2D, both precisions (in MS_FP32_REFINED DE is a float-float field and its
+ * update, the small difference of two large terms, is formed in float-float); not for batches,
+ * sources or the reverse pass.  DE starts as the exact Delta E of the modes (ms_init_modes) or as
  * Delta_h E^0 (ms_set_fields); it is internal state, not returned by ms_get_fields. */
 typedef enum { MS_SCHEME_C4 = 0, MS_SCHEME_YEE2 = 1, MS_SCHEME_NC4 = 2, MS_SCHEME_C4_DE = 3 } ms_scheme;
 

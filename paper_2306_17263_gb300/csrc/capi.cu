@@ -17,6 +17,7 @@
 #include "k_mixed.cuh"
 #include "k_src3.cuh"
 #include "k_tiled.cuh"
+#include "k_tracked32.cuh"
 
 using namespace ms;
 
@@ -231,6 +232,12 @@ ms_status step_any(ms_grid* g) {
   if (g->g3) return step3d(g);
   if (g->desc.precision == MS_FP64) return step64(g);
   int nl = 0;
+  if (g->de_hi) {
+    const ms_status s = step_mixed_tracked(g, &nl);
+    if (s != MS_OK) return fail(s, "tracked Delta E step failed");
+    g->launches_per_step = nl;
+    return check_launch("tracked mixed step");
+  }
   ms_status s = step_mixed(g, &nl);
   if (s != MS_OK) return fail(s, mixed_last_error());
   g->launches_per_step = nl;
@@ -420,7 +427,7 @@ void prof_mark(ms_grid* g, int kind, double bytes) {
 const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"filter64", "pade64", "p1sweep64", "yee64", "curl32", "solve32",
                                         "filter3d64", "pade3d64", "sweep3d64", "filt3d32", "band3d32",
-                                        "sweep3d32", "nc64", "source", "term3d32", "tsgemm", "tspack"};
+                                        "sweep3d32", "nc64", "source", "term3d32", "tsgemm", "tspack", "tracked32"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "";
 }
 
@@ -529,8 +536,10 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
   if (d->scheme != MS_SCHEME_C4 && d->scheme != MS_SCHEME_YEE2 && d->scheme != MS_SCHEME_NC4 &&
       d->scheme != MS_SCHEME_C4_DE)
     return fail(MS_EINVAL, "unknown scheme");
-  if (d->scheme != MS_SCHEME_C4 && d->precision != MS_FP64)
-    return fail(MS_EUNSUPPORTED, "the tracked-Delta-E variant and the Yee and NC comparators run in FP64 only");
+  if ((d->scheme == MS_SCHEME_YEE2 || d->scheme == MS_SCHEME_NC4) && d->precision != MS_FP64)
+    return fail(MS_EUNSUPPORTED, "the Yee and NC comparators run in FP64 only");
+  if (d->scheme == MS_SCHEME_C4_DE && shared64)
+    return fail(MS_EUNSUPPORTED, "batches run the compact scheme MS_SCHEME_C4");
   const bool compact = d->scheme == MS_SCHEME_C4 || d->scheme == MS_SCHEME_C4_DE;
   if (compact) {
     const double rmax = stability_limit_2d();
@@ -612,6 +621,10 @@ static ms_status create_grid_impl(const ms_grid_desc* d, double* const* shared64
       s = mixed_setup(g);
       if (s != MS_OK) fail(s, mixed_last_error());
     }
+    if (s == MS_OK && d->scheme == MS_SCHEME_C4_DE) {
+      s = tracked32_setup(g);
+      if (s != MS_OK) fail(s, "cudaMalloc of the tracked Delta E planes failed");
+    }
   }
   if (s == MS_OK) s = dalloc(&g->d_result, 8);
   if (s == MS_OK) s = ensure_partial(g, nmax);
@@ -648,6 +661,7 @@ ms_status ms_destroy(ms_grid* g) {
     dev_free(g->lo[f]);
   }
   dev_free(g->de64);
+  tracked32_teardown(g);
   dev_free(g->d_src);
   dev_free(g->d_srctab);
   dev_free(g->d_srctab32);
@@ -672,12 +686,13 @@ ms_status ms_init_modes(ms_grid* g, const ms_mode* modes, int nmodes) {
   if (nmodes < 0 || (nmodes > 0 && !modes)) return fail(MS_EINVAL, "invalid modes");
   for (int m = 0; m < nmodes; ++m)
     if (modes[m].m < 1 || modes[m].n < 1) return fail(MS_EINVAL, "mode indices must be >= 1");
-  if (g->de64) {
+  if (g->de64 || g->de_hi) {
     // Delta E of a mode is -pi^2 (m^2 + n^2) E: the exact E_z field of the rescaled amplitudes
     std::vector<ms_mode> lap(modes, modes + nmodes);
     for (ms_mode& m : lap) m.amp *= -M_PI * M_PI * ((double)m.m * m.m + (double)m.n * m.n);
-    double* dd[3] = {g->de64, g->s64[0], g->s64[1]};
+    double* dd[3] = {g->de64 ? g->de64 : g->s64[2], g->s64[0], g->s64[1]};
     MS_TRY(exact_fields64(g, lap.data(), nmodes, 0.0, 0.5 * g->ht, dd));
+    if (g->de_hi) tracked32_set_de(g, g->s64[2]);
   }
   double* dst[3] = {g->s64[3], g->s64[4], g->s64[5]};
   MS_TRY(exact_fields64(g, modes, nmodes, 0.0, 0.5 * g->ht, dst));
@@ -699,6 +714,11 @@ ms_status ms_set_fields_device(ms_grid* g, const double* const* comps, long step
     if (!comps[f]) return fail(MS_EINVAL, "NULL component");
   MS_TRY(store_state(g, comps));
   if (g->de64) launch_lap_e64(g->f64[EZ], g->de64, g->N, g->h, g->stream);  // DE^0 = Delta_h E^0
+  if (g->de_hi) {  // DE^0 = Delta_h E^0 of the stored (wall-zeroed) E
+    launch_join(g->hi[EZ], g->lo[EZ], g->s64[1], g->sh[EZ].size(), g->stream);
+    launch_lap_e64(g->s64[1], g->s64[0], g->N, g->h, g->stream);
+    tracked32_set_de(g, g->s64[0]);
+  }
   g->step = step;
   MS_TRY(sync_step(g));
   return check_launch("set fields");
@@ -732,6 +752,11 @@ ms_status ms_set_fields(ms_grid* g, const double* const* comps, long step) {
   }
   MS_TRY(store_state(g, dst));
   if (g->de64) launch_lap_e64(g->f64[EZ], g->de64, g->N, g->h, g->stream);  // DE^0 = Delta_h E^0
+  if (g->de_hi) {  // DE^0 = Delta_h E^0 of the stored (wall-zeroed) E
+    launch_join(g->hi[EZ], g->lo[EZ], g->s64[1], g->sh[EZ].size(), g->stream);
+    launch_lap_e64(g->s64[1], g->s64[0], g->N, g->h, g->stream);
+    tracked32_set_de(g, g->s64[0]);
+  }
   g->step = step;
   MS_TRY(sync_step(g));
   return check_launch("set fields");

@@ -4,7 +4,7 @@
 // scheme, ncomp, the doubles z_imp and r, the int64 step, and per component its point count
 // (int64) followed by the raw state: FP64 values (MS_FP64) or the FP32 hi array then the FP32 lo
 // array (MS_FP32_REFINED, so a resume is bit-exact); for MS_SCHEME_C4_DE the tracked Delta E_z
-// plane follows as one more FP64 component.  Sources are configuration, not state: they are not
+// plane follows as one more component in the grid's precision.  Sources are configuration, not state: they are not
 // saved.
 #include <cstdio>
 #include <cstring>
@@ -39,9 +39,10 @@ int state_arrays(ms_grid* g, double** f64, float** hi, float** lo, size_t* n) {
     lo[f] = g->lo[f];
     n[f] = g->sh[f].size();
   }
-  if (g->de64) {
+  if (g->de64 || g->de_hi) {
     f64[3] = g->de64;
-    hi[3] = lo[3] = nullptr;
+    hi[3] = g->de_hi;
+    lo[3] = g->de_lo;
     n[3] = g->sh[EZ].size();
     return 4;
   }

@@ -76,7 +76,8 @@ struct PhaseArgs {
 
 // One Pade phase on the tile: y(a, r) for lines c = c0 + a (a < TB) and outputs r = r0 + o
 // (o < TB), handed to out(a, o, y).  Caller synchronises before reusing dlt / dd.
-template <typename Out>
+// FILTER false: d = delta (the source is already filtered, as G~_E of the tracked-Delta-E step).
+template <bool FILTER, typename Out>
 __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, float* dlt, float* dd, Out out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mb = r0 - KMAX - 1;  // along index of raw-difference column 0
@@ -206,8 +207,12 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
         if (32 * cc + 32 <= DL || lane + 32 * cc < DL) {
           const int q = 32 * cc;
           const float x = r1[q];
-          const float lap = fmaf(-4.0f, x, (r1[q - 1] + r1[q + 1]) + (r1[q - XLP] + r1[q + XLP]));
-          o[q] = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
+          if (FILTER) {
+            const float lap = fmaf(-4.0f, x, (r1[q - 1] + r1[q + 1]) + (r1[q - XLP] + r1[q + XLP]));
+            o[q] = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
+          } else {
+            o[q] = x;
+          }
         }
       }
     }
@@ -221,8 +226,12 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
       float v = 0.0f;
       if (line_ok && (inside || (m >= 0 && m < p.M))) {
         const float x = r1[q];
-        const float lap = ((r1[q - 1] - x) + (r1[q + 1] - x)) + ((r1[q - XLP] - x) + (r1[q + XLP] - x));
-        v = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
+        if (FILTER) {
+          const float lap = ((r1[q - 1] - x) + (r1[q + 1] - x)) + ((r1[q - XLP] - x) + (r1[q + XLP] - x));
+          v = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
+        } else {
+          v = x;
+        }
       }
       dd[a * DLP + q] = v;
     }
@@ -301,7 +310,7 @@ namespace {
 
 // STEP 0: right-hand side of Step 1 on E_z; STEP 1: right-hand sides of Step 2 on H_x, H_y;
 // the tile with origin (i0, j0).
-template <int STEP>
+template <int STEP, bool FILTER = true>
 __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
   extern __shared__ float sm[];
   float* dlt = sm;
@@ -310,10 +319,10 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
   const int N = A.N;
   if (STEP == 0) {
     // x-Pade of H_y: line = row j (c0 = j0), output node i = r + 1 (r0 = i0 - 1)
-    pade_phase(A.ph[0], j0, i0 - 1, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
+    pade_phase<FILTER>(A.ph[0], j0, i0 - 1, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
     __syncthreads();
     // y-Pade of H_x: line = column i (c0 = i0), output node j = r + 1 (r0 = j0 - 1)
-    pade_phase(A.ph[1], i0, j0 - 1, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] -= v; });
+    pade_phase<FILTER>(A.ph[1], i0, j0 - 1, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] -= v; });
     __syncthreads();
     for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
       const int j = j0 + jj;
@@ -327,7 +336,7 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
     }
   } else {
     // y-Pade of E for H_x: line = column i (c0 = i0), output half-row jh = r (r0 = j0)
-    pade_phase(A.ph[0], i0, j0, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] = v; });
+    pade_phase<FILTER>(A.ph[0], i0, j0, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] = v; });
     __syncthreads();
     for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
       const int jh = j0 + jj;
@@ -340,7 +349,7 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
     }
     __syncthreads();
     // x-Pade of E for H_y: line = row j (c0 = j0), output half-column ih = r (r0 = i0)
-    pade_phase(A.ph[1], j0, i0, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
+    pade_phase<FILTER>(A.ph[1], j0, i0, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
     __syncthreads();
     for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
       const int j = j0 + jj;
@@ -376,11 +385,11 @@ __host__ __device__ __forceinline__ void ring_first_tile(int b, int nt, int* tx,
   }
 }
 
-template <int STEP>
+template <int STEP, bool FILTER = true>
 __global__ void __launch_bounds__(NT, 3) k_curl_tile(CurlArgs A) {
   int tx, ty;
   ring_first_tile(blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, &tx, &ty);
-  curl_body<STEP>(A, tx * TB, ty * TB);
+  curl_body<STEP, FILTER>(A, tx * TB, ty * TB);
 }
 
 // Words of a small argument struct copied from global to shared memory by the first warp.
@@ -914,6 +923,7 @@ int tiled_configure() {
   const int cs = (int)tiled_curl_smem(), ss = (int)tiled_solve_smem();
   if (cudaFuncSetAttribute(k_curl_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
       cudaFuncSetAttribute(k_curl_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
+      cudaFuncSetAttribute(k_curl_tile<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
       cudaFuncSetAttribute(k_curl_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
       cudaFuncSetAttribute(k_curl_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs) != cudaSuccess ||
       cudaFuncSetAttribute(k_solve_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, ss) != cudaSuccess ||
@@ -947,6 +957,16 @@ void tiled_curl(ms_grid* g, int step, float cb_hi, float cb_lo, float* b0, float
   dim3 grid(A.ntiles, A.ntiles);
   if (step == 0) k_curl_tile<0><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
   else k_curl_tile<1><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
+}
+
+void tiled_curl_unfiltered(ms_grid* g, const float* hi, const float* lo, float* b0, float* b1) {
+  CurlArgs A = make_curl(g, 1, 1.0f, 0.0f, b0, b1);
+  for (int k = 0; k < 2; ++k) {
+    A.ph[k].hi = hi;
+    A.ph[k].lo = lo;
+  }
+  dim3 grid(A.ntiles, A.ntiles);
+  k_curl_tile<1, false><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
 }
 
 void tiled_solve(ms_grid* g, int nfields, const int* fields, const float* const* b, int S, float d_hi, float d_lo,

@@ -24,6 +24,8 @@ size_t tiled_curl_smem();
 size_t tiled_solve_smem();
 // step 0: b0 = Step 1 right-hand side on E_z; step 1: b0, b1 = Step 2 right-hand sides on H_x, H_y.
 void tiled_curl(ms_grid* g, int step, float cb_hi, float cb_lo, float* b0, float* b1);
+// Step 2 right-hand sides from an already filtered E_z-shaped float-float field (hi, lo).
+void tiled_curl_unfiltered(ms_grid* g, const float* hi, const float* lo, float* b0, float* b1);
 // S sweeps of 6 h^2 P1 x = b and the float-float update (hi, lo) += (s_hi + s_lo) x for 1 or 2 fields.
 void tiled_solve(ms_grid* g, int nfields, const int* fields, const float* const* b, int S, float d_hi, float d_lo,
                  float omega, float s_hi, float s_lo);

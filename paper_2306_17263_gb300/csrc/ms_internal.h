@@ -60,7 +60,7 @@ struct Graph {
 enum KernelKind {
   KK_FILTER64 = 0, KK_PADE64 = 1, KK_P1SWEEP64 = 2, KK_YEE64 = 3, KK_CURL32 = 4, KK_SOLVE32 = 5,
   KK_FILTER3D64 = 6, KK_PADE3D64 = 7, KK_SWEEP3D64 = 8, KK_FILT3D32 = 9, KK_BAND3D32 = 10, KK_SWEEP3D32 = 11,
-  KK_NC64 = 12, KK_SRC = 13, KK_TERM3D32 = 14, KK_TSGEMM = 15, KK_TSPACK = 16,
+  KK_NC64 = 12, KK_SRC = 13, KK_TERM3D32 = 14, KK_TSGEMM = 15, KK_TSPACK = 16, KK_TRACKED32 = 17,
   KK_COUNT
 };
 const char* kernel_kind_name(int k);
@@ -114,6 +114,9 @@ struct ms_grid {
   // FP64 state and scratch
   double* f64[3] = {nullptr, nullptr, nullptr};   // E_z, H_x, H_y
   double* de64 = nullptr;                          // tracked Delta E_z (MS_SCHEME_C4_DE)
+  float* de_hi = nullptr;                          // the same in MS_FP32_REFINED (float-float)
+  float* de_lo = nullptr;
+  float* t32[8] = {};                              // its scratch: E^n, y_x, y_y, G~_E (hi, lo each)
   double* s64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool shared64 = false;  // s64 planes belong to a batch
   // FP32 hi/lo state (MS_FP32_REFINED)

@@ -41,7 +41,7 @@ def _desc(**kw):
     (dict(scheme=4), -1), (dict(r=0.70), -2), (dict(r=1 / math.sqrt(2)), -2),
     (dict(scheme=1, r=0.75), -2), (dict(scheme=1, precision=1), -7),
     (dict(scheme=2, r=0.61), -2), (dict(scheme=2, precision=1), -7), (dict(scheme=4), -1),
-    (dict(scheme=3, precision=1), -7), (dict(scheme=3, r=0.70), -2),
+    (dict(scheme=3, r=0.70), -2),
 ])
 def test_descriptor_validation(kw, status):
     L = pkg.load()
