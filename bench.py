@@ -54,6 +54,12 @@ def parse():
     p.add_argument("--only-sources", type=int, default=None, metavar="STEPS",
                    help="run only the FP32_REFINED 2048^2 step with two current sources (STEPS profiled "
                         "steps and STEPS graph-replayed ones) and print its JSON (profiling)")
+    p.add_argument("--only-batched", type=int, default=None, metavar="STEPS",
+                   help="run only the batch leg (512 uneven cavities, autotuned plan, STEPS timed steps) and print "
+                        "its JSON (profiling)")
+    p.add_argument("--only-variants", action="store_true",
+                   help="run only the step-variants leg (sources, wall sources, tracked Delta E; FP64 and "
+                        "FP32_REFINED) and print its JSON (profiling)")
     return p.parse_args()
 
 
@@ -775,6 +781,18 @@ def main():
         torch.cuda.set_stream(torch.cuda.Stream())
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         print(json.dumps(sources_leg(pkg, torch, workloads.config2()["r"], args.only_sources, flush)), flush=True)
+        return 0
+    if args.only_batched is not None or args.only_variants:
+        import torch
+
+        import paper_2306_17263_gb300 as pkg
+        torch.cuda.set_device(local)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        if args.only_batched is not None:
+            print(json.dumps(batched_leg(pkg, torch, steps=args.only_batched)), flush=True)
+        else:
+            c = workloads.config2()
+            print(json.dumps(variants_leg(pkg, torch, c["modes"], c["r"])), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args, ws, rank)
