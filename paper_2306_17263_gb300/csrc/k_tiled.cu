@@ -269,24 +269,31 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
       yv[k] = fmaf(c_w[KB], dv[k + KB], acc);
     }
   } else {
+    // explicit end rows: the tap loop unrolled to the largest half-width the tile holds, taps beyond
+    // the table's K predicated off; taps past the line read the zero differences stored there, so
+    // the sums are those of the taps inside the line
     for (int k = 0; k < SEG; ++k) {
       const int r = rf + k;
       float acc = 0.0f, lo = 0.0f;
       if (r >= 0 && r < p.M) {
-        const float* wh = pade_row_ptr(p.whi, r, p.M, p.Kt, p.Bt, p.all_explicit);
-        const float* wl = pade_row_ptr(p.wlo, r, p.M, p.Kt, p.Bt, p.all_explicit);
-        for (int dist = p.Kt + 1; dist >= 1; --dist) {
-          for (int side = 1; side >= -1; side -= 2) {
-            const int m = r + side * dist, t = m - r + p.Kt;
-            if (t < 0 || t > 2 * p.Kt + 1 || m < 0 || m >= p.M) continue;
-            const float dm = drow[m - rf];
-            acc = fmaf(__ldg(wh + t), dm, acc);
-            lo = fmaf(__ldg(wl + t), dm, lo);
+        const float* wh = pade_row_ptr(p.whi, r, p.M, p.Kt, p.Bt, p.all_explicit) + p.Kt;  // wh[d]: delta_{r+d}
+        const float* wl = pade_row_ptr(p.wlo, r, p.M, p.Kt, p.Bt, p.all_explicit) + p.Kt;
+        const float* dc = drow + (r - rf);
+#pragma unroll
+        for (int dist = KMAX + 1; dist >= 1; --dist) {
+          if (dist <= p.Kt + 1) {
+            const float dm = dc[dist];
+            acc = fmaf(__ldg(wh + dist), dm, acc);
+            lo = fmaf(__ldg(wl + dist), dm, lo);
+          }
+          if (dist <= p.Kt) {
+            const float dm = dc[-dist];
+            acc = fmaf(__ldg(wh - dist), dm, acc);
+            lo = fmaf(__ldg(wl - dist), dm, lo);
           }
         }
-        const float dc = drow[r - rf];
-        lo = fmaf(__ldg(wl + p.Kt), dc, lo);
-        acc = fmaf(__ldg(wh + p.Kt), dc, acc + lo);
+        lo = fmaf(__ldg(wl), dc[0], lo);
+        acc = fmaf(__ldg(wh), dc[0], acc + lo);
       }
       yv[k] = acc;
     }
