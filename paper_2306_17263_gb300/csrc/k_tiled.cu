@@ -675,6 +675,9 @@ __device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* 
   }
 #pragma unroll
   for (int k = 0; k < FR; ++k) {
+    if constexpr (LAST) {  // rows outside the output tile (the same for every lane of the warp)
+      if (!rowok[k]) continue;
+    }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const float* w = j ? w1 : w0;
@@ -688,13 +691,11 @@ __device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* 
       const float res = __fsub_rn(__fsub_rn(bv[k][j], ph), pl) - rest;
       const float corr = A.omega * res;
       if constexpr (LAST) {
-        if (rowok[k]) {
-          float h = sh[k][j], lo = sl[k][j];
-          ff_add_scaled2_t(h, lo, x, corr, A.s_hi, A.s_lo);
-          if (j ? colok1 : colok0) {
-            shi[gp + k * nx + j] = h;
-            slo[gp + k * nx + j] = lo;
-          }
+        float h = sh[k][j], lo = sl[k][j];
+        ff_add_scaled2_t(h, lo, x, corr, A.s_hi, A.s_lo);
+        if (j ? colok1 : colok0) {
+          shi[gp + k * nx + j] = h;
+          slo[gp + k * nx + j] = lo;
         }
       } else {
         xv[k][j] = x + corr;
