@@ -93,6 +93,25 @@ def test_fp32_refined_random_fields_close_to_oracle(closure):
     assert rel <= 2e-6, rel
 
 
+@pytest.mark.parametrize("closure", [pkg.CLOSURE_PAPER, pkg.CLOSURE_REFLECT])
+@pytest.mark.parametrize("n,steps", [(5, 4), (40, 3), (71, 2)])
+def test_fp32_refined_random_fields_ragged_sizes(closure, n, steps):
+    """The smallest FP32 grid (n = 5: every Pade row explicit, sweep tiles of two or three
+    unknowns) and grids of several filter, term and sweep tiles with ragged tails (40, 71): random
+    fields within 2e-6 of the oracle."""
+    r = 0.4
+    init = workloads.random_fields3(n, seed=300 + n)
+    o = oracle.Oracle3D(n, r, closure=closure)
+    ref = [a.copy() for a in init]
+    o.run(ref, steps)
+    with pkg.Grid(n, r, precision=pkg.FP32_REFINED, closure=closure, dim=3) as g:
+        g.set_fields(*init)
+        g.run(steps)
+        got = g.get_fields()
+    rel = np.linalg.norm(_cat(got) - _cat(ref)) / np.linalg.norm(_cat(ref))
+    assert rel <= 2e-6, rel
+
+
 @pytest.mark.parametrize("precision,steps", [(pkg.FP32_REFINED, 500), (pkg.FP64, 40)])
 def test_full_size_reflect_closed_form(precision, steps):
     """256^3 cells: under the REFLECT closure each mode evolves by its 6x6 step matrix; sampled
