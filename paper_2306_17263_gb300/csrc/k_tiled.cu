@@ -197,22 +197,38 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
   // 2) filtered differences d = 12 beta delta + L delta on lines c0 .. c0+TB-1, m in [mb+1, mb+1+DL);
   //    the 12 beta delta term dominates (beta = 1 + 2/r^2), so L delta is summed plainly
   if (inside) {
+    // warp w filters lines 4w .. 4w+3, walking down them: the differences above and below a line
+    // are the centres of its neighbour lines, carried in registers (three shared loads per element)
+    constexpr int LPW = TB / NW;  // lines per warp
+    constexpr int NCC = (DL + 31) / 32;
+    const int a0 = LPW * warp;
+    float up[NCC], mid[NCC];
 #pragma unroll
-    for (int it = 0; it < TB / NW; ++it) {
-      const int a = warp + it * NW;
+    for (int cc = 0; cc < NCC; ++cc) {
+      const bool ok = 32 * cc + 32 <= DL || lane + 32 * cc < DL;
+      const float* r0 = dlt + a0 * XLP + 1 + lane + 32 * cc;  // line a0 - 1 of the filter
+      up[cc] = ok ? r0[0] : 0.0f;
+      mid[cc] = ok ? r0[XLP] : 0.0f;
+    }
+#pragma unroll
+    for (int it = 0; it < LPW; ++it) {
+      const int a = a0 + it;
       const float* r1 = dlt + (a + 1) * XLP + 1 + lane;
       float* o = dd + a * DLP + lane;
 #pragma unroll
-      for (int cc = 0; cc < (DL + 31) / 32; ++cc) {
+      for (int cc = 0; cc < NCC; ++cc) {
         if (32 * cc + 32 <= DL || lane + 32 * cc < DL) {
           const int q = 32 * cc;
-          const float x = r1[q];
+          const float x = mid[cc];
+          const float dn = r1[q + XLP];
           if (FILTER) {
-            const float lap = fmaf(-4.0f, x, (r1[q - 1] + r1[q + 1]) + (r1[q - XLP] + r1[q + XLP]));
+            const float lap = fmaf(-4.0f, x, (r1[q - 1] + r1[q + 1]) + (up[cc] + dn));
             o[q] = fmaf(p.cb_hi, x, fmaf(p.cb_lo, x, lap));
           } else {
             o[q] = x;
           }
+          up[cc] = x;
+          mid[cc] = dn;
         }
       }
     }
