@@ -19,6 +19,8 @@ def _make(kind):
         return pkg.Grid(40, 0.5, precision=pkg.FP32_REFINED)
     if kind == "de_2d":
         return pkg.Grid(24, 0.4, precision=pkg.FP64, scheme=pkg.SCHEME_C4_DE)
+    if kind == "de32_2d":
+        return pkg.Grid(40, 0.4, precision=pkg.FP32_REFINED, scheme=pkg.SCHEME_C4_DE)
     if kind == "fp64_3d":
         return pkg.Grid(8, 0.4, precision=pkg.FP64, dim=3)
     if kind == "fp32_3d":
@@ -35,7 +37,7 @@ def _allocs_of(fn):
     return obj, n, base
 
 
-@pytest.mark.parametrize("kind", ["fp64_2d", "fp32_2d", "de_2d", "fp64_3d", "fp32_3d", "batch"])
+@pytest.mark.parametrize("kind", ["fp64_2d", "fp32_2d", "de_2d", "de32_2d", "fp64_3d", "fp32_3d", "batch"])
 def test_every_creation_allocation_failure_is_reported_and_released(kind):
     obj, n, base = _allocs_of(lambda: _make(kind))
     obj.close()
