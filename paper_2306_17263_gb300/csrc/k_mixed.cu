@@ -130,8 +130,8 @@ ms_status mixed_setup(ms_grid* g) {
       g_mixed_err = err;
       return MS_EINVAL;
     }
-    // the interior fast path needs K >= kTiledKFast; short lines store every row explicitly
-    if (t.K > kTiledKMax || (t.K < kTiledKFast && !t.all_explicit)) {
+    // the explicit rows of the tile kernels hold half-widths up to kTiledKMax
+    if (t.K > kTiledKMax) {
       g_mixed_err = "FP32 Pade band half-width outside the range the tile kernels hold";
       return MS_EUNSUPPORTED;
     }

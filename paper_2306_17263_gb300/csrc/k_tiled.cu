@@ -5,8 +5,8 @@
 //                  state in float-float, delta_m = (hi_{m+1} - hi_m) + (lo_{m+1} - lo_m), filters
 //                  them, d = 12 beta delta + L delta (the filter of Eq. "eq:ell" commutes with the
 //                  difference: D1 (12 beta + L) u = (12 beta + L') D1 u with the ghost rules below),
-//                  and applies the band of A^{-1} (App. A.1, Eq. "eq:lhs") from shared memory with
-//                  a register window.  Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y)
+//                  and applies A^{-1} (App. A.1, Eq. "eq:lhs"): rows near a wall as explicit rows
+//                  of its band, interior rows as the two first-order recurrences A factors into.  Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y)
 //                  on E_z; Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x).
 //   k_solve_tile : S Richardson sweeps of 6 h^2 P1 (Def. "def:operatorsP") on the tile plus an
 //                  (S-1)-cell halo in shared memory, then the float-float state update of the
@@ -25,8 +25,9 @@
 //
 // Instruction budget: both kernels are bound by issue, not by DRAM, so loops have constant
 // strides and 32-bit offsets, tiles away from the walls take block-uniform paths without any
-// boundary test, and the interior band of A^{-1} (the same Toeplitz row for every grid,
-// 24 (-rho) rho^|d| / (1 - rho^2), rho = -11 + sqrt(120)) is read from constant memory.
+// boundary test, and interior rows of A^{-1} (the same Toeplitz row for every grid,
+// 24 (-rho) rho^|d| / (1 - rho^2), rho = -11 + sqrt(120)) cost two FMAs per output and
+// recurrence instead of one per tap.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -39,12 +40,12 @@ namespace ms {
 namespace {
 
 constexpr int TB = 64;               // output tile edge
-constexpr int KB = kTiledKFast;      // band half-width of the interior fast path
 constexpr int KMAX = kTiledKMax;     // largest band half-width of the explicit end rows
 constexpr int NT = 512;              // threads per block
 constexpr int NW = NT / 32;          // warps per block
-constexpr int SEG = 4;               // outputs per band segment along a line
-constexpr int NSEG = TB / SEG / (NW / 2);  // band segments per thread
+constexpr int SEG = 8;               // outputs per segment of A^{-1} along a line (one per thread)
+static_assert(TB / SEG == NW / 2, "two warps per 64 lines, one segment per thread");
+constexpr int KR = 6;                // warm-up length of the interior recurrences
 constexpr int DL = TB + 2 * KMAX + 2;  // filtered differences held per line
 constexpr int DLP = DL | 1;            // odd row pitch: conflict-free across lanes
 constexpr int XL = DL + 2;             // raw differences per line (one more on each side)
@@ -56,9 +57,9 @@ constexpr int RSP = RS + 1;
 constexpr int MAXR = (RS + NW / 2 - 1) / (NW / 2);  // rows of a sweep strip, at most
 constexpr int PF = 4;                                // state rows fetched ahead in the last sweep
 
-// interior row of A^{-1} at offsets -KB .. KB+1 (hi), and the lo parts of offsets -1, 0, 1
-__constant__ float c_w[2 * KB + 2];
-__constant__ float c_wl[3];
+// interior A^{-1} as two first-order recurrences: rho, 1 / (1 - rho), and the scale (1 - rho)^2
+// split hi + lo (rho is the FP32 root, so the scale gives the recurrences a DC gain of exactly 1)
+__constant__ float c_rec[4];
 
 struct PhaseArgs {
   const float* hi;
@@ -253,36 +254,33 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
     }
   }
   __syncthreads();
-  // 3) band of A^{-1}: lane -> line, warp -> (line half, NSEG segments of SEG outputs)
+  // 3) A^{-1} d: lane -> line, warp -> (line half, segment of SEG outputs)
   const int a = lane + 32 * (warp & 1);
-#pragma unroll
-  for (int sg = 0; sg < NSEG; ++sg) {
-  const int s = (warp >> 1) + (NW / 2) * sg;
+  const int s = warp >> 1;
   const int rf = r0 + s * SEG;  // first output of this segment
   const float* drow = dd + a * DLP + (rf - (mb + 1));  // drow[j] = d_{rf + j}
-  float yv[SEG];
   const bool fast = !p.all_explicit && rf >= p.Bt && rf + SEG - 1 < p.M - p.Bt;
-  // Summation order matters: the taps fall off like |rho|^|d| ~ 0.046^|d|, so a tap added after
-  // the centre tap (|w| ~ 1.1) is lost once it drops below half an ulp of the partial sum (from
-  // |d| = 6 on).  Losing the taps of one side only is a coherent, odd-symmetric error of the
-  // derivative (~1e-8, a phase error that grows with time), so the taps are summed farthest
-  // first from both sides, then the lo parts, then the centre.
   if (fast) {
-    float dv[SEG + 2 * KB + 1];
+    // Interior rows: A = (1/24) tridiag(1, 22, 1) factors as (1 - rho E^-1)(1 - rho E) / (1 - rho)^2
+    // (rho^2 + 22 rho + 1 = 0, so (1 - rho)^2 = -24 rho), and A^{-1} d is a forward recurrence
+    // z_i = d_i + rho z_{i-1}, a backward one y_i = z_i + rho y_{i+1}, and the scale (1 - rho)^2.
+    // Each recurrence starts KR + 1 rows outside the segment from the steady state of the value
+    // there (d / (1 - rho), z / (1 - rho)): its error reaches the segment damped by
+    // |rho|^(KR+1) ~ 4e-10, times the change of d over those rows.  Every product enters through
+    // one FMA, so no tap is dropped against a larger partial sum.
+    const float rho = c_rec[0], inv1mr = c_rec[1];
+    float zs[SEG + KR];
+    float z = drow[-KR - 1] * inv1mr;
 #pragma unroll
-    for (int q = 0; q < SEG + 2 * KB + 1; ++q) dv[q] = drow[q - KB];
+    for (int q = -KR; q < SEG + KR; ++q) {
+      z = fmaf(rho, z, drow[q]);
+      if (q >= 0) zs[q] = z;
+    }
+    float y = z * inv1mr;
 #pragma unroll
-    for (int k = 0; k < SEG; ++k) {
-      float acc = c_w[2 * KB + 1] * dv[k + 2 * KB + 1];  // offset +(KB+1)
-#pragma unroll
-      for (int dist = KB; dist >= 1; --dist) {
-        acc = fmaf(c_w[KB + dist], dv[k + KB + dist], acc);
-        acc = fmaf(c_w[KB - dist], dv[k + KB - dist], acc);
-      }
-      acc = fmaf(c_wl[0], dv[k + KB - 1], acc);
-      acc = fmaf(c_wl[2], dv[k + KB + 1], acc);
-      acc = fmaf(c_wl[1], dv[k + KB], acc);
-      yv[k] = fmaf(c_w[KB], dv[k + KB], acc);
+    for (int q = SEG + KR - 1; q >= 0; --q) {
+      y = fmaf(rho, y, zs[q]);
+      if (q < SEG) out(a, s * SEG + q, fmaf(c_rec[2], y, c_rec[3] * y));
     }
   } else {
     // explicit end rows: the tap loop unrolled to the largest half-width the tile holds, taps beyond
@@ -311,11 +309,8 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
         lo = fmaf(__ldg(wl), dc[0], lo);
         acc = fmaf(__ldg(wh), dc[0], acc + lo);
       }
-      yv[k] = acc;
+      out(a, s * SEG + k, acc);
     }
-  }
-#pragma unroll
-  for (int k = 0; k < SEG; ++k) out(a, s * SEG + k, yv[k]);
   }
 }
 
@@ -961,17 +956,17 @@ int tiled_configure() {
     return -1;
   g_curl_resident = sms * pc;
   g_solve_resident = sms * ps;
-  // interior Toeplitz row of A^{-1}: 24 (-rho) rho^|d| / (1 - rho^2) (rho < 0), split hi + lo
-  const long double rho = -11.0L + std::sqrt(120.0L);
-  float w[2 * KB + 2], wl[3];
-  for (int t = 0; t < 2 * KB + 2; ++t) {
-    const int d = t - KB;
-    long double v = 24.0L * (-rho) / (1.0L - rho * rho);
-    for (int k = 0; k < (d < 0 ? -d : d); ++k) v *= rho;
-    w[t] = (float)v;
-    if (d >= -1 && d <= 1) wl[d + 1] = (float)(v - (long double)w[t]);
-  }
-  if (cudaMemcpyToSymbol(c_w, w, sizeof w) != cudaSuccess || cudaMemcpyToSymbol(c_wl, wl, sizeof wl) != cudaSuccess)
+  // interior recurrences of A^{-1}: rho rounded to FP32, and the scale (1 - rho_f)^2 that makes
+  // their DC gain exactly 1 with that rho_f, split hi + lo
+  const float rho_f = (float)(-11.0L + std::sqrt(120.0L));
+  const long double one_m = 1.0L - (long double)rho_f;
+  const long double scale = one_m * one_m;
+  float rec[4];
+  rec[0] = rho_f;
+  rec[1] = (float)(1.0L / one_m);
+  rec[2] = (float)scale;
+  rec[3] = (float)(scale - (long double)rec[2]);
+  if (cudaMemcpyToSymbol(c_rec, rec, sizeof rec) != cudaSuccess)
     return -1;
   return 0;
 }

@@ -9,7 +9,6 @@ namespace ms {
 
 constexpr int kTiledKMax = 12;       // largest Pade band half-width the tiles hold
 constexpr int kTiledMaxSweeps = 6;   // largest Richardson sweep count (halo = sweeps - 1)
-constexpr int kTiledKFast = 7;       // band half-width of the interior fast path
 
 // Coefficients of the FP32 step of a grid (k_mixed.cu): 12 beta, 6 c1 h^2, the Richardson
 // relaxation, the increment scales 12 Z / r and 12 / (r Z), all split hi + lo; S sweeps.
