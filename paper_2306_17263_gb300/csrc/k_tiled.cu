@@ -75,6 +75,62 @@ struct PhaseArgs {
   float cb_hi, cb_lo;  // 12 beta
 };
 
+// Interior rows of A^{-1} d for the segment of SEG outputs starting at row rf (drow[j] = d_{rf+j}).
+// A = (1/24) tridiag(1, 22, 1) factors as (1 - rho E^-1)(1 - rho E) / (1 - rho)^2 (rho^2 + 22 rho
+// + 1 = 0, so (1 - rho)^2 = -24 rho), and A^{-1} d is a forward recurrence z_i = d_i + rho z_{i-1},
+// a backward one y_i = z_i + rho y_{i+1}, and the scale (1 - rho)^2.  Each recurrence starts
+// KR + 1 rows outside the segment from the steady state of the value there (d / (1 - rho),
+// z / (1 - rho)): its error reaches the segment damped by |rho|^(KR+1) ~ 4e-10, times the change
+// of d over those rows.  Every product enters through one FMA, so no tap is dropped against a
+// larger partial sum.  SKIP: rows inside the line whose row of A^{-1} is not the interior one
+// (r < B or r >= M - B) are left to the explicit rows; rows past the line are emitted (unused).
+template <bool SKIP, typename Emit>
+__device__ __forceinline__ void interior_rows(const float* drow, int rf, int M, int B, Emit emit) {
+  const float rho = c_rec[0], inv1mr = c_rec[1];
+  float zs[SEG + KR];
+  float z = drow[-KR - 1] * inv1mr;
+#pragma unroll
+  for (int q = -KR; q < SEG + KR; ++q) {
+    z = fmaf(rho, z, drow[q]);
+    if (q >= 0) zs[q] = z;
+  }
+  float y = z * inv1mr;
+#pragma unroll
+  for (int q = SEG + KR - 1; q >= 0; --q) {
+    y = fmaf(rho, y, zs[q]);
+    if (q < SEG) {
+      const int r = rf + q;
+      if (!SKIP || r < 0 || r >= M || (r >= B && r < M - B)) emit(q, fmaf(c_rec[2], y, c_rec[3] * y));
+    }
+  }
+}
+
+// Explicit row r of the band table (dc[j] = d_{r+j}): the tap loop unrolled to the largest
+// half-width the tile holds, taps beyond the table's K predicated off; taps past the line read the
+// zero differences stored there, so the sums are those of the taps inside the line.  Rows past
+// the line give 0.
+__device__ __forceinline__ float explicit_row(const PhaseArgs& p, const float* dc, int r) {
+  if (r < 0 || r >= p.M) return 0.0f;
+  const float* wh = pade_row_ptr(p.whi, r, p.M, p.Kt, p.Bt, p.all_explicit) + p.Kt;  // wh[d]: d_{r+d}
+  const float* wl = pade_row_ptr(p.wlo, r, p.M, p.Kt, p.Bt, p.all_explicit) + p.Kt;
+  float acc = 0.0f, lo = 0.0f;
+#pragma unroll
+  for (int dist = KMAX + 1; dist >= 1; --dist) {
+    if (dist <= p.Kt + 1) {
+      const float dm = dc[dist];
+      acc = fmaf(__ldg(wh + dist), dm, acc);
+      lo = fmaf(__ldg(wl + dist), dm, lo);
+    }
+    if (dist <= p.Kt) {
+      const float dm = dc[-dist];
+      acc = fmaf(__ldg(wh - dist), dm, acc);
+      lo = fmaf(__ldg(wl - dist), dm, lo);
+    }
+  }
+  lo = fmaf(__ldg(wl), dc[0], lo);
+  return fmaf(__ldg(wh), dc[0], acc + lo);
+}
+
 // One Pade phase on the tile: y(a, r) for lines c = c0 + a (a < TB) and outputs r = r0 + o
 // (o < TB), handed to out(a, o, y).  Caller synchronises before reusing dlt / dd.
 // FILTER false: d = delta (the source is already filtered, as G~_E of the tracked-Delta-E step).
@@ -254,62 +310,33 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
     }
   }
   __syncthreads();
-  // 3) A^{-1} d: lane -> line, warp -> (line half, segment of SEG outputs)
+  // 3) A^{-1} d: lane -> line, warp -> (line half, segment of SEG outputs).  Rows whose row of
+  //    A^{-1} is the interior one come from the recurrences; the explicit rows near the ends of
+  //    the line are dealt out over the line's TB / SEG threads.
   const int a = lane + 32 * (warp & 1);
   const int s = warp >> 1;
   const int rf = r0 + s * SEG;  // first output of this segment
   const float* drow = dd + a * DLP + (rf - (mb + 1));  // drow[j] = d_{rf + j}
-  const bool fast = !p.all_explicit && rf >= p.Bt && rf + SEG - 1 < p.M - p.Bt;
-  if (fast) {
-    // Interior rows: A = (1/24) tridiag(1, 22, 1) factors as (1 - rho E^-1)(1 - rho E) / (1 - rho)^2
-    // (rho^2 + 22 rho + 1 = 0, so (1 - rho)^2 = -24 rho), and A^{-1} d is a forward recurrence
-    // z_i = d_i + rho z_{i-1}, a backward one y_i = z_i + rho y_{i+1}, and the scale (1 - rho)^2.
-    // Each recurrence starts KR + 1 rows outside the segment from the steady state of the value
-    // there (d / (1 - rho), z / (1 - rho)): its error reaches the segment damped by
-    // |rho|^(KR+1) ~ 4e-10, times the change of d over those rows.  Every product enters through
-    // one FMA, so no tap is dropped against a larger partial sum.
-    const float rho = c_rec[0], inv1mr = c_rec[1];
-    float zs[SEG + KR];
-    float z = drow[-KR - 1] * inv1mr;
-#pragma unroll
-    for (int q = -KR; q < SEG + KR; ++q) {
-      z = fmaf(rho, z, drow[q]);
-      if (q >= 0) zs[q] = z;
-    }
-    float y = z * inv1mr;
-#pragma unroll
-    for (int q = SEG + KR - 1; q >= 0; --q) {
-      y = fmaf(rho, y, zs[q]);
-      if (q < SEG) out(a, s * SEG + q, fmaf(c_rec[2], y, c_rec[3] * y));
-    }
+  auto emit = [&](int q, float v) { out(a, s * SEG + q, v); };
+  if (!p.all_explicit && r0 >= p.Bt && r0 + TB - 1 < p.M - p.Bt) {  // block-uniform: no end row
+    interior_rows<false>(drow, rf, p.M, p.Bt, emit);
   } else {
-    // explicit end rows: the tap loop unrolled to the largest half-width the tile holds, taps beyond
-    // the table's K predicated off; taps past the line read the zero differences stored there, so
-    // the sums are those of the taps inside the line
-    for (int k = 0; k < SEG; ++k) {
-      const int r = rf + k;
-      float acc = 0.0f, lo = 0.0f;
-      if (r >= 0 && r < p.M) {
-        const float* wh = pade_row_ptr(p.whi, r, p.M, p.Kt, p.Bt, p.all_explicit) + p.Kt;  // wh[d]: delta_{r+d}
-        const float* wl = pade_row_ptr(p.wlo, r, p.M, p.Kt, p.Bt, p.all_explicit) + p.Kt;
-        const float* dc = drow + (r - rf);
-#pragma unroll
-        for (int dist = KMAX + 1; dist >= 1; --dist) {
-          if (dist <= p.Kt + 1) {
-            const float dm = dc[dist];
-            acc = fmaf(__ldg(wh + dist), dm, acc);
-            lo = fmaf(__ldg(wl + dist), dm, lo);
-          }
-          if (dist <= p.Kt) {
-            const float dm = dc[-dist];
-            acc = fmaf(__ldg(wh - dist), dm, acc);
-            lo = fmaf(__ldg(wl - dist), dm, lo);
-          }
-        }
-        lo = fmaf(__ldg(wl), dc[0], lo);
-        acc = fmaf(__ldg(wh), dc[0], acc + lo);
-      }
-      out(a, s * SEG + k, acc);
+    if (!p.all_explicit) interior_rows<true>(drow, rf, p.M, p.Bt, emit);
+    // explicit rows of the tile: [max(r0, 0), min(B, r0 + TB)) and [max(M - B, r0), min(M, r0 + TB));
+    // every row of the tile when the table is all explicit (rows past the line give 0)
+    int s1, n1, s2, n2;
+    if (p.all_explicit) {
+      s1 = r0; n1 = TB; s2 = 0; n2 = 0;
+    } else {
+      s1 = max(r0, 0);
+      n1 = max(0, min(p.Bt, r0 + TB) - s1);
+      s2 = max(p.M - p.Bt, r0);
+      n2 = max(0, min(p.M, r0 + TB) - s2);
+    }
+    const float* dline = dd + a * DLP - (mb + 1);  // dline[m] = d_m
+    for (int t = s; t < n1 + n2; t += TB / SEG) {
+      const int r = t < n1 ? s1 + t : s2 + (t - n1);
+      out(a, r - r0, explicit_row(p, dline + r, r));
     }
   }
 }
