@@ -13,7 +13,7 @@
 // first differences of G along the line (the filter commutes with the difference under the ghost
 // rules) and applies the A^{-1} band (farthest taps first), accumulating the right-hand side (a
 // difference kernel and a band kernel take over for tables wider than the tile holds); the solve
-// (k_sweep3d32) is the Richardson iteration on 6 h^2 P1 with the exact two-product residual and
+// (k_sweep3d32) is the Richardson iteration on 6 h^2 P1 with the exact-product residual and
 // the split last correction, each sweep one launch that marches tiles along z.
 #include <cmath>
 #include <cstdio>
@@ -745,15 +745,15 @@ __global__ void __launch_bounds__(SWX * SWT, LAST ? 4 : 5) k_sweep3d32(const flo
   int p = (lo2 + k0) * sz + (lo1 + ju) * n0 + lo0 + iu;
   fetch_pt(p);
   const int c0 = tx + 1, r0 = ty + 1;  // halo coordinates in the pair layout
-  const float2 m2 = bc2(-2.0f), m6 = bc2(-6.0f), dh2 = bc2(d_hi), dl2 = bc2(d_lo), sh2 = bc2(s_hi), sl2 = bc2(s_lo);
+  const float2 m2 = bc2(-2.0f), m6 = bc2(-6.0f), ndh2 = bc2(-d_hi), ndl2 = bc2(-d_lo), sh2 = bc2(s_hi), sl2 = bc2(s_lo);
   for (int k = k0; k < k1; ++k, p += sz) {
     stage(Zp);
     __syncthreads();
     if (k + 1 < k1) fetch(k + 2);
     const float2 bc = bq, hc = hq, lc = lq;
     if (k + 1 < k1) fetch_pt(p + sz);
-    // second differences as a + b - 2 v: the residual's dominant term d x is an exact
-    // two-product, so the rounding of these sums is far below an ulp of the residual
+    // second differences as a + b - 2 v: the residual's dominant term d x enters exactly, so
+    // the rounding of these sums is far below an ulp of the residual
     auto LX = [&](const float2(*Pl)[SWXP], int rr) { return fma2(m2, Pl[rr][c0], add2(Pl[rr][c0 - 1], Pl[rr][c0 + 1])); };
     auto LY = [&](const float2(*Pl)[SWXP]) { return fma2(m2, Pl[r0][c0], add2(Pl[r0 - 1][c0], Pl[r0 + 1][c0])); };
     const float2 x = Z0[r0][c0];
@@ -763,9 +763,8 @@ __global__ void __launch_bounds__(SWX * SWT, LAST ? 4 : 5) k_sweep3d32(const flo
     const float2 lxlz = fma2(m2, lx, add2(LX(Zm, r0), LX(Zp, r0)));
     const float2 lylz = fma2(m2, ly, add2(LY(Zm), LY(Zp)));
     const float2 rest = fma2(m6, add2(add2(lx, ly), lz), neg2(add2(add2(lxly, lylz), lxlz)));
-    const float2 ph = mul2(dh2, x);
-    const float2 pl = fma2(dl2, x, fma2(dh2, x, neg2(ph)));
-    const float2 res = sub2(sub2(sub2(bc, ph), pl), rest);
+    // b - d x with the product exact: b - d_hi x, then - d_lo x, one rounding each
+    const float2 res = sub2(fma2(ndl2, x, fma2(ndh2, x, bc)), rest);
     if (LAST) {
       const float2 corr = mul2(om2, res);
       float2 h = hc, l = lc;

@@ -17,7 +17,7 @@
 // would be amplified by 1/theta in every step.  The kernels therefore take the first
 // differences of the float-float state, (hi_{m+1} - hi_m) + (lo_{m+1} - lo_m), filter the
 // differences (the filter commutes with D1~), and only then apply the well-conditioned A^{-1}
-// band.  The Richardson residual uses an exact two-product of the dominant diagonal term, and
+// band.  The Richardson residual forms the dominant diagonal product exactly (FMA), and
 // the last correction is added to the state separately so the iteration cannot stall into a
 // coherent bias.  The state is a float-float pair updated with error-free transformations.
 //

@@ -10,7 +10,7 @@
 //                  on E_z; Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x).
 //   k_solve_tile : S Richardson sweeps of 6 h^2 P1 (Def. "def:operatorsP") on the tile plus an
 //                  (S-1)-cell halo in shared memory, then the float-float state update of the
-//                  paper's E += h_tau E* / H += h_tau H* with the exact two-product residual and
+//                  paper's E += h_tau E* / H += h_tau H* with the exact-product residual and
 //                  the split last correction (see k_mixed.cu).
 //
 // Ghost rules of the difference field along a Pade line: a source that is Neumann along the
@@ -353,6 +353,23 @@ struct CurlArgs {
 
 namespace {
 
+// The TB x TB tile ys (row jj, column ii at ys[jj * YSP + ii]) to dst[jj * ld + ii], negated if
+// NEG, for a tile whose entries all lie inside the array and off the walls: no tests, strides only.
+template <bool NEG>
+__device__ __forceinline__ void store_tile(float* dst, size_t ld, const float* ys) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* d = dst + (size_t)warp * ld + lane;
+  const float* y = ys + warp * YSP + lane;
+  const size_t st = (size_t)NW * ld;
+#pragma unroll
+  for (int k = 0; k < TB / NW; ++k) {
+    const float v0 = y[k * NW * YSP], v1 = y[k * NW * YSP + 32];
+    d[0] = NEG ? -v0 : v0;
+    d[32] = NEG ? -v1 : v1;
+    d += st;
+  }
+}
+
 // STEP 0: right-hand side of Step 1 on E_z; STEP 1: right-hand sides of Step 2 on H_x, H_y;
 // the tile with origin (i0, j0).
 template <int STEP, bool FILTER = true>
@@ -362,6 +379,8 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
   float* dd = dlt + XROWS * XLP;
   float* ys = dd + TB * DLP;
   const int N = A.N;
+  // every output of the tile is off the walls and inside its array (all three layouts)
+  const bool interior = i0 >= 1 && j0 >= 1 && i0 + TB <= N && j0 + TB <= N;
   if (STEP == 0) {
     // x-Pade of H_y: line = row j (c0 = j0), output node i = r + 1 (r0 = i0 - 1)
     pade_phase<FILTER>(A.ph[0], j0, i0 - 1, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
@@ -369,6 +388,10 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
     // y-Pade of H_x: line = column i (c0 = i0), output node j = r + 1 (r0 = j0 - 1)
     pade_phase<FILTER>(A.ph[1], i0, j0 - 1, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] -= v; });
     __syncthreads();
+    if (interior) {
+      store_tile<false>(A.b0 + (size_t)j0 * (N + 1) + i0, (size_t)(N + 1), ys);
+      return;
+    }
     for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
       const int j = j0 + jj;
       if (j > N) break;
@@ -383,6 +406,8 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
     // y-Pade of E for H_x: line = column i (c0 = i0), output half-row jh = r (r0 = j0)
     pade_phase<FILTER>(A.ph[0], i0, j0, dlt, dd, [&](int a, int o, float v) { ys[o * YSP + a] = v; });
     __syncthreads();
+    if (interior) store_tile<true>(A.b0 + (size_t)j0 * (N + 1) + i0, (size_t)(N + 1), ys);
+    else
     for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
       const int jh = j0 + jj;
       if (jh >= N) break;
@@ -396,6 +421,10 @@ __device__ __forceinline__ void curl_body(const CurlArgs& A, int i0, int j0) {
     // x-Pade of E for H_y: line = row j (c0 = j0), output half-column ih = r (r0 = i0)
     pade_phase<FILTER>(A.ph[1], j0, i0, dlt, dd, [&](int a, int o, float v) { ys[a * YSP + o] = v; });
     __syncthreads();
+    if (interior) {
+      store_tile<false>(A.b1 + (size_t)j0 * N + i0, (size_t)N, ys);
+      return;
+    }
     for (int jj = threadIdx.x >> 5; jj < TB; jj += NW) {
       const int j = j0 + jj;
       if (j > N) break;
@@ -512,6 +541,13 @@ __device__ __forceinline__ void ff_add_scaled2_t(float& hi, float& lo, float x, 
   hi = h2;
 }
 
+// Residual b - d x - rest of 6 h^2 P1 x = b (d the diagonal, rest the stencil Laplacians): the
+// product (d_hi + d_lo) x enters exactly, through two FMAs (b - d_hi x, then - d_lo x), each
+// rounded once at the size of b - d x.
+__device__ __forceinline__ float p1_resid(float b, float x, float d_hi, float d_lo, float rest) {
+  return fmaf(-d_lo, x, fmaf(-d_hi, x, b)) - rest;
+}
+
 // Fill the even ghosts of the Neumann axes from the edge values (only tiles at such an edge).
 __device__ __forceinline__ void fill_ghosts(float* x, int gx0, int gy0, int nx, int ny, bool neu_x, bool neu_y) {
   if (neu_x) {
@@ -533,7 +569,7 @@ __device__ __forceinline__ void fill_ghosts(float* x, int gx0, int gy0, int nx, 
 // Sweeps 1 .. S-1 of one region (see solve_body); EDGE: the region touches a wall, so points
 // off the unknowns are masked and Neumann ghosts refilled after every sweep.
 // One column strip of one sweep: rows ly0 .. ly1-1 of column c, sliding down a window of rows
-// ly-1, ly, ly+1.  The residual's dominant term d x is an exact two-product, so the stencil
+// ly-1, ly, ly+1.  The residual's dominant term d x enters exactly (p1_resid), so the stencil
 // Laplacians around it are summed plainly (their rounding is ~1e-3 ulp of the residual).
 // LAST: add the iterate and its correction to the state instead of writing the next iterate.
 template <bool EDGE, bool LAST>
@@ -569,9 +605,7 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
         const float lyv = fmaf(-2.0f, x, a0 + c0v);
         const float lxly = fmaf(-2.0f, lxb, lxa + lxc);
         const float rest = fmaf(-6.0f, lxb + lyv, -lxly);
-        const float ph = __fmul_rn(A.d_hi, x);
-        const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
-        const float res = __fsub_rn(__fsub_rn(bs[ly * RSP + c], ph), pl) - rest;
+        const float res = p1_resid(bs[ly * RSP + c], x, A.d_hi, A.d_lo, rest);
         const float corr = A.omega * res;
         const bool unk = !EDGE || (col_unk && gy0 + ly >= 0 && gy0 + ly < ny && interior(bcy, gy0 + ly, ny));
         if (unk) {
@@ -596,9 +630,7 @@ __device__ __forceinline__ void sweep_column(const SolveArgs& A, const float* bs
     const float lyv = fmaf(-2.0f, x, a0 + c0v);
     const float lxly = fmaf(-2.0f, lxb, lxa + lxc);
     const float rest = fmaf(-6.0f, lxb + lyv, -lxly);
-    const float ph = __fmul_rn(A.d_hi, x);
-    const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
-    const float res = __fsub_rn(__fsub_rn(bs[ly * RSP + c], ph), pl) - rest;
+    const float res = p1_resid(bs[ly * RSP + c], x, A.d_hi, A.d_lo, rest);
     const float corr = A.omega * res;
     bool unk = true;
     if (EDGE) {
@@ -724,9 +756,7 @@ __device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* 
       const float lyv = fmaf(-2.0f, x, w[k] + w[k + 2]);
       const float lxly = fmaf(-2.0f, l[k + 1], l[k] + l[k + 2]);
       const float rest = fmaf(-6.0f, l[k + 1] + lyv, -lxly);
-      const float ph = __fmul_rn(A.d_hi, x);
-      const float pl = fmaf(A.d_lo, x, fmaf(A.d_hi, x, -ph));
-      const float res = __fsub_rn(__fsub_rn(bv[k][j], ph), pl) - rest;
+      const float res = p1_resid(bv[k][j], x, A.d_hi, A.d_lo, rest);
       const float corr = A.omega * res;
       if constexpr (LAST) {
         float h = sh[k][j], lo = sl[k][j];
