@@ -217,6 +217,9 @@ __device__ __forceinline__ void ff_add_scaled3(float& hi, float& lo, float x, fl
 constexpr int KB3 = 7;
 __constant__ float c_w3[2 * KB3 + 2];
 __constant__ float c_wl3[3];
+// The interior rows as the recurrences A factors into: rho (FP32), 1 / (1 - rho), and the scale
+// (1 - rho_f) / (1 + rho_f) (hi, lo) that gives them a DC gain of exactly 1.
+__constant__ float c_rec3[4];
 
 // Paired FP32 arithmetic (two correctly rounded operations per instruction, sm_100 and later):
 // bitwise the same as the scalar operations on each half.
@@ -430,6 +433,37 @@ __device__ __forceinline__ float band_fast3(const float* d) {
   return fmaf(c_w3[KB3], d[KB3], acc);
 }
 
+// Eight interior rows rb .. rb + 7 of A^{-1} d (v[t] = d_{rb + t}, t = -KR3 - 1 .. 8 + KR3).
+// A = (1/24) tridiag(1, 22, 1) = (1 - rho E^-1)(1 - rho E) / (1 - rho)^2 with rho^2 + 22 rho + 1 = 0,
+// and by partial fractions 1 / ((1 - rho E^-1)(1 - rho E)) = (F + G - 1) / (1 - rho^2) with
+// F = (1 - rho E^-1)^-1, G = (1 - rho E)^-1: A^{-1} d = (1 - rho) / (1 + rho) (f + g - d) for
+// the forward recurrence f_i = d_i + rho f_{i-1} and the backward one g_i = d_i + rho g_{i+1}.
+// The two are independent chains over d (half the dependent depth of running one after the
+// other).  Each starts KR3 + 1 rows outside the eight from the steady state d / (1 - rho), an
+// error damped by |rho|^(KR3+1) ~ 4e-10 times the change of d over those rows; every product
+// enters through one FMA.
+constexpr int KR3 = 6;
+template <typename Emit>
+__device__ __forceinline__ void rec_rows3(const float* v, Emit emit) {
+  const float rho = c_rec3[0], inv1mr = c_rec3[1];
+  float fs[8];
+  float f = v[-KR3 - 1] * inv1mr;
+#pragma unroll
+  for (int t = -KR3; t < 8; ++t) {
+    f = fmaf(rho, f, v[t]);
+    if (t >= 0) fs[t] = f;
+  }
+  float g = v[8 + KR3] * inv1mr;
+#pragma unroll
+  for (int t = 7 + KR3; t >= 0; --t) {
+    g = fmaf(rho, g, v[t]);
+    if (t < 8) {
+      const float u = (fs[t] + g) - v[t];
+      emit(t, fmaf(c_rec3[2], u, c_rec3[3] * u));
+    }
+  }
+}
+
 // Explicit table row r (hi + lo), dc[t] = delta_{r + t}, taps farthest first as in the interior
 // row, hi and lo products summed apart.  The loop is unrolled to the largest half-width the tile
 // holds, the taps beyond K predicated off; taps outside the line read the zeros stored there.
@@ -584,15 +618,35 @@ __global__ void __launch_bounds__(256, AXIS == 0 ? 4 : 5) k_term3d32(const float
     }
   }
   __syncthreads();
+  if (AXIS != 0) {
+    // y and z lines: each result goes straight to R
+    if (!live) return;
+    const float* row = dd + lane * DP3;
+    float* Rp = R + ld + (rb + out_off) * sA;
+    auto put = [&](int u, float v) { Rp[u * sA] = accumulate ? racc[u] + sign * v : sign * v; };
+    if (rb + 7 < M && fast(rb) && fast(rb + 7)) {
+      rec_rows3(row + ob + K3H, put);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int rr = rb + u;
+        const float* dc = row + rr - r0 + K3H;
+        if (rr < M) put(u, fast(rr) ? band_fast3(dc - KB3) : band_gen3(dc, rr, M, whi, wlo, K, B, all_explicit));
+      }
+    }
+    if (!accumulate && warp == 0) {
+      if (tr == 0)
+        for (int od = 0; od < out_off; ++od) R[ld + od * sA] = 0.0f;
+      if (last_tile)
+        for (int od = M + out_off; od < nA; ++od) R[ld + od * sA] = 0.0f;
+    }
+    return;
+  }
   float y[8];
   if (live) {
     const float* row = dd + lane * DP3;
     if (rb + 7 < M && fast(rb) && fast(rb + 7)) {
-      float v[23];
-#pragma unroll
-      for (int i = 0; i < 23; ++i) v[i] = row[ob + K3H - KB3 + i];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) y[u] = band_fast3(v + u);
+      rec_rows3(row + ob + K3H, [&](int u, float v) { y[u] = v; });
     } else {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -601,19 +655,6 @@ __global__ void __launch_bounds__(256, AXIS == 0 ? 4 : 5) k_term3d32(const float
         y[u] = rr >= M ? 0.0f : (fast(rr) ? band_fast3(dc - KB3) : band_gen3(dc, rr, M, whi, wlo, K, B, all_explicit));
       }
     }
-  }
-  if (AXIS != 0) {
-    if (!live) return;
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (rb + u < M) R[ld + (rb + u + out_off) * sA] = accumulate ? racc[u] + sign * y[u] : sign * y[u];
-    if (!accumulate && warp == 0) {
-      if (tr == 0)
-        for (int od = 0; od < out_off; ++od) R[ld + od * sA] = 0.0f;
-      if (last_tile)
-        for (int od = M + out_off; od < nA; ++od) R[ld + od * sA] = 0.0f;
-    }
-    return;
   }
   // x lines: y through shared memory (row = line, column = band row), written along x
   __syncthreads();
@@ -1114,7 +1155,8 @@ double max_amp2_3d(double r) {
   return worst;
 }
 
-// Interior row of A^{-1} in closed form (long double), split hi + lo, into constant memory.
+// Interior row of A^{-1} in closed form (long double), split hi + lo, and the constants of its
+// recurrences, into constant memory.
 int upload_band_row() {
   const long double rho = -11.0L + std::sqrt(120.0L);
   float w[2 * KB3 + 2], wl[3];
@@ -1127,6 +1169,15 @@ int upload_band_row() {
   }
   if (cudaMemcpyToSymbol(c_w3, w, sizeof w) != cudaSuccess || cudaMemcpyToSymbol(c_wl3, wl, sizeof wl) != cudaSuccess)
     return -1;
+  const float rho_f = (float)rho;
+  const long double one_m = 1.0L - (long double)rho_f;
+  const long double scale = one_m / (1.0L + (long double)rho_f);
+  float rec[4];
+  rec[0] = rho_f;
+  rec[1] = (float)(1.0L / one_m);
+  rec[2] = (float)scale;
+  rec[3] = (float)(scale - (long double)rec[2]);
+  if (cudaMemcpyToSymbol(c_rec3, rec, sizeof rec) != cudaSuccess) return -1;
   return 0;
 }
 
