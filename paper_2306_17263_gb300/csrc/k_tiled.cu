@@ -19,9 +19,8 @@
 // wall, filter zero there) has even differences (delta_{-1} = delta_0, delta_M = delta_{M-1}).
 // Across the line every source is Dirichlet with stored zeros.
 //
-// Launch order: the curl launches the boundary ring of tiles first (those take the general paths
-// and run about twice as long); the solve runs its tiles in row order, so neighbouring tiles
-// that share halo rows run together.
+// Launch order: both kernels launch the boundary ring of tiles first (those take the general
+// paths and run about twice as long), so they do not form the tail of the launch.
 //
 // Instruction budget: both kernels are bound by issue, not by DRAM, so loops have constant
 // strides and 32-bit offsets, tiles away from the walls take block-uniform paths without any
@@ -900,7 +899,25 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
   }
 }
 
-__global__ void __launch_bounds__(NT, 2) k_solve_tile(SolveArgs A) { solve_body(A, blockIdx.z, blockIdx.x, blockIdx.y); }
+// Block b of the launch -> (field, tile): the boundary-ring tiles of every field first (they take
+// the masked edge path and run longest), then the interior tiles of each field row by row.
+__global__ void __launch_bounds__(NT, 2) k_solve_tile(SolveArgs A) {
+  const int nt = gridDim.x, nf = gridDim.z;
+  const int b = blockIdx.x + nt * (blockIdx.y + nt * blockIdx.z);
+  const int ring = nt > 1 ? 4 * (nt - 1) : 1;
+  int f, k;
+  if (b < nf * ring) {
+    f = b / ring;
+    k = b - f * ring;
+  } else {
+    const int c = b - nf * ring, ni = nt * nt - ring;  // ni > 0 here
+    f = c / ni;
+    k = ring + (c - f * ni);
+  }
+  int tx, ty;
+  ring_first_tile(k, nt, &tx, &ty);
+  solve_body(A, f, tx, ty);
+}
 
 
 
