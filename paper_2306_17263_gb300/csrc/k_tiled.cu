@@ -60,6 +60,14 @@ constexpr int PF = 4;                                // state rows fetched ahead
 // split hi + lo (rho is the FP32 root, so the scale gives the recurrences a DC gain of exactly 1)
 __constant__ float c_rec[4];
 
+// Programmatic dependent launch.  A tile kernel lets the next kernel of the stream start launching
+// as soon as every one of its own blocks has started (pdl_trigger), and reads no global memory
+// before every kernel it depends on has completed and its writes are visible (pdl_wait).  Blocks
+// that wait hold only slots the earlier grids no longer need (all their blocks are resident by
+// then), and launch latency at kernel boundaries overlaps the previous kernel's tail.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 struct PhaseArgs {
   const float* hi;
   const float* lo;
@@ -460,6 +468,8 @@ __host__ __device__ __forceinline__ void ring_first_tile(int b, int nt, int* tx,
 
 template <int STEP, bool FILTER = true>
 __global__ void __launch_bounds__(NT, 3) k_curl_tile(CurlArgs A) {
+  pdl_trigger();
+  pdl_wait();
   int tx, ty;
   ring_first_tile(blockIdx.y * gridDim.x + blockIdx.x, gridDim.x, &tx, &ty);
   curl_body<STEP, FILTER>(A, tx * TB, ty * TB);
@@ -902,6 +912,8 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
 // Block b of the launch -> (field, tile): the boundary-ring tiles of every field first (they take
 // the masked edge path and run longest), then the interior tiles of each field row by row.
 __global__ void __launch_bounds__(NT, 2) k_solve_tile(SolveArgs A) {
+  pdl_trigger();
+  pdl_wait();
   const int nt = gridDim.x, nf = gridDim.z;
   const int b = blockIdx.x + nt * (blockIdx.y + nt * blockIdx.z);
   const int ring = nt > 1 ? 4 * (nt - 1) : 1;
@@ -1045,11 +1057,28 @@ int tiled_configure() {
   return 0;
 }
 
+// Launch with programmatic stream serialisation (the kernels above wait for their predecessors
+// themselves); errors surface through cudaGetLastError as for <<<>>> launches.
+template <typename Kern, typename Arg>
+static void launch_pdl(Kern kernel, dim3 grid, size_t smem, cudaStream_t st, const Arg& arg) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, arg);
+}
+
 void tiled_curl(ms_grid* g, int step, float cb_hi, float cb_lo, float* b0, float* b1) {
   const CurlArgs A = make_curl(g, step, cb_hi, cb_lo, b0, b1);
   dim3 grid(A.ntiles, A.ntiles);
-  if (step == 0) k_curl_tile<0><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
-  else k_curl_tile<1><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
+  if (step == 0) launch_pdl(k_curl_tile<0>, grid, tiled_curl_smem(), g->stream, A);
+  else launch_pdl(k_curl_tile<1>, grid, tiled_curl_smem(), g->stream, A);
 }
 
 void tiled_curl_unfiltered(ms_grid* g, const float* hi, const float* lo, float* b0, float* b1) {
@@ -1059,14 +1088,14 @@ void tiled_curl_unfiltered(ms_grid* g, const float* hi, const float* lo, float* 
     A.ph[k].lo = lo;
   }
   dim3 grid(A.ntiles, A.ntiles);
-  k_curl_tile<1, false><<<grid, NT, tiled_curl_smem(), g->stream>>>(A);
+  launch_pdl(k_curl_tile<1, false>, grid, tiled_curl_smem(), g->stream, A);
 }
 
 void tiled_solve(ms_grid* g, int nfields, const int* fields, const float* const* b, int S, float d_hi, float d_lo,
                  float omega, float s_hi, float s_lo) {
   const SolveArgs A = make_solve(g, nfields, fields, b, S, d_hi, d_lo, omega, s_hi, s_lo);
   dim3 grid(A.ntiles, A.ntiles, nfields);
-  k_solve_tile<<<grid, NT, tiled_solve_smem(), g->stream>>>(A);
+  launch_pdl(k_solve_tile, grid, tiled_solve_smem(), g->stream, A);
 }
 
 // ---------------------------------------------------------------------------------------
