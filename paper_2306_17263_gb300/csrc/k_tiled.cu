@@ -166,19 +166,29 @@ __device__ __forceinline__ void pade_phase(const PhaseArgs& p, int c0, int r0, f
             db[a * XLP + 32 * cc] = (hr[32 * cc + 1] - hr[32 * cc]) + (lr[32 * cc + 1] - lr[32 * cc]);
       }
     } else {
-      // lines a = lane, lane + 32 (lanes along x); the two last lines with lanes along m
-      const size_t base = (size_t)mb * p.snx + (c0 - 1) + lane;
-      const float* hb = p.hi + base;
-      const float* lb = p.lo + base;
+      // lines a = lane, lane + 32 (lanes along x); warp w walks rows q = QW w .. QW w + QW - 1,
+      // carrying each source row in registers to the next difference (every row loaded once);
+      // the two last lines with lanes along m
+      constexpr int QW = (XL + NW - 1) / NW;
+      const int q0 = QW * warp;
       const size_t sn = (size_t)p.snx;
-#pragma unroll 2
-      for (int q = warp; q < XL; q += NW) {
-        const float* hr = hb + (size_t)q * sn;
-        const float* lr = lb + (size_t)q * sn;
-        const float v0 = (hr[sn] - hr[0]) + (lr[sn] - lr[0]);
-        const float v1 = (hr[sn + 32] - hr[32]) + (lr[sn + 32] - lr[32]);
-        dlt[lane * XLP + q] = v0;
-        dlt[(lane + 32) * XLP + q] = v1;
+      const size_t base = (size_t)(mb + q0) * sn + (c0 - 1) + lane;
+      const float* hr = p.hi + base;
+      const float* lr = p.lo + base;
+      float h0 = hr[0], h1 = hr[32], l0 = lr[0], l1 = lr[32];
+#pragma unroll
+      for (int t = 0; t < QW; ++t) {
+        if (q0 + t < XL) {  // warp-uniform
+          hr += sn;
+          lr += sn;
+          const float nh0 = hr[0], nh1 = hr[32], nl0 = lr[0], nl1 = lr[32];
+          dlt[lane * XLP + q0 + t] = (nh0 - h0) + (nl0 - l0);
+          dlt[(lane + 32) * XLP + q0 + t] = (nh1 - h1) + (nl1 - l1);
+          h0 = nh0;
+          h1 = nh1;
+          l0 = nl0;
+          l1 = nl1;
+        }
       }
       for (int idx = threadIdx.x; idx < (XROWS - 64) * XL; idx += NT) {
         const int e = idx / XL, q = idx - e * XL;
