@@ -716,10 +716,14 @@ __device__ __forceinline__ int xi2(int ly, int lx) { return (ly + 1) * XP2 + lx 
 
 // One sweep of an interior region.  LAST: add the iterate and its correction to the state at the
 // output points (region rows and columns H .. RS-1-H) instead of writing the next iterate.
-template <bool LAST>
+// MASK: the region touches a wall; bit 2k + j of um marks the thread's unknowns (inside the field
+// and off its Dirichlet walls).  Every other point is held at 0 (Neumann ghosts are refilled by the
+// caller), and only unknowns read or write the state.
+template <bool LAST, bool MASK>
 __device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* xc, float* xn, const float (&bv)[FR][2],
                                                float (&xv)[FR][2], int r0, int c, float* shi, float* slo, int gp,
-                                               int nx, int H) {
+                                               int nx, int H, unsigned um) {
+  auto unk = [&](int k, int j) { return !MASK || ((um >> (2 * k + j)) & 1u); };
   // output rows (the same for every lane of the warp) and output columns of the thread
   float sh[FR][2], sl[FR][2];
   bool rowok[FR];
@@ -731,8 +735,8 @@ __device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* 
       rowok[k] = r0 + k >= H && r0 + k < RS - H;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        sh[k][j] = rowok[k] ? shi[gp + k * nx + j] : 0.0f;
-        sl[k][j] = rowok[k] ? slo[gp + k * nx + j] : 0.0f;
+        sh[k][j] = rowok[k] && unk(k, j) ? shi[gp + k * nx + j] : 0.0f;
+        sl[k][j] = rowok[k] && unk(k, j) ? slo[gp + k * nx + j] : 0.0f;
       }
     }
   }
@@ -780,12 +784,12 @@ __device__ __forceinline__ void interior_sweep(const SolveArgs& A, const float* 
       if constexpr (LAST) {
         float h = sh[k][j], lo = sl[k][j];
         ff_add_scaled2_t(h, lo, x, corr, A.s_hi, A.s_lo);
-        if (j ? colok1 : colok0) {
+        if ((j ? colok1 : colok0) && unk(k, j)) {
           shi[gp + k * nx + j] = h;
           slo[gp + k * nx + j] = lo;
         }
       } else {
-        xv[k][j] = x + corr;
+        xv[k][j] = unk(k, j) ? x + corr : 0.0f;
       }
     }
   }
@@ -812,23 +816,66 @@ __device__ __forceinline__ void zero_pads(float* xa, float* xb) {
   }
 }
 
-// The whole solve of an interior region with origin (gx0, gy0) in the field (S >= 2).
+// Even ghosts of a Neumann axis in a region that reaches past that wall (2D fields have at most
+// one Neumann axis): a ghost point (index -1 or n along the axis) takes the value its mirror (0 or
+// n - 1) has in the plane just written, in the plane and in the owner's registers.
+__device__ __forceinline__ void refill_ghosts(float* xp, float (&xv)[FR][2], int r0, int c, int gx, int gy, int nx,
+                                              int ny, bool neu_x, bool neu_y) {
+#pragma unroll
+  for (int k = 0; k < FR; ++k)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int px = gx + j, py = gy + k;
+      const int dx = neu_x ? (px == -1 ? 1 : (px == nx ? -1 : 0)) : 0;
+      const int dy = neu_y ? (py == -1 ? 1 : (py == ny ? -1 : 0)) : 0;
+      if (dx | dy) {
+        const float v = xp[xi2(r0 + k + dy, c + j + dx)];
+        xv[k][j] = v;
+        xp[xi2(r0 + k, c + j)] = v;
+      }
+    }
+}
+
+// The whole solve of a region with origin (gx0, gy0) in the field (S >= 2).  MASK false: every
+// point of the region is an unknown.  MASK true: the region touches a wall (see interior_sweep).
+template <bool MASK>
 __device__ __forceinline__ void solve_interior(const SolveArgs& A, const float* __restrict__ b, float* shi, float* slo,
-                                               int nx, int gx0, int gy0) {
+                                               int nx, int ny, int bcx, int bcy, int gx0, int gy0) {
   extern __shared__ float sm[];
   float* xa = sm;
   float* xb = sm + XPL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = 2 * lane, r0 = FR * warp;
+  const int gx = gx0 + c, gy = gy0 + r0;  // field coordinates of the thread's first point
   zero_pads(xa, xb);
-  // 32-bit offsets from the region's first own point (planes hold fewer than 2^31 points)
-  const size_t base = (size_t)(gy0 + r0) * nx + (gx0 + c);
-  const float* bp = b + base;
+  unsigned um = 0xffu;
+  bool neu_x = false, neu_y = false;
   float bv[FR][2], xv[FR][2];
+  if constexpr (MASK) {
+    um = 0u;
 #pragma unroll
-  for (int k = 0; k < FR; ++k) {
-    bv[k][0] = bp[k * nx];
-    bv[k][1] = bp[k * nx + 1];
+    for (int k = 0; k < FR; ++k)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int px = gx + j, py = gy + k;
+        if (px >= 0 && px < nx && py >= 0 && py < ny && interior(bcx, px, nx) && interior(bcy, py, ny))
+          um |= 1u << (2 * k + j);
+      }
+    neu_x = bcx == NEU && (gx0 < 0 || gx0 + RS > nx);
+    neu_y = bcy == NEU && (gy0 < 0 || gy0 + RS > ny);
+#pragma unroll
+    for (int k = 0; k < FR; ++k)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        bv[k][j] = ((um >> (2 * k + j)) & 1u) ? b[(gy + k) * nx + gx + j] : 0.0f;
+  } else {
+    // 32-bit offsets from the region's first own point (planes hold fewer than 2^31 points)
+    const float* bp = b + ((size_t)gy * nx + gx);
+#pragma unroll
+    for (int k = 0; k < FR; ++k) {
+      bv[k][0] = bp[k * nx];
+      bv[k][1] = bp[k * nx + 1];
+    }
   }
 #pragma unroll
   for (int k = 0; k < FR; ++k) {
@@ -837,19 +884,30 @@ __device__ __forceinline__ void solve_interior(const SolveArgs& A, const float* 
     *reinterpret_cast<float2*>(xa + xi2(r0 + k, c)) = make_float2(xv[k][0], xv[k][1]);
   }
   __syncthreads();
-  float* const shb = shi + base;
-  float* const slb = slo + base;
+  if (MASK && (neu_x || neu_y)) {
+    refill_ghosts(xa, xv, r0, c, gx, gy, nx, ny, neu_x, neu_y);
+    __syncthreads();
+  }
+  // the state from the region's first own point (MASK: from the field's origin, so offsets of
+  // points off the field are never formed into addresses)
+  float* const shb = MASK ? shi : shi + ((size_t)gy * nx + gx);
+  float* const slb = MASK ? slo : slo + ((size_t)gy * nx + gx);
+  const int gp = MASK ? gy * nx + gx : 0;
   const int H = A.S - 1;
   float* xc = xa;
   float* xn = xb;
   for (int k = 1; k < A.S - 1; ++k) {
-    interior_sweep<false>(A, xc, xn, bv, xv, r0, c, shb, slb, 0, nx, H);
+    interior_sweep<false, MASK>(A, xc, xn, bv, xv, r0, c, shb, slb, gp, nx, H, um);
     __syncthreads();
+    if (MASK && (neu_x || neu_y)) {
+      refill_ghosts(xn, xv, r0, c, gx, gy, nx, ny, neu_x, neu_y);
+      __syncthreads();
+    }
     float* t = xc;
     xc = xn;
     xn = t;
   }
-  interior_sweep<true>(A, xc, xn, bv, xv, r0, c, shb, slb, 0, nx, H);
+  interior_sweep<true, MASK>(A, xc, xn, bv, xv, r0, c, shb, slb, gp, nx, H, um);
 }
 
 // Region of RS x RS points = output tile (RS - 2H)^2 plus an H-cell halo, H = S - 1.  Warp w owns
@@ -871,8 +929,9 @@ __device__ __forceinline__ void solve_body(const SolveArgs& A, int f, int tbx, i
   const int gx0 = tx0 - H, gy0 = ty0 - H;
   // interior tile: the region holds only unknowns, so no boundary tests and no ghosts
   const bool edge = !(gx0 >= 1 && gy0 >= 1 && gx0 + RS <= nx - 1 && gy0 + RS <= ny - 1);
-  if (!edge && A.S >= 2) {
-    solve_interior(A, b, shi, slo, nx, gx0, gy0);
+  if (A.S >= 2) {
+    if (edge) solve_interior<true>(A, b, shi, slo, nx, ny, bcx, bcy, gx0, gy0);
+    else solve_interior<false>(A, b, shi, slo, nx, ny, bcx, bcy, gx0, gy0);
     return;
   }
   const bool neu_x = edge && bcx == NEU, neu_y = edge && bcy == NEU;
