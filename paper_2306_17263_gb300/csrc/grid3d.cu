@@ -11,8 +11,9 @@
 // state; each half-step first filters its three source components once into float-float
 // G = 12 beta u + L u (k_ffilt3d32), then per Pade term one tile kernel (k_term3d32) forms the
 // first differences of G along the line (the filter commutes with the difference under the ghost
-// rules) and applies the A^{-1} band (farthest taps first), accumulating the right-hand side (a
-// difference kernel and a band kernel take over for tables wider than the tile holds); the solve
+// rules) and applies A^{-1} (interior rows by two first-order recurrences, rows near a wall by the
+// explicit band rows, farthest taps first), accumulating the right-hand side (a difference kernel
+// and a band kernel take over for tables wider than the tile holds); the solve
 // (k_sweep3d32) is the Richardson iteration on 6 h^2 P1 with the exact-product residual and
 // the split last correction, each sweep one launch that marches tiles along z.
 #include <cmath>
@@ -419,7 +420,8 @@ constexpr int K3H = 13;             // reach held in shared memory (table half-w
 constexpr int D3L = T3O + 2 * K3H;  // differences per line
 
 // Interior row of the band at row r, d[t] = delta_{r - KB3 + t} (t = 0 .. 2 KB3 + 1), taps summed
-// farthest first, the lo parts of the three central taps before the central hi tap.
+// farthest first, the lo parts of the three central taps before the central hi tap (rows of a
+// run that also holds end rows; whole interior runs take rec_rows3).
 __device__ __forceinline__ float band_fast3(const float* d) {
   float acc = c_w3[2 * KB3 + 1] * d[2 * KB3 + 1];
 #pragma unroll
@@ -494,10 +496,11 @@ __device__ __forceinline__ float band_gen3(const float* dc, int r, int M, const 
 // coordinate q of the other transverse axis Q.  The first differences of G over the rows' reach
 // (K3H on each side) go to shared memory, a row per line; a thread then takes eight consecutive
 // rows of one line (lanes across the lines, so every lane of a warp is at the same rows and the
-// end rows of the table take their path together) through a register window.  x lines are read
-// and written along x by whole warps, the results passing through shared memory; y and z lines
-// are read and written with the lanes across x.  Rows away from the line ends take the interior
-// row from constant memory; the end rows take the explicit FP32 hi + lo table rows.  Wall lines
+// end rows of the table take their path together).  x lines are read and written along x by whole
+// warps, the results passing through shared memory; y and z lines are read and written with the
+// lanes across x.  Runs of rows away from the line ends take the recurrences (rec_rows3); runs
+// that hold end rows take the explicit FP32 hi + lo table rows there and the interior band row
+// from constant memory elsewhere.  Wall lines
 // need no test: G is 0 on them, so y is 0 there.  Without accumulation the first and last tiles of
 // a line also write the wall points beyond the band rows (0).
 template <int AXIS>

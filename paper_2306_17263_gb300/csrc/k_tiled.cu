@@ -6,8 +6,9 @@
 //                  them, d = 12 beta delta + L delta (the filter of Eq. "eq:ell" commutes with the
 //                  difference: D1 (12 beta + L) u = (12 beta + L') D1 u with the ghost rules below),
 //                  and applies A^{-1} (App. A.1, Eq. "eq:lhs"): rows near a wall as explicit rows
-//                  of its band, interior rows as the two first-order recurrences A factors into.  Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y)
-//                  on E_z; Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x).
+//                  of its band, interior rows as the two first-order recurrences A factors into.
+//                  Step 1: b = A^{-1} D1 G~_y (along x) - A^{-1} D1 G~_x (along y) on E_z;
+//                  Step 2: b_x = -A^{-1} D1 G~_E (along y), b_y = +A^{-1} D1 G~_E (along x).
 //   k_solve_tile : S Richardson sweeps of 6 h^2 P1 (Def. "def:operatorsP") on the tile plus an
 //                  (S-1)-cell halo in shared memory, then the float-float state update of the
 //                  paper's E += h_tau E* / H += h_tau H* with the exact-product residual and
