@@ -283,3 +283,23 @@ def test_headline_config_mixed_within_fp64_discretisation_error():
     diff = math.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(f32, f64)) / N ** 2)
     assert e32 <= 2 * e64, (e32, e64)
     assert diff <= e64, (diff, e64)
+
+
+@pytest.mark.parametrize("N", [5, 6, 7, 12, 56, 57, 58, 59, 114, 115, 116, 117])
+@pytest.mark.parametrize("closure", [pkg.CLOSURE_PAPER, pkg.CLOSURE_REFLECT])
+def test_mixed_solve_region_edges_close_to_oracle(N, closure):
+    """Sizes around the solve regions' output width (64 - 2(S-1) = 58 at r = 0.5): one region that
+    reaches past both walls, a last region one or two points wide, Neumann ghost columns and rows at
+    either lane of a column pair, and the smallest grids; FP32_REFINED against the oracle on random
+    fields (every region at a wall takes the masked path with ghost refills)."""
+    r, steps = 0.5, 6
+    init = workloads.random_fields(N, seed=3000 + N)
+    o = oracle.Oracle2D(N, r, closure=closure)
+    ref = [a.copy() for a in init]
+    o.run(*ref, steps)
+    with pkg.Grid(N, r, precision=pkg.FP32_REFINED, closure=closure) as g:
+        g.set_fields(*init)
+        g.run(steps)
+        got = g.get_fields()
+    cat = lambda fs: np.concatenate([np.ravel(a) for a in fs])
+    assert np.linalg.norm(cat(got) - cat(ref)) <= 2e-6 * np.linalg.norm(cat(ref))
