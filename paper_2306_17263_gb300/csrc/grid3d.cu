@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(256, AXIS == 0 ? 4 : 5) k_term3d32(const float
   int tr, p0, q;
   if (AXIS == 0) { tr = blockIdx.x; p0 = blockIdx.y * 32; q = blockIdx.z; }
   else if (AXIS == 1) { p0 = blockIdx.x * 32; tr = blockIdx.y; q = blockIdx.z; }
-  else { p0 = blockIdx.x * 32; q = blockIdx.y; tr = blockIdx.z; }
+  else { p0 = blockIdx.x * 32; tr = blockIdx.y; q = blockIdx.z; }  // tiles along z a few blocks apart
   const int r0 = tr * T3O;  // first band row of the tile
   const int st[3] = {1, ss.n[0], ss.n[0] * ss.n[1]};
   const int sdt[3] = {1, sd.n[0], sd.n[0] * sd.n[1]};
@@ -1000,7 +1000,7 @@ int term3d32(ms_grid* g, int axis, int cs, int cd, float sign, int accumulate) {
       k_term3d32<1><<<grd, 256, 0, g->stream>>>(gh, gl, ss, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit,
                                                  sign, accumulate);
     } else {
-      const dim3 grd((sd.n[0] + 31) / 32, sd.n[1], nt);
+      const dim3 grd((sd.n[0] + 31) / 32, nt, sd.n[1]);
       k_term3d32<2><<<grd, 256, 0, g->stream>>>(gh, gl, ss, R, sd, off, t.M, t.d_whi, t.d_wlo, t.K, t.B, t.all_explicit,
                                                  sign, accumulate);
     }
